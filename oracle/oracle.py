@@ -1,0 +1,196 @@
+"""ctypes wrapper of the plain sequential FP64 CPU oracle (``oracle/bgk_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg
+of ``bench.py`` may use this module; the product path never imports it.  It shares no
+code with the CUDA library.
+
+The C source follows the paper's statement step by step (its header lists the sections
+and the readings taken where the paper is silent).  This wrapper only marshals arrays.
+
+Parity status per function (pins live in ``tests/test_oracle_pins.py``):
+  velocity grid, element matrices, projection, moments, sweep graph / generations,
+  one sweep, one time step (BE, DIRK2, DIRK3, B-stable DIRK2, BDF2): pinned.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bgk_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "libbgk_oracle.so")
+
+INTEGRATORS = {"BE": 0, "DIRK2": 1, "DIRK3": 2, "BSTABLE2": 3, "BDF2": 4}
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C11, no fused multiply-add)."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+                               "-fno-fast-math", "-o", _LIB_PATH, _SRC, "-lm"])
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = C.CDLL(build())
+        P = C.c_void_p
+        dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+        ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+        up = np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")
+        lib.orc_create.restype = P
+        lib.orc_create.argtypes = [C.c_int, C.c_int, C.c_int, dp, C.c_int, ip, C.c_int, C.c_int, C.c_double]
+        lib.orc_destroy.argtypes = [P]
+        lib.orc_info.argtypes = [P, ip]
+        lib.orc_velocity.argtypes = [P, dp, dp, dp, dp]
+        lib.orc_cell.argtypes = [P, C.c_int, dp, dp, dp, dp, dp, dp, ip, ip]
+        lib.orc_project_1d.argtypes = [P, C.c_double, C.c_double, dp]
+        lib.orc_maxwellian.argtypes = [P, dp, dp]
+        lib.orc_moments.argtypes = [P, dp, dp]
+        lib.orc_build_dags.restype = C.c_long
+        lib.orc_build_dags.argtypes = [P]
+        lib.orc_generations.restype = C.c_int
+        lib.orc_generations.argtypes = [P, C.c_int, ip, up]
+        lib.orc_face_signs.argtypes = [P, C.c_int, ip]
+        lib.orc_sweep.argtypes = [P, dp, dp, dp, dp, C.c_double, C.c_double, dp]
+        lib.orc_dt_explicit.restype = C.c_double
+        lib.orc_dt_explicit.argtypes = [P]
+        lib.orc_tableau.restype = C.c_int
+        lib.orc_tableau.argtypes = [C.c_int, dp, dp, dp]
+        lib.orc_conv_measure.restype = C.c_double
+        lib.orc_conv_measure.argtypes = [P, dp, dp]
+        lib.orc_set_physics.argtypes = [P, C.c_double, C.c_double, C.c_int, C.c_double, C.c_int]
+        lib.orc_step.restype = C.c_int
+        lib.orc_step.argtypes = [P, dp, C.c_void_p, dp, ip, dp]
+        _lib = lib
+    return _lib
+
+
+def tableau(integrator: str):
+    lib = _load()
+    A, b, c = np.zeros(9), np.zeros(3), np.zeros(3)
+    S = lib.orc_tableau(INTEGRATORS[integrator], A, b, c)
+    return A.reshape(3, 3)[:S, :S].copy(), b[:S].copy(), c[:S].copy()
+
+
+class Oracle:
+    """One problem: mesh + spatial degree + velocity grid (+ physics for time steps)."""
+
+    def __init__(self, dim, kx, xyz, cells, n1d, kv, L):
+        self.lib = _load()
+        self.dim, self.kx, self.n1d, self.kv, self.L = dim, kx, n1d, kv, L
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        cells = np.ascontiguousarray(cells, dtype=np.int32)
+        self.h = self.lib.orc_create(dim, kx, xyz.shape[0], xyz, cells.shape[0], cells, n1d, kv, float(L))
+        if not self.h:
+            raise ValueError("oracle rejected the problem")
+        info = np.zeros(5, dtype=np.int32)
+        self.lib.orc_info(self.h, info)
+        self.nv, self.nnode, self.ndof, self.nface, self.ncell = (int(x) for x in info)
+        self._dags = False
+
+    @classmethod
+    def from_workload(cls, w):
+        return cls(w.mesh.dim, w.kx, w.mesh.xyz, w.mesh.cells, w.n_v, w.k_v, w.L)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            self.lib.orc_destroy(self.h)
+            self.h = None
+
+    # --- grid and geometry -------------------------------------------------------
+    def velocity(self):
+        v = np.zeros(self.nv * self.dim)
+        w = np.zeros(self.nv)
+        x1, w1 = np.zeros(self.n1d), np.zeros(self.n1d)
+        self.lib.orc_velocity(self.h, v, w, x1, w1)
+        return v.reshape(self.nv, self.dim), w, x1, w1
+
+    def cell(self, c):
+        nd, nf, d = self.ndof, self.nface, self.dim
+        vol = np.zeros(1)
+        M, G = np.zeros(nd * nd), np.zeros(d * nd * nd)
+        Fm, un, ar = np.zeros(nf * nd * nd), np.zeros(nf * d), np.zeros(nf)
+        nbr, nn = np.zeros(nf, dtype=np.int32), np.zeros(nf * nd, dtype=np.int32)
+        self.lib.orc_cell(self.h, int(c), vol, M, G, Fm, un, ar, nbr, nn)
+        return dict(vol=vol[0], M=M.reshape(nd, nd), G=G.reshape(d, nd, nd), F=Fm.reshape(nf, nd, nd),
+                    unit_n=un.reshape(nf, d), area=ar, nbr=nbr, nbr_node=nn.reshape(nf, nd))
+
+    def dt_explicit(self):
+        return self.lib.orc_dt_explicit(self.h)
+
+    # --- Maxwellian and moments --------------------------------------------------
+    def project_1d(self, u, theta):
+        c = np.zeros(self.n1d)
+        self.lib.orc_project_1d(self.h, float(u), float(theta), c)
+        return c
+
+    def maxwellian(self, nut):
+        """nut [nnode, d+2] -> f [nv, nnode] (projected Maxwellian at every node)."""
+        out = np.zeros((self.nv, self.nnode))
+        self.lib.orc_maxwellian(self.h, np.ascontiguousarray(nut, dtype=np.float64), out)
+        return out
+
+    def moments(self, f):
+        U = np.zeros((self.nnode, self.dim + 2))
+        self.lib.orc_moments(self.h, np.ascontiguousarray(f, dtype=np.float64), U)
+        return U
+
+    def conv_measure(self, Unew, Uold):
+        return self.lib.orc_conv_measure(self.h, np.ascontiguousarray(Unew), np.ascontiguousarray(Uold))
+
+    # --- sweep graphs --------------------------------------------------------------
+    def build_dags(self):
+        n = self.lib.orc_build_dags(self.h)
+        if n < 0:
+            raise RuntimeError("oracle DAG construction failed")
+        self._dags = True
+        return int(n)
+
+    def generations(self, j):
+        if not self._dags:
+            self.build_dags()
+        gen = np.zeros(self.ncell, dtype=np.int32)
+        lag = np.zeros(self.ncell * self.nface, dtype=np.uint8)
+        G = self.lib.orc_generations(self.h, int(j), gen, lag)
+        return gen, lag.reshape(self.ncell, self.nface), G
+
+    def face_signs(self, j):
+        s = np.zeros(self.ncell * self.nface, dtype=np.int32)
+        self.lib.orc_face_signs(self.h, int(j), s)
+        return s.reshape(self.ncell, self.nface)
+
+    # --- sweep and step ------------------------------------------------------------
+    def sweep(self, fold, Mn, q, fbc, nu, nu_s):
+        if not self._dags:
+            self.build_dags()
+        fnew = np.zeros((self.nv, self.nnode))
+        c = lambda a: np.ascontiguousarray(a, dtype=np.float64).reshape(self.nv, self.nnode)  # noqa: E731
+        self.lib.orc_sweep(self.h, c(fold), c(Mn), c(q), c(fbc), float(nu), float(nu_s), fnew)
+        return fnew
+
+    def set_physics(self, nu, dt, integrator="BE", tau=1e-8, lmax=1000):
+        self.integrator = integrator
+        self.lib.orc_set_physics(self.h, float(nu), float(dt), INTEGRATORS[integrator], float(tau), int(lmax))
+
+    def step(self, f, fbc, fprev=None):
+        """One time step in place on a copy; returns (f_next, iters per stage, measures, status)."""
+        if not self._dags:
+            self.build_dags()
+        f = np.array(f, dtype=np.float64, order="C").reshape(self.nv, self.nnode)
+        fbc = np.ascontiguousarray(fbc, dtype=np.float64).reshape(self.nv, self.nnode)
+        iters = np.zeros(3, dtype=np.int32)
+        meas = np.zeros(3)
+        pp = None
+        if fprev is not None:
+            fprev = np.ascontiguousarray(fprev, dtype=np.float64).reshape(self.nv, self.nnode)
+            pp = fprev.ctypes.data_as(C.c_void_p)
+        st = self.lib.orc_step(self.h, f, pp, fbc, iters, meas)
+        return f, iters, meas, st
