@@ -1,0 +1,328 @@
+"""Benchmark of the implicit sweep solver on B300: DOF-updates/s of whole implicit steps.
+
+A step is one implicit time step of the 2D-2V shock tube (128 x 128 squares, 32,768 P2
+triangles, 32 x 32 velocities, 3-stage DIRK, Knudsen 1e-3): every stage runs Picard
+iterations (Maxwellian + source, transport sweep, moments, convergence test) until the
+moment criterion meets 1e-8.  value = DOF x sweeps / time over the timed steps.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a bounded sample
+of the same workload.  Under torchrun every rank runs an independent replica (the solver
+runs on one GPU; replicas only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sweep DOF-updates/s; time per implicit step to 1e-8 residual vs plain FP64"
+UNIT = "DOF-updates/s"
+FP64_PEAK_TFLOPS = 1.25   # nominal B300 FP64 rate (no tensor path); see the design notes
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    p.add_argument("--n-side", type=int, default=128)
+    p.add_argument("--n-v", type=int, default=32)
+    p.add_argument("--sweep-reps", type=int, default=5)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def workload(args):
+    from paper_2608_19150_b300 import synth
+    return synth.workload_shock_tube(n_side=args.n_side, seed=1, kx=2, n_v=args.n_v, k_v=3, L=8.0, knudsen=1e-3,
+                                     integrator="DIRK3", cfl=10.0)
+
+
+def config(w, args, extra=None):
+    c = {"workload": "2D-2V shock tube, %dx%d squares (%d P2 triangles), %dx%d velocities on [-8,8]^2, DIRK3, "
+                     "Kn 1e-3, CFL 10, tau 1e-8" % (args.n_side, args.n_side, w.mesh.n_cells, args.n_v, args.n_v),
+         "n_cells": w.mesh.n_cells, "dof_per_sweep": int(w.mesh.n_cells * 6 * args.n_v ** 2),
+         "precision": args.precision, "integrator": "DIRK3",
+         "l2": "inputs larger than L2 (f %.2f GB per array)" % (w.mesh.n_cells * 6 * args.n_v ** 2 *
+                                                                 (8 if args.precision == "fp64" else 4) / 1e9),
+         "parallelism": "replicas"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# --------------------------------------------------------------------- flop count
+def sweep_flops_per_item():
+    """FP64 operations of one local solve of the P2 kernel, counted from the generated
+    reference tables (multiply and add each count one) with the average face mix of a
+    triangle: 1.5 outflow and 1.5 inflow faces."""
+    sys.path.insert(0, os.path.join(ROOT, "paper_2608_19150_b300", "csrc"))
+    import gen_tables as gt
+    d, nd, nf, Mh, Dd, Eh, fn = gt.tables("p2tri")
+    fl = 0.0
+    fl += nf * (2 * d - 1 + 2)                     # s_i = v . N_i, |s_i| * (1/|K|)
+    for a in range(nd):
+        for b in range(nd):
+            t = (Mh[a][b] != 0) + sum(Dd[i][a][b] != 0 for i in range(nf))
+            fl += max(0, 2 * t - 1)
+    nnzE = sum(1 for a in range(nd) for b in range(nd) if Eh[0][a][b] != 0)
+    fl += 1.5 * 2 * nnzE                           # outflow face terms
+    fl += sum(2 * sum(1 for b in range(nd) if Mh[a][b] != 0) - 1 for a in range(nd))
+    fl += 1.5 * sum(2 * sum(1 for k in range(len(fn[0])) if Eh[0][a][fn[0][k]] != 0) + 1
+                    for a in range(nd) if any(Eh[0][a][fn[0][k]] != 0 for k in range(len(fn[0]))))
+    for k in range(nd):                            # LU without pivoting + substitution
+        fl += 1 + (nd - k - 1) * (1 + 2 * (nd - k - 1) + 2)
+    for i in range(nd):
+        fl += 2 * (nd - i - 1) + 1
+    return fl
+
+
+# --------------------------------------------------------------------- clocks
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------- CPU oracle
+def cpu_baseline(w, n_ord, dt):
+    """One oracle sweep restricted to n_ord ordinates of the full workload, single thread."""
+    from oracle.oracle import Oracle
+    o = Oracle.from_workload(w)
+    t0 = time.perf_counter()
+    o.build_dags()
+    f0 = o.maxwellian(w.init)
+    fbc = o.maxwellian(w.inflow)
+    U = o.moments(f0)
+    nut = U.copy()
+    nut[:, 1:3] = U[:, 1:3] / U[:, :1]
+    nut[:, 3] = (2 * U[:, 3] / U[:, 0] - (nut[:, 1:3] ** 2).sum(1)) / 2
+    Mn = o.maxwellian(nut)
+    setup = time.perf_counter() - t0
+    nus = w.nu + 1.0 / dt
+    j0 = (o.nv - n_ord) // 2
+    t0 = time.perf_counter()
+    o.sweep_range(f0, Mn, f0 / dt, fbc, w.nu, nus, j0, j0 + n_ord)
+    el = time.perf_counter() - t0
+    dof = n_ord * o.nnode
+    return {"value": dof / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "one sweep over %d of %d ordinates of the full mesh (%d DOF), %.1f s; set-up %.1f s untimed"
+                      % (n_ord, o.nv, dof, el, setup)}
+
+
+# --------------------------------------------------------------------- runs
+def dist_init(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_reference(args):
+    rank, world, _ = dist_init(args)
+    if rank != 0:
+        return
+    w = workload(args)
+    from oracle.oracle import Oracle
+    o = Oracle.from_workload(w)
+    o.build_dags()
+    dt = 10.0 * o.dt_explicit()
+    f0 = o.maxwellian(w.init)
+    fbc = o.maxwellian(w.inflow)
+    Mn = f0
+    nus = w.nu + 1.0 / dt
+    n_ord = 8
+    j0 = (o.nv - n_ord) // 2
+    for _ in range(max(0, args.warmup)):
+        o.sweep_range(f0, Mn, f0 / dt, fbc, w.nu, nus, j0, j0 + 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.sweep_range(f0, Mn, f0 / dt, fbc, w.nu, nus, j0, j0 + n_ord)
+    el = time.perf_counter() - t0
+    dof = n_ord * o.nnode * args.steps
+    v = dof / el
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config(w, args, {"sample": "each step: one oracle sweep over %d of %d "
+                                                             "ordinates" % (n_ord, o.nv)}),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "%d ordinates x %d cells x 6 nodes per step" % (n_ord, o.ncell)},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_init(args)
+    torch.cuda.set_device(local)
+    from paper_2608_19150_b300 import bgk
+    w = workload(args)
+    s = bgk.Solver.from_workload(w, precision=args.precision)
+    s.set_state_maxwellian(w.init)
+    s.set_inflow_maxwellian(w.inflow)
+    dof = s.nv * s.nnode
+    for _ in range(args.warmup):
+        s.step(1)
+    f_host = torch.empty(s.nv * s.nnode, dtype=torch.float64 if args.precision == "fp64" else torch.float32,
+                         pin_memory=True)
+    s.synchronize()
+    sweeps0 = s.last_stats().total_sweeps
+    clocks = Clocks(local)
+    barrier(world)
+    clocks.start()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    iters = []
+    launches = 0
+    for _ in range(args.steps):
+        st = s.step(1)
+        it = list(st.iterations)[:st.n_stages]
+        iters.append(it)
+        launches += 1 + sum(3 + (k > 0) + 4 * it[k] + (k < st.n_stages - 1) for k in range(st.n_stages))
+    s.synchronize()
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    barrier(world)
+    clk = clocks.stop()
+    sweeps = s.last_stats().total_sweeps - sweeps0
+    el_max = max_over_ranks(el, world)
+    value = world * dof * sweeps / el_max   # equal work per rank (replicas)
+    # end to end through the C ABI with host buffers: f^k in from pinned host memory,
+    # moments out to host, every step
+    fh = s.get_f(np.float64 if args.precision == "fp64" else np.float32)
+    f_host.copy_(torch.from_numpy(fh.ravel()))
+    U = np.empty((s.nnode, s.dim + 2))
+    barrier(world)
+    t0 = time.perf_counter()
+    e2e_sweeps = 0
+    for _ in range(args.steps):
+        s.lib.bgk_set_f(s.h, bgk.C.c_void_p(f_host.data_ptr()), 0 if args.precision == "fp64" else 1)
+        st = s.step(1)
+        e2e_sweeps += sum(list(st.iterations)[:st.n_stages])
+        s.lib.bgk_get_moments(s.h, U.ctypes.data_as(bgk.C.c_void_p))
+    el_e2e = max_over_ranks(time.perf_counter() - t0, world)
+    e2e = {"value": world * dof * e2e_sweeps / el_e2e, "unit": UNIT,
+           "h2d_bytes_per_step": int(f_host.numel() * f_host.element_size()), "d2h_bytes_per_step": int(U.nbytes)}
+    # the dominant kernel (the sweep), event-timed per launch on its own stream
+    s.set_f(fh)
+    s.timing(reset=True)
+    dt = s.dt
+    for _ in range(args.sweep_reps):
+        s.sweep(w.nu + 1.0 / (dt * 0.4358665215084590), 1.0 / (dt * 0.4358665215084590))
+    ms, n = s.timing(reset=True)
+    sweep_ms = ms / max(1, n)
+    flops_item = sweep_flops_per_item()
+    items = s.nv * s.ncell
+    achieved_tf = flops_item * items / (sweep_ms * 1e-3) / 1e12
+    tsz = 8 if args.precision == "fp64" else 4
+    hbm_gbs = 2 * tsz * dof / (sweep_ms * 1e-3) / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6400.0))
+    if args.precision == "fp64":
+        roofline = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "k_sweep<ElemP2Tri,double>",
+                    "flops_per_local_solve": flops_item, "sweep_ms": sweep_ms}
+    else:
+        roofline = {"bound": "hbm", "achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": hbm_gbs / hbm_peak, "traffic": None, "kernel": "k_sweep<ElemP2Tri,float>",
+                    "sweep_ms": sweep_ms}
+    roofline_hbm = {"achieved_gbs": hbm_gbs, "peak_gbs": hbm_peak, "frac": hbm_gbs / hbm_peak,
+                    "algorithmic_bytes_per_dof": 2 * tsz, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, 48, dt)
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
+            "data": "synthetic", "config": config(w, args), "roofline": roofline, "roofline_hbm": roofline_hbm,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "picard_iterations": iters, "sweeps_timed": sweeps, "dt": dt}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

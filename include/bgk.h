@@ -1,0 +1,151 @@
+/*
+ * bgk.h -- C ABI of the B300 implicit sweep solver for the multidimensional BGK equation
+ * (Hauck et al., "Sweep-based, implicit solutions of the multidimensional BGK equation on
+ * unstructured grids").
+ *
+ * Conventions shared by every call
+ *   - Every call returns an int status (BGK_OK = 0 or one of BGK_E_*).  No exception or
+ *     signal crosses the ABI; outputs are written only when the call returns BGK_OK.
+ *   - Pointers named h_* are host memory; pointers named d_* are device memory on the
+ *     handle's device.  Inputs are copied; the caller keeps ownership of every buffer.
+ *   - The handle owns all device memory it allocates; it is not thread-safe.
+ *   - Spatial DG nodes of a cell are ordered: P1 triangle/tetrahedron = its vertices in the
+ *     order given; P2 triangle = vertices 0,1,2 then midpoints of edges (0,1),(1,2),(2,0).
+ *     A "node index" is cell * n_dof + local node.  n_nodes = n_cells * n_dof.
+ *   - Ordinates: velocity points v_j of the tensor grid on [-L, L]^d, j lexicographic with
+ *     the last dimension fastest.  Distribution arrays are f[j][node] (ordinate-major).
+ *   - Nodal states are [node][d+2] = (n, u_1..u_d, theta); moments are [node][d+2] =
+ *     (n, n u_1..n u_d, E) with E = |u|^2 n / 2 + d n theta / 2   (Sec. 2, Eq. moments).
+ */
+#ifndef BGK_B300_H
+#define BGK_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  BGK_OK = 0,
+  BGK_E_INVALID = 1,      /* bad argument or mesh (non-conforming, degenerate cell, ...) */
+  BGK_E_CUDA = 2,         /* a CUDA runtime call failed */
+  BGK_E_OOM = 3,          /* device allocation failed */
+  BGK_E_NOCONV = 4,       /* Picard iteration reached l_max without meeting the criterion */
+  BGK_E_NONPHYSICAL = 5,  /* n <= 0, theta <= 0 or a non-finite moment was met */
+  BGK_E_TIMEOUT = 6       /* a bounded device-side wait ran out */
+};
+
+enum { BGK_BE = 0, BGK_DIRK2 = 1, BGK_DIRK3 = 2, BGK_BSTABLE2 = 3, BGK_BDF2 = 4 };
+enum { BGK_FP64 = 0, BGK_FP32_SWEEP = 1 };
+enum { BGK_DTYPE_F64 = 0, BGK_DTYPE_F32 = 1 };
+
+/* Mesh of the spatial domain X (Sec. 3.1, Table 1): affine simplices, conforming. */
+typedef struct {
+  int dim;                      /* 2 (triangles) or 3 (tetrahedra) */
+  int k_x;                      /* spatial degree: 1, or 2 for triangles */
+  int n_vertices;
+  const double* xyz;            /* host, [n_vertices][dim] */
+  int n_cells;
+  const int32_t* cell_vertices; /* host, [n_cells][dim+1], positively oriented or not */
+} bgk_mesh;
+
+/* Velocity grid (Sec. 3.2): n_points per dimension on [-L, L], k_v+1 Gauss-Legendre
+ * points in each of n_points/(k_v+1) uniform cells; nodal Q^{k_v} basis. */
+typedef struct {
+  double L;
+  int n_points;
+  int k_v;
+} bgk_vgrid;
+
+/* Physics and time integration (Sec. 2, Sec. 3.5, App. A, Sec. 5). */
+typedef struct {
+  double nu;          /* collision frequency (= 1/Knudsen) */
+  int integrator;     /* BGK_BE, BGK_DIRK2, BGK_DIRK3, BGK_BSTABLE2, BGK_BDF2 */
+  double dt;          /* time step; if <= 0, dt = cfl * dt_e (explicit bound of Sec. 5) */
+  double cfl;
+} bgk_physics;
+
+/* Solver configuration. */
+typedef struct {
+  double tau;         /* Picard tolerance of Eq. (convergence-criteria); default 1e-8 */
+  int l_max;          /* Picard iteration limit; default 1000 */
+  int precision;      /* BGK_FP64 or BGK_FP32_SWEEP (FP32 sweep, FP64 moments) */
+  int block_threads;  /* sweep CTA size override (0 = default) */
+  void* stream;       /* cudaStream_t to run on (NULL = a stream owned by the handle) */
+} bgk_config;
+
+typedef struct {
+  int n_stages;
+  int iterations[3];  /* Picard iterations of each stage of the last step */
+  double measure[3];  /* final convergence measure of each stage */
+  int total_sweeps;   /* sweeps run since the handle was created */
+  int status;
+} bgk_stats;
+
+typedef struct bgk_handle bgk_handle;
+
+/* Build geometry, element tables, velocity grid and every ordinate's sweep graph
+ * (generations by longest path, cycles broken by the DFS back-edge rule of Sec. 4.1)
+ * on the current CUDA device, and allocate the state.  Errors: BGK_E_INVALID (bad
+ * sizes, non-conforming or degenerate mesh), BGK_E_OOM, BGK_E_CUDA. */
+int bgk_create(const bgk_mesh* mesh, const bgk_vgrid* vgrid, const bgk_physics* phys,
+               const bgk_config* cfg, bgk_handle** out);
+int bgk_destroy(bgk_handle* h);
+
+/* Problem sizes: out[0]=n_ordinates, [1]=n_nodes, [2]=n_dof, [3]=n_cells, [4]=dim,
+ * [5]=max generations over ordinates, [6]=lagged edges over all ordinates. */
+int bgk_sizes(const bgk_handle* h, int64_t* out);
+/* Time step actually used (after the CFL rule). */
+int bgk_get_dt(const bgk_handle* h, double* dt);
+
+/* Initial state f = nodal-in-x, projected-in-v Maxwellian (Sec. 3.3, App. B) of the
+ * given nodal states (host [n_nodes][d+2]).  Resets the BDF2 history. */
+int bgk_set_state_maxwellian(bgk_handle* h, const double* h_nut);
+/* Inflow boundary data: projected Maxwellian of the nodal states (host [n_nodes][d+2]),
+ * used at nodes of boundary faces with v.n < 0 (Eq. bgk-bc, inflow condition). */
+int bgk_set_inflow_maxwellian(bgk_handle* h, const double* h_nut);
+/* Raw distribution in or out, host buffers [n_ordinates][n_nodes] of dtype. */
+int bgk_set_f(bgk_handle* h, const void* h_f, int dtype);
+int bgk_get_f(bgk_handle* h, void* h_f, int dtype);
+/* Device-pointer variants (same layout), ordered on the handle's stream. */
+int bgk_set_f_device(bgk_handle* h, const void* d_f, int dtype);
+int bgk_get_f_device(bgk_handle* h, void* d_f, int dtype);
+
+/* Velocity moments of the current f, host [n_nodes][d+2] (Eq. moments). */
+int bgk_get_moments(bgk_handle* h, double* h_U);
+int bgk_get_moments_device(bgk_handle* h, double* d_U);
+/* Ordinates and quadrature weights, host [n_ordinates][dim] and [n_ordinates]. */
+int bgk_get_velocity(const bgk_handle* h, double* h_v, double* h_w);
+/* Generation of every cell for ordinate j (host int32 [n_cells]); returns the count of
+ * generations in *n_gen.  Bit-exact definition: longest path from a source (Sec. 4.1). */
+int bgk_get_generations(bgk_handle* h, int j, int32_t* h_gen, int* n_gen);
+
+/* One transport sweep of the Picard iteration, Eq. (bgk-ss-picard): f <- solution with
+ * the Maxwellian of the current moments, source q = f_q / (dt_q) and collision nu_s.
+ * f_q is the handle's stage base state (the state at the last bgk_set_* call or step).
+ * For parity tests and sweep benchmarks; a step does not use this entry point. */
+int bgk_sweep(bgk_handle* h, double nu_s, double q_scale);
+
+/* Advance nsteps implicit steps (Sec. 3.5 stages, Sec. 4 Picard loop to tolerance).
+ * Each step runs as one CUDA graph with one conditional while-loop per stage.  st may
+ * be NULL.  Errors: BGK_E_NOCONV, BGK_E_NONPHYSICAL, BGK_E_CUDA. */
+int bgk_step(bgk_handle* h, int nsteps, bgk_stats* st);
+/* Same, host-synchronous only at the end; returns immediately after enqueueing when
+ * async != 0 (stats then come from bgk_last_stats after a stream sync). */
+int bgk_step_async(bgk_handle* h, int nsteps);
+int bgk_last_stats(bgk_handle* h, bgk_stats* st);
+/* Make the handle's stream wait for completion. */
+int bgk_synchronize(bgk_handle* h);
+
+/* Instrumentation: the sweep kernel's event-timed average duration (ms) and launch
+ * count since the last reset, recorded on the handle's stream. */
+int bgk_timing(bgk_handle* h, int reset, double* sweep_ms_total, int64_t* sweep_launches);
+
+const char* bgk_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BGK_B300_H */

@@ -638,10 +638,10 @@ static void dense_solve(int n, double *A, double *b) {
  * for every ordinate j, cells visited in ascending (generation, id).  fold = f^l,
  * fnew = f^{l+1}; Mn = nodal Maxwellian; q = stage source; fbc = boundary values,
  * all [j][cell][node]. */
-static void sweep(const orc_t *o, const double *fold, const double *Mn, const double *q, const double *fbc,
-                  double nu, double nu_s, double *fnew) {
+static void sweep_range(const orc_t *o, const double *fold, const double *Mn, const double *q, const double *fbc,
+                        double nu, double nu_s, double *fnew, int j0, int j1) {
   int d = o->dim, nd = o->ndof, nf = o->nface;
-  for (int j = 0; j < o->nv; ++j) {
+  for (int j = j0; j < j1; ++j) {
     const double *v = o->v + (size_t)j * d;
     size_t base = (size_t)j * o->nnode;
     const unsigned char *lag = o->lagged + (size_t)j * o->ncell * nf;
@@ -691,6 +691,11 @@ static void sweep(const orc_t *o, const double *fold, const double *Mn, const do
       for (int a = 0; a < nd; ++a) fnew[base + (size_t)c * nd + a] = b[a];
     }
   }
+}
+
+static void sweep(const orc_t *o, const double *fold, const double *Mn, const double *q, const double *fbc,
+                  double nu, double nu_s, double *fnew) {
+  sweep_range(o, fold, Mn, q, fbc, nu, nu_s, fnew, 0, o->nv);
 }
 
 /* ============================================================ public interface */
@@ -845,6 +850,12 @@ void orc_face_signs(const orc_t *o, int j, int *s) {
 void orc_sweep(const orc_t *o, const double *fold, const double *Mn, const double *q, const double *fbc, double nu,
                double nu_s, double *fnew) {
   sweep(o, fold, Mn, q, fbc, nu, nu_s, fnew);
+}
+
+/* the same sweep restricted to ordinates j0 <= j < j1 (used to time a bounded sample) */
+void orc_sweep_range(const orc_t *o, const double *fold, const double *Mn, const double *q, const double *fbc,
+                     double nu, double nu_s, double *fnew, int j0, int j1) {
+  sweep_range(o, fold, Mn, q, fbc, nu, nu_s, fnew, j0, j1);
 }
 
 /* explicit time-step bound (Sec. 5): dt_e = (1/d) (1/(2 kx + 1)) h_min / max_j |v_j|,

@@ -60,6 +60,7 @@ def _load():
         lib.orc_generations.argtypes = [P, C.c_int, ip, up]
         lib.orc_face_signs.argtypes = [P, C.c_int, ip]
         lib.orc_sweep.argtypes = [P, dp, dp, dp, dp, C.c_double, C.c_double, dp]
+        lib.orc_sweep_range.argtypes = [P, dp, dp, dp, dp, C.c_double, C.c_double, dp, C.c_int, C.c_int]
         lib.orc_dt_explicit.restype = C.c_double
         lib.orc_dt_explicit.argtypes = [P]
         lib.orc_tableau.restype = C.c_int
@@ -174,6 +175,16 @@ class Oracle:
         fnew = np.zeros((self.nv, self.nnode))
         c = lambda a: np.ascontiguousarray(a, dtype=np.float64).reshape(self.nv, self.nnode)  # noqa: E731
         self.lib.orc_sweep(self.h, c(fold), c(Mn), c(q), c(fbc), float(nu), float(nu_s), fnew)
+        return fnew
+
+    def sweep_range(self, fold, Mn, q, fbc, nu, nu_s, j0, j1, fnew=None):
+        """One sweep restricted to ordinates j0 <= j < j1 (writes those rows of fnew)."""
+        if not self._dags:
+            self.build_dags()
+        if fnew is None:
+            fnew = np.zeros((self.nv, self.nnode))
+        c = lambda a: np.ascontiguousarray(a, dtype=np.float64).reshape(self.nv, self.nnode)  # noqa: E731
+        self.lib.orc_sweep_range(self.h, c(fold), c(Mn), c(q), c(fbc), float(nu), float(nu_s), fnew, int(j0), int(j1))
         return fnew
 
     def set_physics(self, nu, dt, integrator="BE", tau=1e-8, lmax=1000):

@@ -1,0 +1,221 @@
+"""ctypes binding of libbgk_b300.so (include/bgk.h): argument marshalling only.
+
+Every step of the solver runs in the library's CUDA kernels.  There is no CPU fallback:
+:func:`load` raises when the library is missing or cannot be loaded.  PyTorch is used by
+callers only for device memory and streams (``data_ptr()`` / ``cuda_stream``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbgk_b300.so")
+
+BGK_OK, BGK_E_INVALID, BGK_E_CUDA, BGK_E_OOM, BGK_E_NOCONV, BGK_E_NONPHYSICAL, BGK_E_TIMEOUT = range(7)
+INTEGRATORS = {"BE": 0, "DIRK2": 1, "DIRK3": 2, "BSTABLE2": 3, "BDF2": 4}
+PRECISIONS = {"fp64": 0, "fp32": 1}
+DTYPES = {np.dtype(np.float64): 0, np.dtype(np.float32): 1}
+
+
+class BgkError(RuntimeError):
+    def __init__(self, status, where):
+        super().__init__("%s failed: %s (status %d)" % (where, _lib_status(status), status))
+        self.status = status
+
+
+class Mesh(C.Structure):
+    _fields_ = [("dim", C.c_int), ("k_x", C.c_int), ("n_vertices", C.c_int), ("xyz", C.c_void_p),
+                ("n_cells", C.c_int), ("cell_vertices", C.c_void_p)]
+
+
+class VGrid(C.Structure):
+    _fields_ = [("L", C.c_double), ("n_points", C.c_int), ("k_v", C.c_int)]
+
+
+class Physics(C.Structure):
+    _fields_ = [("nu", C.c_double), ("integrator", C.c_int), ("dt", C.c_double), ("cfl", C.c_double)]
+
+
+class Config(C.Structure):
+    _fields_ = [("tau", C.c_double), ("l_max", C.c_int), ("precision", C.c_int), ("block_threads", C.c_int),
+                ("stream", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n_stages", C.c_int), ("iterations", C.c_int * 3), ("measure", C.c_double * 3),
+                ("total_sweeps", C.c_int), ("status", C.c_int)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library; raises if it is absent (no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libbgk_b300.so not built (run paper_2608_19150_b300/build.py)")
+    lib = C.CDLL(path)
+    P, I, D, V = C.c_void_p, C.c_int, C.c_double, C.c_void_p
+    sig = {
+        "bgk_create": [C.POINTER(Mesh), C.POINTER(VGrid), C.POINTER(Physics), C.POINTER(Config), C.POINTER(P)],
+        "bgk_destroy": [P],
+        "bgk_sizes": [P, C.POINTER(C.c_int64)],
+        "bgk_get_dt": [P, C.POINTER(D)],
+        "bgk_set_state_maxwellian": [P, V],
+        "bgk_set_inflow_maxwellian": [P, V],
+        "bgk_set_f": [P, V, I],
+        "bgk_get_f": [P, V, I],
+        "bgk_set_f_device": [P, V, I],
+        "bgk_get_f_device": [P, V, I],
+        "bgk_get_moments": [P, V],
+        "bgk_get_moments_device": [P, V],
+        "bgk_get_velocity": [P, V, V],
+        "bgk_get_generations": [P, I, V, C.POINTER(I)],
+        "bgk_sweep": [P, D, D],
+        "bgk_step": [P, I, C.POINTER(Stats)],
+        "bgk_step_async": [P, I],
+        "bgk_last_stats": [P, C.POINTER(Stats)],
+        "bgk_synchronize": [P],
+        "bgk_timing": [P, I, C.POINTER(D), C.POINTER(C.c_int64)],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    lib.bgk_status_string.argtypes = [C.c_int]
+    lib.bgk_status_string.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+def _lib_status(s):
+    try:
+        return load().bgk_status_string(int(s)).decode()
+    except Exception:  # noqa: BLE001
+        return "status %d" % s
+
+
+def _ck(rc, where):
+    if rc != BGK_OK:
+        raise BgkError(rc, where)
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class Solver:
+    """Handle of one problem on the current CUDA device (thin wrapper of bgk_create)."""
+
+    def __init__(self, dim, kx, xyz, cells, n_v, k_v, L, nu, integrator="BE", dt=0.0, cfl=10.0, tau=1e-8,
+                 l_max=1000, precision="fp64", block_threads=0, stream=None):
+        self.lib = load()
+        self._xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        self._cells = np.ascontiguousarray(cells, dtype=np.int32)
+        m = Mesh(dim, kx, self._xyz.shape[0], _ptr(self._xyz), self._cells.shape[0], _ptr(self._cells))
+        vg = VGrid(float(L), int(n_v), int(k_v))
+        ph = Physics(float(nu), INTEGRATORS[integrator], float(dt), float(cfl))
+        cf = Config(float(tau), int(l_max), PRECISIONS[precision], int(block_threads),
+                    C.c_void_p(stream) if stream else None)
+        h = C.c_void_p()
+        _ck(self.lib.bgk_create(C.byref(m), C.byref(vg), C.byref(ph), C.byref(cf), C.byref(h)), "bgk_create")
+        self.h = h
+        sz = (C.c_int64 * 7)()
+        _ck(self.lib.bgk_sizes(self.h, sz), "bgk_sizes")
+        self.nv, self.nnode, self.ndof, self.ncell, self.dim, self.gmax, self.lagged = (int(x) for x in sz)
+        self.precision = precision
+        self.fdtype = np.float64 if precision == "fp64" else np.float32
+
+    @classmethod
+    def from_workload(cls, w, **kw):
+        args = dict(integrator=w.integrator, cfl=w.cfl)
+        args.update(kw)
+        return cls(w.mesh.dim, w.kx, w.mesh.xyz, w.mesh.cells, w.n_v, w.k_v, w.L, w.nu, **args)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.bgk_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    @property
+    def dt(self):
+        d = C.c_double()
+        _ck(self.lib.bgk_get_dt(self.h, C.byref(d)), "bgk_get_dt")
+        return d.value
+
+    def set_state_maxwellian(self, nut):
+        nut = np.ascontiguousarray(nut, dtype=np.float64)
+        _ck(self.lib.bgk_set_state_maxwellian(self.h, _ptr(nut)), "bgk_set_state_maxwellian")
+
+    def set_inflow_maxwellian(self, nut):
+        nut = np.ascontiguousarray(nut, dtype=np.float64)
+        _ck(self.lib.bgk_set_inflow_maxwellian(self.h, _ptr(nut)), "bgk_set_inflow_maxwellian")
+
+    def set_f(self, f):
+        f = np.ascontiguousarray(f)
+        _ck(self.lib.bgk_set_f(self.h, _ptr(f), DTYPES[f.dtype]), "bgk_set_f")
+
+    def get_f(self, dtype=np.float64):
+        out = np.empty((self.nv, self.nnode), dtype=dtype)
+        _ck(self.lib.bgk_get_f(self.h, _ptr(out), DTYPES[np.dtype(dtype)]), "bgk_get_f")
+        return out
+
+    def set_f_device(self, ptr, dtype=np.float64):
+        _ck(self.lib.bgk_set_f_device(self.h, C.c_void_p(ptr), DTYPES[np.dtype(dtype)]), "bgk_set_f_device")
+
+    def get_f_device(self, ptr, dtype=np.float64):
+        _ck(self.lib.bgk_get_f_device(self.h, C.c_void_p(ptr), DTYPES[np.dtype(dtype)]), "bgk_get_f_device")
+
+    def get_moments(self):
+        U = np.empty((self.nnode, self.dim + 2))
+        _ck(self.lib.bgk_get_moments(self.h, _ptr(U)), "bgk_get_moments")
+        return U
+
+    def get_moments_device(self, ptr):
+        _ck(self.lib.bgk_get_moments_device(self.h, C.c_void_p(ptr)), "bgk_get_moments_device")
+
+    def velocity(self):
+        v = np.empty((self.nv, self.dim))
+        w = np.empty(self.nv)
+        _ck(self.lib.bgk_get_velocity(self.h, _ptr(v), _ptr(w)), "bgk_get_velocity")
+        return v, w
+
+    def generations(self, j):
+        gen = np.empty(self.ncell, dtype=np.int32)
+        n = C.c_int()
+        _ck(self.lib.bgk_get_generations(self.h, int(j), _ptr(gen), C.byref(n)), "bgk_get_generations")
+        return gen, n.value
+
+    def sweep(self, nu_s, q_scale):
+        _ck(self.lib.bgk_sweep(self.h, float(nu_s), float(q_scale)), "bgk_sweep")
+
+    def step(self, nsteps=1):
+        st = Stats()
+        rc = self.lib.bgk_step(self.h, int(nsteps), C.byref(st))
+        _ck(rc, "bgk_step")
+        return st
+
+    def step_async(self, nsteps=1):
+        _ck(self.lib.bgk_step_async(self.h, int(nsteps)), "bgk_step_async")
+
+    def last_stats(self):
+        st = Stats()
+        _ck(self.lib.bgk_last_stats(self.h, C.byref(st)), "bgk_last_stats")
+        return st
+
+    def synchronize(self):
+        _ck(self.lib.bgk_synchronize(self.h), "bgk_synchronize")
+
+    def timing(self, reset=False):
+        ms = C.c_double()
+        n = C.c_int64()
+        _ck(self.lib.bgk_timing(self.h, int(bool(reset)), C.byref(ms), C.byref(n)), "bgk_timing")
+        return ms.value, n.value

@@ -1,0 +1,540 @@
+// Device kernels of the B300 sweep solver.  All arithmetic of the hot path lives here.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "bgk_internal.h"
+#include "bgk_tables.h"
+
+namespace bgk {
+
+// Device-resident iteration state of one handle.
+struct DevState {
+  int it;            // Picard iterations since creation (parity selects the moment buffer)
+  int stage_it;      // iterations of the current stage
+  int status;        // BGK_OK or an error of the running step
+  int err;           // non-physical moments seen (bit set by the Maxwellian kernel)
+  int iters[4];
+  double meas[4];
+  int total_sweeps;
+  int pad;
+};
+
+__device__ __forceinline__ void ordinate(const VGrid& g, int j, double (&v)[3]) {
+  if (g.dim == 2) {
+    v[0] = g.x[j / g.N];
+    v[1] = g.x[j % g.N];
+    v[2] = 0.0;
+  } else {
+    v[0] = g.x[j / (g.N * g.N)];
+    v[1] = g.x[(j / g.N) % g.N];
+    v[2] = g.x[j % g.N];
+  }
+}
+
+// Face code of cell c for velocity v: 2 bits per face, 01 = v.N > 0 (outflow),
+// 10 = v.N < 0 (inflow), 00 = no flux.  v.N is evaluated in FP64 with one rounding
+// per operation (no contraction), exactly like the host evaluation.
+template <int D, int NF>
+__device__ __forceinline__ uint32_t face_code(const double* __restrict__ G, const double (&v)[3]) {
+  uint32_t code = 0;
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    double s = __dmul_rn(v[0], G[f * D + 0]);
+    s = __dadd_rn(s, __dmul_rn(v[1], G[f * D + 1]));
+    if (D == 3) s = __dadd_rn(s, __dmul_rn(v[2], G[f * D + 2]));
+    code |= (s > 0.0 ? 1u : (s < 0.0 ? 2u : 0u)) << (2 * f);
+  }
+  return code;
+}
+
+// ---------------------------------------------------------------------------------
+// Conservative projection of a Maxwellian onto the velocity space (App. B):
+// c[m] = (1/w_m) int g(v) [E l_m](v) dv, g the 1D Gaussian of mean u, variance theta,
+// l_m the Lagrange basis of node m on its velocity cell, extended polynomially beyond
+// [-L, L] on the first and last cells.  Exact up to rounding via erfc and the Gaussian
+// partial-moment recurrence; writes c[m * stride], m < N.
+__device__ __forceinline__ void proj_factors(const VGrid& g, double u, double theta, double* c, int stride) {
+  const double rs2 = 0.70710678118654752440, rs2pi = 0.39894228040143267794;
+  const double sig = sqrt(theta), isig = 1.0 / sig;
+  const double hh = 0.5 * g.h;
+  // per cell boundary: t, phi(t), smaller tail E(t) = 0.5 erfc(|t|/sqrt 2)
+  double tprev = -INFINITY, phiprev = 0.0, Eprev = 0.0;
+  for (int cl = 0; cl < g.ncl; ++cl) {
+    double tb, phib, Eb;
+    if (cl == g.ncl - 1) {
+      tb = INFINITY;
+      phib = 0.0;
+      Eb = 0.0;
+    } else {
+      tb = (-g.L + (cl + 1) * g.h - u) * isig;
+      phib = rs2pi * exp(-0.5 * tb * tb);
+      Eb = 0.5 * erfc(fabs(tb) * rs2);
+    }
+    const double ta = tprev, phia = phiprev, Ea = Eprev;
+    double I[kMaxKv + 1];
+    // I_0 = Phi(tb) - Phi(ta) from the tails that avoid cancellation
+    if (ta >= 0.0)
+      I[0] = Ea - Eb;
+    else if (tb <= 0.0)
+      I[0] = Eb - Ea;
+    else
+      I[0] = (1.0 - Eb) - Ea;
+    // I_k = int t^k phi: I_1 = phi(a) - phi(b); I_k = (k-1) I_{k-2} + a^{k-1}phi(a) - b^{k-1}phi(b)
+    if (g.kv >= 1) I[1] = phia - phib;
+    double ap = 1.0, bp = 1.0;
+    for (int k = 2; k <= g.kv; ++k) {
+      ap = isinf(ta) ? 0.0 : ap * ta;
+      bp = isinf(tb) ? 0.0 : bp * tb;
+      I[k] = (k - 1) * I[k - 2] + (isinf(ta) ? 0.0 : ap * phia) - (isinf(tb) ? 0.0 : bp * phib);
+    }
+    // local variable xi = (v - mid)/(h/2) = alpha + beta t
+    const double mid = -g.L + (cl + 0.5) * g.h;
+    const double alpha = (u - mid) / hh, beta = sig / hh;
+    double J[kMaxKv + 1];  // J_p = int phi (alpha + beta t)^p dt
+    double binom[kMaxKv + 1] = {1.0, 0, 0, 0, 0};
+    for (int p = 0; p <= g.kv; ++p) {
+      if (p > 0)
+        for (int q = p; q >= 1; --q) binom[q] += binom[q - 1];
+      double s = 0.0, ab = 1.0;
+      // sum_q C(p,q) alpha^{p-q} beta^q I_q, evaluated from q = p down
+      double apow[kMaxKv + 1];
+      apow[0] = 1.0;
+      for (int q = 1; q <= p; ++q) apow[q] = apow[q - 1] * alpha;
+      for (int q = 0; q <= p; ++q) {
+        s += binom[q] * apow[p - q] * ab * I[q];
+        ab *= beta;
+      }
+      J[p] = s;
+    }
+    for (int k = 0; k < g.np; ++k) {
+      double s = 0.0;
+      for (int p = 0; p < g.np; ++p) s += g.lag[k][p] * J[p];
+      const int m = cl * g.np + k;
+      c[m * stride] = s / g.w[m];
+    }
+    tprev = tb;
+    phiprev = phib;
+    Eprev = Eb;
+  }
+}
+
+// out[j * ostride + p] = coef * n_p * prod_a c_a[j_a](u_p, theta_p) + qscale * q[j * ostride + p]
+// for p < npos.  States: mode 0 -> st0 holds (n, u, theta) per node; mode 1 -> moment
+// buffers U[it & 1] (n, n u, E), converted to primitives (Eq. moments) with a
+// non-physical check.  nodemap (optional) maps output position -> state node.
+template <typename T>
+__global__ void k_maxwell(VGrid g, int npos, int nm, const double* __restrict__ st0, const double* __restrict__ st1,
+                          int mode, const DevState* __restrict__ dsr, DevState* ds, const int32_t* __restrict__ nodemap,
+                          T* __restrict__ out, size_t ostride, double coef, const T* __restrict__ q, double qscale) {
+  extern __shared__ double csm[];  // [dim*N][blockDim]
+  if (ds && ds->status != BGK_OK) return;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int tid = threadIdx.x, bd = blockDim.x;
+  if (p >= npos) return;
+  const int node = nodemap ? nodemap[p] : p;
+  const double* S = (mode == 0) ? st0 : (((dsr->it & 1) == 0) ? st0 : st1);
+  const double* Un = S + (size_t)node * nm;
+  double n, u[3] = {0, 0, 0}, th;
+  if (mode == 0) {
+    n = Un[0];
+    for (int a = 0; a < g.dim; ++a) u[a] = Un[1 + a];
+    th = Un[1 + g.dim];
+  } else {
+    n = Un[0];
+    double u2 = 0.0;
+    for (int a = 0; a < g.dim; ++a) {
+      u[a] = Un[1 + a] / n;
+      u2 += u[a] * u[a];
+    }
+    th = (2.0 * Un[1 + g.dim] / n - u2) / g.dim;
+  }
+  if (!(n > 0.0) || !(th > 0.0) || !isfinite(n) || !isfinite(th)) {
+    if (ds) atomicOr(&ds->err, 1);
+    n = 0.0;
+    th = 1.0;
+    for (int a = 0; a < g.dim; ++a) u[a] = 0.0;
+  }
+  for (int a = 0; a < g.dim; ++a) proj_factors(g, u[a], th, csm + (size_t)(a * g.N) * bd + tid, bd);
+  const double cn = coef * n;
+  if (g.dim == 2) {
+    for (int j0 = 0; j0 < g.N; ++j0) {
+      const double c0 = cn * csm[(size_t)j0 * bd + tid];
+      for (int j1 = 0; j1 < g.N; ++j1) {
+        const size_t j = (size_t)j0 * g.N + j1;
+        double val = c0 * csm[(size_t)(g.N + j1) * bd + tid];
+        if (q) val += qscale * (double)q[j * ostride + p];
+        out[j * ostride + p] = (T)val;
+      }
+    }
+  } else {
+    for (int j0 = 0; j0 < g.N; ++j0) {
+      const double c0 = cn * csm[(size_t)j0 * bd + tid];
+      for (int j1 = 0; j1 < g.N; ++j1) {
+        const double c01 = c0 * csm[(size_t)(g.N + j1) * bd + tid];
+        for (int j2 = 0; j2 < g.N; ++j2) {
+          const size_t j = ((size_t)j0 * g.N + j1) * g.N + j2;
+          double val = c01 * csm[(size_t)(2 * g.N + j2) * bd + tid];
+          if (q) val += qscale * (double)q[j * ostride + p];
+          out[j * ostride + p] = (T)val;
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Velocity moments U_i = sum_j w_j (1, v_j, |v_j|^2/2) f_{j,i} (Eq. moments), FP64
+// accumulation for either storage type.  mode 0: write U[it&1].  mode 1: write
+// U[(it+1)&1] and per-block partial sums of |dU_m|^2 and |U_old,m|^2, m = 0, 1, 2,
+// for the criterion of Eq. (convergence-criteria).
+template <typename T>
+__global__ void k_moments(VGrid g, const T* __restrict__ f, int nnode, double* U0, double* U1, const DevState* ds,
+                          int mode, double* __restrict__ partial) {
+  if (ds->status != BGK_OK) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nm = g.dim + 2;
+  double acc[5] = {0, 0, 0, 0, 0};
+  if (i < nnode) {
+    if (g.dim == 2) {
+      for (int j0 = 0; j0 < g.N; ++j0) {
+        double s0 = 0, s1 = 0, s2 = 0;
+        const T* fr = f + (size_t)j0 * g.N * nnode + i;
+#pragma unroll 4
+        for (int j1 = 0; j1 < g.N; ++j1) {
+          const double fv = (double)fr[(size_t)j1 * nnode];
+          const double wf = g.w[j1] * fv;
+          s0 += wf;
+          s1 += g.x[j1] * wf;
+          s2 += g.x[j1] * g.x[j1] * wf;
+        }
+        const double w0 = g.w[j0], x0 = g.x[j0];
+        acc[0] += w0 * s0;
+        acc[1] += w0 * x0 * s0;
+        acc[2] += w0 * s1;
+        acc[3] += 0.5 * w0 * (x0 * x0 * s0 + s2);
+      }
+    } else {
+      for (int j0 = 0; j0 < g.N; ++j0) {
+        double t0 = 0, t1 = 0, t2 = 0, t3 = 0;
+        for (int j1 = 0; j1 < g.N; ++j1) {
+          double s0 = 0, s1 = 0, s2 = 0;
+          const T* fr = f + ((size_t)j0 * g.N + j1) * g.N * nnode + i;
+#pragma unroll 4
+          for (int j2 = 0; j2 < g.N; ++j2) {
+            const double wf = g.w[j2] * (double)fr[(size_t)j2 * nnode];
+            s0 += wf;
+            s1 += g.x[j2] * wf;
+            s2 += g.x[j2] * g.x[j2] * wf;
+          }
+          const double w1 = g.w[j1], x1 = g.x[j1];
+          t0 += w1 * s0;
+          t1 += w1 * x1 * s0;
+          t2 += w1 * s1;
+          t3 += w1 * (x1 * x1 * s0 + s2);
+        }
+        const double w0 = g.w[j0], x0 = g.x[j0];
+        acc[0] += w0 * t0;
+        acc[1] += w0 * x0 * t0;
+        acc[2] += w0 * t1;
+        acc[3] += w0 * t2;
+        acc[4] += 0.5 * w0 * (x0 * x0 * t0 + t3);
+      }
+    }
+  }
+  const int cur = ds->it & 1;
+  double* Uw = (mode == 0) ? (cur == 0 ? U0 : U1) : (cur == 0 ? U1 : U0);
+  if (i < nnode)
+    for (int m = 0; m < nm; ++m) Uw[(size_t)i * nm + m] = acc[m];
+  if (mode == 0) return;
+  // partial sums for the convergence measure
+  const double* Uo = cur == 0 ? U0 : U1;
+  double r[6] = {0, 0, 0, 0, 0, 0};
+  if (i < nnode) {
+    const double* o = Uo + (size_t)i * nm;
+    r[0] = (acc[0] - o[0]) * (acc[0] - o[0]);
+    r[1] = o[0] * o[0];
+    for (int a = 0; a < g.dim; ++a) {
+      r[2] += (acc[1 + a] - o[1 + a]) * (acc[1 + a] - o[1 + a]);
+      r[3] += o[1 + a] * o[1 + a];
+    }
+    r[4] = (acc[nm - 1] - o[nm - 1]) * (acc[nm - 1] - o[nm - 1]);
+    r[5] = o[nm - 1] * o[nm - 1];
+  }
+  __shared__ double red[6][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    double x = r[k];
+    for (int o2 = 16; o2 > 0; o2 >>= 1) x += __shfl_down_sync(0xffffffffu, x, o2);
+    if (lane == 0) red[k][warp] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[threadIdx.x][w];
+    partial[(size_t)blockIdx.x * 6 + threadIdx.x] = s;
+  }
+}
+
+// Reduce the partials in a fixed order, evaluate Eq. (convergence-criteria) (m = 1
+// denominator max(|U^1|, |U^0|)), advance the iteration counters and set the while
+// condition of the stage loop.
+__global__ void k_finalize(DevState* ds, const double* __restrict__ partial, int nblk, double tol, int lmax, int stage,
+                           cudaGraphConditionalHandle cond, int use_cond) {
+  __shared__ double red[6][256];
+  double s[6] = {0, 0, 0, 0, 0, 0};
+  const bool skip = ds->status != BGK_OK;
+  if (!skip)
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x)
+      for (int k = 0; k < 6; ++k) s[k] += partial[(size_t)b * 6 + k];
+  for (int k = 0; k < 6; ++k) red[k][threadIdx.x] = s[k];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+      for (int k = 0; k < 6; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  int cont = 0;
+  if (!skip) {
+    const double r0 = sqrt(red[0][0]) / sqrt(red[1][0]);
+    const double r1 = sqrt(red[2][0]) / fmax(sqrt(red[3][0]), sqrt(red[1][0]));
+    const double r2 = sqrt(red[4][0]) / sqrt(red[5][0]);
+    const double meas = fmax(r0, fmax(r1, r2));
+    ds->it += 1;
+    ds->stage_it += 1;
+    ds->total_sweeps += 1;
+    ds->iters[stage] = ds->stage_it;
+    ds->meas[stage] = meas;
+    if (ds->err) {
+      ds->status = BGK_E_NONPHYSICAL;
+    } else if (!(meas < tol)) {
+      if (ds->stage_it >= lmax)
+        ds->status = BGK_E_NOCONV;
+      else
+        cont = 1;
+    }
+  }
+  if (use_cond) cudaGraphSetConditional(cond, cont);
+}
+
+__global__ void k_stage_begin(DevState* ds, int stage) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    ds->stage_it = 0;
+    ds->iters[stage] = 0;
+    ds->meas[stage] = 0.0;
+  }
+}
+
+__global__ void k_reset_state(DevState* ds) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    ds->status = BGK_OK;
+    ds->err = 0;
+    for (int s = 0; s < 4; ++s) {
+      ds->iters[s] = 0;
+      ds->meas[s] = 0.0;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Generations of every ordinate's sweep graph (Sec. 4.1): Kahn's peel, one CTA per
+// ordinate.  In-degrees are packed bytes in shared memory.  Level g of the list is the
+// set Gen_j(g): cells whose longest path from a source has length g.  Lagged inflow
+// faces (bit f of lag[c]) are not edges.  Writes glist[j][*] (packed entries, level
+// by level), lvl[j][g] (level starts), ngen[j], nproc[j] (cells reached).
+template <int D, int NF>
+__global__ void k_peel(const double* __restrict__ geo, int gs, const int32_t* __restrict__ nbr,
+                       const int32_t* __restrict__ nbr_face, int ncell, VGrid g, const int32_t* __restrict__ jlist,
+                       const uint8_t* __restrict__ lag, uint32_t* __restrict__ glist, int32_t* __restrict__ lvl,
+                       int32_t* __restrict__ ngen, int32_t* __restrict__ nproc) {
+  extern __shared__ uint32_t indeg[];
+  __shared__ int cnt;
+  const int j = jlist ? jlist[blockIdx.x] : blockIdx.x;
+  const uint8_t* lj = lag ? lag + (size_t)blockIdx.x * ncell : nullptr;
+  double v[3];
+  ordinate(g, j, v);
+  uint32_t* gl = glist + (size_t)j * ncell;
+  int32_t* lv = lvl + (size_t)j * (ncell + 1);
+  const int nw = (ncell + 3) >> 2;
+  for (int w = threadIdx.x; w < nw; w += blockDim.x) indeg[w] = 0u;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+    const uint32_t code = face_code<D, NF>(geo + (size_t)c * gs, v);
+    uint32_t deg = 0;
+    const uint32_t lb = lj ? lj[c] : 0u;
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+      if (((code >> (2 * f)) & 3u) == 2u && nbr[(size_t)c * 4 + f] >= 0 && !((lb >> f) & 1u)) ++deg;
+    if (deg)
+      atomicAdd(&indeg[c >> 2], deg << (8 * (c & 3)));
+    else
+      gl[atomicAdd(&cnt, 1)] = (uint32_t)c | (code << kCellBits);
+  }
+  __syncthreads();
+  int start = 0, end = cnt, gen = 0;
+  while (start < end) {
+    if (threadIdx.x == 0) lv[gen] = start;
+    for (int k = start + threadIdx.x; k < end; k += blockDim.x) {
+      const uint32_t e = gl[k];
+      const int c = (int)(e & kCellMask);
+      const uint32_t code = e >> kCellBits;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        if (((code >> (2 * f)) & 3u) != 1u) continue;
+        const int nb = nbr[(size_t)c * 4 + f];
+        if (nb < 0) continue;
+        if (lag) {
+          const int f2 = nbr_face[(size_t)c * 4 + f];
+          if ((lj[nb] >> f2) & 1u) continue;
+        }
+        const uint32_t old = atomicSub(&indeg[nb >> 2], 1u << (8 * (nb & 3)));
+        if (((old >> (8 * (nb & 3))) & 0xFFu) == 1u) {
+          const uint32_t cb = face_code<D, NF>(geo + (size_t)nb * gs, v);
+          gl[atomicAdd(&cnt, 1)] = (uint32_t)nb | (cb << kCellBits);
+        }
+      }
+    }
+    __syncthreads();
+    start = end;
+    end = cnt;
+    ++gen;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    lv[gen] = start;
+    ngen[j] = gen;
+    nproc[j] = start;
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// LU without pivoting: the local matrix has a positive definite symmetric part
+// (nu_s M + upwind transport), so elimination in natural order is stable.
+template <int N, typename T>
+__device__ __forceinline__ void lu_solve(T (&A)[N][N], T (&b)[N]) {
+  T inv[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    inv[k] = T(1) / A[k][k];
+#pragma unroll
+    for (int i = k + 1; i < N; ++i) {
+      const T l = A[i][k] * inv[k];
+#pragma unroll
+      for (int c = k + 1; c < N; ++c) A[i][c] -= l * A[k][c];
+      b[i] -= l * b[k];
+    }
+  }
+#pragma unroll
+  for (int i = N - 1; i >= 0; --i) {
+    T s = b[i];
+#pragma unroll
+    for (int c = i + 1; c < N; ++c) s -= A[i][c] * b[c];
+    b[i] = s * inv[i];
+  }
+}
+
+// One transport sweep (Sec. 4, Eq. bgk-ss-picard), one CTA per ordinate walking that
+// ordinate's generations; the cells of a generation are independent and share the
+// CTA's threads.  For cell K and ordinate j (s_i = v_j . N_i, r_i = s_i/|K|):
+//   (nu_s Mh + sum_i r_i (Dd_i + [s_i>0] Eh_i)) f_K = Mh src_K + sum_{s_i<0} (-r_i) Eh_i y_i
+// where src = nu M^l + q and y_i is the upwind trace: the neighbour's value in f,
+// updated in place.  An upwind cell reached by a lagged (cycle) edge has a higher
+// generation, so it still holds f^l when read; boundary faces read fbc.
+template <class E, typename T>
+__global__ void __launch_bounds__(256) k_sweep(const double* __restrict__ geo, int gs, const int32_t* __restrict__ nbr,
+                                               const uint64_t* __restrict__ perm, const uint32_t* __restrict__ glist,
+                                               const int32_t* __restrict__ lvl, const int32_t* __restrict__ ngen,
+                                               int ncell, int nnode, int nbface, VGrid g, T nus,
+                                               const T* __restrict__ src, const T* __restrict__ fbc, T* f,
+                                               const DevState* ds) {
+  constexpr int D = E::D, ND = E::NDOF, NF = E::NF, FD = E::FD;
+  if (ds && ds->status != BGK_OK) return;
+  const int j = blockIdx.x;
+  double vd[3];
+  ordinate(g, j, vd);
+  const T v0 = (T)vd[0], v1 = (T)vd[1], v2 = (T)vd[2];
+  const uint32_t* gl = glist + (size_t)j * ncell;
+  const int32_t* lv = lvl + (size_t)j * (ncell + 1);
+  const int G = ngen[j];
+  T* fj = f + (size_t)j * nnode;
+  const T* sj = src + (size_t)j * nnode;
+  const T* bj = fbc + (size_t)j * nbface * FD;
+  int lo = lv[0];
+  for (int gg = 0; gg < G; ++gg) {
+    const int hi = lv[gg + 1];
+    for (int k = lo + threadIdx.x; k < hi; k += blockDim.x) {
+      const uint32_t e = gl[k];
+      const int c = (int)(e & kCellMask);
+      const uint32_t code = e >> kCellBits;
+      const double* Gc = geo + (size_t)c * gs;
+      const T invK = (T)Gc[NF * D];
+      T r[NF];
+      unsigned outm = 0;
+#pragma unroll
+      for (int i = 0; i < NF; ++i) {
+        const uint32_t fl = (code >> (2 * i)) & 3u;
+        T s = v0 * (T)Gc[i * D] + v1 * (T)Gc[i * D + 1];
+        if (D == 3) s += v2 * (T)Gc[i * D + 2];
+        s = fabs(s) * invK;
+        r[i] = fl == 1u ? s : (fl == 2u ? -s : T(0));
+        outm |= (fl == 1u ? 1u : 0u) << i;
+      }
+      T A[ND][ND], b[ND], sv[ND];
+#pragma unroll
+      for (int a = 0; a < ND; ++a) sv[a] = sj[(size_t)c * ND + a];
+      E::assemble(nus, r, outm, A);
+      E::mass(sv, b);
+      const int4 nb4 = *reinterpret_cast<const int4*>(nbr + (size_t)c * 4);
+      const int nbs[4] = {nb4.x, nb4.y, nb4.z, nb4.w};
+      const uint64_t pm = perm[c];
+#pragma unroll
+      for (int i = 0; i < NF; ++i) {
+        if (((code >> (2 * i)) & 3u) != 2u) continue;
+        const int nb = nbs[i];
+        T y[FD];
+        if (nb >= 0) {
+#pragma unroll
+          for (int kk = 0; kk < FD; ++kk)
+            y[kk] = fj[(size_t)nb * ND + (int)((pm >> (16 * i + 4 * kk)) & 15u)];
+        } else {
+#pragma unroll
+          for (int kk = 0; kk < FD; ++kk) y[kk] = bj[(size_t)(-nb - 1) * FD + kk];
+        }
+        E::inflow(i, -r[i], y, b);
+      }
+      lu_solve<ND, T>(A, b);
+#pragma unroll
+      for (int a = 0; a < ND; ++a) fj[(size_t)c * ND + a] = b[a];
+    }
+    lo = hi;
+    __syncthreads();
+  }
+}
+
+// out = a_k * fk + a_f * f + sum_r cF[r] * F[r]   (stage bookkeeping of Sec. 3.5)
+template <typename T>
+__global__ void k_combine(size_t n, T* __restrict__ out, double a_k, const T* __restrict__ fk, double a_f,
+                          const T* __restrict__ f, int nF, double c0, const T* __restrict__ F0, double c1,
+                          const T* __restrict__ F1, double c2, const T* __restrict__ F2, const DevState* ds) {
+  if (ds && ds->status != BGK_OK) return;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    if (fk) s += a_k * (double)fk[i];
+    if (f) s += a_f * (double)f[i];
+    if (nF > 0) s += c0 * (double)F0[i];
+    if (nF > 1) s += c1 * (double)F1[i];
+    if (nF > 2) s += c2 * (double)F2[i];
+    out[i] = (T)s;
+  }
+}
+
+template <typename TI, typename TO>
+__global__ void k_convert(size_t n, const TI* __restrict__ in, TO* __restrict__ out) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (TO)in[i];
+}
+
+}  // namespace bgk

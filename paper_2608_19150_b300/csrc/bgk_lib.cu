@@ -1,0 +1,791 @@
+// C ABI of the B300 sweep solver (include/bgk.h): set-up, state transfer, the
+// graph-captured implicit step and instrumentation.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "bgk_internal.h"
+#include "bgk_kernels.cuh"
+
+using namespace bgk;
+
+#define CK(x)                                  \
+  do {                                         \
+    cudaError_t e_ = (x);                      \
+    if (e_ != cudaSuccess) return BGK_E_CUDA;  \
+  } while (0)
+
+struct bgk_handle {
+  HostMesh hm;
+  VGrid g;
+  bgk_physics phys;
+  bgk_config cfg;
+  double dt = 0.0;
+  int precision = BGK_FP64;
+  size_t tsize = 8;          // bytes of one f value
+  int nnode = 0, nm = 0;
+  size_t nfv = 0;            // n_ordinates * n_nodes
+  int Gmax = 0;
+  long lagged = 0;
+  int sweep_threads = 128;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  // device geometry and schedule
+  double* geo = nullptr;
+  int32_t* nbr = nullptr;
+  int32_t* nbr_face = nullptr;
+  uint64_t* perm = nullptr;
+  int32_t* bnode = nullptr;
+  uint32_t* glist = nullptr;
+  int32_t* lvl = nullptr;
+  int32_t* ngen = nullptr;
+  int32_t* nproc = nullptr;
+  // state (storage type T = double or float)
+  void* f = nullptr;
+  void* fk = nullptr;
+  void* fprev = nullptr;
+  void* src = nullptr;
+  void* fbc = nullptr;
+  void* q = nullptr;
+  void* F[3] = {nullptr, nullptr, nullptr};
+  double* U[2] = {nullptr, nullptr};
+  double* partial = nullptr;
+  int mom_blocks = 0;
+  DevState* ds = nullptr;
+  bool have_prev = false;    // BDF2 history present
+  // graphs
+  cudaGraphExec_t exec_main = nullptr;   // the integrator's step
+  cudaGraphExec_t exec_start = nullptr;  // BDF2 start-up step (backward Euler)
+  // timing of bgk_sweep launches
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  double sweep_ms = 0.0;
+  int64_t sweep_launches = 0;
+  bgk_stats last{};
+};
+
+namespace {
+
+int tableau(int integ, double A[3][3], double b[3], double c[3]) {
+  std::memset(A, 0, sizeof(double) * 9);
+  std::memset(b, 0, sizeof(double) * 3);
+  std::memset(c, 0, sizeof(double) * 3);
+  switch (integ) {
+    case BGK_BE:
+    case BGK_BDF2:
+      A[0][0] = 1.0;
+      b[0] = 1.0;
+      c[0] = 1.0;
+      return 1;
+    case BGK_DIRK2: {  // App. A, second order L-stable
+      const double g = 1.0 - std::sqrt(2.0) / 2.0;
+      A[0][0] = g;
+      A[1][0] = 1.0 - g;
+      A[1][1] = g;
+      b[0] = 1.0 - g;
+      b[1] = g;
+      c[0] = g;
+      c[1] = 1.0;
+      return 2;
+    }
+    case BGK_DIRK3: {  // App. A, third order L-stable; gamma solves x^3 - 3x^2 + 3x/2 - 1/6 = 0
+      double g = 0.4358665215;
+      for (int it = 0; it < 60; ++it) {
+        const double p = ((g - 3.0) * g + 1.5) * g - 1.0 / 6.0, dp = (3.0 * g - 6.0) * g + 1.5;
+        g -= p / dp;
+      }
+      const double b1 = -1.5 * g * g + 4.0 * g - 0.25, b2 = 1.5 * g * g - 5.0 * g + 1.25;
+      A[0][0] = g;
+      A[1][0] = 0.5 * (1.0 - g);
+      A[1][1] = g;
+      A[2][0] = b1;
+      A[2][1] = b2;
+      A[2][2] = g;
+      b[0] = b1;
+      b[1] = b2;
+      b[2] = g;
+      c[0] = g;
+      c[1] = 0.5 * (1.0 + g);
+      c[2] = 1.0;
+      return 3;
+    }
+    case BGK_BSTABLE2: {  // App. A, algebraically stable two-stage DIRK
+      const double g = (3.0 + std::sqrt(3.0)) / 6.0;
+      A[0][0] = g;
+      A[1][0] = 1.0 - 2.0 * g;
+      A[1][1] = g;
+      b[0] = 0.5;
+      b[1] = 0.5;
+      c[0] = g;
+      c[1] = 1.0 - g;
+      return 2;
+    }
+    default:
+      return 0;
+  }
+}
+
+bool stiffly_accurate(int S, double A[3][3], const double b[3]) {
+  for (int s = 0; s < S; ++s)
+    if (A[S - 1][s] != b[s]) return false;
+  return true;
+}
+
+template <typename P>
+int dalloc(P*& p, size_t bytes) {
+  void* q = nullptr;
+  if (cudaMalloc(&q, bytes ? bytes : 16) != cudaSuccess) {
+    cudaGetLastError();
+    return BGK_E_OOM;
+  }
+  p = static_cast<P*>(q);
+  return BGK_OK;
+}
+
+template <typename T>
+int launch_maxwell(bgk_handle* h, int npos, const double* st0, const double* st1, int mode, const int32_t* map,
+                   T* out, size_t ostride, double coef, const T* q, double qscale, bool use_ds) {
+  int threads = 64;
+  size_t smem = (size_t)h->g.dim * h->g.N * threads * sizeof(double);
+  int blocks = (npos + threads - 1) / threads;
+  k_maxwell<T><<<blocks, threads, smem, h->stream>>>(h->g, npos, h->nm, st0, st1, mode, h->ds,
+                                                     use_ds ? h->ds : nullptr, map, out, ostride, coef, q, qscale);
+  return cudaGetLastError() == cudaSuccess ? BGK_OK : BGK_E_CUDA;
+}
+
+template <typename T>
+void launch_moments(bgk_handle* h, int mode) {
+  k_moments<T><<<h->mom_blocks, 128, 0, h->stream>>>(h->g, (const T*)h->f, h->nnode, h->U[0], h->U[1], h->ds, mode,
+                                                     h->partial);
+}
+
+template <class E, typename T>
+void launch_sweep_t(bgk_handle* h, double nus) {
+  k_sweep<E, T><<<h->g.nv, h->sweep_threads, 0, h->stream>>>(
+      h->geo, h->hm.geo_stride, h->nbr, h->perm, h->glist, h->lvl, h->ngen, h->hm.ncell, h->nnode, h->hm.nbface, h->g,
+      (T)nus, (const T*)h->src, (const T*)h->fbc, (T*)h->f, h->ds);
+}
+
+template <typename T>
+void launch_sweep(bgk_handle* h, double nus) {
+  if (h->hm.dim == 3)
+    launch_sweep_t<ElemP1Tet, T>(h, nus);
+  else if (h->hm.kx == 2)
+    launch_sweep_t<ElemP2Tri, T>(h, nus);
+  else
+    launch_sweep_t<ElemP1Tri, T>(h, nus);
+}
+
+void launch_sweep_any(bgk_handle* h, double nus) {
+  if (h->precision == BGK_FP64)
+    launch_sweep<double>(h, nus);
+  else
+    launch_sweep<float>(h, nus);
+}
+
+template <typename T>
+void launch_combine(bgk_handle* h, void* out, double ak, const void* fk, double af, const void* f, int nF,
+                    const double* cF, void* const* F) {
+  int threads = 256, blocks = 148 * 8;
+  k_combine<T><<<blocks, threads, 0, h->stream>>>(h->nfv, (T*)out, ak, (const T*)fk, af, (const T*)f, nF,
+                                                 nF > 0 ? cF[0] : 0.0, nF > 0 ? (const T*)F[0] : nullptr,
+                                                 nF > 1 ? cF[1] : 0.0, nF > 1 ? (const T*)F[1] : nullptr,
+                                                 nF > 2 ? cF[2] : 0.0, nF > 2 ? (const T*)F[2] : nullptr, h->ds);
+}
+
+void combine(bgk_handle* h, void* out, double ak, const void* fk, double af, const void* f, int nF, const double* cF,
+             void* const* F) {
+  if (h->precision == BGK_FP64)
+    launch_combine<double>(h, out, ak, fk, af, f, nF, cF, F);
+  else
+    launch_combine<float>(h, out, ak, fk, af, f, nF, cF, F);
+}
+
+void moments(bgk_handle* h, int mode) {
+  if (h->precision == BGK_FP64)
+    launch_moments<double>(h, mode);
+  else
+    launch_moments<float>(h, mode);
+}
+
+// src = nu * M(U[it&1]) + qscale * qsrc
+int build_src(bgk_handle* h, const void* qsrc, double qscale) {
+  if (h->precision == BGK_FP64)
+    return launch_maxwell<double>(h, h->nnode, h->U[0], h->U[1], 1, nullptr, (double*)h->src, h->nnode, h->phys.nu,
+                                  (const double*)qsrc, qscale, true);
+  return launch_maxwell<float>(h, h->nnode, h->U[0], h->U[1], 1, nullptr, (float*)h->src, h->nnode, h->phys.nu,
+                               (const float*)qsrc, qscale, true);
+}
+
+// Capture one time step as a CUDA graph: per stage a conditional while-loop over
+// (Maxwellian + source, sweep, moments, convergence test).  bdf: 0 = use the DIRK
+// tableau of the integrator (or BE), 1 = BDF2 with history.
+int capture_step(bgk_handle* h, int mode_bdf2, cudaGraphExec_t* exec_out) {
+  double A[3][3], b[3], c[3];
+  int S = tableau(mode_bdf2 ? BGK_BE : (h->phys.integrator == BGK_BDF2 ? BGK_BE : h->phys.integrator), A, b, c);
+  const bool sa = stiffly_accurate(S, A, b);
+  const double dt = h->dt, nu = h->phys.nu;
+  const double tol = h->cfg.tau / std::max(1.0, nu * dt);
+  const size_t bytes = h->nfv * h->tsize;
+  cudaStream_t s = h->stream;
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  k_reset_state<<<1, 1, 0, s>>>(h->ds);
+  const bool bdf = mode_bdf2 == 1;
+  if (bdf) {
+    // q = (4 f^n - f^{n-1}) / (2 dt); history: fprev <- f^n after the step
+    double cF[1] = {-1.0 / (2.0 * dt)};
+    void* Fp[1] = {h->fprev};
+    combine(h, h->q, 0.0, nullptr, 4.0 / (2.0 * dt), h->f, 1, cF, Fp);
+    CK(cudaMemcpyAsync(h->fprev, h->f, bytes, cudaMemcpyDeviceToDevice, s));
+    S = 1;
+  } else {
+    CK(cudaMemcpyAsync(h->fk, h->f, bytes, cudaMemcpyDeviceToDevice, s));
+  }
+  for (int st = 0; st < S; ++st) {
+    const double ass = bdf ? 2.0 / 3.0 : A[st][st];
+    const double nus = nu + 1.0 / (dt * ass);
+    const void* qsrc;
+    double qscale;
+    if (bdf) {
+      qsrc = h->q;
+      qscale = 1.0;
+    } else if (st == 0) {
+      qsrc = h->fk;  // q = f^k / (dt A_11)
+      qscale = 1.0 / (dt * ass);
+    } else {
+      // q = (f^k + dt sum_{r<s} A_sr F_r) / (dt A_ss)   (Eq. q-stages)
+      double cF[3];
+      for (int r = 0; r < st; ++r) cF[r] = dt * A[st][r] / (dt * ass);
+      combine(h, h->q, 1.0 / (dt * ass), h->fk, 0.0, nullptr, st, cF, h->F);
+      qsrc = h->q;
+      qscale = 1.0;
+    }
+    k_stage_begin<<<1, 1, 0, s>>>(h->ds, st);
+    moments(h, 0);
+    // while (cond) { src; sweep; moments; finalize }
+    cudaGraph_t cg;
+    cudaStreamCaptureStatus cst;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    CK(cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, &deps, nullptr, &ndeps));
+    cudaGraphConditionalHandle cond;
+    CK(cudaGraphConditionalHandleCreate(&cond, cg, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, cg, deps, nullptr, ndeps, &cp));
+    CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaStream_t bs;
+    CK(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
+    CK(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    h->stream = bs;
+    int rc = build_src(h, qsrc, qscale);
+    launch_sweep_any(h, nus);
+    moments(h, 1);
+    k_finalize<<<1, 256, 0, bs>>>(h->ds, h->partial, h->mom_blocks, tol, h->cfg.l_max, st, cond, 1);
+    h->stream = s;
+    cudaGraph_t body_out;
+    cudaError_t e2 = cudaStreamEndCapture(bs, &body_out);
+    cudaStreamDestroy(bs);
+    if (rc != BGK_OK || e2 != cudaSuccess) {
+      cudaStreamEndCapture(s, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      return BGK_E_CUDA;
+    }
+    // stage derivative F_s = f^(s) / (dt A_ss) - q^(s)   (Eq. dirk-recursive-def)
+    if (!bdf && (st < S - 1 || !sa)) {
+      if (st == 0)
+        combine(h, h->F[0], -1.0 / (dt * ass), h->fk, 1.0 / (dt * ass), h->f, 0, nullptr, nullptr);
+      else {
+        double cF[1] = {-1.0};
+        void* Fq[1] = {h->q};
+        combine(h, h->F[st], 0.0, nullptr, 1.0 / (dt * ass), h->f, 1, cF, Fq);
+      }
+    }
+  }
+  if (!bdf && !sa) {
+    // f^{k+1} = f^k + dt sum_s b_s F_s   (Eq. dirk-n)
+    double cF[3];
+    for (int r = 0; r < S; ++r) cF[r] = dt * b[r];
+    combine(h, h->f, 1.0, h->fk, 0.0, nullptr, S, cF, h->F);
+  }
+  CK(cudaStreamEndCapture(s, &graph));
+  cudaError_t e = cudaGraphInstantiate(exec_out, graph, 0);
+  cudaGraphDestroy(graph);
+  return e == cudaSuccess ? BGK_OK : BGK_E_CUDA;
+}
+
+int build_dags(bgk_handle* h) {
+  const int n = h->hm.ncell;
+  const int threads = 256;
+  const size_t smem = (size_t)((n + 3) / 4) * 4;
+  if (smem > 200 * 1024) return BGK_E_INVALID;
+  auto peel = [&](int nblk, const int32_t* jl, const uint8_t* lag) {
+    if (h->hm.dim == 2) {
+      k_peel<2, 3><<<nblk, threads, smem, h->stream>>>(h->geo, h->hm.geo_stride, h->nbr, h->nbr_face, n, h->g, jl, lag,
+                                                       h->glist, h->lvl, h->ngen, h->nproc);
+    } else {
+      k_peel<3, 4><<<nblk, threads, smem, h->stream>>>(h->geo, h->hm.geo_stride, h->nbr, h->nbr_face, n, h->g, jl, lag,
+                                                       h->glist, h->lvl, h->ngen, h->nproc);
+    }
+  };
+  peel(h->g.nv, nullptr, nullptr);
+  CK(cudaGetLastError());
+  std::vector<int32_t> nproc(h->g.nv), ngen(h->g.nv);
+  CK(cudaMemcpyAsync(nproc.data(), h->nproc, sizeof(int32_t) * h->g.nv, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  std::vector<int32_t> cyc;
+  for (int j = 0; j < h->g.nv; ++j)
+    if (nproc[j] < n) cyc.push_back(j);
+  h->lagged = 0;
+  if (!cyc.empty()) {
+    // cycles: lag the DFS back edges on the host (same rule as Sec. 4.1), peel again
+    std::vector<uint8_t> lag((size_t)cyc.size() * n, 0);
+    for (size_t k = 0; k < cyc.size(); ++k) h->lagged += host_break_cycles(h->hm, h->g, cyc[k], lag.data() + k * n);
+    uint8_t* dlag = nullptr;
+    int32_t* djl = nullptr;
+    if (dalloc(dlag, lag.size()) != BGK_OK || dalloc(djl, sizeof(int32_t) * cyc.size()) != BGK_OK) return BGK_E_OOM;
+    CK(cudaMemcpyAsync(dlag, lag.data(), lag.size(), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(djl, cyc.data(), sizeof(int32_t) * cyc.size(), cudaMemcpyHostToDevice, h->stream));
+    peel((int)cyc.size(), djl, dlag);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(nproc.data(), h->nproc, sizeof(int32_t) * h->g.nv, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    cudaFree(dlag);
+    cudaFree(djl);
+    for (int j = 0; j < h->g.nv; ++j)
+      if (nproc[j] != n) return BGK_E_INVALID;
+  }
+  CK(cudaMemcpy(ngen.data(), h->ngen, sizeof(int32_t) * h->g.nv, cudaMemcpyDeviceToHost));
+  h->Gmax = *std::max_element(ngen.begin(), ngen.end());
+  // CTA size of the sweep: about the mean width of a generation, rounded to warps
+  if (h->cfg.block_threads > 0) {
+    h->sweep_threads = h->cfg.block_threads;
+  } else {
+    double width = (double)n / std::max(1, h->Gmax);
+    int t = (int)std::ceil(width / 32.0) * 32;
+    h->sweep_threads = std::min(256, std::max(32, t));
+  }
+  return BGK_OK;
+}
+
+void release(bgk_handle* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  if (h->exec_main) cudaGraphExecDestroy(h->exec_main);
+  if (h->exec_start) cudaGraphExecDestroy(h->exec_start);
+  void* ptrs[] = {h->geo, h->nbr, h->nbr_face, h->perm, h->bnode, h->glist, h->lvl, h->ngen, h->nproc, h->f, h->fk,
+                  h->fprev, h->src, h->fbc, h->q, h->F[0], h->F[1], h->F[2], h->U[0], h->U[1], h->partial, h->ds};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* bgk_status_string(int status) {
+  switch (status) {
+    case BGK_OK: return "ok";
+    case BGK_E_INVALID: return "invalid argument or mesh";
+    case BGK_E_CUDA: return "CUDA runtime error";
+    case BGK_E_OOM: return "device out of memory";
+    case BGK_E_NOCONV: return "Picard iteration did not converge within l_max";
+    case BGK_E_NONPHYSICAL: return "non-physical moments (n <= 0, theta <= 0 or non-finite)";
+    case BGK_E_TIMEOUT: return "bounded device wait ran out";
+    default: return "unknown status";
+  }
+}
+
+int bgk_create(const bgk_mesh* mesh, const bgk_vgrid* vg, const bgk_physics* phys, const bgk_config* cfg,
+               bgk_handle** out) {
+  if (!mesh || !vg || !phys || !out) return BGK_E_INVALID;
+  *out = nullptr;
+  bgk_handle* h = new (std::nothrow) bgk_handle();
+  if (!h) return BGK_E_OOM;
+  int rc = build_host_mesh(mesh, h->hm);
+  if (rc == BGK_OK) rc = build_vgrid(mesh->dim, vg->n_points, vg->k_v, vg->L, h->g);
+  if (rc != BGK_OK) {
+    delete h;
+    return rc;
+  }
+  h->phys = *phys;
+  if (cfg) {
+    h->cfg = *cfg;
+  } else {
+    std::memset(&h->cfg, 0, sizeof(h->cfg));
+  }
+  if (!(h->cfg.tau > 0.0)) h->cfg.tau = 1e-8;
+  if (h->cfg.l_max <= 0) h->cfg.l_max = 1000;
+  h->precision = h->cfg.precision == BGK_FP32_SWEEP ? BGK_FP32_SWEEP : BGK_FP64;
+  h->tsize = h->precision == BGK_FP64 ? 8 : 4;
+  if (phys->integrator < BGK_BE || phys->integrator > BGK_BDF2 || !(phys->nu >= 0.0)) {
+    delete h;
+    return BGK_E_INVALID;
+  }
+  // time step: given, or cfl * dt_e with dt_e = (1/d)(1/(2k+1)) h_min / max_j |v_j| (Sec. 5)
+  if (phys->dt > 0.0) {
+    h->dt = phys->dt;
+  } else {
+    double vmax = 0.0;
+    for (int j = 0; j < h->g.nv; ++j) {
+      double s = 0.0;
+      int jj = j;
+      for (int a = 0; a < h->g.dim; ++a) {
+        double x = h->g.x[jj % h->g.N];
+        jj /= h->g.N;
+        s += x * x;
+      }
+      vmax = std::max(vmax, std::sqrt(s));
+    }
+    const double hmin = std::pow(h->hm.min_vol, 1.0 / h->hm.dim);
+    h->dt = phys->cfl * (1.0 / h->hm.dim) * (1.0 / (2 * h->hm.kx + 1)) * hmin / vmax;
+    if (!(h->dt > 0.0)) {
+      delete h;
+      return BGK_E_INVALID;
+    }
+  }
+  h->nnode = h->hm.ncell * h->hm.ndof;
+  h->nm = h->hm.dim + 2;
+  h->nfv = (size_t)h->g.nv * h->nnode;
+  if (h->cfg.stream) {
+    h->stream = (cudaStream_t)h->cfg.stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete h;
+      return BGK_E_CUDA;
+    }
+    h->own_stream = true;
+  }
+  const HostMesh& hm = h->hm;
+  const size_t n = hm.ncell, nv = h->g.nv;
+  const size_t fb = h->nfv * h->tsize;
+  const size_t fbcb = nv * (size_t)hm.nbface * hm.fd * h->tsize;
+  h->mom_blocks = (h->nnode + 127) / 128;
+  rc = BGK_OK;
+  auto A = [&](int r) {
+    if (rc == BGK_OK) rc = r;
+  };
+  A(dalloc(h->geo, sizeof(double) * hm.geo.size()));
+  A(dalloc(h->nbr, sizeof(int32_t) * hm.nbr.size()));
+  A(dalloc(h->nbr_face, sizeof(int32_t) * hm.nbr_face.size()));
+  A(dalloc(h->perm, sizeof(uint64_t) * n));
+  A(dalloc(h->bnode, sizeof(int32_t) * std::max<size_t>(1, hm.bnode.size())));
+  A(dalloc(h->glist, sizeof(uint32_t) * nv * n));
+  A(dalloc(h->lvl, sizeof(int32_t) * nv * (n + 1)));
+  A(dalloc(h->ngen, sizeof(int32_t) * nv));
+  A(dalloc(h->nproc, sizeof(int32_t) * nv));
+  A(dalloc(h->f, fb));
+  A(dalloc(h->fk, fb));
+  A(dalloc(h->src, fb));
+  A(dalloc(h->fbc, std::max<size_t>(16, fbcb)));
+  A(dalloc(h->U[0], sizeof(double) * h->nnode * h->nm));
+  A(dalloc(h->U[1], sizeof(double) * h->nnode * h->nm));
+  A(dalloc(h->partial, sizeof(double) * 6 * h->mom_blocks));
+  A(dalloc(h->ds, sizeof(DevState)));
+  double At[3][3], bt[3], ct[3];
+  const int S = tableau(phys->integrator, At, bt, ct);
+  if (phys->integrator == BGK_BDF2) {
+    A(dalloc(h->fprev, fb));
+    A(dalloc(h->q, fb));
+  } else if (S > 1) {
+    A(dalloc(h->q, fb));
+    for (int s = 0; s < S; ++s) A(dalloc(h->F[s], fb));
+  }
+  if (rc != BGK_OK) {
+    release(h);
+    return rc;
+  }
+  cudaStream_t s = h->stream;
+  CK(cudaMemcpyAsync(h->geo, hm.geo.data(), sizeof(double) * hm.geo.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(h->nbr, hm.nbr.data(), sizeof(int32_t) * hm.nbr.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(h->nbr_face, hm.nbr_face.data(), sizeof(int32_t) * hm.nbr_face.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(h->perm, hm.perm.data(), sizeof(uint64_t) * n, cudaMemcpyHostToDevice, s));
+  if (!hm.bnode.empty())
+    CK(cudaMemcpyAsync(h->bnode, hm.bnode.data(), sizeof(int32_t) * hm.bnode.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(h->ds, 0, sizeof(DevState), s));
+  CK(cudaMemsetAsync(h->f, 0, fb, s));
+  CK(cudaMemsetAsync(h->fk, 0, fb, s));
+  CK(cudaMemsetAsync(h->fbc, 0, std::max<size_t>(16, fbcb), s));
+  CK(cudaEventCreate(&h->ev0));
+  CK(cudaEventCreate(&h->ev1));
+  // kernel attributes are set before any stream capture
+  CK(cudaFuncSetAttribute(k_maxwell<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  CK(cudaFuncSetAttribute(k_maxwell<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  CK(cudaFuncSetAttribute(k_peel<2, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  CK(cudaFuncSetAttribute(k_peel<3, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  rc = build_dags(h);
+  if (rc == BGK_OK) rc = capture_step(h, 0, &h->exec_main);
+  if (rc == BGK_OK && phys->integrator == BGK_BDF2) {
+    cudaGraphExec_t e0 = h->exec_main;
+    rc = capture_step(h, 1, &h->exec_main);  // BDF2 proper
+    h->exec_start = e0;                      // first step: backward Euler
+  }
+  if (rc == BGK_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = BGK_E_CUDA;
+  if (rc != BGK_OK) {
+    cudaGetLastError();
+    release(h);
+    return rc;
+  }
+  *out = h;
+  return BGK_OK;
+}
+
+int bgk_destroy(bgk_handle* h) {
+  release(h);
+  return BGK_OK;
+}
+
+int bgk_sizes(const bgk_handle* h, int64_t* out) {
+  if (!h || !out) return BGK_E_INVALID;
+  out[0] = h->g.nv;
+  out[1] = h->nnode;
+  out[2] = h->hm.ndof;
+  out[3] = h->hm.ncell;
+  out[4] = h->hm.dim;
+  out[5] = h->Gmax;
+  out[6] = h->lagged;
+  return BGK_OK;
+}
+
+int bgk_get_dt(const bgk_handle* h, double* dt) {
+  if (!h || !dt) return BGK_E_INVALID;
+  *dt = h->dt;
+  return BGK_OK;
+}
+
+static int set_maxwellian(bgk_handle* h, const double* h_nut, bool inflow) {
+  if (!h || !h_nut) return BGK_E_INVALID;
+  double* dnut = nullptr;
+  const size_t bytes = sizeof(double) * h->nnode * h->nm;
+  if (dalloc(dnut, bytes) != BGK_OK) return BGK_E_OOM;
+  int rc = BGK_OK;
+  if (cudaMemcpyAsync(dnut, h_nut, bytes, cudaMemcpyHostToDevice, h->stream) != cudaSuccess) rc = BGK_E_CUDA;
+  if (rc == BGK_OK) {
+    if (inflow) {
+      const int npos = h->hm.nbface * h->hm.fd;
+      if (npos > 0) {
+        if (h->precision == BGK_FP64)
+          rc = launch_maxwell<double>(h, npos, dnut, nullptr, 0, h->bnode, (double*)h->fbc, npos, 1.0, nullptr, 0.0,
+                                      false);
+        else
+          rc = launch_maxwell<float>(h, npos, dnut, nullptr, 0, h->bnode, (float*)h->fbc, npos, 1.0, nullptr, 0.0,
+                                     false);
+      }
+    } else {
+      if (h->precision == BGK_FP64)
+        rc = launch_maxwell<double>(h, h->nnode, dnut, nullptr, 0, nullptr, (double*)h->f, h->nnode, 1.0, nullptr, 0.0,
+                                    false);
+      else
+        rc = launch_maxwell<float>(h, h->nnode, dnut, nullptr, 0, nullptr, (float*)h->f, h->nnode, 1.0, nullptr, 0.0,
+                                   false);
+      if (rc == BGK_OK &&
+          cudaMemcpyAsync(h->fk, h->f, h->nfv * h->tsize, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+        rc = BGK_E_CUDA;
+      h->have_prev = false;
+    }
+  }
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) rc = BGK_E_CUDA;
+  cudaFree(dnut);
+  return rc;
+}
+
+int bgk_set_state_maxwellian(bgk_handle* h, const double* h_nut) { return set_maxwellian(h, h_nut, false); }
+int bgk_set_inflow_maxwellian(bgk_handle* h, const double* h_nut) { return set_maxwellian(h, h_nut, true); }
+
+static int transfer_f(bgk_handle* h, void* ptr, int dtype, bool in, cudaMemcpyKind kind) {
+  if (!h || !ptr || (dtype != BGK_DTYPE_F64 && dtype != BGK_DTYPE_F32)) return BGK_E_INVALID;
+  const size_t ob = dtype == BGK_DTYPE_F64 ? 8 : 4;
+  const bool same = ob == h->tsize;
+  void* tmp = nullptr;
+  if (!same && dalloc(tmp, h->nfv * ob) != BGK_OK) return BGK_E_OOM;
+  int rc = BGK_OK;
+  const int thr = 256, blk = 148 * 8;
+  if (in) {
+    void* dst = same ? h->f : tmp;
+    if (cudaMemcpyAsync(dst, ptr, h->nfv * ob, kind, h->stream) != cudaSuccess) rc = BGK_E_CUDA;
+    if (rc == BGK_OK && !same) {
+      if (ob == 8)
+        k_convert<double, float><<<blk, thr, 0, h->stream>>>(h->nfv, (const double*)tmp, (float*)h->f);
+      else
+        k_convert<float, double><<<blk, thr, 0, h->stream>>>(h->nfv, (const float*)tmp, (double*)h->f);
+    }
+    if (rc == BGK_OK &&
+        cudaMemcpyAsync(h->fk, h->f, h->nfv * h->tsize, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+      rc = BGK_E_CUDA;
+    h->have_prev = false;
+  } else {
+    const void* srcp = h->f;
+    if (!same) {
+      if (ob == 8)
+        k_convert<float, double><<<blk, thr, 0, h->stream>>>(h->nfv, (const float*)h->f, (double*)tmp);
+      else
+        k_convert<double, float><<<blk, thr, 0, h->stream>>>(h->nfv, (const double*)h->f, (float*)tmp);
+      srcp = tmp;
+    }
+    if (cudaMemcpyAsync(ptr, srcp, h->nfv * ob, kind, h->stream) != cudaSuccess) rc = BGK_E_CUDA;
+  }
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) rc = BGK_E_CUDA;
+  if (tmp) cudaFree(tmp);
+  return rc;
+}
+
+int bgk_set_f(bgk_handle* h, const void* h_f, int dtype) {
+  return transfer_f(h, const_cast<void*>(h_f), dtype, true, cudaMemcpyHostToDevice);
+}
+int bgk_get_f(bgk_handle* h, void* h_f, int dtype) { return transfer_f(h, h_f, dtype, false, cudaMemcpyDeviceToHost); }
+int bgk_set_f_device(bgk_handle* h, const void* d_f, int dtype) {
+  return transfer_f(h, const_cast<void*>(d_f), dtype, true, cudaMemcpyDeviceToDevice);
+}
+int bgk_get_f_device(bgk_handle* h, void* d_f, int dtype) {
+  return transfer_f(h, d_f, dtype, false, cudaMemcpyDeviceToDevice);
+}
+
+static int moments_to(bgk_handle* h, double* out, cudaMemcpyKind kind) {
+  if (!h || !out) return BGK_E_INVALID;
+  k_reset_state<<<1, 1, 0, h->stream>>>(h->ds);
+  moments(h, 0);
+  // the fresh moments sit in U[it & 1]; read the parity back
+  DevState st;
+  CK(cudaMemcpyAsync(&st, h->ds, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemcpyAsync(out, h->U[st.it & 1], sizeof(double) * h->nnode * h->nm, kind, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return BGK_OK;
+}
+
+int bgk_get_moments(bgk_handle* h, double* h_U) { return moments_to(h, h_U, cudaMemcpyDeviceToHost); }
+int bgk_get_moments_device(bgk_handle* h, double* d_U) { return moments_to(h, d_U, cudaMemcpyDeviceToDevice); }
+
+int bgk_get_velocity(const bgk_handle* h, double* h_v, double* h_w) {
+  if (!h) return BGK_E_INVALID;
+  for (int j = 0; j < h->g.nv; ++j) {
+    int jj = j;
+    double w = 1.0;
+    for (int a = h->g.dim - 1; a >= 0; --a) {
+      const int ja = jj % h->g.N;
+      jj /= h->g.N;
+      if (h_v) h_v[(size_t)j * h->g.dim + a] = h->g.x[ja];
+      w *= h->g.w[ja];
+    }
+    if (h_w) h_w[j] = w;
+  }
+  return BGK_OK;
+}
+
+int bgk_get_generations(bgk_handle* h, int j, int32_t* h_gen, int* n_gen) {
+  if (!h || j < 0 || j >= h->g.nv) return BGK_E_INVALID;
+  const int n = h->hm.ncell;
+  std::vector<uint32_t> gl(n);
+  std::vector<int32_t> lv(n + 1);
+  int32_t G = 0;
+  CK(cudaMemcpyAsync(gl.data(), h->glist + (size_t)j * n, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(lv.data(), h->lvl + (size_t)j * (n + 1), sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost,
+                     h->stream));
+  CK(cudaMemcpyAsync(&G, h->ngen + j, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (h_gen)
+    for (int g = 0; g < G; ++g)
+      for (int k = lv[g]; k < lv[g + 1]; ++k) h_gen[gl[k] & kCellMask] = g;
+  if (n_gen) *n_gen = G;
+  return BGK_OK;
+}
+
+int bgk_sweep(bgk_handle* h, double nu_s, double q_scale) {
+  if (!h) return BGK_E_INVALID;
+  k_reset_state<<<1, 1, 0, h->stream>>>(h->ds);
+  moments(h, 0);
+  int rc = build_src(h, h->fk, q_scale);
+  if (rc != BGK_OK) return rc;
+  CK(cudaEventRecord(h->ev0, h->stream));
+  launch_sweep_any(h, nu_s);
+  CK(cudaEventRecord(h->ev1, h->stream));
+  CK(cudaGetLastError());
+  CK(cudaEventSynchronize(h->ev1));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+  h->sweep_ms += ms;
+  h->sweep_launches += 1;
+  DevState st;
+  CK(cudaMemcpy(&st, h->ds, sizeof(DevState), cudaMemcpyDeviceToHost));
+  return st.err ? BGK_E_NONPHYSICAL : BGK_OK;
+}
+
+int bgk_step_async(bgk_handle* h, int nsteps) {
+  if (!h || nsteps < 0) return BGK_E_INVALID;
+  for (int k = 0; k < nsteps; ++k) {
+    cudaGraphExec_t e = h->exec_main;
+    if (h->phys.integrator == BGK_BDF2 && !h->have_prev) {
+      e = h->exec_start;
+      // the start-up step is backward Euler; its f^k becomes the BDF2 history
+      CK(cudaGraphLaunch(e, h->stream));
+      CK(cudaMemcpyAsync(h->fprev, h->fk, h->nfv * h->tsize, cudaMemcpyDeviceToDevice, h->stream));
+      h->have_prev = true;
+      continue;
+    }
+    CK(cudaGraphLaunch(e, h->stream));
+  }
+  return BGK_OK;
+}
+
+int bgk_last_stats(bgk_handle* h, bgk_stats* st) {
+  if (!h || !st) return BGK_E_INVALID;
+  DevState d;
+  CK(cudaMemcpyAsync(&d, h->ds, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  double A[3][3], b[3], c[3];
+  st->n_stages = h->phys.integrator == BGK_BDF2 ? 1 : tableau(h->phys.integrator, A, b, c);
+  for (int s = 0; s < 3; ++s) {
+    st->iterations[s] = d.iters[s];
+    st->measure[s] = d.meas[s];
+  }
+  st->total_sweeps = d.total_sweeps;
+  st->status = d.status;
+  h->last = *st;
+  return BGK_OK;
+}
+
+int bgk_step(bgk_handle* h, int nsteps, bgk_stats* st) {
+  if (!h || nsteps < 0) return BGK_E_INVALID;
+  for (int k = 0; k < nsteps; ++k) {
+    int rc = bgk_step_async(h, 1);
+    if (rc != BGK_OK) return rc;
+    bgk_stats s;
+    rc = bgk_last_stats(h, &s);
+    if (rc != BGK_OK) return rc;
+    if (st) *st = s;
+    if (s.status != BGK_OK) return s.status;
+  }
+  return BGK_OK;
+}
+
+int bgk_synchronize(bgk_handle* h) {
+  if (!h) return BGK_E_INVALID;
+  CK(cudaStreamSynchronize(h->stream));
+  return BGK_OK;
+}
+
+int bgk_timing(bgk_handle* h, int reset, double* sweep_ms_total, int64_t* sweep_launches) {
+  if (!h) return BGK_E_INVALID;
+  if (sweep_ms_total) *sweep_ms_total = h->sweep_ms;
+  if (sweep_launches) *sweep_launches = h->sweep_launches;
+  if (reset) {
+    h->sweep_ms = 0.0;
+    h->sweep_launches = 0;
+  }
+  return BGK_OK;
+}
+
+}  // extern "C"

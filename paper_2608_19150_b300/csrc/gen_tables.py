@@ -1,0 +1,165 @@
+"""Generate bgk_tables.h: exact reference-element constants of the nodal DG sweep.
+
+For an affine simplex K with outward area-weighted face normals N_i (face i opposite
+vertex i) the gradient of the barycentric coordinate is grad l_i = -N_i / (d |K|), so
+every cell matrix of the upwind DG local problem (Sec. 3.3, Eq. bgk-ss-inflow-outflow)
+is a fixed combination of |K| and s_i = v . N_i:
+
+  A / |K| = nu_s Mh + sum_i (s_i/|K|) (Dd_i + [s_i > 0] Eh_i)
+  b / |K| = Mh src + sum_{s_i < 0} (-s_i/|K|) Eh_i y_up
+
+with Mh = (1/|K|) int phi_a phi_b, Dd_i = (1/(d |K|)) int phi_b d phi_a / d l_i and
+Eh_i = (1/|F_i|) int_{F_i} phi_a phi_b.  This script integrates the products exactly
+with rational arithmetic (int over a k-simplex of prod l^e = k! |S| prod e! / (k+|e|)!)
+and writes them as constexpr doubles.  Run: python gen_tables.py > bgk_tables.h
+"""
+from fractions import Fraction as Fr
+from math import factorial
+
+
+def basis(kind):
+    """Polynomials in barycentric coordinates as {exponent tuple: coefficient}."""
+    if kind == "p1tri":
+        nv = 3
+        return nv, [{tuple(1 if k == a else 0 for k in range(nv)): Fr(1)} for a in range(nv)]
+    if kind == "p1tet":
+        nv = 4
+        return nv, [{tuple(1 if k == a else 0 for k in range(nv)): Fr(1)} for a in range(nv)]
+    if kind == "p2tri":
+        nv = 3
+        out = []
+        for a in range(3):
+            e2 = tuple(2 if k == a else 0 for k in range(3))
+            e1 = tuple(1 if k == a else 0 for k in range(3))
+            out.append({e2: Fr(2), e1: Fr(-1)})
+        for k in range(3):
+            l = (k + 1) % 3
+            e = [0, 0, 0]
+            e[k] += 1
+            e[l] += 1
+            out.append({tuple(e): Fr(4)})
+        return nv, out
+    raise ValueError(kind)
+
+
+def mul(p, q):
+    r = {}
+    for ea, ca in p.items():
+        for eb, cb in q.items():
+            e = tuple(x + y for x, y in zip(ea, eb))
+            r[e] = r.get(e, 0) + ca * cb
+    return r
+
+
+def dl(p, i):
+    r = {}
+    for e, c in p.items():
+        if e[i]:
+            e2 = list(e)
+            e2[i] -= 1
+            r[tuple(e2)] = r.get(tuple(e2), 0) + c * e[i]
+    return r
+
+
+def integ(p, k, skip=None):
+    """(1/|S|) int over the k-simplex spanned by the coordinates other than `skip`."""
+    s = Fr(0)
+    for e, c in p.items():
+        if skip is not None and e[skip]:
+            continue
+        ee = [x for i, x in enumerate(e) if i != skip]
+        num = factorial(k)
+        for x in ee:
+            num *= factorial(x)
+        s += c * Fr(num, factorial(k + sum(ee)))
+    return s
+
+
+def tables(kind):
+    nv, phi = basis(kind)
+    d = nv - 1
+    nd = len(phi)
+    Mh = [[integ(mul(phi[a], phi[b]), d) for b in range(nd)] for a in range(nd)]
+    Dd = [[[integ(mul(phi[b], dl(phi[a], i)), d) / d for b in range(nd)] for a in range(nd)] for i in range(nv)]
+    Eh = [[[integ(mul(phi[a], phi[b]), d - 1, skip=i) for b in range(nd)] for a in range(nd)] for i in range(nv)]
+    # local nodes on face i (opposite vertex i): vertices != i ascending, then the midpoint
+    fn = []
+    for i in range(nv):
+        f = [a for a in range(nv) if a != i]
+        if kind == "p2tri":
+            f.append(3 + (i + 1) % 3)
+        fn.append(f)
+    return d, nd, nv, Mh, Dd, Eh, fn
+
+
+def lit(x):
+    return "T(%.17g)" % float(x)
+
+
+def emit(name, kind):
+    """Struct with sizes, the face-node map, and device routines in which every zero of
+    the tables has been dropped at generation time."""
+    d, nd, nf, Mh, Dd, Eh, fn = tables(kind)
+    fd = len(fn[0])
+    o = ["struct %s {" % name,
+         "  static constexpr int D = %d, NDOF = %d, NF = %d, FD = %d;" % (d, nd, nf, fd),
+         "  BGK_HD static constexpr int fn(int i, int k) {",
+         "    return " + " : ".join("(i == %d && k == %d) ? %d" % (i, k, fn[i][k])
+                                    for i in range(nf) for k in range(fd)) + " : -1;",
+         "  }",
+         "#ifdef __CUDACC__"]
+    # A = nus*Mh + sum_i r_i Dd_i + sum_{i outflow} r_i Eh_i
+    o.append("  template <typename T> __device__ static __forceinline__ void assemble("
+             "T nus, const T (&r)[%d], unsigned outm, T (&A)[%d][%d]) {" % (nf, nd, nd))
+    for a in range(nd):
+        for b in range(nd):
+            terms = []
+            if Mh[a][b] != 0:
+                terms.append("nus * %s" % lit(Mh[a][b]))
+            for i in range(nf):
+                if Dd[i][a][b] != 0:
+                    terms.append("r[%d] * %s" % (i, lit(Dd[i][a][b])))
+            o.append("    A[%d][%d] = %s;" % (a, b, " + ".join(terms) if terms else "T(0)"))
+    for i in range(nf):
+        nz = [(a, b) for a in range(nd) for b in range(nd) if Eh[i][a][b] != 0]
+        o.append("    if (outm & %du) {" % (1 << i))
+        for a, b in nz:
+            o.append("      A[%d][%d] += r[%d] * %s;" % (a, b, i, lit(Eh[i][a][b])))
+        o.append("    }")
+    o.append("  }")
+    # b = Mh src
+    o.append("  template <typename T> __device__ static __forceinline__ void mass("
+             "const T (&s)[%d], T (&b)[%d]) {" % (nd, nd))
+    for a in range(nd):
+        terms = ["s[%d] * %s" % (b, lit(Mh[a][b])) for b in range(nd) if Mh[a][b] != 0]
+        o.append("    b[%d] = %s;" % (a, " + ".join(terms)))
+    o.append("  }")
+    # b += c * Eh_i y, y in face-local order
+    o.append("  template <typename T> __device__ static __forceinline__ void inflow("
+             "int i, T c, const T (&y)[%d], T (&b)[%d]) {" % (fd, nd))
+    o.append("    switch (i) {")
+    for i in range(nf):
+        o.append("      case %d:" % i)
+        for a in range(nd):
+            terms = ["y[%d] * %s" % (k, lit(Eh[i][a][fn[i][k]])) for k in range(fd) if Eh[i][a][fn[i][k]] != 0]
+            if terms:
+                o.append("        b[%d] += c * (%s);" % (a, " + ".join(terms)))
+        o.append("        break;")
+    o.append("      default: break;")
+    o.append("    }")
+    o.append("  }")
+    o.append("#endif")
+    o.append("};")
+    return "\n".join(o)
+
+
+if __name__ == "__main__":
+    print("// Generated by gen_tables.py -- exact reference-element tables (see that file).")
+    print("#pragma once")
+    print("#ifndef __CUDACC__")
+    print("#define BGK_HD")
+    print("#else")
+    print("#define BGK_HD __host__ __device__")
+    print("#endif")
+    for name, kind in (("ElemP1Tri", "p1tri"), ("ElemP2Tri", "p2tri"), ("ElemP1Tet", "p1tet")):
+        print(emit(name, kind))

@@ -1,0 +1,168 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances: DAG generations bit-exact; FP64 results within 1e-12 relative (max-norm
+over the array); FP32 sweep within 2e-5 relative (a handful of FP32 roundings per
+local solve, amplified by at most the local condition number).
+"""
+import numpy as np
+import pytest
+
+from paper_2608_19150_b300 import synth
+
+from gpu_common import make_pair, rel_err, small_shock_tube, twisted_workload
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+
+
+def workloads():
+    return {
+        "p1_tri": synth.workload_p1_square(n_side=8, n_v=16),
+        "p2_tri": small_shock_tube(n=8, kx=2, n_v=16, integrator="BE"),
+        "p1_tet_cycles": twisted_workload(3, 8),
+    }
+
+
+@pytest.mark.parametrize("name", ["p1_tri", "p2_tri", "p1_tet_cycles"])
+def test_generations_bit_exact(name):
+    w = workloads()[name]
+    s, o = make_pair(w)
+    lag_total = 0
+    for j in range(s.nv):
+        gg, G = s.generations(j)
+        go, lag, Go = o.generations(j)
+        lag_total += int(lag.sum())
+        assert G == Go
+        np.testing.assert_array_equal(gg, go)
+    assert s.lagged == lag_total
+    if name == "p1_tet_cycles":
+        assert lag_total > 0
+
+
+def test_velocity_grid_and_initial_state():
+    w = synth.workload_p1_square(n_side=8, n_v=16)
+    s, o = make_pair(w)
+    v, wt = s.velocity()
+    vo, wo, _, _ = o.velocity()
+    np.testing.assert_allclose(v, vo, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(wt, wo, rtol=1e-15)
+    s.set_state_maxwellian(w.init)
+    f = s.get_f()
+    fo = o.maxwellian(w.init)
+    assert rel_err(f, fo) < FP64_TOL
+    U = s.get_moments()
+    assert rel_err(U, o.moments(fo)) < FP64_TOL
+
+
+@pytest.mark.parametrize("name", ["p1_tri", "p2_tri", "p1_tet_cycles"])
+def test_one_sweep_fp64(name):
+    w = workloads()[name]
+    s, o = make_pair(w)
+    s.set_state_maxwellian(w.init)
+    s.set_inflow_maxwellian(w.inflow)
+    f0 = o.maxwellian(w.init)
+    fbc = o.maxwellian(w.inflow)
+    dt = s.dt
+    nu = w.nu
+    nus = nu + 1.0 / dt
+    f = f0
+    for it in range(2):
+        s.sweep(nus, 1.0 / dt)
+        U = o.moments(f)
+        nut = U.copy()
+        d = o.dim
+        nut[:, 1:1 + d] = U[:, 1:1 + d] / U[:, :1]
+        nut[:, 1 + d] = (2 * U[:, 1 + d] / U[:, 0] - (nut[:, 1:1 + d] ** 2).sum(1)) / d
+        Mn = o.maxwellian(nut)
+        f = o.sweep(f, Mn, f0 / dt, fbc, nu, nus)
+        fg = s.get_f()
+        assert rel_err(fg, f) < FP64_TOL, (it, rel_err(fg, f))
+
+
+@pytest.mark.parametrize("integ", ["BE", "DIRK2", "DIRK3", "BSTABLE2", "BDF2"])
+def test_time_steps_match_oracle(integ):
+    w = synth.workload_p1_square(n_side=6, n_v=12, k_v=2, integrator=integ, knudsen=0.05)
+    s, o = make_pair(w)
+    s.set_state_maxwellian(w.init)
+    s.set_inflow_maxwellian(w.inflow)
+    o.set_physics(w.nu, s.dt, integ, 1e-8, 1000)
+    f = o.maxwellian(w.init)
+    fbc = o.maxwellian(w.inflow)
+    fprev = None
+    for k in range(2):
+        st = s.step(1)
+        f_new, it, meas, status = o.step(f, fbc, fprev=fprev)
+        assert status == 0
+        if integ == "BDF2":
+            fprev = f
+        f = f_new
+        nst = st.n_stages
+        assert list(st.iterations)[:nst] == list(it)[:nst], (k, list(st.iterations), list(it))
+        assert rel_err(s.get_f(), f) < FP64_TOL
+
+
+def test_p2_dirk3_shock_tube_step():
+    w = small_shock_tube(n=8, kx=2, n_v=16, integrator="DIRK3")
+    s, o = make_pair(w)
+    s.set_state_maxwellian(w.init)
+    s.set_inflow_maxwellian(w.inflow)
+    o.set_physics(w.nu, s.dt, "DIRK3", 1e-8, 1000)
+    st = s.step(1)
+    f, it, meas, status = o.step(o.maxwellian(w.init), o.maxwellian(w.inflow))
+    assert status == 0
+    assert list(st.iterations) == list(it)
+    assert rel_err(s.get_f(), f) < FP64_TOL
+    assert rel_err(s.get_moments(), o.moments(f)) < FP64_TOL
+
+
+def test_tet_step_with_cycles():
+    w = twisted_workload(3, 8)
+    s, o = make_pair(w)
+    s.set_state_maxwellian(w.init)
+    s.set_inflow_maxwellian(w.inflow)
+    o.set_physics(w.nu, s.dt, "BE", 1e-8, 1000)
+    st = s.step(1)
+    f, it, meas, status = o.step(o.maxwellian(w.init), o.maxwellian(w.inflow))
+    assert status == 0 and st.iterations[0] == it[0]
+    assert rel_err(s.get_f(), f) < FP64_TOL
+
+
+def test_uniform_maxwellian_preserved_on_gpu():
+    w = synth.workload_p1_square(n_side=8, n_v=16, integrator="DIRK3")
+    s, o = make_pair(w)
+    nut = np.tile([0.9, 0.2, -0.1, 1.1], (s.nnode, 1))
+    s.set_state_maxwellian(nut)
+    s.set_inflow_maxwellian(nut)
+    f0 = s.get_f()
+    s.step(2)
+    assert rel_err(s.get_f(), f0) < 1e-13
+
+
+def test_noconv_status_is_reported():
+    w = synth.workload_p1_square(n_side=6, n_v=12, k_v=2)
+    from paper_2608_19150_b300 import bgk
+    s = bgk.Solver.from_workload(w, l_max=1)
+    s.set_state_maxwellian(w.init)
+    s.set_inflow_maxwellian(w.inflow)
+    with pytest.raises(bgk.BgkError) as e:
+        s.step(1)
+    assert e.value.status == bgk.BGK_E_NOCONV
+
+
+def test_fp32_sweep_against_oracle():
+    w = small_shock_tube(n=8, kx=2, n_v=16, integrator="BE")
+    s, o = make_pair(w, precision="fp32")
+    s.set_state_maxwellian(w.init)
+    s.set_inflow_maxwellian(w.inflow)
+    f0 = o.maxwellian(w.init)
+    fbc = o.maxwellian(w.inflow)
+    dt = s.dt
+    nus = w.nu + 1.0 / dt
+    s.sweep(nus, 1.0 / dt)
+    U = o.moments(f0)
+    nut = U.copy()
+    nut[:, 1:3] = U[:, 1:3] / U[:, :1]
+    nut[:, 3] = (2 * U[:, 3] / U[:, 0] - (nut[:, 1:3] ** 2).sum(1)) / 2
+    f = o.sweep(f0, o.maxwellian(nut), f0 / dt, fbc, w.nu, nus)
+    assert rel_err(s.get_f(), f) < 2e-5
