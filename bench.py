@@ -40,6 +40,8 @@ def parse():
     p.add_argument("--n-v", type=int, default=32)
     p.add_argument("--sweep-reps", type=int, default=5)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--eager", action="store_true",
+                   help="launch each step's kernels from a host loop instead of one CUDA graph (profiling)")
     return p.parse_args()
 
 
@@ -56,7 +58,8 @@ def config(w, args, extra=None):
          "precision": args.precision, "integrator": "DIRK3",
          "l2": "inputs larger than L2 (f %.2f GB per array)" % (w.mesh.n_cells * 6 * args.n_v ** 2 *
                                                                  (8 if args.precision == "fp64" else 4) / 1e9),
-         "parallelism": "replicas"}
+         "parallelism": "replicas", "launch": "eager host loop" if args.eager else
+         "one CUDA graph per step, conditional while-node per stage"}
     if extra:
         c.update(extra)
     return c
@@ -227,7 +230,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     from paper_2608_19150_b300 import bgk
     w = workload(args)
-    s = bgk.Solver.from_workload(w, precision=args.precision)
+    s = bgk.Solver.from_workload(w, precision=args.precision, eager=args.eager)
     s.set_state_maxwellian(w.init)
     s.set_inflow_maxwellian(w.inflow)
     dof = s.nv * s.nnode

@@ -74,6 +74,8 @@ typedef struct {
   int precision;      /* BGK_FP64 or BGK_FP32_SWEEP (FP32 sweep, FP64 moments) */
   int block_threads;  /* sweep CTA size override (0 = default) */
   void* stream;       /* cudaStream_t to run on (NULL = a stream owned by the handle) */
+  int eager;          /* 0: each step is one CUDA graph (conditional while-node per stage);
+                         1: the same kernels launched from a host loop (profiling aid) */
 } bgk_config;
 
 typedef struct {

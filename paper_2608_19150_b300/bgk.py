@@ -41,7 +41,7 @@ class Physics(C.Structure):
 
 class Config(C.Structure):
     _fields_ = [("tau", C.c_double), ("l_max", C.c_int), ("precision", C.c_int), ("block_threads", C.c_int),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("eager", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -113,7 +113,7 @@ class Solver:
     """Handle of one problem on the current CUDA device (thin wrapper of bgk_create)."""
 
     def __init__(self, dim, kx, xyz, cells, n_v, k_v, L, nu, integrator="BE", dt=0.0, cfl=10.0, tau=1e-8,
-                 l_max=1000, precision="fp64", block_threads=0, stream=None):
+                 l_max=1000, precision="fp64", block_threads=0, stream=None, eager=False):
         self.lib = load()
         self._xyz = np.ascontiguousarray(xyz, dtype=np.float64)
         self._cells = np.ascontiguousarray(cells, dtype=np.int32)
@@ -121,7 +121,7 @@ class Solver:
         vg = VGrid(float(L), int(n_v), int(k_v))
         ph = Physics(float(nu), INTEGRATORS[integrator], float(dt), float(cfl))
         cf = Config(float(tau), int(l_max), PRECISIONS[precision], int(block_threads),
-                    C.c_void_p(stream) if stream else None)
+                    C.c_void_p(stream) if stream else None, int(bool(eager)))
         h = C.c_void_p()
         _ck(self.lib.bgk_create(C.byref(m), C.byref(vg), C.byref(ph), C.byref(cf), C.byref(h)), "bgk_create")
         self.h = h

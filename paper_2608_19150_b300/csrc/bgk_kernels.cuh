@@ -17,7 +17,7 @@ struct DevState {
   int iters[4];
   double meas[4];
   int total_sweeps;
-  int pad;
+  int cont;          // the stage loop continues (read by the host in eager mode)
 };
 
 __device__ __forceinline__ void ordinate(const VGrid& g, int j, double (&v)[3]) {
@@ -316,6 +316,7 @@ __global__ void k_finalize(DevState* ds, const double* __restrict__ partial, int
         cont = 1;
     }
   }
+  ds->cont = cont;
   if (use_cond) cudaGraphSetConditional(cond, cont);
 }
 

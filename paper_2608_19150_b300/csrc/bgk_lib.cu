@@ -220,10 +220,15 @@ int build_src(bgk_handle* h, const void* qsrc, double qscale) {
                                (const float*)qsrc, qscale, true);
 }
 
-// Capture one time step as a CUDA graph: per stage a conditional while-loop over
-// (Maxwellian + source, sweep, moments, convergence test).  bdf: 0 = use the DIRK
-// tableau of the integrator (or BE), 1 = BDF2 with history.
-int capture_step(bgk_handle* h, int mode_bdf2, cudaGraphExec_t* exec_out) {
+// One time step: per stage a while-loop over (Maxwellian + source, sweep, moments,
+// convergence test).  With exec_out != nullptr the step is captured as a CUDA graph in
+// which each stage loop is a conditional while-node; with exec_out == nullptr the same
+// kernels are launched eagerly and the host reads the loop condition after every
+// iteration (used for profiling, where kernels inside conditional graphs are not
+// visible).  mode_bdf2: 0 = the integrator's DIRK tableau (backward Euler for the
+// BDF2 start-up), 1 = BDF2 with history.
+int enqueue_step(bgk_handle* h, int mode_bdf2, cudaGraphExec_t* exec_out) {
+  const bool capture = exec_out != nullptr;
   double A[3][3], b[3], c[3];
   int S = tableau(mode_bdf2 ? BGK_BE : (h->phys.integrator == BGK_BDF2 ? BGK_BE : h->phys.integrator), A, b, c);
   const bool sa = stiffly_accurate(S, A, b);
@@ -232,7 +237,7 @@ int capture_step(bgk_handle* h, int mode_bdf2, cudaGraphExec_t* exec_out) {
   const size_t bytes = h->nfv * h->tsize;
   cudaStream_t s = h->stream;
   cudaGraph_t graph = nullptr;
-  CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  if (capture) CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   k_reset_state<<<1, 1, 0, s>>>(h->ds);
   const bool bdf = mode_bdf2 == 1;
   if (bdf) {
@@ -266,39 +271,54 @@ int capture_step(bgk_handle* h, int mode_bdf2, cudaGraphExec_t* exec_out) {
     }
     k_stage_begin<<<1, 1, 0, s>>>(h->ds, st);
     moments(h, 0);
-    // while (cond) { src; sweep; moments; finalize }
-    cudaGraph_t cg;
-    cudaStreamCaptureStatus cst;
-    const cudaGraphNode_t* deps = nullptr;
-    size_t ndeps = 0;
-    CK(cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, &deps, nullptr, &ndeps));
-    cudaGraphConditionalHandle cond;
-    CK(cudaGraphConditionalHandleCreate(&cond, cg, 1, cudaGraphCondAssignDefault));
-    cudaGraphNodeParams cp = {};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = cond;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    cudaGraphNode_t node;
-    CK(cudaGraphAddNode(&node, cg, deps, nullptr, ndeps, &cp));
-    CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    cudaStream_t bs;
-    CK(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
-    CK(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    h->stream = bs;
-    int rc = build_src(h, qsrc, qscale);
-    launch_sweep_any(h, nus);
-    moments(h, 1);
-    k_finalize<<<1, 256, 0, bs>>>(h->ds, h->partial, h->mom_blocks, tol, h->cfg.l_max, st, cond, 1);
-    h->stream = s;
-    cudaGraph_t body_out;
-    cudaError_t e2 = cudaStreamEndCapture(bs, &body_out);
-    cudaStreamDestroy(bs);
-    if (rc != BGK_OK || e2 != cudaSuccess) {
-      cudaStreamEndCapture(s, &graph);
-      if (graph) cudaGraphDestroy(graph);
-      return BGK_E_CUDA;
+    if (capture) {
+      // while (cond) { src; sweep; moments; finalize }
+      cudaGraph_t cg;
+      cudaStreamCaptureStatus cst;
+      const cudaGraphNode_t* deps = nullptr;
+      size_t ndeps = 0;
+      CK(cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, &deps, nullptr, &ndeps));
+      cudaGraphConditionalHandle cond;
+      CK(cudaGraphConditionalHandleCreate(&cond, cg, 1, cudaGraphCondAssignDefault));
+      cudaGraphNodeParams cp = {};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = cond;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      cudaGraphNode_t node;
+      CK(cudaGraphAddNode(&node, cg, deps, nullptr, ndeps, &cp));
+      CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+      cudaGraph_t body = cp.conditional.phGraph_out[0];
+      cudaStream_t bs;
+      CK(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
+      CK(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+      h->stream = bs;
+      int rc = build_src(h, qsrc, qscale);
+      launch_sweep_any(h, nus);
+      moments(h, 1);
+      k_finalize<<<1, 256, 0, bs>>>(h->ds, h->partial, h->mom_blocks, tol, h->cfg.l_max, st, cond, 1);
+      h->stream = s;
+      cudaGraph_t body_out;
+      cudaError_t e2 = cudaStreamEndCapture(bs, &body_out);
+      cudaStreamDestroy(bs);
+      if (rc != BGK_OK || e2 != cudaSuccess) {
+        cudaStreamEndCapture(s, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        return BGK_E_CUDA;
+      }
+    } else {
+      for (;;) {
+        int rc = build_src(h, qsrc, qscale);
+        if (rc != BGK_OK) return rc;
+        launch_sweep_any(h, nus);
+        moments(h, 1);
+        k_finalize<<<1, 256, 0, s>>>(h->ds, h->partial, h->mom_blocks, tol, h->cfg.l_max, st, 0, 0);
+        CK(cudaGetLastError());
+        DevState d;
+        CK(cudaMemcpyAsync(&d, h->ds, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (!d.cont) break;
+      }
     }
     // stage derivative F_s = f^(s) / (dt A_ss) - q^(s)   (Eq. dirk-recursive-def)
     if (!bdf && (st < S - 1 || !sa)) {
@@ -316,6 +336,10 @@ int capture_step(bgk_handle* h, int mode_bdf2, cudaGraphExec_t* exec_out) {
     double cF[3];
     for (int r = 0; r < S; ++r) cF[r] = dt * b[r];
     combine(h, h->f, 1.0, h->fk, 0.0, nullptr, S, cF, h->F);
+  }
+  if (!capture) {
+    CK(cudaGetLastError());
+    return BGK_OK;
   }
   CK(cudaStreamEndCapture(s, &graph));
   cudaError_t e = cudaGraphInstantiate(exec_out, graph, 0);
@@ -527,10 +551,10 @@ int bgk_create(const bgk_mesh* mesh, const bgk_vgrid* vg, const bgk_physics* phy
   CK(cudaFuncSetAttribute(k_peel<2, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   CK(cudaFuncSetAttribute(k_peel<3, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   rc = build_dags(h);
-  if (rc == BGK_OK) rc = capture_step(h, 0, &h->exec_main);
-  if (rc == BGK_OK && phys->integrator == BGK_BDF2) {
+  if (rc == BGK_OK && !h->cfg.eager) rc = enqueue_step(h, 0, &h->exec_main);
+  if (rc == BGK_OK && !h->cfg.eager && phys->integrator == BGK_BDF2) {
     cudaGraphExec_t e0 = h->exec_main;
-    rc = capture_step(h, 1, &h->exec_main);  // BDF2 proper
+    rc = enqueue_step(h, 1, &h->exec_main);  // BDF2 proper
     h->exec_start = e0;                      // first step: backward Euler
   }
   if (rc == BGK_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = BGK_E_CUDA;
@@ -726,16 +750,18 @@ int bgk_sweep(bgk_handle* h, double nu_s, double q_scale) {
 int bgk_step_async(bgk_handle* h, int nsteps) {
   if (!h || nsteps < 0) return BGK_E_INVALID;
   for (int k = 0; k < nsteps; ++k) {
-    cudaGraphExec_t e = h->exec_main;
-    if (h->phys.integrator == BGK_BDF2 && !h->have_prev) {
-      e = h->exec_start;
+    const bool start = h->phys.integrator == BGK_BDF2 && !h->have_prev;
+    if (h->cfg.eager) {
+      int rc = enqueue_step(h, h->phys.integrator == BGK_BDF2 && !start ? 1 : 0, nullptr);
+      if (rc != BGK_OK) return rc;
+    } else {
+      CK(cudaGraphLaunch(start ? h->exec_start : h->exec_main, h->stream));
+    }
+    if (start) {
       // the start-up step is backward Euler; its f^k becomes the BDF2 history
-      CK(cudaGraphLaunch(e, h->stream));
       CK(cudaMemcpyAsync(h->fprev, h->fk, h->nfv * h->tsize, cudaMemcpyDeviceToDevice, h->stream));
       h->have_prev = true;
-      continue;
     }
-    CK(cudaGraphLaunch(e, h->stream));
   }
   return BGK_OK;
 }

@@ -166,3 +166,17 @@ def test_fp32_sweep_against_oracle():
     nut[:, 3] = (2 * U[:, 3] / U[:, 0] - (nut[:, 1:3] ** 2).sum(1)) / 2
     f = o.sweep(f0, o.maxwellian(nut), f0 / dt, fbc, w.nu, nus)
     assert rel_err(s.get_f(), f) < 2e-5
+
+
+def test_eager_mode_matches_graph_mode_bitwise():
+    from paper_2608_19150_b300 import bgk
+    w = small_shock_tube(n=8, kx=2, n_v=16, integrator="DIRK3")
+    out = []
+    for eager in (False, True):
+        s = bgk.Solver.from_workload(w, eager=eager)
+        s.set_state_maxwellian(w.init)
+        s.set_inflow_maxwellian(w.inflow)
+        st = s.step(2)
+        out.append((s.get_f(), list(st.iterations)))
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1]
