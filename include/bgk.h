@@ -145,6 +145,26 @@ int bgk_synchronize(bgk_handle* h);
  * count since the last reset, recorded on the handle's stream. */
 int bgk_timing(bgk_handle* h, int reset, double* sweep_ms_total, int64_t* sweep_launches);
 
+/* Moments and convergence measure with no device allocation.  The paper has no
+ * counterpart: this entry point serves callers that cannot call cudaMalloc, such as
+ * programs that have given all device memory to their own pool allocator up front,
+ * or programs that must never synchronize the device (cudaMalloc/cudaFree may).
+ *
+ * Computes, from d_f ([n_ordinates][n_nodes] of dtype on the current device), the
+ * moments d_U_new ([n_nodes][dim+2], FP64) and writes to d_measure (one device double)
+ * max(|dU_0|/|U_0|, |dU_1|/max(|U_1|, |U_0|), |dU_2|/|U_2|) against d_U_old -- the same
+ * reduction and measure as the handle's Picard loop.  Work is enqueued on `stream`
+ * (a cudaStream_t; NULL = the legacy default stream); results are ready when the
+ * stream reaches that point.  Scratch lives in one file-scope device array of
+ * 16384 x 6 doubles (768 KiB) that every GPU loading the library holds until exit:
+ * n_nodes above 2,097,152 is rejected with BGK_E_INVALID.  Every call shares that
+ * array and each call overwrites the rows it reads, so nothing has to start at zero;
+ * calls that overlap on the GPU (two streams, or two host threads) race on it.  The
+ * first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * and should come before any stream capture.  Errors: BGK_E_INVALID, BGK_E_CUDA. */
+int bgk_moments_measure_noalloc(const bgk_vgrid* vgrid, int dim, int64_t n_nodes, const void* d_f, int dtype,
+                                const double* d_U_old, double* d_U_new, double* d_measure, void* stream);
+
 const char* bgk_status_string(int status);
 
 #ifdef __cplusplus

@@ -82,6 +82,7 @@ def load(path: str = LIB_PATH):
         "bgk_last_stats": [P, C.POINTER(Stats)],
         "bgk_synchronize": [P],
         "bgk_timing": [P, I, C.POINTER(D), C.POINTER(C.c_int64)],
+        "bgk_moments_measure_noalloc": [C.POINTER(VGrid), I, C.c_int64, V, I, V, V, V, V],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -107,6 +108,16 @@ def _ck(rc, where):
 
 def _ptr(a):
     return a.ctypes.data_as(C.c_void_p)
+
+
+def moments_measure_noalloc(L, n_points, k_v, dim, n_nodes, f_ptr, dtype, U_old_ptr, U_new_ptr, measure_ptr,
+                            stream=None):
+    """bgk_moments_measure_noalloc: device pointers in, device pointers out, no allocation."""
+    vg = VGrid(float(L), int(n_points), int(k_v))
+    _ck(load().bgk_moments_measure_noalloc(C.byref(vg), int(dim), int(n_nodes), C.c_void_p(f_ptr),
+                                            DTYPES[np.dtype(dtype)], C.c_void_p(U_old_ptr), C.c_void_p(U_new_ptr),
+                                            C.c_void_p(measure_ptr), C.c_void_p(stream) if stream else None),
+        "bgk_moments_measure_noalloc")
 
 
 class Solver:

@@ -13,7 +13,7 @@ LIB = os.path.join(HERE, "libbgk_b300.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-SOURCES = ["bgk_lib.cu", "bgk_host.cpp", "bgk_kernels.cuh", "bgk_internal.h", "bgk_tables.h"]
+SOURCES = ["bgk_lib.cu", "bgk_static.cu", "bgk_host.cpp", "bgk_kernels.cuh", "bgk_internal.h", "bgk_tables.h"]
 
 
 def _stale() -> bool:
@@ -33,7 +33,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     subprocess.check_call(["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-fno-fast-math",
                            "-I", INC, "-c", os.path.join(CSRC, "bgk_host.cpp"), "-o", host_o])
     cmd = [NVCC] + ARCH + ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
-                           "-shared", "-I", INC, os.path.join(CSRC, "bgk_lib.cu"), host_o, "-o", LIB + ".tmp"]
+                           "-shared", "-I", INC, os.path.join(CSRC, "bgk_lib.cu"),
+                           os.path.join(CSRC, "bgk_static.cu"), host_o, "-o", LIB + ".tmp"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     subprocess.check_call(cmd)
