@@ -76,6 +76,9 @@ typedef struct {
   void* stream;       /* cudaStream_t to run on (NULL = a stream owned by the handle) */
   int eager;          /* 0: each step is one CUDA graph (conditional while-node per stage);
                          1: the same kernels launched from a host loop (profiling aid) */
+  int cache_inverse;  /* local-inverse cache for the stage coefficient: 0 = when it fits in half
+                         of the free device memory, 1 = always (BGK_E_OOM if it cannot),
+                         2 = never (assemble and factorise every local matrix in the sweep) */
 } bgk_config;
 
 typedef struct {
@@ -97,7 +100,9 @@ int bgk_create(const bgk_mesh* mesh, const bgk_vgrid* vgrid, const bgk_physics* 
 int bgk_destroy(bgk_handle* h);
 
 /* Problem sizes: out[0]=n_ordinates, [1]=n_nodes, [2]=n_dof, [3]=n_cells, [4]=dim,
- * [5]=max generations over ordinates, [6]=lagged edges over all ordinates. */
+ * [5]=max generations over ordinates, [6]=lagged edges over all ordinates,
+ * [7]=bytes of the local-inverse cache (0 if none), [8]=threads per sweep CTA.
+ * out holds 9 values. */
 int bgk_sizes(const bgk_handle* h, int64_t* out);
 /* Time step actually used (after the CFL rule). */
 int bgk_get_dt(const bgk_handle* h, double* dt);
@@ -125,8 +130,10 @@ int bgk_get_velocity(const bgk_handle* h, double* h_v, double* h_w);
 int bgk_get_generations(bgk_handle* h, int j, int32_t* h_gen, int* n_gen);
 
 /* One transport sweep of the Picard iteration, Eq. (bgk-ss-picard): f <- solution with
- * the Maxwellian of the current moments, source q = f_q / (dt_q) and collision nu_s.
+ * the Maxwellian of the current moments, source q = q_scale * f_q and collision nu_s.
  * f_q is the handle's stage base state (the state at the last bgk_set_* call or step).
+ * nu_s <= 0 / q_scale <= 0 select the first stage's values nu + 1/(dt A_11) and
+ * 1/(dt A_11), for which the local-inverse cache (if any) was built.
  * For parity tests and sweep benchmarks; a step does not use this entry point. */
 int bgk_sweep(bgk_handle* h, double nu_s, double q_scale);
 

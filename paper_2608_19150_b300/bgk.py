@@ -41,7 +41,8 @@ class Physics(C.Structure):
 
 class Config(C.Structure):
     _fields_ = [("tau", C.c_double), ("l_max", C.c_int), ("precision", C.c_int), ("block_threads", C.c_int),
-                ("stream", C.c_void_p), ("eager", C.c_int)]
+                ("stream", C.c_void_p), ("eager", C.c_int),
+                ("cache_inverse", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -124,7 +125,7 @@ class Solver:
     """Handle of one problem on the current CUDA device (thin wrapper of bgk_create)."""
 
     def __init__(self, dim, kx, xyz, cells, n_v, k_v, L, nu, integrator="BE", dt=0.0, cfl=10.0, tau=1e-8,
-                 l_max=1000, precision="fp64", block_threads=0, stream=None, eager=False):
+                 l_max=1000, precision="fp64", block_threads=0, stream=None, eager=False, cache_inverse="auto"):
         self.lib = load()
         self._xyz = np.ascontiguousarray(xyz, dtype=np.float64)
         self._cells = np.ascontiguousarray(cells, dtype=np.int32)
@@ -132,13 +133,15 @@ class Solver:
         vg = VGrid(float(L), int(n_v), int(k_v))
         ph = Physics(float(nu), INTEGRATORS[integrator], float(dt), float(cfl))
         cf = Config(float(tau), int(l_max), PRECISIONS[precision], int(block_threads),
-                    C.c_void_p(stream) if stream else None, int(bool(eager)))
+                    C.c_void_p(stream) if stream else None, int(bool(eager)),
+                    {"auto": 0, "on": 1, "off": 2}[cache_inverse])
         h = C.c_void_p()
         _ck(self.lib.bgk_create(C.byref(m), C.byref(vg), C.byref(ph), C.byref(cf), C.byref(h)), "bgk_create")
         self.h = h
-        sz = (C.c_int64 * 7)()
+        sz = (C.c_int64 * 9)()
         _ck(self.lib.bgk_sizes(self.h, sz), "bgk_sizes")
-        self.nv, self.nnode, self.ndof, self.ncell, self.dim, self.gmax, self.lagged = (int(x) for x in sz)
+        (self.nv, self.nnode, self.ndof, self.ncell, self.dim, self.gmax, self.lagged, self.cache_bytes,
+         self.sweep_threads) = (int(x) for x in sz)
         self.precision = precision
         self.fdtype = np.float64 if precision == "fp64" else np.float32
 

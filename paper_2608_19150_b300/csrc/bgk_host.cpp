@@ -207,6 +207,15 @@ int build_vgrid(int dim, int N, int kv, double L, VGrid& g) {
       g.x[cl * n + k] = mid + 0.5 * g.h * xi[k];
       g.w[cl * n + k] = 0.5 * g.h * wi[k];
     }
+  for (int m = 0; m < N; ++m) {
+    g.wx[m] = g.w[m] * g.x[m];
+    g.wxx[m] = g.w[m] * g.x[m] * g.x[m];
+    const double src3[3] = {g.w[m], g.wx[m], g.wxx[m]};
+    for (int k = 0; k < 3; ++k) {
+      g.wh[k][m] = (float)src3[k];
+      g.wl[k][m] = (float)(src3[k] - (double)g.wh[k][m]);
+    }
+  }
   // Lagrange basis on the reference cell: monomial coefficients by expansion
   for (int k = 0; k < n; ++k) {
     double c[kMaxKv + 2] = {1.0};

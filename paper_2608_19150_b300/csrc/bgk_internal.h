@@ -16,6 +16,10 @@ struct VGrid {
   int dim, N, kv, np, ncl, nv;
   double L, h;
   double x[kMaxN1D], w[kMaxN1D];
+  // moment weights w, w x, w x^2 per 1D point; and each split into two floats (hi + lo)
+  // for the compensated FP32 reduction of FP32 distributions
+  double wx[kMaxN1D], wxx[kMaxN1D];
+  float wh[3][kMaxN1D], wl[3][kMaxN1D];
   // Lagrange basis of one velocity cell in its local variable xi in [-1, 1]:
   // l_k(xi) = sum_p lag[k][p] xi^p  (same for every cell of the uniform grid).
   double lag[kMaxKv + 1][kMaxKv + 1];

@@ -184,8 +184,46 @@ __global__ void k_maxwell(VGrid g, int npos, int nm, const double* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------------
+// Inner moment sums over the last velocity dimension: S_k = sum_m W_k[m] f_m with
+// W = (w, w x, w x^2).  FP64 data: FP64 fused multiply-adds.  FP32 data: the
+// compensated dot product of Ogita, Rump and Oishi (2005) in FP32 (error-free
+// TwoProduct by fma and TwoSum), with each FP64 weight split into two floats, so the
+// sums carry about 48 significant bits -- FP64 accuracy at FP32 instruction rate.
+template <typename T>
+struct InnerSums;
+
+template <>
+struct InnerSums<double> {
+  double s[3] = {0, 0, 0};
+  __device__ __forceinline__ void add(const VGrid& g, int m, double f) {
+    s[0] = fma(g.w[m], f, s[0]);
+    s[1] = fma(g.wx[m], f, s[1]);
+    s[2] = fma(g.wxx[m], f, s[2]);
+  }
+  __device__ __forceinline__ double get(int k) const { return s[k]; }
+};
+
+template <>
+struct InnerSums<float> {
+  float hi[3] = {0.f, 0.f, 0.f}, lo[3] = {0.f, 0.f, 0.f};
+  __device__ __forceinline__ void add(const VGrid& g, int m, float f) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float wh = g.wh[k][m];
+      const float p = wh * f;
+      const float ep = fmaf(wh, f, -p) + g.wl[k][m] * f;  // p + ep = (wh + wl) f
+      const float t = hi[k] + p;                          // TwoSum(hi, p)
+      const float z = t - hi[k];
+      const float es = (hi[k] - (t - z)) + (p - z);
+      hi[k] = t;
+      lo[k] += es + ep;
+    }
+  }
+  __device__ __forceinline__ double get(int k) const { return (double)hi[k] + (double)lo[k]; }
+};
+
 // Velocity moments U_i = sum_j w_j (1, v_j, |v_j|^2/2) f_{j,i} (Eq. moments), FP64
-// accumulation for either storage type.  mode 0: write U[it&1].  mode 1: write
+// accuracy for either storage type.  mode 0: write U[it&1].  mode 1: write
 // U[(it+1)&1] and per-block partial sums of |dU_m|^2 and |U_old,m|^2, m = 0, 1, 2,
 // for the criterion of Eq. (convergence-criteria).
 template <typename T>
@@ -198,16 +236,11 @@ __global__ void k_moments(VGrid g, const T* __restrict__ f, int nnode, double* U
   if (i < nnode) {
     if (g.dim == 2) {
       for (int j0 = 0; j0 < g.N; ++j0) {
-        double s0 = 0, s1 = 0, s2 = 0;
+        InnerSums<T> S;
         const T* fr = f + (size_t)j0 * g.N * nnode + i;
-#pragma unroll 4
-        for (int j1 = 0; j1 < g.N; ++j1) {
-          const double fv = (double)fr[(size_t)j1 * nnode];
-          const double wf = g.w[j1] * fv;
-          s0 += wf;
-          s1 += g.x[j1] * wf;
-          s2 += g.x[j1] * g.x[j1] * wf;
-        }
+#pragma unroll 8
+        for (int j1 = 0; j1 < g.N; ++j1) S.add(g, j1, fr[(size_t)j1 * nnode]);
+        const double s0 = S.get(0), s1 = S.get(1), s2 = S.get(2);
         const double w0 = g.w[j0], x0 = g.x[j0];
         acc[0] += w0 * s0;
         acc[1] += w0 * x0 * s0;
@@ -218,15 +251,11 @@ __global__ void k_moments(VGrid g, const T* __restrict__ f, int nnode, double* U
       for (int j0 = 0; j0 < g.N; ++j0) {
         double t0 = 0, t1 = 0, t2 = 0, t3 = 0;
         for (int j1 = 0; j1 < g.N; ++j1) {
-          double s0 = 0, s1 = 0, s2 = 0;
+          InnerSums<T> S;
           const T* fr = f + ((size_t)j0 * g.N + j1) * g.N * nnode + i;
-#pragma unroll 4
-          for (int j2 = 0; j2 < g.N; ++j2) {
-            const double wf = g.w[j2] * (double)fr[(size_t)j2 * nnode];
-            s0 += wf;
-            s1 += g.x[j2] * wf;
-            s2 += g.x[j2] * g.x[j2] * wf;
-          }
+#pragma unroll 8
+          for (int j2 = 0; j2 < g.N; ++j2) S.add(g, j2, fr[(size_t)j2 * nnode]);
+          const double s0 = S.get(0), s1 = S.get(1), s2 = S.get(2);
           const double w1 = g.w[j1], x1 = g.x[j1];
           t0 += w1 * s0;
           t1 += w1 * x1 * s0;
@@ -274,6 +303,60 @@ __global__ void k_moments(VGrid g, const T* __restrict__ f, int nnode, double* U
     double s = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[threadIdx.x][w];
     partial[(size_t)blockIdx.x * 6 + threadIdx.x] = s;
+  }
+}
+
+// Projected-Maxwellian factors of every node from the current moments U[it & 1]:
+// cf[a][m][i] = c_a[m](u_i, theta_i) (App. B), with coef * n_i folded into a = 0.
+// Non-physical moments set the error flag (the stage loop then stops).
+template <typename T>
+__global__ void k_factors(VGrid g, int nnode, const double* __restrict__ U0, const double* __restrict__ U1,
+                          DevState* ds, double coef, T* __restrict__ cf) {
+  if (ds->status != BGK_OK) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nnode) return;
+  const int nm = g.dim + 2;
+  const double* Un = (((ds->it & 1) == 0) ? U0 : U1) + (size_t)i * nm;
+  const double n = Un[0];
+  double u[3] = {0, 0, 0}, u2 = 0.0;
+  for (int a = 0; a < g.dim; ++a) {
+    u[a] = Un[1 + a] / n;
+    u2 += u[a] * u[a];
+  }
+  double th = (2.0 * Un[1 + g.dim] / n - u2) / g.dim;
+  double scale = coef * n;
+  if (!(n > 0.0) || !(th > 0.0) || !isfinite(n) || !isfinite(th)) {
+    atomicOr(&ds->err, 1);
+    scale = 0.0;
+    th = 1.0;
+    u[0] = u[1] = u[2] = 0.0;
+  }
+  double c[kMaxN1D];
+  for (int a = 0; a < g.dim; ++a) {
+    proj_factors(g, u[a], th, c, 1);
+    const double sa = a == 0 ? scale : 1.0;
+    T* out = cf + (size_t)a * g.N * nnode + i;
+    for (int m = 0; m < g.N; ++m) out[(size_t)m * nnode] = (T)(sa * c[m]);
+  }
+}
+
+// src[j][i] = prod_a cf[a][j_a][i] + qscale * q[j][i]  (nu M^l + q of Eq. bgk-ss-picard)
+template <typename T>
+__global__ void k_source(VGrid g, int nnode, const T* __restrict__ cf, const T* __restrict__ q, T qscale,
+                         T* __restrict__ src, const DevState* ds) {
+  if (ds->status != BGK_OK) return;
+  const size_t total = (size_t)g.nv * nnode;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(t / nnode);
+    const int i = (int)(t - (size_t)j * nnode);
+    T m;
+    if (g.dim == 2) {
+      m = cf[(size_t)(j / g.N) * nnode + i] * cf[(size_t)(g.N + j % g.N) * nnode + i];
+    } else {
+      m = cf[(size_t)(j / (g.N * g.N)) * nnode + i] * cf[(size_t)(g.N + (j / g.N) % g.N) * nnode + i] *
+          cf[(size_t)(2 * g.N + j % g.N) * nnode + i];
+    }
+    src[t] = fma(qscale, q[t], m);
   }
 }
 
@@ -437,6 +520,109 @@ __device__ __forceinline__ void lu_solve(T (&A)[N][N], T (&b)[N]) {
   }
 }
 
+// Sweep schedule of one ordinate, as the kernels see it.
+struct SweepArgs {
+  const double* geo;
+  int gs;
+  const int32_t* nbr;
+  const uint64_t* perm;
+  const uint32_t* glist;
+  const int32_t* lvl;
+  const int32_t* ngen;
+  int ncell, nnode, nbface;
+};
+
+// Local operator of one (cell, ordinate) from its packed schedule entry (Sec. 3.3):
+// r_i = s_i / |K| with the sign taken from the entry's face code.
+template <class E, typename T>
+__device__ __forceinline__ void face_rates(const double* __restrict__ Gc, uint32_t code, T v0, T v1, T v2,
+                                           T (&r)[E::NF], unsigned& outm) {
+  constexpr int D = E::D, NF = E::NF;
+  const T invK = (T)Gc[NF * D];
+  outm = 0;
+#pragma unroll
+  for (int i = 0; i < NF; ++i) {
+    const uint32_t fl = (code >> (2 * i)) & 3u;
+    T s = v0 * (T)Gc[i * D] + v1 * (T)Gc[i * D + 1];
+    if (D == 3) s += v2 * (T)Gc[i * D + 2];
+    s = fabs(s) * invK;
+    r[i] = fl == 1u ? s : (fl == 2u ? -s : T(0));
+    outm |= (fl == 1u ? 1u : 0u) << i;
+  }
+}
+
+// Inverse of the local matrix of every (ordinate, schedule position), computed in FP64
+// by Gauss-Jordan elimination in natural order and stored as T in schedule order:
+// Ainv[(j * ncell + k) * ND * ND + a * ND + b].  Valid for one nu_s; a sweep with that
+// nu_s then needs only the right-hand side and one matrix-vector product per cell.
+template <class E, typename T>
+__global__ void k_local_inverse(SweepArgs sa, VGrid g, double nus, T* __restrict__ Ainv) {
+  constexpr int ND = E::NDOF, NF = E::NF;
+  const size_t total = (size_t)g.nv * sa.ncell;
+  for (size_t it = (size_t)blockIdx.x * blockDim.x + threadIdx.x; it < total; it += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(it / sa.ncell);
+    const int k = (int)(it % sa.ncell);
+    double vd[3];
+    ordinate(g, j, vd);
+    const uint32_t e = sa.glist[(size_t)j * sa.ncell + k];
+    const int c = (int)(e & kCellMask);
+    double r[NF];
+    unsigned outm;
+    face_rates<E, double>(sa.geo + (size_t)c * sa.gs, e >> kCellBits, vd[0], vd[1], vd[2], r, outm);
+    double A[ND][ND], X[ND][ND];
+    E::assemble(nus, r, outm, A);
+#pragma unroll
+    for (int a = 0; a < ND; ++a)
+#pragma unroll
+      for (int bb = 0; bb < ND; ++bb) X[a][bb] = a == bb ? 1.0 : 0.0;
+#pragma unroll
+    for (int p = 0; p < ND; ++p) {
+      const double inv = 1.0 / A[p][p];
+#pragma unroll
+      for (int cc = 0; cc < ND; ++cc) {
+        A[p][cc] *= inv;
+        X[p][cc] *= inv;
+      }
+#pragma unroll
+      for (int i = 0; i < ND; ++i) {
+        if (i == p) continue;
+        const double l = A[i][p];
+#pragma unroll
+        for (int cc = 0; cc < ND; ++cc) {
+          A[i][cc] -= l * A[p][cc];
+          X[i][cc] -= l * X[p][cc];
+        }
+      }
+    }
+    T* out = Ainv + it * (ND * ND);
+#pragma unroll
+    for (int a = 0; a < ND; ++a)
+#pragma unroll
+      for (int bb = 0; bb < ND; ++bb) out[a * ND + bb] = (T)X[a][bb];
+  }
+}
+
+// Per-item data that does not depend on values written during the sweep, so the next
+// item's copy can be loaded while the current item is processed.
+template <class E, typename T>
+struct SweepItem {
+  uint32_t e;
+  int4 nb;
+  uint64_t pm;
+  T src[E::NDOF];
+};
+
+template <class E, typename T>
+__device__ __forceinline__ void fetch_item(const SweepArgs& sa, const uint32_t* __restrict__ gl,
+                                           const T* __restrict__ sj, int k, SweepItem<E, T>& it) {
+  it.e = gl[k];
+  const int c = (int)(it.e & kCellMask);
+  it.nb = *reinterpret_cast<const int4*>(sa.nbr + (size_t)c * 4);
+  it.pm = sa.perm[c];
+#pragma unroll
+  for (int a = 0; a < E::NDOF; ++a) it.src[a] = sj[(size_t)c * E::NDOF + a];
+}
+
 // One transport sweep (Sec. 4, Eq. bgk-ss-picard), one CTA per ordinate walking that
 // ordinate's generations; the cells of a generation are independent and share the
 // CTA's threads.  For cell K and ordinate j (s_i = v_j . N_i, r_i = s_i/|K|):
@@ -444,12 +630,13 @@ __device__ __forceinline__ void lu_solve(T (&A)[N][N], T (&b)[N]) {
 // where src = nu M^l + q and y_i is the upwind trace: the neighbour's value in f,
 // updated in place.  An upwind cell reached by a lagged (cycle) edge has a higher
 // generation, so it still holds f^l when read; boundary faces read fbc.
-template <class E, typename T>
-__global__ void __launch_bounds__(256) k_sweep(const double* __restrict__ geo, int gs, const int32_t* __restrict__ nbr,
-                                               const uint64_t* __restrict__ perm, const uint32_t* __restrict__ glist,
-                                               const int32_t* __restrict__ lvl, const int32_t* __restrict__ ngen,
-                                               int ncell, int nnode, int nbface, VGrid g, T nus,
-                                               const T* __restrict__ src, const T* __restrict__ fbc, T* f,
+// CACHED: the local inverse comes from k_local_inverse (schedule order, coalesced);
+// otherwise the matrix is assembled and factorised in place.  The schedule entry, the
+// neighbour ids, the node permutation and src of the thread's next item are loaded
+// before the current item is solved (they are not written during the sweep).
+template <class E, typename T, bool CACHED>
+__global__ void __launch_bounds__(256) k_sweep(SweepArgs sa, VGrid g, T nus, const T* __restrict__ src,
+                                               const T* __restrict__ fbc, const T* __restrict__ Ainv, T* f,
                                                const DevState* ds) {
   constexpr int D = E::D, ND = E::NDOF, NF = E::NF, FD = E::FD;
   if (ds && ds->status != BGK_OK) return;
@@ -457,40 +644,41 @@ __global__ void __launch_bounds__(256) k_sweep(const double* __restrict__ geo, i
   double vd[3];
   ordinate(g, j, vd);
   const T v0 = (T)vd[0], v1 = (T)vd[1], v2 = (T)vd[2];
-  const uint32_t* gl = glist + (size_t)j * ncell;
-  const int32_t* lv = lvl + (size_t)j * (ncell + 1);
-  const int G = ngen[j];
-  T* fj = f + (size_t)j * nnode;
-  const T* sj = src + (size_t)j * nnode;
-  const T* bj = fbc + (size_t)j * nbface * FD;
-  int lo = lv[0];
+  const uint32_t* gl = sa.glist + (size_t)j * sa.ncell;
+  const int32_t* lv = sa.lvl + (size_t)j * (sa.ncell + 1);
+  const T* Aj = CACHED ? Ainv + (size_t)j * sa.ncell * (ND * ND) : nullptr;
+  const int G = sa.ngen[j];
+  T* fj = f + (size_t)j * sa.nnode;
+  const T* sj = src + (size_t)j * sa.nnode;
+  const T* bj = fbc + (size_t)j * sa.nbface * FD;
+  const int bd = blockDim.x, tid = threadIdx.x;
+  int lo = lv[0], hi = G > 0 ? lv[1] : lv[0];
+  int k = lo + tid;
+  SweepItem<E, T> cur, nxt;
+  bool have = k < hi;
+  if (have) fetch_item<E, T>(sa, gl, sj, k, cur);
+  int kpend = -1;
   for (int gg = 0; gg < G; ++gg) {
-    const int hi = lv[gg + 1];
-    for (int k = lo + threadIdx.x; k < hi; k += blockDim.x) {
-      const uint32_t e = gl[k];
-      const int c = (int)(e & kCellMask);
-      const uint32_t code = e >> kCellBits;
-      const double* Gc = geo + (size_t)c * gs;
-      const T invK = (T)Gc[NF * D];
-      T r[NF];
-      unsigned outm = 0;
-#pragma unroll
-      for (int i = 0; i < NF; ++i) {
-        const uint32_t fl = (code >> (2 * i)) & 3u;
-        T s = v0 * (T)Gc[i * D] + v1 * (T)Gc[i * D + 1];
-        if (D == 3) s += v2 * (T)Gc[i * D + 2];
-        s = fabs(s) * invK;
-        r[i] = fl == 1u ? s : (fl == 2u ? -s : T(0));
-        outm |= (fl == 1u ? 1u : 0u) << i;
+    while (have) {
+      // prefetch the thread's next item: same generation, else the next generation
+      int kn = k + bd;
+      bool same = kn < hi;
+      if (!same && gg + 1 < G) {
+        kn = hi + tid;
+        if (kn >= lv[gg + 2]) kn = -1;
+      } else if (!same) {
+        kn = -1;
       }
-      T A[ND][ND], b[ND], sv[ND];
-#pragma unroll
-      for (int a = 0; a < ND; ++a) sv[a] = sj[(size_t)c * ND + a];
-      E::assemble(nus, r, outm, A);
-      E::mass(sv, b);
-      const int4 nb4 = *reinterpret_cast<const int4*>(nbr + (size_t)c * 4);
-      const int nbs[4] = {nb4.x, nb4.y, nb4.z, nb4.w};
-      const uint64_t pm = perm[c];
+      if (kn >= 0) fetch_item<E, T>(sa, gl, sj, kn, nxt);
+      // ---- solve item k
+      const int c = (int)(cur.e & kCellMask);
+      const uint32_t code = cur.e >> kCellBits;
+      T r[NF];
+      unsigned outm;
+      face_rates<E, T>(sa.geo + (size_t)c * sa.gs, code, v0, v1, v2, r, outm);
+      T b[ND];
+      E::mass(cur.src, b);
+      const int nbs[4] = {cur.nb.x, cur.nb.y, cur.nb.z, cur.nb.w};
 #pragma unroll
       for (int i = 0; i < NF; ++i) {
         if (((code >> (2 * i)) & 3u) != 2u) continue;
@@ -498,20 +686,54 @@ __global__ void __launch_bounds__(256) k_sweep(const double* __restrict__ geo, i
         T y[FD];
         if (nb >= 0) {
 #pragma unroll
-          for (int kk = 0; kk < FD; ++kk)
-            y[kk] = fj[(size_t)nb * ND + (int)((pm >> (16 * i + 4 * kk)) & 15u)];
+          for (int kk = 0; kk < FD; ++kk) y[kk] = fj[(size_t)nb * ND + (int)((cur.pm >> (16 * i + 4 * kk)) & 15u)];
         } else {
 #pragma unroll
           for (int kk = 0; kk < FD; ++kk) y[kk] = bj[(size_t)(-nb - 1) * FD + kk];
         }
         E::inflow(i, -r[i], y, b);
       }
-      lu_solve<ND, T>(A, b);
+      T x[ND];
+      if (CACHED) {
+        const T* Ak = Aj + (size_t)k * (ND * ND);
 #pragma unroll
-      for (int a = 0; a < ND; ++a) fj[(size_t)c * ND + a] = b[a];
+        for (int a = 0; a < ND; ++a) {
+          T s = T(0);
+#pragma unroll
+          for (int bb = 0; bb < ND; ++bb) s += Ak[a * ND + bb] * b[bb];
+          x[a] = s;
+        }
+      } else {
+        T A[ND][ND];
+        E::assemble(nus, r, outm, A);
+        lu_solve<ND, T>(A, b);
+#pragma unroll
+        for (int a = 0; a < ND; ++a) x[a] = b[a];
+      }
+#pragma unroll
+      for (int a = 0; a < ND; ++a) fj[(size_t)c * ND + a] = x[a];
+      // ---- advance
+      if (same) {
+        cur = nxt;
+        k = kn;
+      } else {
+        have = false;
+        kpend = kn;
+        if (kn >= 0) cur = nxt;
+      }
     }
-    lo = hi;
     __syncthreads();
+    lo = hi;
+    hi = gg + 1 < G ? lv[gg + 2] : hi;
+    if (kpend >= 0) {
+      k = kpend;
+      have = true;
+    } else {
+      k = lo + tid;
+      have = gg + 1 < G && k < hi;
+      if (have) fetch_item<E, T>(sa, gl, sj, k, cur);
+    }
+    kpend = -1;
   }
 }
 

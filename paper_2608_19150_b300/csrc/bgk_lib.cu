@@ -44,6 +44,10 @@ struct bgk_handle {
   int32_t* lvl = nullptr;
   int32_t* ngen = nullptr;
   int32_t* nproc = nullptr;
+  void* Ainv = nullptr;      // cached local inverses (schedule order), valid for nus_cached
+  double nus_cached = -1.0;
+  double nus_main = 0.0, qscale_main = 0.0;  // stage coefficient and 1/(dt A_ss) of the step
+  size_t ainv_bytes = 0;
   // state (storage type T = double or float)
   void* f = nullptr;
   void* fk = nullptr;
@@ -54,6 +58,7 @@ struct bgk_handle {
   void* F[3] = {nullptr, nullptr, nullptr};
   double* U[2] = {nullptr, nullptr};
   double* partial = nullptr;
+  void* cf = nullptr;        // Maxwellian factors [dim][N][node] of the current iterate
   int mom_blocks = 0;
   DevState* ds = nullptr;
   bool have_prev = false;    // BDF2 history present
@@ -162,11 +167,60 @@ void launch_moments(bgk_handle* h, int mode) {
                                                      h->partial);
 }
 
+SweepArgs sweep_args(const bgk_handle* h) {
+  SweepArgs a;
+  a.geo = h->geo;
+  a.gs = h->hm.geo_stride;
+  a.nbr = h->nbr;
+  a.perm = h->perm;
+  a.glist = h->glist;
+  a.lvl = h->lvl;
+  a.ngen = h->ngen;
+  a.ncell = h->hm.ncell;
+  a.nnode = h->nnode;
+  a.nbface = h->hm.nbface;
+  return a;
+}
+
 template <class E, typename T>
 void launch_sweep_t(bgk_handle* h, double nus) {
-  k_sweep<E, T><<<h->g.nv, h->sweep_threads, 0, h->stream>>>(
-      h->geo, h->hm.geo_stride, h->nbr, h->perm, h->glist, h->lvl, h->ngen, h->hm.ncell, h->nnode, h->hm.nbface, h->g,
-      (T)nus, (const T*)h->src, (const T*)h->fbc, (T*)h->f, h->ds);
+  const bool cached = h->Ainv && nus == h->nus_cached;
+  if (cached)
+    k_sweep<E, T, true><<<h->g.nv, h->sweep_threads, 0, h->stream>>>(
+        sweep_args(h), h->g, (T)nus, (const T*)h->src, (const T*)h->fbc, (const T*)h->Ainv, (T*)h->f, h->ds);
+  else
+    k_sweep<E, T, false><<<h->g.nv, h->sweep_threads, 0, h->stream>>>(
+        sweep_args(h), h->g, (T)nus, (const T*)h->src, (const T*)h->fbc, nullptr, (T*)h->f, h->ds);
+}
+
+template <class E, typename T>
+void launch_inverse_t(bgk_handle* h, double nus) {
+  k_local_inverse<E, T><<<148 * 16, 128, 0, h->stream>>>(sweep_args(h), h->g, nus, (T*)h->Ainv);
+}
+
+// Precompute the local inverses for the stage coefficient nus (once per handle).
+int build_inverse_cache(bgk_handle* h, double nus) {
+  const int nd = h->hm.ndof;
+  h->ainv_bytes = (size_t)h->g.nv * h->hm.ncell * nd * nd * h->tsize;
+  if (h->cfg.cache_inverse == 2) return BGK_OK;
+  if (h->cfg.cache_inverse == 0) {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess || h->ainv_bytes > fr / 2) return BGK_OK;  // does not fit: skip
+  }
+  if (dalloc(h->Ainv, h->ainv_bytes) != BGK_OK) {
+    h->Ainv = nullptr;
+    return h->cfg.cache_inverse == 1 ? BGK_E_OOM : BGK_OK;
+  }
+  const bool f64 = h->precision == BGK_FP64;
+  if (h->hm.dim == 3)
+    f64 ? launch_inverse_t<ElemP1Tet, double>(h, nus) : launch_inverse_t<ElemP1Tet, float>(h, nus);
+  else if (h->hm.kx == 2)
+    f64 ? launch_inverse_t<ElemP2Tri, double>(h, nus) : launch_inverse_t<ElemP2Tri, float>(h, nus);
+  else
+    f64 ? launch_inverse_t<ElemP1Tri, double>(h, nus) : launch_inverse_t<ElemP1Tri, float>(h, nus);
+  CK(cudaGetLastError());
+  h->nus_cached = nus;
+  return BGK_OK;
 }
 
 template <typename T>
@@ -211,13 +265,18 @@ void moments(bgk_handle* h, int mode) {
     launch_moments<float>(h, mode);
 }
 
-// src = nu * M(U[it&1]) + qscale * qsrc
+// src = nu * M(U[it&1]) + qscale * qsrc: per-node factors, then a streaming product
+template <typename T>
+int build_src_t(bgk_handle* h, const void* qsrc, double qscale) {
+  k_factors<T><<<(h->nnode + 127) / 128, 128, 0, h->stream>>>(h->g, h->nnode, h->U[0], h->U[1], h->ds, h->phys.nu,
+                                                              (T*)h->cf);
+  k_source<T><<<148 * 16, 256, 0, h->stream>>>(h->g, h->nnode, (const T*)h->cf, (const T*)qsrc, (T)qscale, (T*)h->src,
+                                               h->ds);
+  return cudaGetLastError() == cudaSuccess ? BGK_OK : BGK_E_CUDA;
+}
+
 int build_src(bgk_handle* h, const void* qsrc, double qscale) {
-  if (h->precision == BGK_FP64)
-    return launch_maxwell<double>(h, h->nnode, h->U[0], h->U[1], 1, nullptr, (double*)h->src, h->nnode, h->phys.nu,
-                                  (const double*)qsrc, qscale, true);
-  return launch_maxwell<float>(h, h->nnode, h->U[0], h->U[1], 1, nullptr, (float*)h->src, h->nnode, h->phys.nu,
-                               (const float*)qsrc, qscale, true);
+  return h->precision == BGK_FP64 ? build_src_t<double>(h, qsrc, qscale) : build_src_t<float>(h, qsrc, qscale);
 }
 
 // One time step: per stage a while-loop over (Maxwellian + source, sweep, moments,
@@ -406,8 +465,9 @@ void release(bgk_handle* h) {
   cudaStreamSynchronize(h->stream);
   if (h->exec_main) cudaGraphExecDestroy(h->exec_main);
   if (h->exec_start) cudaGraphExecDestroy(h->exec_start);
-  void* ptrs[] = {h->geo, h->nbr, h->nbr_face, h->perm, h->bnode, h->glist, h->lvl, h->ngen, h->nproc, h->f, h->fk,
-                  h->fprev, h->src, h->fbc, h->q, h->F[0], h->F[1], h->F[2], h->U[0], h->U[1], h->partial, h->ds};
+  void* ptrs[] = {h->geo, h->nbr, h->nbr_face, h->perm, h->bnode, h->glist, h->lvl, h->ngen, h->nproc, h->Ainv, h->f, h->fk,
+                  h->fprev, h->src, h->fbc, h->q, h->F[0], h->F[1], h->F[2], h->U[0], h->U[1], h->partial, h->cf,
+                  h->ds};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->ev0) cudaEventDestroy(h->ev0);
@@ -518,6 +578,7 @@ int bgk_create(const bgk_mesh* mesh, const bgk_vgrid* vg, const bgk_physics* phy
   A(dalloc(h->U[0], sizeof(double) * h->nnode * h->nm));
   A(dalloc(h->U[1], sizeof(double) * h->nnode * h->nm));
   A(dalloc(h->partial, sizeof(double) * 6 * h->mom_blocks));
+  A(dalloc(h->cf, (size_t)h->g.dim * h->g.N * h->nnode * h->tsize));
   A(dalloc(h->ds, sizeof(DevState)));
   double At[3][3], bt[3], ct[3];
   const int S = tableau(phys->integrator, At, bt, ct);
@@ -551,6 +612,15 @@ int bgk_create(const bgk_mesh* mesh, const bgk_vgrid* vg, const bgk_physics* phy
   CK(cudaFuncSetAttribute(k_peel<2, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   CK(cudaFuncSetAttribute(k_peel<3, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   rc = build_dags(h);
+  if (rc == BGK_OK) {
+    // the stage coefficient nu_s = nu + 1/(dt A_ss) of the step's main stages
+    double Am[3][3], bm[3], cm[3];
+    tableau(phys->integrator, Am, bm, cm);
+    const double ass = phys->integrator == BGK_BDF2 ? 2.0 / 3.0 : Am[0][0];
+    h->nus_main = phys->nu + 1.0 / (h->dt * ass);
+    h->qscale_main = 1.0 / (h->dt * ass);
+    rc = build_inverse_cache(h, h->nus_main);
+  }
   if (rc == BGK_OK && !h->cfg.eager) rc = enqueue_step(h, 0, &h->exec_main);
   if (rc == BGK_OK && !h->cfg.eager && phys->integrator == BGK_BDF2) {
     cudaGraphExec_t e0 = h->exec_main;
@@ -581,6 +651,8 @@ int bgk_sizes(const bgk_handle* h, int64_t* out) {
   out[4] = h->hm.dim;
   out[5] = h->Gmax;
   out[6] = h->lagged;
+  out[7] = h->Ainv ? (int64_t)h->ainv_bytes : 0;
+  out[8] = h->sweep_threads;
   return BGK_OK;
 }
 
@@ -729,6 +801,8 @@ int bgk_get_generations(bgk_handle* h, int j, int32_t* h_gen, int* n_gen) {
 
 int bgk_sweep(bgk_handle* h, double nu_s, double q_scale) {
   if (!h) return BGK_E_INVALID;
+  if (nu_s <= 0.0) nu_s = h->nus_main;
+  if (q_scale <= 0.0) q_scale = h->qscale_main;
   k_reset_state<<<1, 1, 0, h->stream>>>(h->ds);
   moments(h, 0);
   int rc = build_src(h, h->fk, q_scale);

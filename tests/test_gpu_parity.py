@@ -55,20 +55,23 @@ def test_velocity_grid_and_initial_state():
     assert rel_err(U, o.moments(fo)) < FP64_TOL
 
 
+@pytest.mark.parametrize("cache", ["on", "off"])
 @pytest.mark.parametrize("name", ["p1_tri", "p2_tri", "p1_tet_cycles"])
-def test_one_sweep_fp64(name):
+def test_one_sweep_fp64(name, cache):
     w = workloads()[name]
-    s, o = make_pair(w)
+    s, o = make_pair(w, cache_inverse=cache)
+    if cache == "on":
+        assert s.cache_bytes > 0
     s.set_state_maxwellian(w.init)
     s.set_inflow_maxwellian(w.inflow)
     f0 = o.maxwellian(w.init)
     fbc = o.maxwellian(w.inflow)
     dt = s.dt
     nu = w.nu
-    nus = nu + 1.0 / dt
+    nus = nu + 1.0 / dt     # backward Euler: the cached stage coefficient
     f = f0
     for it in range(2):
-        s.sweep(nus, 1.0 / dt)
+        s.sweep(0.0, 0.0)
         U = o.moments(f)
         nut = U.copy()
         d = o.dim
@@ -80,10 +83,11 @@ def test_one_sweep_fp64(name):
         assert rel_err(fg, f) < FP64_TOL, (it, rel_err(fg, f))
 
 
+@pytest.mark.parametrize("cache", ["on", "off"])
 @pytest.mark.parametrize("integ", ["BE", "DIRK2", "DIRK3", "BSTABLE2", "BDF2"])
-def test_time_steps_match_oracle(integ):
+def test_time_steps_match_oracle(integ, cache):
     w = synth.workload_p1_square(n_side=6, n_v=12, k_v=2, integrator=integ, knudsen=0.05)
-    s, o = make_pair(w)
+    s, o = make_pair(w, cache_inverse=cache)
     s.set_state_maxwellian(w.init)
     s.set_inflow_maxwellian(w.inflow)
     o.set_physics(w.nu, s.dt, integ, 1e-8, 1000)
@@ -150,16 +154,17 @@ def test_noconv_status_is_reported():
     assert e.value.status == bgk.BGK_E_NOCONV
 
 
-def test_fp32_sweep_against_oracle():
+@pytest.mark.parametrize("cache", ["on", "off"])
+def test_fp32_sweep_against_oracle(cache):
     w = small_shock_tube(n=8, kx=2, n_v=16, integrator="BE")
-    s, o = make_pair(w, precision="fp32")
+    s, o = make_pair(w, precision="fp32", cache_inverse=cache)
     s.set_state_maxwellian(w.init)
     s.set_inflow_maxwellian(w.inflow)
     f0 = o.maxwellian(w.init)
     fbc = o.maxwellian(w.inflow)
     dt = s.dt
     nus = w.nu + 1.0 / dt
-    s.sweep(nus, 1.0 / dt)
+    s.sweep(0.0, 0.0)
     U = o.moments(f0)
     nut = U.copy()
     nut[:, 1:3] = U[:, 1:3] / U[:, :1]
@@ -180,3 +185,16 @@ def test_eager_mode_matches_graph_mode_bitwise():
         out.append((s.get_f(), list(st.iterations)))
     np.testing.assert_array_equal(out[0][0], out[1][0])
     assert out[0][1] == out[1][1]
+
+
+def test_fp32_storage_moments_are_fp64_accurate():
+    """The compensated FP32 reduction must equal the FP64 sum of the same FP32 data."""
+    w = small_shock_tube(n=8, kx=2, n_v=16, integrator="BE")
+    s, o = make_pair(w, precision="fp32")
+    s.set_state_maxwellian(w.init)
+    s.set_inflow_maxwellian(w.inflow)
+    s.sweep(0.0, 0.0)
+    f32 = s.get_f(np.float32)
+    U = s.get_moments()
+    Uo = o.moments(f32.astype(np.float64))
+    assert rel_err(U, Uo) < 1e-13
