@@ -152,6 +152,37 @@ int bgk_synchronize(bgk_handle* h);
  * count since the last reset, recorded on the handle's stream. */
 int bgk_timing(bgk_handle* h, int reset, double* sweep_ms_total, int64_t* sweep_launches);
 
+/* ---- Batched instances ---------------------------------------------------------------
+ * Many independent problems (own mesh, velocity grid, nu, dt; backward Euler) advanced
+ * together.  Per Picard iteration the sweeps of all instances run as one persistent
+ * kernel over (instance, ordinate-block) units; each instance's Picard loop ends on its
+ * own criterion (Eq. convergence-criteria) and finished instances skip their work; one
+ * CUDA graph (a conditional while-node) covers a whole step.  Results of each instance
+ * are identical to a single-instance run of the same configuration.  Arrays meshes,
+ * vgrids, phys have n entries; cfg applies to all (its stream is shared).  Errors as
+ * bgk_create; BGK_E_INVALID if an integrator is not BGK_BE. */
+typedef struct bgk_batch bgk_batch;
+int bgk_batch_create(int n, const bgk_mesh* meshes, const bgk_vgrid* vgrids, const bgk_physics* phys,
+                     const bgk_config* cfg, bgk_batch** out);
+int bgk_batch_destroy(bgk_batch* b);
+/* The handle of instance i (owned by the batch; use it for bgk_set_*, bgk_get_*). */
+int bgk_batch_instance(bgk_batch* b, int i, bgk_handle** h);
+/* Autotuner: for each instance class (element type, ordinates, log2 cells) time the
+ * batched sweep with 1, 2 and 4 ordinates per CTA (128, 64, 32 threads per ordinate)
+ * over reps launches and keep the fastest (cached per class for the process); f is
+ * restored afterwards.  h_block (optional, n entries) receives the choice. */
+int bgk_batch_autotune(bgk_batch* b, int reps, int32_t* h_block);
+/* nsteps steps of every instance; h_iters / h_status (optional, n entries) receive the
+ * Picard iterations and status of each instance's last step.  Returns the first error. */
+int bgk_batch_step(bgk_batch* b, int nsteps, int32_t* h_iters, int32_t* h_status);
+/* One batched sweep of all instances (Maxwellian of the current moments, q = f^k/dt),
+ * event-timed; bgk_batch_timing returns the accumulated time and launch count. */
+int bgk_batch_sweep(bgk_batch* b);
+int bgk_batch_timing(bgk_batch* b, int reset, double* sweep_ms_total, int64_t* sweep_launches);
+/* out[0] = instances, [1] = total DOF (sum of n_ordinates * n_nodes), [2] = sweep units,
+ * [3] = CTAs of the persistent sweep. */
+int bgk_batch_info(const bgk_batch* b, int64_t* out);
+
 /* Moments and convergence measure with no device allocation.  The paper has no
  * counterpart: this entry point serves callers that cannot call cudaMalloc, such as
  * programs that have given all device memory to their own pool allocator up front,

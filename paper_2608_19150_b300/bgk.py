@@ -84,6 +84,15 @@ def load(path: str = LIB_PATH):
         "bgk_synchronize": [P],
         "bgk_timing": [P, I, C.POINTER(D), C.POINTER(C.c_int64)],
         "bgk_moments_measure_noalloc": [C.POINTER(VGrid), I, C.c_int64, V, I, V, V, V, V],
+        "bgk_batch_create": [I, C.POINTER(Mesh), C.POINTER(VGrid), C.POINTER(Physics), C.POINTER(Config),
+                             C.POINTER(P)],
+        "bgk_batch_destroy": [P],
+        "bgk_batch_instance": [P, I, C.POINTER(P)],
+        "bgk_batch_autotune": [P, I, V],
+        "bgk_batch_step": [P, I, V, V],
+        "bgk_batch_sweep": [P],
+        "bgk_batch_timing": [P, I, C.POINTER(D), C.POINTER(C.c_int64)],
+        "bgk_batch_info": [P, C.POINTER(C.c_int64)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -151,7 +160,25 @@ class Solver:
         args.update(kw)
         return cls(w.mesh.dim, w.kx, w.mesh.xyz, w.mesh.cells, w.n_v, w.k_v, w.L, w.nu, **args)
 
+    @classmethod
+    def wrap(cls, handle, precision, owner):
+        """A view of a handle owned elsewhere (an instance of a Batch)."""
+        self = cls.__new__(cls)
+        self.lib = load()
+        self.h = handle
+        self._owner = owner
+        sz = (C.c_int64 * 9)()
+        _ck(self.lib.bgk_sizes(self.h, sz), "bgk_sizes")
+        (self.nv, self.nnode, self.ndof, self.ncell, self.dim, self.gmax, self.lagged, self.cache_bytes,
+         self.sweep_threads) = (int(x) for x in sz)
+        self.precision = precision
+        self.fdtype = np.float64 if precision == "fp64" else np.float32
+        return self
+
     def close(self):
+        if getattr(self, "_owner", None) is not None:
+            self.h = None
+            return
         if getattr(self, "h", None):
             self.lib.bgk_destroy(self.h)
             self.h = None
@@ -233,3 +260,71 @@ class Solver:
         n = C.c_int64()
         _ck(self.lib.bgk_timing(self.h, int(bool(reset)), C.byref(ms), C.byref(n)), "bgk_timing")
         return ms.value, n.value
+
+
+class Batch:
+    """Many independent backward-Euler problems advanced together (bgk_batch_*)."""
+
+    def __init__(self, workloads, precision="fp64", tau=1e-8, l_max=1000, cache_inverse="auto", dt=None):
+        self.lib = load()
+        n = len(workloads)
+        self._keep = []
+        meshes = (Mesh * n)()
+        vgrids = (VGrid * n)()
+        phys = (Physics * n)()
+        for i, w in enumerate(workloads):
+            xyz = np.ascontiguousarray(w.mesh.xyz, dtype=np.float64)
+            cells = np.ascontiguousarray(w.mesh.cells, dtype=np.int32)
+            self._keep += [xyz, cells]
+            meshes[i] = Mesh(w.mesh.dim, w.kx, xyz.shape[0], _ptr(xyz), cells.shape[0], _ptr(cells))
+            vgrids[i] = VGrid(float(w.L), int(w.n_v), int(w.k_v))
+            phys[i] = Physics(float(w.nu), INTEGRATORS["BE"], float(dt[i]) if dt else 0.0, float(w.cfl))
+        cf = Config(float(tau), int(l_max), PRECISIONS[precision], 0, None, 0,
+                    {"auto": 0, "on": 1, "off": 2}[cache_inverse])
+        h = C.c_void_p()
+        _ck(self.lib.bgk_batch_create(n, meshes, vgrids, phys, C.byref(cf), C.byref(h)), "bgk_batch_create")
+        self.h = h
+        self.n = n
+        self.precision = precision
+        self.instances = []
+        for i in range(n):
+            hi = C.c_void_p()
+            _ck(self.lib.bgk_batch_instance(self.h, i, C.byref(hi)), "bgk_batch_instance")
+            self.instances.append(Solver.wrap(hi, precision, self))
+
+    def close(self):
+        if getattr(self, "h", None):
+            for s in self.instances:
+                s.h = None
+            self.lib.bgk_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def autotune(self, reps=3):
+        out = np.zeros(self.n, dtype=np.int32)
+        _ck(self.lib.bgk_batch_autotune(self.h, int(reps), _ptr(out)), "bgk_batch_autotune")
+        return out
+
+    def step(self, nsteps=1, check=True):
+        it = np.zeros(self.n, dtype=np.int32)
+        st = np.zeros(self.n, dtype=np.int32)
+        rc = self.lib.bgk_batch_step(self.h, int(nsteps), _ptr(it), _ptr(st))
+        if check:
+            _ck(rc, "bgk_batch_step")
+        return it, st
+
+    def sweep(self):
+        _ck(self.lib.bgk_batch_sweep(self.h), "bgk_batch_sweep")
+
+    def timing(self, reset=False):
+        ms = C.c_double()
+        n = C.c_int64()
+        _ck(self.lib.bgk_batch_timing(self.h, int(bool(reset)), C.byref(ms), C.byref(n)), "bgk_batch_timing")
+        return ms.value, n.value
+
+    def info(self):
+        out = (C.c_int64 * 4)()
+        _ck(self.lib.bgk_batch_info(self.h, out), "bgk_batch_info")
+        return dict(instances=out[0], dof=out[1], units=out[2], ctas=out[3])

@@ -18,6 +18,8 @@ struct DevState {
   double meas[4];
   int total_sweeps;
   int cont;          // the stage loop continues (read by the host in eager mode)
+  int done;          // the stage loop of this problem has ended (batched runs skip it)
+  int pad;
 };
 
 __device__ __forceinline__ void ordinate(const VGrid& g, int j, double (&v)[3]) {
@@ -229,7 +231,7 @@ struct InnerSums<float> {
 template <typename T>
 __global__ void k_moments(VGrid g, const T* __restrict__ f, int nnode, double* U0, double* U1, const DevState* ds,
                           int mode, double* __restrict__ partial) {
-  if (ds->status != BGK_OK) return;
+  if (ds->status != BGK_OK || ds->done) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int nm = g.dim + 2;
   double acc[5] = {0, 0, 0, 0, 0};
@@ -312,7 +314,7 @@ __global__ void k_moments(VGrid g, const T* __restrict__ f, int nnode, double* U
 template <typename T>
 __global__ void k_factors(VGrid g, int nnode, const double* __restrict__ U0, const double* __restrict__ U1,
                           DevState* ds, double coef, T* __restrict__ cf) {
-  if (ds->status != BGK_OK) return;
+  if (ds->status != BGK_OK || ds->done) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nnode) return;
   const int nm = g.dim + 2;
@@ -344,7 +346,7 @@ __global__ void k_factors(VGrid g, int nnode, const double* __restrict__ U0, con
 template <typename T>
 __global__ void k_source(VGrid g, int nnode, const T* __restrict__ cf, const T* __restrict__ q, T qscale,
                          T* __restrict__ src, const DevState* ds) {
-  if (ds->status != BGK_OK) return;
+  if (ds->status != BGK_OK || ds->done) return;
   const size_t total = (size_t)g.nv * nnode;
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
     const int j = (int)(t / nnode);
@@ -367,7 +369,7 @@ __global__ void k_finalize(DevState* ds, const double* __restrict__ partial, int
                            cudaGraphConditionalHandle cond, int use_cond) {
   __shared__ double red[6][256];
   double s[6] = {0, 0, 0, 0, 0, 0};
-  const bool skip = ds->status != BGK_OK;
+  const bool skip = ds->status != BGK_OK || ds->done;
   if (!skip)
     for (int b = threadIdx.x; b < nblk; b += blockDim.x)
       for (int k = 0; k < 6; ++k) s[k] += partial[(size_t)b * 6 + k];
@@ -400,12 +402,15 @@ __global__ void k_finalize(DevState* ds, const double* __restrict__ partial, int
     }
   }
   ds->cont = cont;
+  ds->done = !cont;
   if (use_cond) cudaGraphSetConditional(cond, cont);
 }
 
 __global__ void k_stage_begin(DevState* ds, int stage) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     ds->stage_it = 0;
+    ds->done = 0;
+    ds->cont = 1;
     ds->iters[stage] = 0;
     ds->meas[stage] = 0.0;
   }
@@ -415,6 +420,7 @@ __global__ void k_reset_state(DevState* ds) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     ds->status = BGK_OK;
     ds->err = 0;
+    ds->done = 0;
     for (int s = 0; s < 4; ++s) {
       ds->iters[s] = 0;
       ds->meas[s] = 0.0;
@@ -623,9 +629,22 @@ __device__ __forceinline__ void fetch_item(const SweepArgs& sa, const uint32_t* 
   for (int a = 0; a < E::NDOF; ++a) it.src[a] = sj[(size_t)c * E::NDOF + a];
 }
 
-// One transport sweep (Sec. 4, Eq. bgk-ss-picard), one CTA per ordinate walking that
-// ordinate's generations; the cells of a generation are independent and share the
-// CTA's threads.  For cell K and ordinate j (s_i = v_j . N_i, r_i = s_i/|K|):
+// Barrier of the threads that share one ordinate's sweep: the whole CTA, or a named
+// barrier over a sub-group of `count` threads (a multiple of 32).
+struct CtaBarrier {
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+struct NamedBarrier {
+  int id, count;
+  __device__ __forceinline__ void sync() const {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+  }
+};
+
+// One ordinate's transport sweep (Sec. 4, Eq. bgk-ss-picard) by a group of `nt` threads
+// (thread `tid` of the group) walking the ordinate's generations; the cells of one
+// generation are independent and share the group's threads.  For cell K and ordinate j
+// (s_i = v_j . N_i, r_i = s_i/|K|):
 //   (nu_s Mh + sum_i r_i (Dd_i + [s_i>0] Eh_i)) f_K = Mh src_K + sum_{s_i<0} (-r_i) Eh_i y_i
 // where src = nu M^l + q and y_i is the upwind trace: the neighbour's value in f,
 // updated in place.  An upwind cell reached by a lagged (cycle) edge has a higher
@@ -634,13 +653,11 @@ __device__ __forceinline__ void fetch_item(const SweepArgs& sa, const uint32_t* 
 // otherwise the matrix is assembled and factorised in place.  The schedule entry, the
 // neighbour ids, the node permutation and src of the thread's next item are loaded
 // before the current item is solved (they are not written during the sweep).
-template <class E, typename T, bool CACHED>
-__global__ void __launch_bounds__(256) k_sweep(SweepArgs sa, VGrid g, T nus, const T* __restrict__ src,
-                                               const T* __restrict__ fbc, const T* __restrict__ Ainv, T* f,
-                                               const DevState* ds) {
-  constexpr int D = E::D, ND = E::NDOF, NF = E::NF, FD = E::FD;
-  if (ds && ds->status != BGK_OK) return;
-  const int j = blockIdx.x;
+template <class E, typename T, bool CACHED, class Bar>
+__device__ __forceinline__ void sweep_ordinate(const SweepArgs& sa, const VGrid& g, int j, T nus,
+                                               const T* __restrict__ src, const T* __restrict__ fbc,
+                                               const T* __restrict__ Ainv, T* f, int tid, int nt, const Bar& bar) {
+  constexpr int ND = E::NDOF, NF = E::NF, FD = E::FD;
   double vd[3];
   ordinate(g, j, vd);
   const T v0 = (T)vd[0], v1 = (T)vd[1], v2 = (T)vd[2];
@@ -651,7 +668,6 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs sa, VGrid g, T nus, con
   T* fj = f + (size_t)j * sa.nnode;
   const T* sj = src + (size_t)j * sa.nnode;
   const T* bj = fbc + (size_t)j * sa.nbface * FD;
-  const int bd = blockDim.x, tid = threadIdx.x;
   int lo = lv[0], hi = G > 0 ? lv[1] : lv[0];
   int k = lo + tid;
   SweepItem<E, T> cur, nxt;
@@ -661,7 +677,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs sa, VGrid g, T nus, con
   for (int gg = 0; gg < G; ++gg) {
     while (have) {
       // prefetch the thread's next item: same generation, else the next generation
-      int kn = k + bd;
+      int kn = k + nt;
       bool same = kn < hi;
       if (!same && gg + 1 < G) {
         kn = hi + tid;
@@ -722,7 +738,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs sa, VGrid g, T nus, con
         if (kn >= 0) cur = nxt;
       }
     }
-    __syncthreads();
+    bar.sync();
     lo = hi;
     hi = gg + 1 < G ? lv[gg + 2] : hi;
     if (kpend >= 0) {
@@ -735,6 +751,16 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs sa, VGrid g, T nus, con
     }
     kpend = -1;
   }
+}
+
+// One sweep of every ordinate of one problem: one CTA per ordinate.
+template <class E, typename T, bool CACHED>
+__global__ void __launch_bounds__(256) k_sweep(SweepArgs sa, VGrid g, T nus, const T* __restrict__ src,
+                                               const T* __restrict__ fbc, const T* __restrict__ Ainv, T* f,
+                                               const DevState* ds) {
+  if (ds && (ds->status != BGK_OK || ds->done)) return;
+  sweep_ordinate<E, T, CACHED>(sa, g, (int)blockIdx.x, nus, src, fbc, Ainv, f, (int)threadIdx.x, (int)blockDim.x,
+                               CtaBarrier());
 }
 
 // out = a_k * fk + a_f * f + sum_r cF[r] * F[r]   (stage bookkeeping of Sec. 3.5)

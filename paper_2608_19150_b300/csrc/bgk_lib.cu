@@ -4,7 +4,11 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -889,3 +893,5 @@ int bgk_timing(bgk_handle* h, int reset, double* sweep_ms_total, int64_t* sweep_
 }
 
 }  // extern "C"
+
+#include "bgk_batch.cuh"
