@@ -638,12 +638,12 @@ static void dense_solve(int n, double *A, double *b) {
  * for every ordinate j, cells visited in ascending (generation, id).  fold = f^l,
  * fnew = f^{l+1}; Mn = nodal Maxwellian; q = stage source; fbc = boundary values,
  * all [j][cell][node]. */
-static void sweep_range(const orc_t *o, const double *fold, const double *Mn, const double *q, const double *fbc,
-                        double nu, double nu_s, double *fnew, int j0, int j1) {
+static void sweep_ordinate(const orc_t *o, int j, const double *fold, const double *Mn, const double *q,
+                           const double *fbc, double nu, double nu_s, double *fnew) {
   int d = o->dim, nd = o->ndof, nf = o->nface;
-  for (int j = j0; j < j1; ++j) {
+  {
     const double *v = o->v + (size_t)j * d;
-    size_t base = (size_t)j * o->nnode;
+    size_t base = 0; /* every array argument is the row of ordinate j */
     const unsigned char *lag = o->lagged + (size_t)j * o->ncell * nf;
     for (int k = 0; k < o->ncell; ++k) {
       int c = o->order[(size_t)j * o->ncell + k];
@@ -691,6 +691,14 @@ static void sweep_range(const orc_t *o, const double *fold, const double *Mn, co
       for (int a = 0; a < nd; ++a) fnew[base + (size_t)c * nd + a] = b[a];
     }
   }
+}
+
+static void sweep_range(const orc_t *o, const double *fold, const double *Mn, const double *q, const double *fbc,
+                        double nu, double nu_s, double *fnew, int j0, int j1) {
+  size_t nn = (size_t)o->nnode;
+  for (int j = j0; j < j1; ++j)
+    sweep_ordinate(o, j, fold + (size_t)j * nn, Mn + (size_t)j * nn, q + (size_t)j * nn, fbc + (size_t)j * nn, nu,
+                   nu_s, fnew + (size_t)j * nn);
 }
 
 static void sweep(const orc_t *o, const double *fold, const double *Mn, const double *q, const double *fbc,
@@ -808,8 +816,9 @@ void orc_maxwellian(const orc_t *o, const double *nut, double *out) {
 
 void orc_moments(const orc_t *o, const double *f, double *U) { moments(o, f, U); }
 
-/* Build every ordinate's DAG; returns total lagged edges, or -1 on failure. */
-long orc_build_dags(orc_t *o) {
+/* Build the DAGs of the listed ordinates (all when js == NULL); returns the total of
+ * lagged edges, or -1 on failure.  Ordinates not listed are left unbuilt. */
+long orc_build_dags_for(orc_t *o, const int *js, int nj) {
   int n = o->ncell;
   size_t nv = o->nv;
   free(o->gen); free(o->order); free(o->lagged); free(o->ngen);
@@ -825,8 +834,10 @@ long orc_build_dags(orc_t *o) {
   int *comp = malloc(sizeof(int) * n), *state = malloc(sizeof(int) * n), *stk = malloc(sizeof(int) * n);
   int *it = malloc(sizeof(int) * n), *indeg = malloc(sizeof(int) * n);
   long total = 0;
-  for (size_t j = 0; j < nv; ++j) {
-    int r = build_dag(o, (int)j, &g, work, comp, state, stk, it, indeg);
+  size_t cnt = js ? (size_t)nj : nv;
+  for (size_t k = 0; k < cnt; ++k) {
+    int j = js ? js[k] : (int)k;
+    int r = build_dag(o, j, &g, work, comp, state, stk, it, indeg);
     if (r < 0) { total = -1; break; }
     total += r;
   }
@@ -834,6 +845,8 @@ long orc_build_dags(orc_t *o) {
   o->n_lagged_total = total;
   return total;
 }
+
+long orc_build_dags(orc_t *o) { return orc_build_dags_for(o, NULL, 0); }
 
 int orc_generations(const orc_t *o, int j, int *gen, unsigned char *lagged) {
   memcpy(gen, o->gen + (size_t)j * o->ncell, sizeof(int) * o->ncell);
@@ -856,6 +869,34 @@ void orc_sweep(const orc_t *o, const double *fold, const double *Mn, const doubl
 void orc_sweep_range(const orc_t *o, const double *fold, const double *Mn, const double *q, const double *fbc,
                      double nu, double nu_s, double *fnew, int j0, int j1) {
   sweep_range(o, fold, Mn, q, fbc, nu, nu_s, fnew, j0, j1);
+}
+
+/* Projected Maxwellian of the nodal states for the listed ordinates only:
+ * out[r][node] for j = js[r], r < nj. */
+void orc_maxwellian_rows(const orc_t *o, const double *nut, const int *js, int nj, double *out) {
+  int d = o->dim, N = o->n1d, nm = d + 2;
+  double c[3][64];
+  for (int i = 0; i < o->nnode; ++i) {
+    const double *p = nut + (size_t)i * nm;
+    for (int al = 0; al < d; ++al) project_1d(o, p[1 + al], p[1 + d], c[al]);
+    for (int r = 0; r < nj; ++r) {
+      int jj = js[r], ja[3];
+      for (int al = d - 1; al >= 0; --al) { ja[al] = jj % N; jj /= N; }
+      double m = p[0];
+      for (int al = 0; al < d; ++al) m *= c[al][ja[al]];
+      out[(size_t)r * o->nnode + i] = m;
+    }
+  }
+}
+
+/* One sweep for the listed ordinates only; all arrays hold just those rows
+ * ([nj][nnode]); the graphs must have been built. */
+void orc_sweep_rows(const orc_t *o, const int *js, int nj, const double *fold, const double *Mn, const double *q,
+                    const double *fbc, double nu, double nu_s, double *fnew) {
+  size_t nn = (size_t)o->nnode;
+  for (int r = 0; r < nj; ++r)
+    sweep_ordinate(o, js[r], fold + (size_t)r * nn, Mn + (size_t)r * nn, q + (size_t)r * nn, fbc + (size_t)r * nn, nu,
+                   nu_s, fnew + (size_t)r * nn);
 }
 
 /* explicit time-step bound (Sec. 5): dt_e = (1/d) (1/(2 kx + 1)) h_min / max_j |v_j|,

@@ -56,11 +56,15 @@ def _load():
         lib.orc_moments.argtypes = [P, dp, dp]
         lib.orc_build_dags.restype = C.c_long
         lib.orc_build_dags.argtypes = [P]
+        lib.orc_build_dags_for.restype = C.c_long
+        lib.orc_build_dags_for.argtypes = [P, ip, C.c_int]
         lib.orc_generations.restype = C.c_int
         lib.orc_generations.argtypes = [P, C.c_int, ip, up]
         lib.orc_face_signs.argtypes = [P, C.c_int, ip]
         lib.orc_sweep.argtypes = [P, dp, dp, dp, dp, C.c_double, C.c_double, dp]
         lib.orc_sweep_range.argtypes = [P, dp, dp, dp, dp, C.c_double, C.c_double, dp, C.c_int, C.c_int]
+        lib.orc_maxwellian_rows.argtypes = [P, dp, ip, C.c_int, dp]
+        lib.orc_sweep_rows.argtypes = [P, ip, C.c_int, dp, dp, dp, dp, C.c_double, C.c_double, dp]
         lib.orc_dt_explicit.restype = C.c_double
         lib.orc_dt_explicit.argtypes = [P]
         lib.orc_tableau.restype = C.c_int
@@ -139,6 +143,23 @@ class Oracle:
         self.lib.orc_maxwellian(self.h, np.ascontiguousarray(nut, dtype=np.float64), out)
         return out
 
+    def maxwellian_rows(self, nut, js):
+        """Projected Maxwellian for the ordinates js only: [len(js), nnode]."""
+        js = np.ascontiguousarray(js, dtype=np.int32)
+        out = np.zeros((len(js), self.nnode))
+        self.lib.orc_maxwellian_rows(self.h, np.ascontiguousarray(nut, dtype=np.float64), js, len(js), out)
+        return out
+
+    def sweep_rows(self, js, fold, Mn, q, fbc, nu, nu_s):
+        """One sweep of the ordinates js; every array holds only those rows."""
+        if not self._dags:
+            self.build_dags()
+        js = np.ascontiguousarray(js, dtype=np.int32)
+        c = lambda a: np.ascontiguousarray(a, dtype=np.float64).reshape(len(js), self.nnode)  # noqa: E731
+        fnew = np.zeros((len(js), self.nnode))
+        self.lib.orc_sweep_rows(self.h, js, len(js), c(fold), c(Mn), c(q), c(fbc), float(nu), float(nu_s), fnew)
+        return fnew
+
     def moments(self, f):
         U = np.zeros((self.nnode, self.dim + 2))
         self.lib.orc_moments(self.h, np.ascontiguousarray(f, dtype=np.float64), U)
@@ -150,6 +171,15 @@ class Oracle:
     # --- sweep graphs --------------------------------------------------------------
     def build_dags(self):
         n = self.lib.orc_build_dags(self.h)
+        if n < 0:
+            raise RuntimeError("oracle DAG construction failed")
+        self._dags = True
+        return int(n)
+
+    def build_dags_for(self, js):
+        """Build the sweep graphs of the ordinates js only (for sampled full-size checks)."""
+        js = np.ascontiguousarray(js, dtype=np.int32)
+        n = self.lib.orc_build_dags_for(self.h, js, len(js))
         if n < 0:
             raise RuntimeError("oracle DAG construction failed")
         self._dags = True

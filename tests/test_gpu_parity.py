@@ -188,13 +188,14 @@ def test_eager_mode_matches_graph_mode_bitwise():
 
 
 def test_fp32_storage_moments_are_fp64_accurate():
-    """The compensated FP32 reduction must equal the FP64 sum of the same FP32 data."""
+    """The compensated FP32 reduction must equal the FP64 sum of the same FP32 data
+    (a seeded FP32 distribution: a Maxwellian-like profile times a random factor)."""
     w = small_shock_tube(n=8, kx=2, n_v=16, integrator="BE")
     s, o = make_pair(w, precision="fp32")
-    s.set_state_maxwellian(w.init)
-    s.set_inflow_maxwellian(w.inflow)
-    s.sweep(0.0, 0.0)
-    f32 = s.get_f(np.float32)
+    f0 = o.maxwellian(w.init)
+    r = synth.splitmix64_uniform(77, f0.size).reshape(f0.shape)
+    f32 = (f0 * (0.5 + r)).astype(np.float32)
+    s.set_f(f32)
     U = s.get_moments()
     Uo = o.moments(f32.astype(np.float64))
     assert rel_err(U, Uo) < 1e-13
