@@ -183,6 +183,43 @@ int bgk_batch_timing(bgk_batch* b, int reset, double* sweep_ms_total, int64_t* s
  * [3] = CTAs of the persistent sweep. */
 int bgk_batch_info(const bgk_batch* b, int64_t* out);
 
+/* ---- Learned initial guess (an addition beside the paper's method) ------------------
+ * A multilayer perceptron F -> H -> H -> H -> O (tanh on the hidden layers, inputs and
+ * outputs normalised column-wise) predicts, for every spatial node, the change of
+ * q = (log n, u, log theta) over a stage from features of the stage-start moments.  With
+ * a network attached (bgk_set_guess), each stage's iterate 0 takes the predicted moments
+ * (nodes with a non-physical prediction keep their own); the Picard loop of Sec. 4 then
+ * runs to the usual criterion, so the converged state is the solver's, not the network's.
+ * Parameters, host or device float arrays, flat in the order W0 [H][F], b0 [H], W1 [H][H],
+ * b1, W2 [H][H], b2, W3 [O][H], b3 [O]; normalisation [mu_x (F), sd_x (F), mu_y (O),
+ * sd_y (O)].  Training runs in FP32 on the current device's default stream; attached
+ * networks run with BF16-stored weights and FP32 accumulation inside the step graph.
+ * A network's scratch is shared: do not run two handles with the same network at once.
+ * F, H, O <= 128.  Features per node (d = dimension, s = sqrt(theta)): q | s dt grad log n |
+ * dt grad u | s dt grad log theta | log10(nu dt) | change of q over the previous stage. */
+typedef struct bgk_mlp bgk_mlp;
+int bgk_mlp_create(int n_in, int n_hidden, int n_out, uint64_t seed, bgk_mlp** out);
+int bgk_mlp_destroy(bgk_mlp* m);
+int bgk_mlp_num_params(const bgk_mlp* m, int64_t* n);
+int bgk_mlp_get_params(const bgk_mlp* m, float* h_params, float* h_norm);
+int bgk_mlp_set_params(bgk_mlp* m, const float* h_params, const float* h_norm);
+/* normalisation from data: column means and standard deviations of d_X [n][F], d_Y [n][O] */
+int bgk_mlp_fit_norm(bgk_mlp* m, const float* d_X, const float* d_Y, int64_t n);
+/* mean squared error on normalised outputs and its gradient (h_grad: host, optional) */
+int bgk_mlp_loss_grad(bgk_mlp* m, const float* d_X, const float* d_Y, int64_t n, double* loss, float* h_grad);
+/* one Adam step (beta 0.9, 0.999, eps 1e-8) on the batch; *loss is before the step */
+int bgk_mlp_train_step(bgk_mlp* m, const float* d_X, const float* d_Y, int64_t n, float lr, double* loss);
+/* de-normalised outputs d_Y [n][O]; bf16 != 0 uses BF16-stored weights */
+int bgk_mlp_predict(bgk_mlp* m, const float* d_X, int64_t n, float* d_Y, int bf16);
+/* feature and output counts of the handle's network: F = guess features, O = dim + 2 */
+int bgk_guess_dims(const bgk_handle* h, int* n_features, int* n_outputs);
+/* features of the current state into d_X [n_nodes][F] (device); records the history */
+int bgk_guess_features(bgk_handle* h, float* d_X);
+/* training targets: change of q from d_Ustart (device moments) to the current moments */
+int bgk_guess_targets(bgk_handle* h, const double* d_Ustart, float* d_Y);
+/* attach (or with NULL detach) a network; its current parameters are copied to BF16 */
+int bgk_set_guess(bgk_handle* h, bgk_mlp* m);
+
 /* Moments and convergence measure with no device allocation.  The paper has no
  * counterpart: this entry point serves callers that cannot call cudaMalloc, such as
  * programs that have given all device memory to their own pool allocator up front,

@@ -93,6 +93,19 @@ def load(path: str = LIB_PATH):
         "bgk_batch_sweep": [P],
         "bgk_batch_timing": [P, I, C.POINTER(D), C.POINTER(C.c_int64)],
         "bgk_batch_info": [P, C.POINTER(C.c_int64)],
+        "bgk_mlp_create": [I, I, I, C.c_uint64, C.POINTER(P)],
+        "bgk_mlp_destroy": [P],
+        "bgk_mlp_num_params": [P, C.POINTER(C.c_int64)],
+        "bgk_mlp_get_params": [P, V, V],
+        "bgk_mlp_set_params": [P, V, V],
+        "bgk_mlp_fit_norm": [P, V, V, C.c_int64],
+        "bgk_mlp_loss_grad": [P, V, V, C.c_int64, C.POINTER(D), V],
+        "bgk_mlp_train_step": [P, V, V, C.c_int64, C.c_float, C.POINTER(D)],
+        "bgk_mlp_predict": [P, V, C.c_int64, V, I],
+        "bgk_guess_dims": [P, C.POINTER(I), C.POINTER(I)],
+        "bgk_guess_features": [P, V],
+        "bgk_guess_targets": [P, V, V],
+        "bgk_set_guess": [P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -261,6 +274,22 @@ class Solver:
         _ck(self.lib.bgk_timing(self.h, int(bool(reset)), C.byref(ms), C.byref(n)), "bgk_timing")
         return ms.value, n.value
 
+    # ---- learned initial guess
+    def guess_dims(self):
+        f, o = C.c_int(), C.c_int()
+        _ck(self.lib.bgk_guess_dims(self.h, C.byref(f), C.byref(o)), "bgk_guess_dims")
+        return f.value, o.value
+
+    def guess_features(self, d_X_ptr):
+        _ck(self.lib.bgk_guess_features(self.h, C.c_void_p(d_X_ptr)), "bgk_guess_features")
+
+    def guess_targets(self, d_Ustart_ptr, d_Y_ptr):
+        _ck(self.lib.bgk_guess_targets(self.h, C.c_void_p(d_Ustart_ptr), C.c_void_p(d_Y_ptr)), "bgk_guess_targets")
+
+    def set_guess(self, mlp):
+        self._guess = mlp
+        _ck(self.lib.bgk_set_guess(self.h, mlp.h if mlp is not None else None), "bgk_set_guess")
+
 
 class Batch:
     """Many independent backward-Euler problems advanced together (bgk_batch_*)."""
@@ -328,3 +357,58 @@ class Batch:
         out = (C.c_int64 * 4)()
         _ck(self.lib.bgk_batch_info(self.h, out), "bgk_batch_info")
         return dict(instances=out[0], dof=out[1], units=out[2], ctas=out[3])
+
+
+class MLP:
+    """The guess network (bgk_mlp_*): FP32 training kernels, BF16 inference."""
+
+    def __init__(self, n_in, n_out, n_hidden=128, seed=0):
+        self.lib = load()
+        h = C.c_void_p()
+        _ck(self.lib.bgk_mlp_create(int(n_in), int(n_hidden), int(n_out), C.c_uint64(seed), C.byref(h)),
+            "bgk_mlp_create")
+        self.h = h
+        self.F, self.H, self.O = int(n_in), int(n_hidden), int(n_out)
+        n = C.c_int64()
+        _ck(self.lib.bgk_mlp_num_params(self.h, C.byref(n)), "bgk_mlp_num_params")
+        self.n_params = n.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.bgk_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def get_params(self):
+        p = np.empty(self.n_params, dtype=np.float32)
+        nrm = np.empty(2 * self.F + 2 * self.O, dtype=np.float32)
+        _ck(self.lib.bgk_mlp_get_params(self.h, _ptr(p), _ptr(nrm)), "bgk_mlp_get_params")
+        return p, nrm
+
+    def set_params(self, p=None, norm=None):
+        pp = None if p is None else np.ascontiguousarray(p, dtype=np.float32)
+        nn = None if norm is None else np.ascontiguousarray(norm, dtype=np.float32)
+        _ck(self.lib.bgk_mlp_set_params(self.h, _ptr(pp) if pp is not None else None,
+                                        _ptr(nn) if nn is not None else None), "bgk_mlp_set_params")
+
+    def fit_norm(self, X_ptr, Y_ptr, n):
+        _ck(self.lib.bgk_mlp_fit_norm(self.h, C.c_void_p(X_ptr), C.c_void_p(Y_ptr), int(n)), "bgk_mlp_fit_norm")
+
+    def loss_grad(self, X_ptr, Y_ptr, n):
+        loss = C.c_double()
+        g = np.empty(self.n_params, dtype=np.float32)
+        _ck(self.lib.bgk_mlp_loss_grad(self.h, C.c_void_p(X_ptr), C.c_void_p(Y_ptr), int(n), C.byref(loss), _ptr(g)),
+            "bgk_mlp_loss_grad")
+        return loss.value, g
+
+    def train_step(self, X_ptr, Y_ptr, n, lr):
+        loss = C.c_double()
+        _ck(self.lib.bgk_mlp_train_step(self.h, C.c_void_p(X_ptr), C.c_void_p(Y_ptr), int(n), C.c_float(lr),
+                                        C.byref(loss)), "bgk_mlp_train_step")
+        return loss.value
+
+    def predict(self, X_ptr, n, Y_ptr, bf16=True):
+        _ck(self.lib.bgk_mlp_predict(self.h, C.c_void_p(X_ptr), int(n), C.c_void_p(Y_ptr), int(bool(bf16))),
+            "bgk_mlp_predict")

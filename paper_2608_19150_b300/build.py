@@ -13,7 +13,7 @@ LIB = os.path.join(HERE, "libbgk_b300.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-SOURCES = ["bgk_lib.cu", "bgk_batch.cuh", "bgk_static.cu", "bgk_host.cpp", "bgk_kernels.cuh", "bgk_internal.h", "bgk_tables.h"]
+SOURCES = ["bgk_lib.cu", "bgk_batch.cuh", "bgk_mlp.cuh", "bgk_guess.cuh", "bgk_static.cu", "bgk_host.cpp", "bgk_kernels.cuh", "bgk_internal.h", "bgk_tables.h"]
 
 
 def _stale() -> bool:

@@ -70,6 +70,12 @@ struct bgk_handle {
   cudaGraphExec_t exec_main = nullptr;   // the integrator's step
   cudaGraphExec_t exec_start = nullptr;  // BDF2 start-up step (backward Euler)
   // timing of bgk_sweep launches
+  // learned initial guess (optional): network, its inputs/outputs and the stage history
+  struct bgk_mlp* guess = nullptr;
+  float* gX = nullptr;
+  float* gY = nullptr;
+  double* Uhist = nullptr;
+  int* have_hist = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   double sweep_ms = 0.0;
   int64_t sweep_launches = 0;
@@ -77,6 +83,8 @@ struct bgk_handle {
 };
 
 namespace {
+
+int guess_hook(bgk_handle* h);  // learned initial guess at a stage start (bgk_mlp.cuh)
 
 int tableau(int integ, double A[3][3], double b[3], double c[3]) {
   std::memset(A, 0, sizeof(double) * 9);
@@ -334,6 +342,10 @@ int enqueue_step(bgk_handle* h, int mode_bdf2, cudaGraphExec_t* exec_out) {
     }
     k_stage_begin<<<1, 1, 0, s>>>(h->ds, st);
     moments(h, 0);
+    if (h->guess) {
+      int rg = guess_hook(h);
+      if (rg != BGK_OK) return rg;
+    }
     if (capture) {
       // while (cond) { src; sweep; moments; finalize }
       cudaGraph_t cg;
@@ -469,7 +481,8 @@ void release(bgk_handle* h) {
   cudaStreamSynchronize(h->stream);
   if (h->exec_main) cudaGraphExecDestroy(h->exec_main);
   if (h->exec_start) cudaGraphExecDestroy(h->exec_start);
-  void* ptrs[] = {h->geo, h->nbr, h->nbr_face, h->perm, h->bnode, h->glist, h->lvl, h->ngen, h->nproc, h->Ainv, h->f, h->fk,
+  void* ptrs[] = {h->gX, h->gY, h->Uhist, h->have_hist,
+                  h->geo, h->nbr, h->nbr_face, h->perm, h->bnode, h->glist, h->lvl, h->ngen, h->nproc, h->Ainv, h->f, h->fk,
                   h->fprev, h->src, h->fbc, h->q, h->F[0], h->F[1], h->F[2], h->U[0], h->U[1], h->partial, h->cf,
                   h->ds};
   for (void* p : ptrs)
@@ -695,6 +708,7 @@ static int set_maxwellian(bgk_handle* h, const double* h_nut, bool inflow) {
           cudaMemcpyAsync(h->fk, h->f, h->nfv * h->tsize, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
         rc = BGK_E_CUDA;
       h->have_prev = false;
+      if (h->have_hist) cudaMemsetAsync(h->have_hist, 0, sizeof(int), h->stream);
     }
   }
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) rc = BGK_E_CUDA;
@@ -895,3 +909,5 @@ int bgk_timing(bgk_handle* h, int reset, double* sweep_ms_total, int64_t* sweep_
 }  // extern "C"
 
 #include "bgk_batch.cuh"
+#include "bgk_mlp.cuh"
+#include "bgk_guess.cuh"

@@ -1,0 +1,104 @@
+"""The learned initial guess: the network's own GPU kernels against the FP64 numpy
+reference (loss, every parameter gradient, predictions), and the gain of the trained
+guess in Picard iterations on held-out runs with unchanged converged results."""
+import numpy as np
+import pytest
+
+from oracle import mlp_oracle as M
+from paper_2608_19150_b300 import bgk, guess, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _seeded_problem(F=17, H=128, O=4, n=700, seed=5):
+    r = synth.splitmix64_uniform(seed, 10 ** 6)
+    npar = H * F + H + 2 * (H * H + H) + O * H + O
+    p = ((r[:npar] - 0.5) * 0.4).astype(np.float32)
+    norm = np.concatenate([r[npar:npar + F] - 0.5, 0.5 + r[npar + F:npar + 2 * F],
+                           r[npar + 2 * F:npar + 2 * F + O] - 0.5, 0.5 + r[npar + 2 * F + O:npar + 2 * F + 2 * O]])
+    k = npar + 2 * F + 2 * O
+    X = ((r[k:k + n * F] - 0.5) * 4).reshape(n, F).astype(np.float32)
+    Y = ((r[k + n * F:k + n * F + n * O] - 0.5) * 2).reshape(n, O).astype(np.float32)
+    return p, norm.astype(np.float32), X, Y
+
+
+def test_mlp_loss_and_gradients_match_reference():
+    import torch
+    F, H, O, n = 17, 128, 4, 700     # 700 rows: ragged against the 32- and 64-row tiles
+    p, norm, X, Y = _seeded_problem(F, H, O, n)
+    m = bgk.MLP(F, O, H, seed=1)
+    assert m.n_params == p.size
+    m.set_params(p, norm)
+    Xd = torch.from_numpy(X).cuda()
+    Yd = torch.from_numpy(Y).cuda()
+    loss, g = m.loss_grad(Xd.data_ptr(), Yd.data_ptr(), n)
+    lo, go = M.loss_grad(p.astype(np.float64), norm.astype(np.float64), X.astype(np.float64),
+                         Y.astype(np.float64), F, H, O)
+    assert abs(loss - lo) <= 1e-5 * lo
+    # FP32 accumulation over 700 rows: compare against the gradient's scale
+    assert np.abs(g - go).max() <= 2e-5 * np.abs(go).max()
+    Yp = torch.empty((n, O), dtype=torch.float32, device="cuda")
+    m.predict(Xd.data_ptr(), n, Yp.data_ptr(), bf16=False)
+    yo = M.predict(p.astype(np.float64), norm.astype(np.float64), X.astype(np.float64), F, H, O)
+    assert np.abs(Yp.cpu().numpy() - yo).max() <= 1e-4 * np.abs(yo).max()
+    m.predict(Xd.data_ptr(), n, Yp.data_ptr(), bf16=True)
+    assert np.abs(Yp.cpu().numpy() - yo).max() <= 5e-2 * np.abs(yo).max()
+
+
+def test_adam_step_reduces_loss():
+    import torch
+    F, H, O, n = 17, 64, 4, 2048
+    p, norm, X, Y = _seeded_problem(F, H, O, n, seed=9)
+    m = bgk.MLP(F, O, H, seed=2)
+    Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
+    m.fit_norm(Xd.data_ptr(), Yd.data_ptr(), n)
+    l0 = m.train_step(Xd.data_ptr(), Yd.data_ptr(), n, 1e-3)
+    for _ in range(200):
+        l1 = m.train_step(Xd.data_ptr(), Yd.data_ptr(), n, 1e-3)
+    assert l1 < 0.7 * l0
+
+
+def _runs(seeds, n_side=12, n_v=12):
+    out = []
+    for s in seeds:
+        r = synth.splitmix64_uniform(s, 1)[0]
+        kn = 10.0 ** (-3.0 + 2.0 * r)
+        out.append(synth.workload_random_smooth(seed=s, n_side=n_side, kx=1, n_v=n_v, knudsen=kn, k_v=2,
+                                                integrator="BDF2"))
+    return out
+
+
+def test_trained_guess_saves_iterations_and_keeps_results():
+    import torch
+    X, Y = [], []
+    for w in _runs(range(1000, 1012)):
+        s = bgk.Solver.from_workload(w)
+        s.set_state_maxwellian(w.init)
+        s.set_inflow_maxwellian(w.inflow)
+        guess.collect(s, 6, X, Y)
+    X = torch.cat(X)
+    Y = torch.cat(Y)
+    F, O = X.shape[1], Y.shape[1]
+    m = bgk.MLP(F, O, 128, seed=7)
+    losses = guess.train(m, X, Y, iters=1500, batch=4096, lr=2e-3, lr_final=2e-4, seed=3)
+    assert losses[-50:].mean() < 0.5 * losses[:20].mean()
+    plain, learned = 0, 0
+    for w in _runs(range(2000, 2003)):
+        res = []
+        for use in (False, True):
+            s = bgk.Solver.from_workload(w)
+            s.set_state_maxwellian(w.init)
+            s.set_inflow_maxwellian(w.inflow)
+            if use:
+                s.set_guess(m)
+            its = 0
+            for _ in range(6):
+                st = s.step(1)
+                its += st.iterations[0]
+            res.append((its, s.get_f()))
+        plain += res[0][0]
+        learned += res[1][0]
+        # both runs met the same criterion: they differ by the Picard tolerance, not more
+        f0, f1 = res[0][1], res[1][1]
+        assert np.abs(f0 - f1).max() <= 1e-6 * np.abs(f0).max()
+    assert learned < plain, (learned, plain)
