@@ -39,7 +39,9 @@ def parse():
     p.add_argument("--n-side", type=int, default=128)
     p.add_argument("--n-v", type=int, default=32)
     p.add_argument("--sweep-reps", type=int, default=5)
-    p.add_argument("--workload", default="shock_tube", choices=["shock_tube", "batched"])
+    p.add_argument("--workload", default="shock_tube", choices=["shock_tube", "batched", "learned"])
+    p.add_argument("--train-runs", type=int, default=200)
+    p.add_argument("--eval-runs", type=int, default=4)
     p.add_argument("--instances", type=int, default=64)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cache", default="auto", choices=["auto", "on", "off"],
@@ -405,10 +407,107 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def _learned_workload(seed, n_side, dt=None):
+    """Held-out / training run of the learned-guess workload: P1, 32x32 velocities, BDF2,
+    Kn log-uniform in [1e-4, 1] drawn from the run's seed, random smooth initial moments."""
+    from paper_2608_19150_b300 import synth
+    r = synth.splitmix64_uniform(seed, 1)[0]
+    kn = 10.0 ** (-4.0 + 4.0 * r)
+    return synth.workload_random_smooth(seed=seed, n_side=n_side, kx=1, n_v=32, knudsen=kn, k_v=3,
+                                        integrator="BDF2")
+
+
+def run_learned(args):
+    """Learned initial guess on the 256x256 P1 BDF2 workload: train on seeded small runs
+    (dt of the full mesh), then time full-size held-out runs with and without it."""
+    import torch
+    rank, world, local = dist_init(args)
+    torch.cuda.set_device(local)
+    from paper_2608_19150_b300 import bgk, guess
+    n_full = args.n_side if args.n_side != 128 else 256
+    probe = _learned_workload(2000, n_full)
+    s0 = bgk.Solver.from_workload(probe, precision=args.precision, cache_inverse="off")
+    dt_full = s0.dt
+    s0.close()
+    del s0
+    # training data: seeded runs 1000.. on 32x32 meshes with the full mesh's time step
+    t0 = time.perf_counter()
+    X, Y, train_iters = [], [], []
+    for k in range(args.train_runs):
+        w = _learned_workload(1000 + k, 32)
+        s = bgk.Solver.from_workload(w, dt=dt_full, l_max=2000)
+        s.set_state_maxwellian(w.init)
+        s.set_inflow_maxwellian(w.inflow)
+        train_iters += guess.collect(s, 4, X, Y)
+        s.close()
+    X = torch.cat(X)
+    Y = torch.cat(Y)
+    gen_s = time.perf_counter() - t0
+    F, O = X.shape[1], Y.shape[1]
+    m = bgk.MLP(F, O, 128, seed=7)
+    t0 = time.perf_counter()
+    losses = guess.train(m, X, Y, iters=3000, batch=8192, lr=2e-3, lr_final=1e-4, seed=3)
+    train_s = time.perf_counter() - t0
+    # held-out full-size runs
+    res = {"plain": [0, 0.0, 0], "learned": [0, 0.0, 0]}
+    per_run = []
+    clocks = Clocks(local)
+    clocks.start()
+    for k in range(args.eval_runs):
+        w = _learned_workload(2000 + k, n_full)
+        row = {"knudsen": w.knudsen}
+        for name in ("plain", "learned"):
+            s = bgk.Solver.from_workload(w, precision=args.precision, l_max=2000)
+            s.set_state_maxwellian(w.init)
+            s.set_inflow_maxwellian(w.inflow)
+            if name == "learned":
+                s.set_guess(m)
+            s.step(1)                                  # BDF2 start-up step (backward Euler), untimed
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            its = 0
+            for _ in range(args.steps):
+                st = s.step(1)
+                its += st.iterations[0]
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            res[name][0] += its
+            res[name][1] += el
+            res[name][2] += args.steps
+            row[name] = {"iterations": its, "ms_per_step": 1e3 * el / args.steps}
+            dof = s.nv * s.nnode
+            s.close()
+        per_run.append(row)
+    clk = clocks.stop()
+    if rank != 0:
+        return
+    ms_plain = 1e3 * res["plain"][1] / res["plain"][2]
+    ms_learn = 1e3 * res["learned"][1] / res["learned"][2]
+    line = {"metric": METRIC, "value": dof * res["learned"][0] / res["learned"][1], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": 1, "ms_per_step": ms_learn, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
+            "config": {"workload": "learned initial guess, 2D-2V: %dx%d squares (%d P1 triangles), 32x32 velocities, "
+                                   "BDF2, CFL 10, Kn log-uniform 1e-4..1 per run; MLP 4 layers x 128 (FP32 training, "
+                                   "BF16 inference)" % (n_full, n_full, 2 * n_full * n_full),
+                       "train_runs": args.train_runs, "train_mesh": "32x32 squares, dt of the full mesh",
+                       "train_samples": int(X.shape[0]), "eval_runs": args.eval_runs, "parallelism": "replicas",
+                       "l2": "inputs larger than L2"},
+            "learned_guess": {"iterations_plain": res["plain"][0], "iterations_learned": res["learned"][0],
+                              "ms_per_step_plain": ms_plain, "ms_per_step_learned": ms_learn,
+                              "speedup": ms_plain / ms_learn, "train_loss_first": float(losses[:20].mean()),
+                              "train_loss_last": float(losses[-50:].mean()), "data_generation_s": gen_s,
+                              "training_s": train_s, "per_run": per_run},
+            "clocks": clk, "cpu_baseline": None, "e2e": None, "roofline": None}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.workload == "batched" and args.impl == "ours":
         run_batched(args)
+        return
+    if args.workload == "learned" and args.impl == "ours":
+        run_learned(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -186,7 +186,8 @@ int bgk_batch_info(const bgk_batch* b, int64_t* out);
 /* ---- Learned initial guess (an addition beside the paper's method) ------------------
  * A multilayer perceptron F -> H -> H -> H -> O (tanh on the hidden layers, inputs and
  * outputs normalised column-wise) predicts, for every spatial node, the change of
- * q = (log n, u, log theta) over a stage from features of the stage-start moments.  With
+ * q = (log n, u, log theta) over a stage from features of the stage-start moments, as a
+ * correction to repeating the previous stage's change (the last feature block).  With
  * a network attached (bgk_set_guess), each stage's iterate 0 takes the predicted moments
  * (nodes with a non-physical prediction keep their own); the Picard loop of Sec. 4 then
  * runs to the usual criterion, so the converged state is the solver's, not the network's.
@@ -215,8 +216,9 @@ int bgk_mlp_predict(bgk_mlp* m, const float* d_X, int64_t n, float* d_Y, int bf1
 int bgk_guess_dims(const bgk_handle* h, int* n_features, int* n_outputs);
 /* features of the current state into d_X [n_nodes][F] (device); records the history */
 int bgk_guess_features(bgk_handle* h, float* d_X);
-/* training targets: change of q from d_Ustart (device moments) to the current moments */
-int bgk_guess_targets(bgk_handle* h, const double* d_Ustart, float* d_Y);
+/* training targets: change of q from d_Ustart (device moments) to the current moments,
+ * minus the previous change recorded in the stage-start features d_X */
+int bgk_guess_targets(bgk_handle* h, const double* d_Ustart, const float* d_X, float* d_Y);
 /* attach (or with NULL detach) a network; its current parameters are copied to BF16 */
 int bgk_set_guess(bgk_handle* h, bgk_mlp* m);
 

@@ -104,7 +104,7 @@ def load(path: str = LIB_PATH):
         "bgk_mlp_predict": [P, V, C.c_int64, V, I],
         "bgk_guess_dims": [P, C.POINTER(I), C.POINTER(I)],
         "bgk_guess_features": [P, V],
-        "bgk_guess_targets": [P, V, V],
+        "bgk_guess_targets": [P, V, V, V],
         "bgk_set_guess": [P, P],
     }
     for name, args in sig.items():
@@ -283,8 +283,9 @@ class Solver:
     def guess_features(self, d_X_ptr):
         _ck(self.lib.bgk_guess_features(self.h, C.c_void_p(d_X_ptr)), "bgk_guess_features")
 
-    def guess_targets(self, d_Ustart_ptr, d_Y_ptr):
-        _ck(self.lib.bgk_guess_targets(self.h, C.c_void_p(d_Ustart_ptr), C.c_void_p(d_Y_ptr)), "bgk_guess_targets")
+    def guess_targets(self, d_Ustart_ptr, d_X_ptr, d_Y_ptr):
+        _ck(self.lib.bgk_guess_targets(self.h, C.c_void_p(d_Ustart_ptr), C.c_void_p(d_X_ptr), C.c_void_p(d_Y_ptr)),
+            "bgk_guess_targets")
 
     def set_guess(self, mlp):
         self._guess = mlp

@@ -26,14 +26,16 @@ void guess_features_launch(bgk_handle* h) {
 }
 
 // Stage start with a network attached: features -> BF16 network -> guessed moments
-// replace iterate 0's moments node by node (non-physical predictions are skipped).
+// (previous change + network correction) replace iterate 0's moments node by node
+// (non-physical predictions are skipped).
 int guess_hook(bgk_handle* h) {
   bgk_mlp* m = h->guess;
   guess_features_launch(h);
   mlp_forward<__nv_bfloat16>(m, h->stream, h->gX, h->nnode, m->pb);
   k_denorm<<<(int)(((int64_t)h->nnode * m->O + 255) / 256), 256, 0, h->stream>>>(
       m->act[3], h->nnode, m->O, m->norm + 2 * m->F, m->norm + 2 * m->F + m->O, h->gY);
-  k_guess_apply<<<(h->nnode + 127) / 128, 128, 0, h->stream>>>(h->nnode, h->hm.dim, h->gY, h->U[0], h->U[1], h->ds);
+  k_guess_apply<<<(h->nnode + 127) / 128, 128, 0, h->stream>>>(h->nnode, h->hm.dim, h->gY, h->gX, h->U[0], h->U[1],
+                                                               h->ds);
   return cudaGetLastError() == cudaSuccess ? BGK_OK : BGK_E_CUDA;
 }
 
@@ -61,12 +63,12 @@ int bgk_guess_features(bgk_handle* h, float* d_X) {
   return BGK_OK;
 }
 
-int bgk_guess_targets(bgk_handle* h, const double* d_Ustart, float* d_Y) {
-  if (!h || !d_Ustart || !d_Y) return BGK_E_INVALID;
+int bgk_guess_targets(bgk_handle* h, const double* d_Ustart, const float* d_X, float* d_Y) {
+  if (!h || !d_Ustart || !d_X || !d_Y) return BGK_E_INVALID;
   k_reset_state<<<1, 1, 0, h->stream>>>(h->ds);
   moments(h, 0);
   k_guess_targets<<<(h->nnode + 127) / 128, 128, 0, h->stream>>>(h->nnode, h->hm.dim, d_Ustart, h->U[0], h->U[1],
-                                                                 h->ds, d_Y);
+                                                                 h->ds, d_X, d_Y);
   CK(cudaStreamSynchronize(h->stream));
   return BGK_OK;
 }

@@ -81,23 +81,28 @@ __global__ void k_guess_history(int nnode, int nm, const double* __restrict__ U0
   if (blockIdx.x == 0 && threadIdx.x == 0) *have_hist = 1;
 }
 
-// Training targets: change of q from the stage-start moments Ustart to the current ones.
+// Training targets: change of q from the stage-start moments Ustart to the current ones,
+// minus the previous stage's change (the last d+2 features X): the network learns the
+// correction to extrapolating the previous change.
 __global__ void k_guess_targets(int nnode, int d, const double* __restrict__ Ustart, const double* __restrict__ U0,
-                                const double* __restrict__ U1, const DevState* __restrict__ ds, float* __restrict__ Y) {
+                                const double* __restrict__ U1, const DevState* __restrict__ ds,
+                                const float* __restrict__ X, float* __restrict__ Y) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nnode) return;
-  const int nm = d + 2;
+  const int nm = d + 2, F = guess_features(d);
   const double* U = ((ds->it & 1) == 0) ? U0 : U1;
   double a[5], b[5];
   prim_log(Ustart + (size_t)i * nm, d, a);
   prim_log(U + (size_t)i * nm, d, b);
-  for (int m = 0; m < nm; ++m) Y[(size_t)i * nm + m] = (float)(b[m] - a[m]);
+  for (int m = 0; m < nm; ++m)
+    Y[(size_t)i * nm + m] = (float)((b[m] - a[m]) - (double)X[(size_t)i * F + F - nm + m]);
 }
 
-// Guess applied to iterate 0: q + dq -> (n, u, theta) -> U; nodes whose prediction is
-// non-physical or non-finite keep their plain moments.
-__global__ void k_guess_apply(int nnode, int d, const float* __restrict__ dq, double* U0, double* U1,
-                              const DevState* __restrict__ ds) {
+// Guess applied to iterate 0: q + (previous change + network correction) -> (n, u,
+// theta) -> U; nodes whose prediction is non-physical or non-finite keep their plain
+// moments.  X: the stage's features (their last d+2 entries are the previous change).
+__global__ void k_guess_apply(int nnode, int d, const float* __restrict__ dq, const float* __restrict__ X, double* U0,
+                              double* U1, const DevState* __restrict__ ds) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nnode) return;
   const int nm = d + 2;
@@ -106,8 +111,9 @@ __global__ void k_guess_apply(int nnode, int d, const float* __restrict__ dq, do
   prim_log(U, d, q);
   double p[5];
   bool ok = true;
+  const int F = guess_features(d);
   for (int m = 0; m < nm; ++m) {
-    p[m] = q[m] + (double)dq[(size_t)i * nm + m];
+    p[m] = q[m] + (double)dq[(size_t)i * nm + m] + (double)X[(size_t)i * F + F - nm + m];
     ok = ok && isfinite(p[m]);
   }
   if (!ok) return;

@@ -13,7 +13,8 @@ from . import bgk
 
 def collect(solver: "bgk.Solver", steps: int, X_out: list, Y_out: list):
     """Advance `solver` by `steps` steps, recording for every step the features of the
-    stage start and the converged change of (log n, u, log theta) at every node."""
+    stage start and the converged change of (log n, u, log theta) at every node, less the
+    previous step's change (what the network learns to correct)."""
     import torch
     F, O = solver.guess_dims()
     iters = []
@@ -25,7 +26,7 @@ def collect(solver: "bgk.Solver", steps: int, X_out: list, Y_out: list):
         solver.get_moments_device(U0.data_ptr())
         st = solver.step(1)
         iters.append(int(sum(st.iterations[:st.n_stages])))
-        solver.guess_targets(U0.data_ptr(), Y.data_ptr())
+        solver.guess_targets(U0.data_ptr(), X.data_ptr(), Y.data_ptr())
         X_out.append(X)
         Y_out.append(Y)
     return iters
