@@ -38,7 +38,12 @@ enum {
 };
 
 enum { BGK_BE = 0, BGK_DIRK2 = 1, BGK_DIRK3 = 2, BGK_BSTABLE2 = 3, BGK_BDF2 = 4 };
-enum { BGK_FP64 = 0, BGK_FP32_SWEEP = 1 };
+/* BGK_FP64: FP64 storage and sweeps.  BGK_FP32_SWEEP: FP32 storage and sweeps, moments
+ * and Maxwellian parameters to FP64 accuracy; it stalls at FP32 rounding (~1e-7 in the
+ * moment change).  BGK_MIXED: FP64 state; each stage first runs FP32 sweeps until the
+ * measure falls below max(tau', fp32_floor), then FP64 sweeps to tau' -- the converged
+ * state is the FP64 one. */
+enum { BGK_FP64 = 0, BGK_FP32_SWEEP = 1, BGK_MIXED = 2 };
 enum { BGK_DTYPE_F64 = 0, BGK_DTYPE_F32 = 1 };
 
 /* Mesh of the spatial domain X (Sec. 3.1, Table 1): affine simplices, conforming. */
@@ -79,6 +84,7 @@ typedef struct {
   int cache_inverse;  /* local-inverse cache for the stage coefficient: 0 = when it fits in half
                          of the free device memory, 1 = always (BGK_E_OOM if it cannot),
                          2 = never (assemble and factorise every local matrix in the sweep) */
+  double fp32_floor;  /* BGK_MIXED: the FP32 phase stops below this measure (0 = 2e-7) */
 } bgk_config;
 
 typedef struct {
@@ -87,6 +93,7 @@ typedef struct {
   double measure[3];  /* final convergence measure of each stage */
   int total_sweeps;   /* sweeps run since the handle was created */
   int status;
+  int iterations_fp32[3];  /* BGK_MIXED: FP32-phase iterations of each stage (else 0) */
 } bgk_stats;
 
 typedef struct bgk_handle bgk_handle;

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libbgk_b300.so")
 
 BGK_OK, BGK_E_INVALID, BGK_E_CUDA, BGK_E_OOM, BGK_E_NOCONV, BGK_E_NONPHYSICAL, BGK_E_TIMEOUT = range(7)
 INTEGRATORS = {"BE": 0, "DIRK2": 1, "DIRK3": 2, "BSTABLE2": 3, "BDF2": 4}
-PRECISIONS = {"fp64": 0, "fp32": 1}
+PRECISIONS = {"fp64": 0, "fp32": 1, "mixed": 2}
 DTYPES = {np.dtype(np.float64): 0, np.dtype(np.float32): 1}
 
 
@@ -42,12 +42,12 @@ class Physics(C.Structure):
 class Config(C.Structure):
     _fields_ = [("tau", C.c_double), ("l_max", C.c_int), ("precision", C.c_int), ("block_threads", C.c_int),
                 ("stream", C.c_void_p), ("eager", C.c_int),
-                ("cache_inverse", C.c_int)]
+                ("cache_inverse", C.c_int), ("fp32_floor", C.c_double)]
 
 
 class Stats(C.Structure):
     _fields_ = [("n_stages", C.c_int), ("iterations", C.c_int * 3), ("measure", C.c_double * 3),
-                ("total_sweeps", C.c_int), ("status", C.c_int)]
+                ("total_sweeps", C.c_int), ("status", C.c_int), ("iterations_fp32", C.c_int * 3)]
 
 
 _lib = None
@@ -147,7 +147,7 @@ class Solver:
     """Handle of one problem on the current CUDA device (thin wrapper of bgk_create)."""
 
     def __init__(self, dim, kx, xyz, cells, n_v, k_v, L, nu, integrator="BE", dt=0.0, cfl=10.0, tau=1e-8,
-                 l_max=1000, precision="fp64", block_threads=0, stream=None, eager=False, cache_inverse="auto"):
+                 l_max=1000, precision="fp64", block_threads=0, stream=None, eager=False, cache_inverse="auto", fp32_floor=0.0):
         self.lib = load()
         self._xyz = np.ascontiguousarray(xyz, dtype=np.float64)
         self._cells = np.ascontiguousarray(cells, dtype=np.int32)
@@ -156,7 +156,7 @@ class Solver:
         ph = Physics(float(nu), INTEGRATORS[integrator], float(dt), float(cfl))
         cf = Config(float(tau), int(l_max), PRECISIONS[precision], int(block_threads),
                     C.c_void_p(stream) if stream else None, int(bool(eager)),
-                    {"auto": 0, "on": 1, "off": 2}[cache_inverse])
+                    {"auto": 0, "on": 1, "off": 2}[cache_inverse], float(fp32_floor))
         h = C.c_void_p()
         _ck(self.lib.bgk_create(C.byref(m), C.byref(vg), C.byref(ph), C.byref(cf), C.byref(h)), "bgk_create")
         self.h = h
@@ -165,7 +165,7 @@ class Solver:
         (self.nv, self.nnode, self.ndof, self.ncell, self.dim, self.gmax, self.lagged, self.cache_bytes,
          self.sweep_threads) = (int(x) for x in sz)
         self.precision = precision
-        self.fdtype = np.float64 if precision == "fp64" else np.float32
+        self.fdtype = np.float32 if precision == "fp32" else np.float64
 
     @classmethod
     def from_workload(cls, w, **kw):
@@ -185,7 +185,7 @@ class Solver:
         (self.nv, self.nnode, self.ndof, self.ncell, self.dim, self.gmax, self.lagged, self.cache_bytes,
          self.sweep_threads) = (int(x) for x in sz)
         self.precision = precision
-        self.fdtype = np.float64 if precision == "fp64" else np.float32
+        self.fdtype = np.float32 if precision == "fp32" else np.float64
         return self
 
     def close(self):
@@ -310,7 +310,7 @@ class Batch:
             vgrids[i] = VGrid(float(w.L), int(w.n_v), int(w.k_v))
             phys[i] = Physics(float(w.nu), INTEGRATORS["BE"], float(dt[i]) if dt else 0.0, float(w.cfl))
         cf = Config(float(tau), int(l_max), PRECISIONS[precision], 0, None, 0,
-                    {"auto": 0, "on": 1, "off": 2}[cache_inverse])
+                    {"auto": 0, "on": 1, "off": 2}[cache_inverse], 0.0)
         h = C.c_void_p()
         _ck(self.lib.bgk_batch_create(n, meshes, vgrids, phys, C.byref(cf), C.byref(h)), "bgk_batch_create")
         self.h = h

@@ -16,6 +16,7 @@ struct DevState {
   int err;           // non-physical moments seen (bit set by the Maxwellian kernel)
   int iters[4];
   double meas[4];
+  int iters32[4];    // mixed precision: FP32-phase iterations of each stage
   int total_sweeps;
   int cont;          // the stage loop continues (read by the host in eager mode)
   int done;          // the stage loop of this problem has ended (batched runs skip it)
@@ -343,8 +344,8 @@ __global__ void k_factors(VGrid g, int nnode, const double* __restrict__ U0, con
 }
 
 // src[j][i] = prod_a cf[a][j_a][i] + qscale * q[j][i]  (nu M^l + q of Eq. bgk-ss-picard)
-template <typename T>
-__global__ void k_source(VGrid g, int nnode, const T* __restrict__ cf, const T* __restrict__ q, T qscale,
+template <typename T, typename TQ = T>
+__global__ void k_source(VGrid g, int nnode, const T* __restrict__ cf, const TQ* __restrict__ q, T qscale,
                          T* __restrict__ src, const DevState* ds) {
   if (ds->status != BGK_OK || ds->done) return;
   const size_t total = (size_t)g.nv * nnode;
@@ -358,15 +359,17 @@ __global__ void k_source(VGrid g, int nnode, const T* __restrict__ cf, const T* 
       m = cf[(size_t)(j / (g.N * g.N)) * nnode + i] * cf[(size_t)(g.N + (j / g.N) % g.N) * nnode + i] *
           cf[(size_t)(2 * g.N + j % g.N) * nnode + i];
     }
-    src[t] = fma(qscale, q[t], m);
+    src[t] = fma(qscale, (T)q[t], m);
   }
 }
 
 // Reduce the partials in a fixed order, evaluate Eq. (convergence-criteria) (m = 1
 // denominator max(|U^1|, |U^0|)), advance the iteration counters and set the while
 // condition of the stage loop.
+// stall_stop (FP32 phase of the mixed mode): also stop once the measure is below 1e-5
+// and has decreased by less than 10% over the last iteration (FP32 rounding floor).
 __global__ void k_finalize(DevState* ds, const double* __restrict__ partial, int nblk, double tol, int lmax, int stage,
-                           cudaGraphConditionalHandle cond, int use_cond) {
+                           cudaGraphConditionalHandle cond, int use_cond, int stall_stop = 0) {
   __shared__ double red[6][256];
   double s[6] = {0, 0, 0, 0, 0, 0};
   const bool skip = ds->status != BGK_OK || ds->done;
@@ -387,14 +390,16 @@ __global__ void k_finalize(DevState* ds, const double* __restrict__ partial, int
     const double r1 = sqrt(red[2][0]) / fmax(sqrt(red[3][0]), sqrt(red[1][0]));
     const double r2 = sqrt(red[4][0]) / sqrt(red[5][0]);
     const double meas = fmax(r0, fmax(r1, r2));
+    const double prev = ds->meas[stage];
     ds->it += 1;
     ds->stage_it += 1;
     ds->total_sweeps += 1;
     ds->iters[stage] = ds->stage_it;
     ds->meas[stage] = meas;
+    const bool stalled = stall_stop && ds->stage_it > 2 && meas < 1e-5 && meas > 0.9 * prev;
     if (ds->err) {
       ds->status = BGK_E_NONPHYSICAL;
-    } else if (!(meas < tol)) {
+    } else if (!(meas < tol) && !stalled) {
       if (ds->stage_it >= lmax)
         ds->status = BGK_E_NOCONV;
       else
@@ -424,6 +429,7 @@ __global__ void k_reset_state(DevState* ds) {
     for (int s = 0; s < 4; ++s) {
       ds->iters[s] = 0;
       ds->meas[s] = 0.0;
+      ds->iters32[s] = 0;
     }
   }
 }
@@ -777,6 +783,32 @@ __global__ void k_combine(size_t n, T* __restrict__ out, double a_k, const T* __
     if (nF > 1) s += c1 * (double)F1[i];
     if (nF > 2) s += c2 * (double)F2[i];
     out[i] = (T)s;
+  }
+}
+
+// out <- in, skipped when gate (if given) reports that its loop failed
+template <typename TI, typename TO>
+__global__ void k_convert_gated(size_t n, const TI* __restrict__ in, TO* __restrict__ out,
+                                const DevState* __restrict__ gate) {
+  if (gate && (gate->err || gate->status == BGK_E_NONPHYSICAL)) return;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (TO)in[i];
+}
+
+// Copy the current moments of one state to another (parities from each state's counter).
+__global__ void k_copy_moments(size_t n, const double* __restrict__ A0, const double* __restrict__ A1,
+                               const DevState* __restrict__ da, double* B0, double* B1, const DevState* db) {
+  const double* A = (da->it & 1) == 0 ? A0 : A1;
+  double* B = (db->it & 1) == 0 ? B0 : B1;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    B[i] = A[i];
+}
+
+// Record the FP32 phase's iteration count of stage st in the main state.
+__global__ void k_record_fp32(const DevState* __restrict__ sh, DevState* main, int st) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    main->iters32[st] = sh->stage_it;
+    main->total_sweeps += sh->stage_it;
   }
 }
 

@@ -70,6 +70,10 @@ struct bgk_handle {
   cudaGraphExec_t exec_main = nullptr;   // the integrator's step
   cudaGraphExec_t exec_start = nullptr;  // BDF2 start-up step (backward Euler)
   // timing of bgk_sweep launches
+  // mixed precision: FP32 shadow of this (FP64) problem, used for the first sweeps of
+  // every stage; its loop stops at the FP32 floor and hands its state back in FP64
+  bgk_handle* shadow = nullptr;
+  double fp32_floor = 2e-7;
   // learned initial guess (optional): network, its inputs/outputs and the stage history
   struct bgk_mlp* guess = nullptr;
   float* gX = nullptr;
@@ -291,6 +295,90 @@ int build_src(bgk_handle* h, const void* qsrc, double qscale) {
   return h->precision == BGK_FP64 ? build_src_t<double>(h, qsrc, qscale) : build_src_t<float>(h, qsrc, qscale);
 }
 
+// FP32 source of the shadow problem with the FP64 stage source q of the main problem.
+int build_src_shadow(bgk_handle* sh, const double* q64, double qscale) {
+  k_factors<float><<<(sh->nnode + 127) / 128, 128, 0, sh->stream>>>(sh->g, sh->nnode, sh->U[0], sh->U[1], sh->ds,
+                                                                   sh->phys.nu, (float*)sh->cf);
+  k_source<float, double><<<148 * 16, 256, 0, sh->stream>>>(sh->g, sh->nnode, (const float*)sh->cf, q64,
+                                                            (float)qscale, (float*)sh->src, sh->ds);
+  return cudaGetLastError() == cudaSuccess ? BGK_OK : BGK_E_CUDA;
+}
+
+// Conditional while-node appended to the capture of stream s; returns the body graph.
+int add_while(cudaStream_t s, cudaGraphConditionalHandle* cond, cudaGraph_t* body) {
+  cudaGraph_t cg;
+  cudaStreamCaptureStatus cst;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  CK(cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, &deps, nullptr, &ndeps));
+  CK(cudaGraphConditionalHandleCreate(cond, cg, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = *cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, cg, deps, nullptr, ndeps, &cp));
+  CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  *body = cp.conditional.phGraph_out[0];
+  return BGK_OK;
+}
+
+// Mixed precision, at a stage start (main moments already in U): FP32 sweeps on the
+// shadow until the FP32 floor (or the main tolerance), then the FP64 state takes the
+// FP32 result (unless that phase failed) and its moments are recomputed.
+int shadow_phase(bgk_handle* h, int st, const void* qsrc, double qscale, double nus, double tol, bool capture) {
+  bgk_handle* sh = h->shadow;
+  cudaStream_t s = h->stream;
+  const int thr = 256, blk = 148 * 8;
+  k_reset_state<<<1, 1, 0, s>>>(sh->ds);
+  k_stage_begin<<<1, 1, 0, s>>>(sh->ds, st);
+  k_convert_gated<double, float><<<blk, thr, 0, s>>>(h->nfv, (const double*)h->f, (float*)sh->f, nullptr);
+  k_copy_moments<<<148, 256, 0, s>>>((size_t)h->nnode * h->nm, h->U[0], h->U[1], h->ds, sh->U[0], sh->U[1], sh->ds);
+  const double tol32 = std::max(tol, h->fp32_floor);
+  cudaStream_t keep = sh->stream;
+  if (capture) {
+    cudaGraphConditionalHandle cond;
+    cudaGraph_t body;
+    int rc = add_while(s, &cond, &body);
+    if (rc != BGK_OK) return rc;
+    cudaStream_t bs;
+    CK(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
+    CK(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    sh->stream = bs;
+    rc = build_src_shadow(sh, (const double*)qsrc, qscale);
+    launch_sweep_any(sh, nus);
+    moments(sh, 1);
+    k_finalize<<<1, 256, 0, bs>>>(sh->ds, sh->partial, sh->mom_blocks, tol32, sh->cfg.l_max, st, cond, 1, 1);
+    sh->stream = keep;
+    cudaGraph_t body_out;
+    cudaError_t e2 = cudaStreamEndCapture(bs, &body_out);
+    cudaStreamDestroy(bs);
+    if (rc != BGK_OK || e2 != cudaSuccess) return BGK_E_CUDA;
+  } else {
+    sh->stream = s;
+    for (;;) {
+      int rc = build_src_shadow(sh, (const double*)qsrc, qscale);
+      if (rc != BGK_OK) {
+        sh->stream = keep;
+        return rc;
+      }
+      launch_sweep_any(sh, nus);
+      moments(sh, 1);
+      k_finalize<<<1, 256, 0, s>>>(sh->ds, sh->partial, sh->mom_blocks, tol32, sh->cfg.l_max, st, 0, 0, 1);
+      DevState d;
+      CK(cudaMemcpyAsync(&d, sh->ds, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (!d.cont) break;
+    }
+    sh->stream = keep;
+  }
+  k_record_fp32<<<1, 1, 0, s>>>(sh->ds, h->ds, st);
+  k_convert_gated<float, double><<<blk, thr, 0, s>>>(h->nfv, (const float*)sh->f, (double*)h->f, sh->ds);
+  moments(h, 0);
+  return cudaGetLastError() == cudaSuccess ? BGK_OK : BGK_E_CUDA;
+}
+
 // One time step: per stage a while-loop over (Maxwellian + source, sweep, moments,
 // convergence test).  With exec_out != nullptr the step is captured as a CUDA graph in
 // which each stage loop is a conditional while-node; with exec_out == nullptr the same
@@ -345,6 +433,10 @@ int enqueue_step(bgk_handle* h, int mode_bdf2, cudaGraphExec_t* exec_out) {
     if (h->guess) {
       int rg = guess_hook(h);
       if (rg != BGK_OK) return rg;
+    }
+    if (h->shadow) {
+      int rs = shadow_phase(h, st, qsrc, qscale, nus, tol, capture);
+      if (rs != BGK_OK) return rs;
     }
     if (capture) {
       // while (cond) { src; sweep; moments; finalize }
@@ -479,6 +571,8 @@ int build_dags(bgk_handle* h) {
 void release(bgk_handle* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
+  if (h->shadow) release(h->shadow);
+  h->shadow = nullptr;
   if (h->exec_main) cudaGraphExecDestroy(h->exec_main);
   if (h->exec_start) cudaGraphExecDestroy(h->exec_start);
   void* ptrs[] = {h->gX, h->gY, h->Uhist, h->have_hist,
@@ -530,7 +624,7 @@ int bgk_create(const bgk_mesh* mesh, const bgk_vgrid* vg, const bgk_physics* phy
   }
   if (!(h->cfg.tau > 0.0)) h->cfg.tau = 1e-8;
   if (h->cfg.l_max <= 0) h->cfg.l_max = 1000;
-  h->precision = h->cfg.precision == BGK_FP32_SWEEP ? BGK_FP32_SWEEP : BGK_FP64;
+  h->precision = h->cfg.precision == BGK_FP32_SWEEP ? BGK_FP32_SWEEP : BGK_FP64;  // BGK_MIXED: FP64 + shadow
   h->tsize = h->precision == BGK_FP64 ? 8 : 4;
   if (phys->integrator < BGK_BE || phys->integrator > BGK_BDF2 || !(phys->nu >= 0.0)) {
     delete h;
@@ -638,6 +732,17 @@ int bgk_create(const bgk_mesh* mesh, const bgk_vgrid* vg, const bgk_physics* phy
     h->qscale_main = 1.0 / (h->dt * ass);
     rc = build_inverse_cache(h, h->nus_main);
   }
+  if (rc == BGK_OK && h->cfg.precision == BGK_MIXED) {
+    // the FP32 shadow: same mesh, grid, physics and stream; no graphs of its own
+    bgk_config c32 = h->cfg;
+    c32.precision = BGK_FP32_SWEEP;
+    c32.eager = 1;
+    c32.stream = h->stream;
+    bgk_physics p32 = *phys;
+    p32.dt = h->dt;
+    rc = bgk_create(mesh, vg, &p32, &c32, &h->shadow);
+    if (h->cfg.fp32_floor > 0.0) h->fp32_floor = h->cfg.fp32_floor;
+  }
   if (rc == BGK_OK && !h->cfg.eager) rc = enqueue_step(h, 0, &h->exec_main);
   if (rc == BGK_OK && !h->cfg.eager && phys->integrator == BGK_BDF2) {
     cudaGraphExec_t e0 = h->exec_main;
@@ -717,7 +822,11 @@ static int set_maxwellian(bgk_handle* h, const double* h_nut, bool inflow) {
 }
 
 int bgk_set_state_maxwellian(bgk_handle* h, const double* h_nut) { return set_maxwellian(h, h_nut, false); }
-int bgk_set_inflow_maxwellian(bgk_handle* h, const double* h_nut) { return set_maxwellian(h, h_nut, true); }
+int bgk_set_inflow_maxwellian(bgk_handle* h, const double* h_nut) {
+  int rc = set_maxwellian(h, h_nut, true);
+  if (rc == BGK_OK && h && h->shadow) rc = set_maxwellian(h->shadow, h_nut, true);
+  return rc;
+}
 
 static int transfer_f(bgk_handle* h, void* ptr, int dtype, bool in, cudaMemcpyKind kind) {
   if (!h || !ptr || (dtype != BGK_DTYPE_F64 && dtype != BGK_DTYPE_F32)) return BGK_E_INVALID;
@@ -868,6 +977,7 @@ int bgk_last_stats(bgk_handle* h, bgk_stats* st) {
   for (int s = 0; s < 3; ++s) {
     st->iterations[s] = d.iters[s];
     st->measure[s] = d.meas[s];
+    st->iterations_fp32[s] = d.iters32[s];
   }
   st->total_sweeps = d.total_sweeps;
   st->status = d.status;

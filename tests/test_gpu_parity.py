@@ -199,3 +199,37 @@ def test_fp32_storage_moments_are_fp64_accurate():
     U = s.get_moments()
     Uo = o.moments(f32.astype(np.float64))
     assert rel_err(U, Uo) < 1e-13
+
+
+@pytest.mark.parametrize("integ", ["BE", "DIRK3", "BDF2"])
+def test_mixed_precision_reaches_the_fp64_fixed_point(integ):
+    """BGK_MIXED: FP32 sweeps to the FP32 floor, then FP64 sweeps to the criterion.  The
+    result matches the oracle's FP64 step to the Picard tolerance (both stop when the
+    moment change is below tau, from different iterates)."""
+    from paper_2608_19150_b300 import bgk
+    w = synth.workload_p1_square(n_side=8, n_v=16, integrator=integ, knudsen=1e-2)
+    s = bgk.Solver.from_workload(w, precision="mixed")
+    o = __import__("oracle.oracle", fromlist=["Oracle"]).Oracle.from_workload(w)
+    o.build_dags()
+    s.set_state_maxwellian(w.init)
+    s.set_inflow_maxwellian(w.inflow)
+    o.set_physics(w.nu, s.dt, integ, 1e-12, 5000)       # the oracle converged far below tau
+    f = o.maxwellian(w.init)
+    fbc = o.maxwellian(w.inflow)
+    fprev = None
+    for k in range(2):
+        st = s.step(1)
+        assert sum(st.iterations_fp32) > 0
+        f_new, it, meas, status = o.step(f, fbc, fprev=fprev)
+        assert status == 0
+        if integ == "BDF2":
+            fprev = f
+        f = f_new
+    # tau' = 1e-8 / max(1, nu dt) on the moment change; allow 1e-6 on f
+    assert rel_err(s.get_f(), f) < 1e-6
+    # a pure FP32 run of the same problem is visibly less accurate
+    s32 = bgk.Solver.from_workload(w, precision="fp32", tau=1e-6)
+    s32.set_state_maxwellian(w.init)
+    s32.set_inflow_maxwellian(w.inflow)
+    s32.step(2)
+    assert rel_err(s32.get_f(), f) > rel_err(s.get_f(), f)
