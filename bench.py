@@ -35,7 +35,7 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    p.add_argument("--precision", default="mixed", choices=["fp64", "fp32", "mixed"])
     p.add_argument("--n-side", type=int, default=128)
     p.add_argument("--n-v", type=int, default=32)
     p.add_argument("--sweep-reps", type=int, default=5)
@@ -61,9 +61,11 @@ def config(w, args, extra=None):
     c = {"workload": "2D-2V shock tube, %dx%d squares (%d P2 triangles), %dx%d velocities on [-8,8]^2, DIRK3, "
                      "Kn 1e-3, CFL 10, tau 1e-8" % (args.n_side, args.n_side, w.mesh.n_cells, args.n_v, args.n_v),
          "n_cells": w.mesh.n_cells, "dof_per_sweep": int(w.mesh.n_cells * 6 * args.n_v ** 2),
-         "precision": args.precision, "integrator": "DIRK3",
+         "precision": {"fp64": "FP64 sweeps", "fp32": "FP32 sweeps, FP64-accurate moments",
+                       "mixed": "FP32 sweeps to the FP32 floor, then FP64 sweeps; FP64 moments"}[args.precision],
+         "integrator": "DIRK3",
          "l2": "inputs larger than L2 (f %.2f GB per array)" % (w.mesh.n_cells * 6 * args.n_v ** 2 *
-                                                                 (8 if args.precision == "fp64" else 4) / 1e9),
+                                                                 (4 if args.precision == "fp32" else 8) / 1e9),
          "parallelism": "replicas", "launch": "eager host loop" if args.eager else
          "one CUDA graph per step, conditional while-node per stage"}
     if extra:
@@ -151,28 +153,26 @@ class Clocks:
 
 # --------------------------------------------------------------------- CPU oracle
 def cpu_baseline(w, n_ord, dt):
-    """One oracle sweep restricted to n_ord ordinates of the full workload, single thread."""
-    from oracle.oracle import Oracle
+    """The oracle as it stands (single thread): one sweep of n_ord ordinates of the full
+    mesh, on the sampled ordinates' own rows (graphs, Maxwellian, sweep)."""
+    from oracle.oracle import Oracle, tableau
     o = Oracle.from_workload(w)
-    t0 = time.perf_counter()
-    o.build_dags()
-    f0 = o.maxwellian(w.init)
-    fbc = o.maxwellian(w.inflow)
-    U = o.moments(f0)
-    nut = U.copy()
-    nut[:, 1:3] = U[:, 1:3] / U[:, :1]
-    nut[:, 3] = (2 * U[:, 3] / U[:, 0] - (nut[:, 1:3] ** 2).sum(1)) / 2
-    Mn = o.maxwellian(nut)
-    setup = time.perf_counter() - t0
-    nus = w.nu + 1.0 / dt
     j0 = (o.nv - n_ord) // 2
+    js = np.arange(j0, j0 + n_ord, dtype=np.int32)
     t0 = time.perf_counter()
-    o.sweep_range(f0, Mn, f0 / dt, fbc, w.nu, nus, j0, j0 + n_ord)
+    o.build_dags_for(js)
+    f0 = o.maxwellian_rows(w.init, js)
+    fbc = o.maxwellian_rows(w.inflow, js)
+    setup = time.perf_counter() - t0
+    A, _, _ = tableau(w.integrator)
+    nus = w.nu + 1.0 / (dt * A[0, 0])
+    t0 = time.perf_counter()
+    o.sweep_rows(js, f0, f0, f0 / (dt * A[0, 0]), fbc, w.nu, nus)
     el = time.perf_counter() - t0
     dof = n_ord * o.nnode
     return {"value": dof / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "one sweep over %d of %d ordinates of the full mesh (%d DOF), %.1f s; set-up %.1f s untimed"
-                      % (n_ord, o.nv, dof, el, setup)}
+            "sample": "one sweep over %d of %d ordinates of the full mesh (%d DOF) in %.1f s, single thread; "
+                      "set-up %.1f s untimed" % (n_ord, o.nv, dof, el, setup)}
 
 
 # --------------------------------------------------------------------- runs
@@ -203,37 +203,112 @@ def max_over_ranks(x, world):
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle as it stands, each step one oracle sweep over a
+    bounded sample of the workload's ordinates (rank 0 only)."""
     rank, world, _ = dist_init(args)
     if rank != 0:
         return
     w = workload(args)
-    from oracle.oracle import Oracle
+    from oracle.oracle import Oracle, tableau
     o = Oracle.from_workload(w)
-    o.build_dags()
-    dt = 10.0 * o.dt_explicit()
-    f0 = o.maxwellian(w.init)
-    fbc = o.maxwellian(w.inflow)
-    Mn = f0
-    nus = w.nu + 1.0 / dt
-    n_ord = 8
+    n_ord = 64
     j0 = (o.nv - n_ord) // 2
+    js = np.arange(j0, j0 + n_ord, dtype=np.int32)
+    o.build_dags_for(js)
+    dt = 10.0 * o.dt_explicit()
+    f0 = o.maxwellian_rows(w.init, js)
+    fbc = o.maxwellian_rows(w.inflow, js)
+    A, _, _ = tableau(w.integrator)
+    nus = w.nu + 1.0 / (dt * A[0, 0])
     for _ in range(max(0, args.warmup)):
-        o.sweep_range(f0, Mn, f0 / dt, fbc, w.nu, nus, j0, j0 + 1)
+        o.sweep_rows(js[:2], f0[:2], f0[:2], f0[:2] / (dt * A[0, 0]), fbc[:2], w.nu, nus)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        o.sweep_range(f0, Mn, f0 / dt, fbc, w.nu, nus, j0, j0 + n_ord)
+        o.sweep_rows(js, f0, f0, f0 / (dt * A[0, 0]), fbc, w.nu, nus)
     el = time.perf_counter() - t0
     dof = n_ord * o.nnode * args.steps
     v = dof / el
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config(w, args, {"sample": "each step: one oracle sweep over %d of %d "
-                                                             "ordinates" % (n_ord, o.nv)}),
+            "data": "synthetic",
+            "config": config(w, args, {"sample": "each step: one oracle sweep over %d of %d ordinates of the "
+                                                 "full mesh" % (n_ord, o.nv), "precision": "FP64 CPU oracle"}),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "%d ordinates x %d cells x 6 nodes per step" % (n_ord, o.ncell)},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def launches_per_step(st, guess=False):
+    """Kernels one step launches (graph nodes of kernel type), from its statistics."""
+    n = 1
+    for k in range(st.n_stages):
+        n += 2 + (k > 0) + (k < st.n_stages - 1)          # stage set-up, moments, stage combines
+        n += 9 if guess else 0
+        if st.iterations_fp32[k]:
+            n += 7 + 5 * st.iterations_fp32[k]            # FP32 phase
+        n += 5 * st.iterations[k]                         # factors, source, sweep, moments, test
+    return n
+
+
+def timed_steps(s, steps, world, local, guess=False):
+    """Run `steps` steps of solver s (already warmed up) timed on the device clock."""
+    import torch
+    s.synchronize()
+    sweeps0 = s.last_stats().total_sweeps
+    clocks = Clocks(local)
+    barrier(world)
+    clocks.start()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    iters, launches = [], 0
+    for _ in range(steps):
+        st = s.step(1)
+        iters.append({"fp64": list(st.iterations)[:st.n_stages], "fp32": list(st.iterations_fp32)[:st.n_stages]})
+        launches += launches_per_step(st, guess)
+    s.synchronize()
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    barrier(world)
+    clk = clocks.stop()
+    sweeps = s.last_stats().total_sweeps - sweeps0
+    return max_over_ranks(el, world), sweeps, iters, launches, clk
+
+
+def sweep_roofline(w, precision, reps, peaks):
+    """Event-timed sweep kernel of the given precision on its own handle (first-stage
+    coefficient, local-inverse cache as in the step) and its roofline entry."""
+    from paper_2608_19150_b300 import bgk
+    s = bgk.Solver.from_workload(w, precision=precision)
+    s.set_state_maxwellian(w.init)
+    s.set_inflow_maxwellian(w.inflow)
+    s.sweep(0.0, 0.0)
+    s.timing(reset=True)
+    for _ in range(reps):
+        s.sweep(0.0, 0.0)
+    ms, n = s.timing(reset=True)
+    sweep_ms = ms / max(1, n)
+    dof = s.nv * s.nnode
+    tsz = 8 if precision == "fp64" else 4
+    hbm_gbs = 2 * tsz * dof / (sweep_ms * 1e-3) / 1e9
+    hbm_peak = float(peaks.get("hbm_gbs", 6400.0))
+    cached = s.cache_bytes > 0
+    if precision == "fp64":
+        fl = sweep_flops_per_item(cached)
+        tf = fl * s.nv * s.ncell / (sweep_ms * 1e-3) / 1e12
+        r = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+             "frac": tf / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "k_sweep<ElemP2Tri,double,%d>" % cached,
+             "flops_per_local_solve": fl, "peak_source": "nominal B300 FP64 rate (measured FMA probe 1.125)"}
+    else:
+        r = {"bound": "hbm", "achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_gbs / hbm_peak,
+             "traffic": None, "kernel": "k_sweep<ElemP2Tri,float,%d>" % cached,
+             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+    r.update({"sweep_ms": sweep_ms, "dof_per_launch": dof, "algorithmic_bytes_per_dof": 2 * tsz,
+              "hbm_achieved_gbs": hbm_gbs, "hbm_frac": hbm_gbs / hbm_peak,
+              "local_inverse_cache_gb": s.cache_bytes / 1e9})
+    s.close()
+    return r
 
 
 def run_ours(args):
@@ -242,95 +317,80 @@ def run_ours(args):
     torch.cuda.set_device(local)
     from paper_2608_19150_b300 import bgk
     w = workload(args)
-    s = bgk.Solver.from_workload(w, precision=args.precision, eager=args.eager, cache_inverse=args.cache)
-    s.set_state_maxwellian(w.init)
-    s.set_inflow_maxwellian(w.inflow)
-    dof = s.nv * s.nnode
-    for _ in range(args.warmup):
-        s.step(1)
-    f_host = torch.empty(s.nv * s.nnode, dtype=torch.float64 if args.precision == "fp64" else torch.float32,
-                         pin_memory=True)
-    s.synchronize()
-    sweeps0 = s.last_stats().total_sweeps
-    clocks = Clocks(local)
-    barrier(world)
-    clocks.start()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    iters = []
-    launches = 0
-    for _ in range(args.steps):
-        st = s.step(1)
-        it = list(st.iterations)[:st.n_stages]
-        iters.append(it)
-        launches += 1 + sum(3 + (k > 0) + 4 * it[k] + (k < st.n_stages - 1) for k in range(st.n_stages))
-    s.synchronize()
-    torch.cuda.synchronize()
-    el = time.perf_counter() - t0
-    barrier(world)
-    clk = clocks.stop()
-    sweeps = s.last_stats().total_sweeps - sweeps0
-    el_max = max_over_ranks(el, world)
-    value = world * dof * sweeps / el_max   # equal work per rank (replicas)
-    # end to end through the C ABI with host buffers: f^k in from pinned host memory,
-    # moments out to host, every step
-    fh = s.get_f(np.float64 if args.precision == "fp64" else np.float32)
-    f_host.copy_(torch.from_numpy(fh.ravel()))
-    U = np.empty((s.nnode, s.dim + 2))
-    barrier(world)
-    t0 = time.perf_counter()
-    e2e_sweeps = 0
-    for _ in range(args.steps):
-        s.lib.bgk_set_f(s.h, bgk.C.c_void_p(f_host.data_ptr()), 0 if args.precision == "fp64" else 1)
-        st = s.step(1)
-        e2e_sweeps += sum(list(st.iterations)[:st.n_stages])
-        s.lib.bgk_get_moments(s.h, U.ctypes.data_as(bgk.C.c_void_p))
-    el_e2e = max_over_ranks(time.perf_counter() - t0, world)
-    e2e = {"value": world * dof * e2e_sweeps / el_e2e, "unit": UNIT,
-           "h2d_bytes_per_step": int(f_host.numel() * f_host.element_size()), "d2h_bytes_per_step": int(U.nbytes)}
-    # the dominant kernel (the sweep), event-timed per launch on its own stream
-    s.set_f(fh)
-    s.timing(reset=True)
-    dt = s.dt
-    for _ in range(args.sweep_reps):
-        s.sweep(0.0, 0.0)          # the step's stage coefficient (the cached local inverses)
-    ms, n = s.timing(reset=True)
-    sweep_ms = ms / max(1, n)
-    flops_item = sweep_flops_per_item(s.cache_bytes > 0)
-    items = s.nv * s.ncell
-    achieved_tf = flops_item * items / (sweep_ms * 1e-3) / 1e12
-    tsz = 8 if args.precision == "fp64" else 4
-    hbm_gbs = 2 * tsz * dof / (sweep_ms * 1e-3) / 1e9
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except OSError:
         pass
-    hbm_peak = float(peaks.get("hbm_gbs", 6400.0))
-    if args.precision == "fp64":
-        roofline = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "k_sweep<ElemP2Tri,double>",
-                    "flops_per_local_solve": flops_item, "sweep_ms": sweep_ms,
-                    "local_inverse_cache_gb": s.cache_bytes / 1e9}
-    else:
-        roofline = {"bound": "hbm", "achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": hbm_gbs / hbm_peak, "traffic": None, "kernel": "k_sweep<ElemP2Tri,float>",
-                    "sweep_ms": sweep_ms, "local_inverse_cache_gb": s.cache_bytes / 1e9}
-    roofline_hbm = {"achieved_gbs": hbm_gbs, "peak_gbs": hbm_peak, "frac": hbm_gbs / hbm_peak,
-                    "algorithmic_bytes_per_dof": 2 * tsz, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+    s = bgk.Solver.from_workload(w, precision=args.precision, eager=args.eager, cache_inverse=args.cache)
+    s.set_state_maxwellian(w.init)
+    s.set_inflow_maxwellian(w.inflow)
+    dof = s.nv * s.nnode
+    fdt = np.float32 if args.precision == "fp32" else np.float64
+    f0 = s.get_f(fdt)
+    for _ in range(args.warmup):
+        s.step(1)
+    el_max, sweeps, iters, launches, clk = timed_steps(s, args.steps, world, local)
+    value = world * dof * sweeps / el_max   # equal work per rank (replicas)
+    # end to end through the C ABI with host buffers: f^k in from pinned host memory,
+    # moments out to host, every step
+    f_host = torch.empty(dof, dtype=torch.float64 if fdt == np.float64 else torch.float32, pin_memory=True)
+    f_host.copy_(torch.from_numpy(s.get_f(fdt).ravel()))
+    U = np.empty((s.nnode, s.dim + 2))
+    barrier(world)
+    t0 = time.perf_counter()
+    e2e_sweeps = 0
+    for _ in range(args.steps):
+        s.lib.bgk_set_f(s.h, bgk.C.c_void_p(f_host.data_ptr()), 0 if fdt == np.float64 else 1)
+        st = s.step(1)
+        e2e_sweeps += sum(list(st.iterations)[:st.n_stages]) + sum(list(st.iterations_fp32)[:st.n_stages])
+        s.lib.bgk_get_moments(s.h, U.ctypes.data_as(bgk.C.c_void_p))
+    el_e2e = max_over_ranks(time.perf_counter() - t0, world)
+    e2e = {"value": world * dof * e2e_sweeps / el_e2e, "unit": UNIT,
+           "h2d_bytes_per_step": int(f_host.numel() * f_host.element_size()), "d2h_bytes_per_step": int(U.nbytes)}
+    dt = s.dt
+    s.close()
+    del s
+    # the plain FP64 path on the same steps, for the comparison the metric asks for
+    plain = None
+    if args.precision != "fp64":
+        p = bgk.Solver.from_workload(w, precision="fp64")
+        p.set_f(f0.astype(np.float64))
+        p.set_inflow_maxwellian(w.inflow)
+        for _ in range(args.warmup):
+            p.step(1)
+        pe, psw, pit, _, pclk = timed_steps(p, args.steps, world, local)
+        plain = {"ms_per_step": 1e3 * pe / args.steps, "value": world * dof * psw / pe, "picard_iterations": pit,
+                 "clocks": pclk}
+        p.close()
+        del p
+    # the sweep kernels, event-timed on their own stream
+    rl = {"fp64": sweep_roofline(w, "fp64", args.sweep_reps, peaks)}
+    if args.precision != "fp64":
+        rl["fp32"] = sweep_roofline(w, "fp32", args.sweep_reps, peaks)
+    # dominant kernel of the timed step: the sweep precision that used the most time
+    n64 = sum(sum(i["fp64"]) for i in iters)
+    n32 = sum(sum(i["fp32"]) for i in iters)
+    dom = "fp64"
+    if "fp32" in rl and n32 * rl["fp32"]["sweep_ms"] > n64 * rl["fp64"]["sweep_ms"]:
+        dom = "fp32"
+    roofline = dict(rl[dom])
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w, 48, dt)
+        cpu = cpu_baseline(w, 400, dt)
     if rank != 0:
         return
+    ms = 1e3 * el_max / args.steps
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * el_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
-            "data": "synthetic", "config": config(w, args), "roofline": roofline, "roofline_hbm": roofline_hbm,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp32": "f32", "mixed": "f32 sweeps then f64 (mixed)"}[args.precision],
+            "data": "synthetic", "config": config(w, args), "roofline": roofline, "rooflines": rl,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-            "picard_iterations": iters, "sweeps_timed": sweeps, "dt": dt,
-            "schedule": {"max_generations": s.gmax, "sweep_cta_threads": s.sweep_threads,
-                         "ctas": s.nv, "lagged_edges": s.lagged}}
+            "picard_iterations": iters, "sweeps_timed": sweeps, "dt": dt}
+    if plain:
+        line["plain_fp64"] = plain
+        line["speedup_vs_plain_fp64"] = plain["ms_per_step"] / ms
     print(json.dumps(line), flush=True)
 
 
