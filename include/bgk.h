@@ -81,10 +81,13 @@ typedef struct {
   void* stream;       /* cudaStream_t to run on (NULL = a stream owned by the handle) */
   int eager;          /* 0: each step is one CUDA graph (conditional while-node per stage);
                          1: the same kernels launched from a host loop (profiling aid) */
-  int cache_inverse;  /* local-inverse cache for the stage coefficient: 0 = when it fits in half
-                         of the free device memory, 1 = always (BGK_E_OOM if it cannot),
+  int cache_inverse;  /* local-inverse cache for the stage coefficient: 0 = FP64 sweeps when it fits
+                         in half of the free device memory, 1 = always (BGK_E_OOM if it cannot),
                          2 = never (assemble and factorise every local matrix in the sweep) */
   double fp32_floor;  /* BGK_MIXED: the FP32 phase stops below this measure (0 = 2e-7) */
+  int prefetch;       /* sweep with cached inverses: 1 = copy each thread's next local inverse and
+                         geometry to shared memory ahead of use (cp.async); otherwise read in
+                         place (FP32 sweeps carry the next cell's geometry in registers) */
 } bgk_config;
 
 typedef struct {

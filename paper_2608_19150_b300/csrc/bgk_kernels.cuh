@@ -56,70 +56,73 @@ __device__ __forceinline__ uint32_t face_code(const double* __restrict__ G, cons
 // c[m] = (1/w_m) int g(v) [E l_m](v) dv, g the 1D Gaussian of mean u, variance theta,
 // l_m the Lagrange basis of node m on its velocity cell, extended polynomially beyond
 // [-L, L] on the first and last cells.  Exact up to rounding via erfc and the Gaussian
-// partial-moment recurrence; writes c[m * stride], m < N.
-__device__ __forceinline__ void proj_factors(const VGrid& g, double u, double theta, double* c, int stride) {
-  const double rs2 = 0.70710678118654752440, rs2pi = 0.39894228040143267794;
-  const double sig = sqrt(theta), isig = 1.0 / sig;
-  const double hh = 0.5 * g.h;
-  // per cell boundary: t, phi(t), smaller tail E(t) = 0.5 erfc(|t|/sqrt 2)
-  double tprev = -INFINITY, phiprev = 0.0, Eprev = 0.0;
+// partial-moment recurrence, in arithmetic R; writes scale * c[m] to out[m * stride].
+template <typename R, typename TO>
+__device__ __forceinline__ void proj_factors_t(const VGrid& g, R u, R theta, TO* out, size_t stride, R scale) {
+  const R rs2 = (R)0.70710678118654752440, rs2pi = (R)0.39894228040143267794;
+  const R sig = sqrt(theta), isig = R(1) / sig;
+  const R hh = (R)(0.5 * g.h);
+  R tprev = -(R)INFINITY, phiprev = 0, Eprev = 0;
   for (int cl = 0; cl < g.ncl; ++cl) {
-    double tb, phib, Eb;
+    R tb, phib, Eb;
     if (cl == g.ncl - 1) {
-      tb = INFINITY;
-      phib = 0.0;
-      Eb = 0.0;
+      tb = (R)INFINITY;
+      phib = 0;
+      Eb = 0;
     } else {
-      tb = (-g.L + (cl + 1) * g.h - u) * isig;
-      phib = rs2pi * exp(-0.5 * tb * tb);
-      Eb = 0.5 * erfc(fabs(tb) * rs2);
+      tb = ((R)(-g.L + (cl + 1) * g.h) - u) * isig;
+      phib = rs2pi * exp(R(-0.5) * tb * tb);
+      Eb = R(0.5) * erfc(fabs(tb) * rs2);
     }
-    const double ta = tprev, phia = phiprev, Ea = Eprev;
-    double I[kMaxKv + 1];
+    const R ta = tprev, phia = phiprev, Ea = Eprev;
+    R I[kMaxKv + 1];
     // I_0 = Phi(tb) - Phi(ta) from the tails that avoid cancellation
-    if (ta >= 0.0)
+    if (ta >= 0)
       I[0] = Ea - Eb;
-    else if (tb <= 0.0)
+    else if (tb <= 0)
       I[0] = Eb - Ea;
     else
-      I[0] = (1.0 - Eb) - Ea;
+      I[0] = (R(1) - Eb) - Ea;
     // I_k = int t^k phi: I_1 = phi(a) - phi(b); I_k = (k-1) I_{k-2} + a^{k-1}phi(a) - b^{k-1}phi(b)
     if (g.kv >= 1) I[1] = phia - phib;
-    double ap = 1.0, bp = 1.0;
+    R ap = 1, bp = 1;
     for (int k = 2; k <= g.kv; ++k) {
-      ap = isinf(ta) ? 0.0 : ap * ta;
-      bp = isinf(tb) ? 0.0 : bp * tb;
-      I[k] = (k - 1) * I[k - 2] + (isinf(ta) ? 0.0 : ap * phia) - (isinf(tb) ? 0.0 : bp * phib);
+      ap = isinf(ta) ? R(0) : ap * ta;
+      bp = isinf(tb) ? R(0) : bp * tb;
+      I[k] = (R)(k - 1) * I[k - 2] + (isinf(ta) ? R(0) : ap * phia) - (isinf(tb) ? R(0) : bp * phib);
     }
     // local variable xi = (v - mid)/(h/2) = alpha + beta t
-    const double mid = -g.L + (cl + 0.5) * g.h;
-    const double alpha = (u - mid) / hh, beta = sig / hh;
-    double J[kMaxKv + 1];  // J_p = int phi (alpha + beta t)^p dt
-    double binom[kMaxKv + 1] = {1.0, 0, 0, 0, 0};
+    const R mid = (R)(-g.L + (cl + 0.5) * g.h);
+    const R alpha = (u - mid) / hh, beta = sig / hh;
+    R J[kMaxKv + 1];  // J_p = int phi (alpha + beta t)^p dt
+    R binom[kMaxKv + 1] = {1, 0, 0, 0, 0};
     for (int p = 0; p <= g.kv; ++p) {
       if (p > 0)
         for (int q = p; q >= 1; --q) binom[q] += binom[q - 1];
-      double s = 0.0, ab = 1.0;
-      // sum_q C(p,q) alpha^{p-q} beta^q I_q, evaluated from q = p down
-      double apow[kMaxKv + 1];
-      apow[0] = 1.0;
+      R apow[kMaxKv + 1];
+      apow[0] = 1;
       for (int q = 1; q <= p; ++q) apow[q] = apow[q - 1] * alpha;
+      R sacc = 0, ab = 1;
       for (int q = 0; q <= p; ++q) {
-        s += binom[q] * apow[p - q] * ab * I[q];
+        sacc += binom[q] * apow[p - q] * ab * I[q];
         ab *= beta;
       }
-      J[p] = s;
+      J[p] = sacc;
     }
     for (int k = 0; k < g.np; ++k) {
-      double s = 0.0;
-      for (int p = 0; p < g.np; ++p) s += g.lag[k][p] * J[p];
+      R sacc = 0;
+      for (int p = 0; p < g.np; ++p) sacc += (R)g.lag[k][p] * J[p];
       const int m = cl * g.np + k;
-      c[m * stride] = s / g.w[m];
+      out[(size_t)m * stride] = (TO)(scale * sacc / (R)g.w[m]);
     }
     tprev = tb;
     phiprev = phib;
     Eprev = Eb;
   }
+}
+
+__device__ __forceinline__ void proj_factors(const VGrid& g, double u, double theta, double* c, int stride) {
+  proj_factors_t<double, double>(g, u, theta, c, (size_t)stride, 1.0);
 }
 
 // out[j * ostride + p] = coef * n_p * prod_a c_a[j_a](u_p, theta_p) + qscale * q[j * ostride + p]
@@ -310,7 +313,9 @@ __global__ void k_moments(VGrid g, const T* __restrict__ f, int nnode, double* U
 }
 
 // Projected-Maxwellian factors of every node from the current moments U[it & 1]:
-// cf[a][m][i] = c_a[m](u_i, theta_i) (App. B), with coef * n_i folded into a = 0.
+// cf[a][m][i] = c_a[m](u_i, theta_i) (App. B), with coef * n_i folded into a = 0.  The
+// moments and primitive variables are FP64; the projection runs in the storage type T
+// (FP64 for FP64 states, FP32 for FP32 sweeps, whose source is FP32 anyway).
 // Non-physical moments set the error flag (the stage loop then stops).
 template <typename T>
 __global__ void k_factors(VGrid g, int nnode, const double* __restrict__ U0, const double* __restrict__ U1,
@@ -334,13 +339,9 @@ __global__ void k_factors(VGrid g, int nnode, const double* __restrict__ U0, con
     th = 1.0;
     u[0] = u[1] = u[2] = 0.0;
   }
-  double c[kMaxN1D];
-  for (int a = 0; a < g.dim; ++a) {
-    proj_factors(g, u[a], th, c, 1);
-    const double sa = a == 0 ? scale : 1.0;
-    T* out = cf + (size_t)a * g.N * nnode + i;
-    for (int m = 0; m < g.N; ++m) out[(size_t)m * nnode] = (T)(sa * c[m]);
-  }
+  for (int a = 0; a < g.dim; ++a)
+    proj_factors_t<T, T>(g, (T)u[a], (T)th, cf + (size_t)a * g.N * nnode + i, (size_t)nnode,
+                         (T)(a == 0 ? scale : 1.0));
 }
 
 // src[j][i] = prod_a cf[a][j_a][i] + qscale * q[j][i]  (nu M^l + q of Eq. bgk-ss-picard)
@@ -548,15 +549,40 @@ struct SweepArgs {
 // r_i = s_i / |K| with the sign taken from the entry's face code.
 template <class E, typename T>
 __device__ __forceinline__ void face_rates(const double* __restrict__ Gc, uint32_t code, T v0, T v1, T v2,
-                                           T (&r)[E::NF], unsigned& outm) {
+                                           T (&r)[E::NF], unsigned& outm, int gstride = 1) {
   constexpr int D = E::D, NF = E::NF;
-  const T invK = (T)Gc[NF * D];
+  const T invK = (T)Gc[(NF * D) * gstride];
   outm = 0;
 #pragma unroll
   for (int i = 0; i < NF; ++i) {
     const uint32_t fl = (code >> (2 * i)) & 3u;
-    T s = v0 * (T)Gc[i * D] + v1 * (T)Gc[i * D + 1];
-    if (D == 3) s += v2 * (T)Gc[i * D + 2];
+    T s = v0 * (T)Gc[(i * D) * gstride] + v1 * (T)Gc[(i * D + 1) * gstride];
+    if (D == 3) s += v2 * (T)Gc[(i * D + 2) * gstride];
+    s = fabs(s) * invK;
+    r[i] = fl == 1u ? s : (fl == 2u ? -s : T(0));
+    outm |= (fl == 1u ? 1u : 0u) << i;
+  }
+}
+
+// Elements per cached local inverse: ND*ND rounded up to a 16-byte multiple, so every
+// inverse starts on a 16-byte boundary (vector loads, 16-byte asynchronous copies).
+template <class E, typename T>
+__host__ __device__ constexpr int ainv_stride() {
+  return (E::NDOF * E::NDOF + (int)(16 / sizeof(T)) - 1) / (int)(16 / sizeof(T)) * (int)(16 / sizeof(T));
+}
+
+// face_rates with the geometry already held in registers as T
+template <class E, typename T>
+__device__ __forceinline__ void face_rates_t(const T (&Gc)[E::NF * E::D + 1], uint32_t code, T v0, T v1, T v2,
+                                             T (&r)[E::NF], unsigned& outm) {
+  constexpr int D = E::D, NF = E::NF;
+  const T invK = Gc[NF * D];
+  outm = 0;
+#pragma unroll
+  for (int i = 0; i < NF; ++i) {
+    const uint32_t fl = (code >> (2 * i)) & 3u;
+    T s = v0 * Gc[i * D] + v1 * Gc[i * D + 1];
+    if (D == 3) s += v2 * Gc[i * D + 2];
     s = fabs(s) * invK;
     r[i] = fl == 1u ? s : (fl == 2u ? -s : T(0));
     outm |= (fl == 1u ? 1u : 0u) << i;
@@ -565,7 +591,7 @@ __device__ __forceinline__ void face_rates(const double* __restrict__ Gc, uint32
 
 // Inverse of the local matrix of every (ordinate, schedule position), computed in FP64
 // by Gauss-Jordan elimination in natural order and stored as T in schedule order:
-// Ainv[(j * ncell + k) * ND * ND + a * ND + b].  Valid for one nu_s; a sweep with that
+// Ainv[(j * ncell + k) * S + a * ND + b], S = ainv_stride.  Valid for one nu_s; a sweep with that
 // nu_s then needs only the right-hand side and one matrix-vector product per cell.
 template <class E, typename T>
 __global__ void k_local_inverse(SweepArgs sa, VGrid g, double nus, T* __restrict__ Ainv) {
@@ -606,7 +632,7 @@ __global__ void k_local_inverse(SweepArgs sa, VGrid g, double nus, T* __restrict
         }
       }
     }
-    T* out = Ainv + it * (ND * ND);
+    T* out = Ainv + it * ainv_stride<E, T>();
 #pragma unroll
     for (int a = 0; a < ND; ++a)
 #pragma unroll
@@ -614,25 +640,78 @@ __global__ void k_local_inverse(SweepArgs sa, VGrid g, double nus, T* __restrict
   }
 }
 
+// Asynchronous global -> shared copies (cp.async, 4 or 8 bytes), per-thread groups.
+__device__ __forceinline__ void cp_async_bytes(void* smem, const void* gmem, int bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if (bytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+// Shared-memory slots of one thread for the prefetched geometry and local inverse: two
+// slots, each the cell's gs geometry doubles followed by the padded inverse, stored
+// contiguously per thread and filled with 16-byte asynchronous copies.
+template <class E, typename T>
+struct PrefetchSlots {
+  unsigned char* base;
+  int nt, tid, gs;
+  static constexpr int AS = ainv_stride<E, T>();
+  __device__ __forceinline__ size_t per_thread() const { return (size_t)gs * sizeof(double) + AS * sizeof(T); }
+  __device__ __forceinline__ unsigned char* slot(int s) const { return base + ((size_t)s * nt + tid) * per_thread(); }
+  __device__ __forceinline__ const double* geo(int s) const { return (const double*)slot(s); }
+  __device__ __forceinline__ const T* ainv(int s) const { return (const T*)(slot(s) + (size_t)gs * sizeof(double)); }
+  // issue the copies of item k (cell c) into slot s and commit them as one group
+  __device__ __forceinline__ void issue(int s, const double* __restrict__ geo_g, const T* __restrict__ ainv_g,
+                                        int c, int k) const {
+    unsigned char* d = slot(s);
+    const unsigned char* gsrc = (const unsigned char*)(geo_g + (size_t)c * gs);
+    for (int q = 0; q < gs * (int)sizeof(double) / 16; ++q) cp_async16(d + 16 * q, gsrc + 16 * q);
+    d += (size_t)gs * sizeof(double);
+    const unsigned char* asrc = (const unsigned char*)(ainv_g + (size_t)k * AS);
+#pragma unroll
+    for (int q = 0; q < AS * (int)sizeof(T) / 16; ++q) cp_async16(d + 16 * q, asrc + 16 * q);
+    cp_async_commit();
+  }
+};
+
 // Per-item data that does not depend on values written during the sweep, so the next
 // item's copy can be loaded while the current item is processed.
-template <class E, typename T>
+// REG: the item also carries its geometry (converted to T), loaded one item ahead in
+// registers (FP32 sweeps; FP64 sweeps are bound by FP64 arithmetic, not by latency).
+template <class E, typename T, bool REG = false>
 struct SweepItem {
   uint32_t e;
   int4 nb;
   uint64_t pm;
   T src[E::NDOF];
+  T geo[REG ? E::NF * E::D + 1 : 1];
 };
 
-template <class E, typename T>
+template <class E, typename T, bool REG>
 __device__ __forceinline__ void fetch_item(const SweepArgs& sa, const uint32_t* __restrict__ gl,
-                                           const T* __restrict__ sj, int k, SweepItem<E, T>& it) {
+                                           const T* __restrict__ sj, int k, SweepItem<E, T, REG>& it) {
   it.e = gl[k];
   const int c = (int)(it.e & kCellMask);
   it.nb = *reinterpret_cast<const int4*>(sa.nbr + (size_t)c * 4);
   it.pm = sa.perm[c];
 #pragma unroll
   for (int a = 0; a < E::NDOF; ++a) it.src[a] = sj[(size_t)c * E::NDOF + a];
+  if constexpr (REG) {
+    const double* Gc = sa.geo + (size_t)c * sa.gs;
+#pragma unroll
+    for (int q = 0; q <= E::NF * E::D; ++q) it.geo[q] = (T)Gc[q];
+  }
 }
 
 // Barrier of the threads that share one ordinate's sweep: the whole CTA, or a named
@@ -659,26 +738,34 @@ struct NamedBarrier {
 // otherwise the matrix is assembled and factorised in place.  The schedule entry, the
 // neighbour ids, the node permutation and src of the thread's next item are loaded
 // before the current item is solved (they are not written during the sweep).
-template <class E, typename T, bool CACHED, class Bar>
+template <class E, typename T, bool CACHED, class Bar, bool PF = false>
 __device__ __forceinline__ void sweep_ordinate(const SweepArgs& sa, const VGrid& g, int j, T nus,
                                                const T* __restrict__ src, const T* __restrict__ fbc,
-                                               const T* __restrict__ Ainv, T* f, int tid, int nt, const Bar& bar) {
+                                               const T* __restrict__ Ainv, T* f, int tid, int nt, const Bar& bar,
+                                               unsigned char* pf_smem = nullptr) {
   constexpr int ND = E::NDOF, NF = E::NF, FD = E::FD;
   double vd[3];
   ordinate(g, j, vd);
   const T v0 = (T)vd[0], v1 = (T)vd[1], v2 = (T)vd[2];
   const uint32_t* gl = sa.glist + (size_t)j * sa.ncell;
   const int32_t* lv = sa.lvl + (size_t)j * (sa.ncell + 1);
-  const T* Aj = CACHED ? Ainv + (size_t)j * sa.ncell * (ND * ND) : nullptr;
+  const T* Aj = CACHED ? Ainv + (size_t)j * sa.ncell * ainv_stride<E, T>() : nullptr;
   const int G = sa.ngen[j];
   T* fj = f + (size_t)j * sa.nnode;
   const T* sj = src + (size_t)j * sa.nnode;
   const T* bj = fbc + (size_t)j * sa.nbface * FD;
   int lo = lv[0], hi = G > 0 ? lv[1] : lv[0];
   int k = lo + tid;
-  SweepItem<E, T> cur, nxt;
+  constexpr bool REG = !PF && sizeof(T) == 4;
+  SweepItem<E, T, REG> cur, nxt;
   bool have = k < hi;
-  if (have) fetch_item<E, T>(sa, gl, sj, k, cur);
+  // prefetch slots (PF): item data of cur in slot `slot`, of nxt in slot ^ 1
+  const PrefetchSlots<E, T> pfs{pf_smem, nt, tid, sa.gs};
+  int slot = 0;
+  if (have) {
+    fetch_item<E, T, REG>(sa, gl, sj, k, cur);
+    if (PF) pfs.issue(slot, sa.geo, Aj, (int)(cur.e & kCellMask), k);
+  }
   int kpend = -1;
   for (int gg = 0; gg < G; ++gg) {
     while (have) {
@@ -691,13 +778,27 @@ __device__ __forceinline__ void sweep_ordinate(const SweepArgs& sa, const VGrid&
       } else if (!same) {
         kn = -1;
       }
-      if (kn >= 0) fetch_item<E, T>(sa, gl, sj, kn, nxt);
+      if (kn >= 0) {
+        fetch_item<E, T, REG>(sa, gl, sj, kn, nxt);
+        if (PF) pfs.issue(slot ^ 1, sa.geo, Aj, (int)(nxt.e & kCellMask), kn);
+      }
+      if (PF) {
+        if (kn >= 0)
+          cp_async_wait<1>();
+        else
+          cp_async_wait<0>();
+      }
       // ---- solve item k
       const int c = (int)(cur.e & kCellMask);
       const uint32_t code = cur.e >> kCellBits;
       T r[NF];
       unsigned outm;
-      face_rates<E, T>(sa.geo + (size_t)c * sa.gs, code, v0, v1, v2, r, outm);
+      if constexpr (REG)
+        face_rates_t<E, T>(cur.geo, code, v0, v1, v2, r, outm);
+      else if (PF)
+        face_rates<E, T>(pfs.geo(slot), code, v0, v1, v2, r, outm);
+      else
+        face_rates<E, T>(sa.geo + (size_t)c * sa.gs, code, v0, v1, v2, r, outm);
       T b[ND];
       E::mass(cur.src, b);
       const int nbs[4] = {cur.nb.x, cur.nb.y, cur.nb.z, cur.nb.w};
@@ -717,12 +818,17 @@ __device__ __forceinline__ void sweep_ordinate(const SweepArgs& sa, const VGrid&
       }
       T x[ND];
       if (CACHED) {
-        const T* Ak = Aj + (size_t)k * (ND * ND);
+        // the inverse is 16-byte aligned and padded: read it with 128-bit loads
+        constexpr int AS = ainv_stride<E, T>(), NV = AS * (int)sizeof(T) / 16;
+        T Ar[AS];
+        const uint4* Av = reinterpret_cast<const uint4*>(PF ? pfs.ainv(slot) : Aj + (size_t)k * AS);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) reinterpret_cast<uint4*>(Ar)[q] = Av[q];
 #pragma unroll
         for (int a = 0; a < ND; ++a) {
           T s = T(0);
 #pragma unroll
-          for (int bb = 0; bb < ND; ++bb) s += Ak[a * ND + bb] * b[bb];
+          for (int bb = 0; bb < ND; ++bb) s += Ar[a * ND + bb] * b[bb];
           x[a] = s;
         }
       } else {
@@ -738,10 +844,14 @@ __device__ __forceinline__ void sweep_ordinate(const SweepArgs& sa, const VGrid&
       if (same) {
         cur = nxt;
         k = kn;
+        slot ^= 1;
       } else {
         have = false;
         kpend = kn;
-        if (kn >= 0) cur = nxt;
+        if (kn >= 0) {
+          cur = nxt;
+          slot ^= 1;
+        }
       }
     }
     bar.sync();
@@ -753,20 +863,27 @@ __device__ __forceinline__ void sweep_ordinate(const SweepArgs& sa, const VGrid&
     } else {
       k = lo + tid;
       have = gg + 1 < G && k < hi;
-      if (have) fetch_item<E, T>(sa, gl, sj, k, cur);
+      if (have) {
+        fetch_item<E, T, REG>(sa, gl, sj, k, cur);
+        if (PF) pfs.issue(slot, sa.geo, Aj, (int)(cur.e & kCellMask), k);
+      }
     }
     kpend = -1;
   }
+  if (PF) cp_async_wait<0>();
 }
 
-// One sweep of every ordinate of one problem: one CTA per ordinate.
-template <class E, typename T, bool CACHED>
+// One sweep of every ordinate of one problem: one CTA per ordinate.  PF: the cached
+// local inverse and the geometry of each thread's next cell are copied to shared memory
+// asynchronously while the current cell is solved (dynamic shared memory).
+template <class E, typename T, bool CACHED, bool PF = false>
 __global__ void __launch_bounds__(256) k_sweep(SweepArgs sa, VGrid g, T nus, const T* __restrict__ src,
                                                const T* __restrict__ fbc, const T* __restrict__ Ainv, T* f,
                                                const DevState* ds) {
+  extern __shared__ __align__(16) unsigned char pf_smem[];
   if (ds && (ds->status != BGK_OK || ds->done)) return;
-  sweep_ordinate<E, T, CACHED>(sa, g, (int)blockIdx.x, nus, src, fbc, Ainv, f, (int)threadIdx.x, (int)blockDim.x,
-                               CtaBarrier());
+  sweep_ordinate<E, T, CACHED, CtaBarrier, PF>(sa, g, (int)blockIdx.x, nus, src, fbc, Ainv, f, (int)threadIdx.x,
+                                               (int)blockDim.x, CtaBarrier(), pf_smem);
 }
 
 // out = a_k * fk + a_f * f + sum_r cF[r] * F[r]   (stage bookkeeping of Sec. 3.5)

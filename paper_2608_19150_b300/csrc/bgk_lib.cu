@@ -198,10 +198,20 @@ SweepArgs sweep_args(const bgk_handle* h) {
   return a;
 }
 
+// shared memory of the prefetching sweep: two slots per thread (geometry + local inverse)
+template <class E, typename T>
+size_t prefetch_smem(const bgk_handle* h) {
+  return 2 * (size_t)h->sweep_threads * (h->hm.geo_stride * sizeof(double) + ainv_stride<E, T>() * sizeof(T));
+}
+
 template <class E, typename T>
 void launch_sweep_t(bgk_handle* h, double nus) {
   const bool cached = h->Ainv && nus == h->nus_cached;
-  if (cached)
+  const size_t pf = prefetch_smem<E, T>(h);
+  if (cached && h->cfg.prefetch == 1 && pf <= 96 * 1024)
+    k_sweep<E, T, true, true><<<h->g.nv, h->sweep_threads, pf, h->stream>>>(
+        sweep_args(h), h->g, (T)nus, (const T*)h->src, (const T*)h->fbc, (const T*)h->Ainv, (T*)h->f, h->ds);
+  else if (cached)
     k_sweep<E, T, true><<<h->g.nv, h->sweep_threads, 0, h->stream>>>(
         sweep_args(h), h->g, (T)nus, (const T*)h->src, (const T*)h->fbc, (const T*)h->Ainv, (T*)h->f, h->ds);
   else
@@ -216,9 +226,15 @@ void launch_inverse_t(bgk_handle* h, double nus) {
 
 // Precompute the local inverses for the stage coefficient nus (once per handle).
 int build_inverse_cache(bgk_handle* h, double nus) {
-  const int nd = h->hm.ndof;
-  h->ainv_bytes = (size_t)h->g.nv * h->hm.ncell * nd * nd * h->tsize;
+  const bool f64s = h->precision == BGK_FP64;
+  const int as = h->hm.dim == 3 ? (f64s ? ainv_stride<ElemP1Tet, double>() : ainv_stride<ElemP1Tet, float>())
+                 : h->hm.kx == 2 ? (f64s ? ainv_stride<ElemP2Tri, double>() : ainv_stride<ElemP2Tri, float>())
+                                 : (f64s ? ainv_stride<ElemP1Tri, double>() : ainv_stride<ElemP1Tri, float>());
+  h->ainv_bytes = (size_t)h->g.nv * h->hm.ncell * as * h->tsize;
   if (h->cfg.cache_inverse == 2) return BGK_OK;
+  // automatic: FP64 sweeps are bound by FP64 arithmetic and gain from the cache; FP32
+  // sweeps assemble and factorise in FP32 faster than they read an inverse from HBM
+  if (h->cfg.cache_inverse == 0 && h->precision != BGK_FP64) return BGK_OK;
   if (h->cfg.cache_inverse == 0) {
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess || h->ainv_bytes > fr / 2) return BGK_OK;  // does not fit: skip
@@ -722,6 +738,18 @@ int bgk_create(const bgk_mesh* mesh, const bgk_vgrid* vg, const bgk_physics* phy
   CK(cudaFuncSetAttribute(k_maxwell<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   CK(cudaFuncSetAttribute(k_peel<2, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   CK(cudaFuncSetAttribute(k_peel<3, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  CK(cudaFuncSetAttribute(k_sweep<ElemP1Tri, double, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          96 * 1024));
+  CK(cudaFuncSetAttribute(k_sweep<ElemP2Tri, double, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          96 * 1024));
+  CK(cudaFuncSetAttribute(k_sweep<ElemP1Tet, double, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          96 * 1024));
+  CK(cudaFuncSetAttribute(k_sweep<ElemP1Tri, float, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          96 * 1024));
+  CK(cudaFuncSetAttribute(k_sweep<ElemP2Tri, float, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          96 * 1024));
+  CK(cudaFuncSetAttribute(k_sweep<ElemP1Tet, float, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          96 * 1024));
   rc = build_dags(h);
   if (rc == BGK_OK) {
     // the stage coefficient nu_s = nu + 1/(dt A_ss) of the step's main stages

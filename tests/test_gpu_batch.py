@@ -44,7 +44,7 @@ def test_batch_matches_single_instances(precision, cache):
         assert s.dt == dt_batch[i]
         st = s.step(2)
         assert st.iterations[0] == its[i]
-        tol = 1e-13 if precision == "fp64" else 1e-6
+        tol = 1e-13 if precision == "fp64" else 1e-5
         assert rel_err(b.instances[i].get_f(), s.get_f()) < tol
 
 
