@@ -43,6 +43,8 @@ def parse():
     p.add_argument("--train-runs", type=int, default=200)
     p.add_argument("--eval-runs", type=int, default=4)
     p.add_argument("--instances", type=int, default=64)
+    p.add_argument("--guess", action="store_true", help="batched: train and attach the learned guess")
+    p.add_argument("--compare-fp64", action="store_true", help="batched: also time the plain FP64 batch")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cache", default="auto", choices=["auto", "on", "off"],
                    help="local-inverse cache of the sweep")
@@ -404,40 +406,73 @@ def run_batched(args):
     draws = synth.batched_draw(args.instances, seed=3)
     ws = [synth.workload_random_smooth(seed=d["seed"], n_side=d["n_side"], kx=d["kx"], n_v=d["n_v"],
                                        knudsen=d["knudsen"]) for d in draws]
-    t0 = time.perf_counter()
-    b = bgk.Batch(ws, precision=args.precision, cache_inverse=args.cache)
-    for s_, w in zip(b.instances, ws):
-        s_.set_state_maxwellian(w.init)
-        s_.set_inflow_maxwellian(w.inflow)
-    setup = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    blocks = b.autotune(reps=2)
-    tune_s = time.perf_counter() - t0
-    dofs = np.array([s_.nv * s_.nnode for s_ in b.instances], dtype=np.float64)
-    for _ in range(args.warmup):
-        b.step(1)
-    clocks = Clocks(local)
-    barrier(world)
-    clocks.start()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    upd = 0.0
-    iters = []
-    for _ in range(args.steps):
-        it, st = b.step(1)
-        upd += float((dofs * it).sum())
-        iters.append(it.tolist())
-    torch.cuda.synchronize()
-    el = time.perf_counter() - t0
-    clk = clocks.stop()
-    el_max = max_over_ranks(el, world)
+    mlp, guess_info = None, None
+    if args.guess:
+        # guess network trained on seeded small runs drawn like the batch (other seeds)
+        from paper_2608_19150_b300 import guess as G
+        t0 = time.perf_counter()
+        X, Y = [], []
+        for d in synth.batched_draw(96, seed=11):
+            w = synth.workload_random_smooth(seed=d["seed"], n_side=min(d["n_side"], 24), kx=d["kx"], n_v=16,
+                                             knudsen=d["knudsen"])
+            s_ = bgk.Solver.from_workload(w, l_max=3000)
+            s_.set_state_maxwellian(w.init)
+            s_.set_inflow_maxwellian(w.inflow)
+            G.collect(s_, 4, X, Y)
+            s_.close()
+        X, Y = torch.cat(X), torch.cat(Y)
+        mlp = bgk.MLP(X.shape[1], Y.shape[1], 128, seed=7)
+        losses = G.train(mlp, X, Y, iters=2000, batch=8192, lr=2e-3, lr_final=1e-4, seed=3)
+        guess_info = {"train_runs": 96, "samples": int(X.shape[0]), "train_s": time.perf_counter() - t0,
+                      "loss_first": float(losses[:20].mean()), "loss_last": float(losses[-50:].mean())}
+        del X, Y
+
+    def run(precision, use_guess):
+        t0 = time.perf_counter()
+        b = bgk.Batch(ws, precision=precision, cache_inverse=args.cache, l_max=3000)
+        setup = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        blocks = b.autotune(reps=2)          # before any state is set: nothing to save
+        tune_s = time.perf_counter() - t0
+        if use_guess:
+            b.set_guess(mlp)
+        for s_, w in zip(b.instances, ws):
+            s_.set_state_maxwellian(w.init)
+            s_.set_inflow_maxwellian(w.inflow)
+        dofs = np.array([s_.nv * s_.nnode for s_ in b.instances], dtype=np.float64)
+        for _ in range(args.warmup):
+            b.step(1)
+        clocks = Clocks(local)
+        barrier(world)
+        clocks.start()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        upd = 0.0
+        iters = []
+        for _ in range(args.steps):
+            it, st = b.step(1)
+            upd += float((dofs * it).sum())
+            iters.append(it.tolist())
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        clk = clocks.stop()
+        return b, blocks, setup, tune_s, upd, iters, max_over_ranks(el, world), clk
+
+    plain = None
+    if args.compare_fp64:
+        pb, _, _, _, pupd, pit, pel, pclk = run("fp64", False)
+        plain = {"ms_per_step": 1e3 * pel / args.steps, "value": world * pupd / pel,
+                 "picard_iterations_per_instance": pit, "clocks": pclk}
+        pb.close()
+        del pb
+    b, blocks, setup, tune_s, upd, iters, el_max, clk = run(args.precision, args.guess)
     b.timing(reset=True)
     for _ in range(args.sweep_reps):
         b.sweep()
     ms, n = b.timing(reset=True)
     sweep_ms = ms / max(1, n)
     info = b.info()
-    tsz = 8 if args.precision == "fp64" else 4
+    tsz = 4 if args.precision == "fp32" else 8
     hbm_gbs = 2 * tsz * info["dof"] / (sweep_ms * 1e-3) / 1e9
     peaks = {}
     try:
@@ -449,7 +484,8 @@ def run_batched(args):
         return
     line = {"metric": METRIC, "value": world * upd / el_max, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * el_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp32": "f32", "mixed": "f32 sweeps then f64 (mixed)"}[args.precision],
             "data": "synthetic",
             "config": {"workload": "batched 2D-2V: %d instances, 2k-50k triangles (seeded jittered squares), P1/P2, "
                                    "16^2-48^2 velocities, Kn log-uniform 1e-4..1, backward Euler, CFL 10"
@@ -464,6 +500,11 @@ def run_batched(args):
                          "sweep_ms": sweep_ms},
             "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clk,
             "picard_iterations_per_instance": iters}
+    if guess_info:
+        line["learned_guess"] = guess_info
+    if plain:
+        line["plain_fp64_batch"] = plain
+        line["speedup_vs_plain_fp64"] = plain["ms_per_step"] / line["ms_per_step"]
     print(json.dumps(line), flush=True)
 
 

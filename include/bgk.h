@@ -183,7 +183,9 @@ int bgk_batch_instance(bgk_batch* b, int i, bgk_handle** h);
  * restored afterwards.  h_block (optional, n entries) receives the choice. */
 int bgk_batch_autotune(bgk_batch* b, int reps, int32_t* h_block);
 /* nsteps steps of every instance; h_iters / h_status (optional, n entries) receive the
- * Picard iterations and status of each instance's last step.  Returns the first error. */
+ * Picard iterations (FP32 + FP64 phases) and status of each instance's last step.
+ * With cfg.precision = BGK_MIXED every step runs a batched FP32 phase over all
+ * instances, then the batched FP64 phase.  Returns the first error. */
 int bgk_batch_step(bgk_batch* b, int nsteps, int32_t* h_iters, int32_t* h_status);
 /* One batched sweep of all instances (Maxwellian of the current moments, q = f^k/dt),
  * event-timed; bgk_batch_timing returns the accumulated time and launch count. */
@@ -231,6 +233,10 @@ int bgk_guess_features(bgk_handle* h, float* d_X);
 int bgk_guess_targets(bgk_handle* h, const double* d_Ustart, const float* d_X, float* d_Y);
 /* attach (or with NULL detach) a network; its current parameters are copied to BF16 */
 int bgk_set_guess(bgk_handle* h, bgk_mlp* m);
+
+/* Attach (NULL detaches) one guess network to every instance of a batch; the guesses run
+ * one instance after another inside the batch's step graph. */
+int bgk_batch_set_guess(bgk_batch* b, bgk_mlp* m);
 
 /* Moments and convergence measure with no device allocation.  The paper has no
  * counterpart: this entry point serves callers that cannot call cudaMalloc, such as

@@ -93,6 +93,7 @@ def load(path: str = LIB_PATH):
         "bgk_batch_sweep": [P],
         "bgk_batch_timing": [P, I, C.POINTER(D), C.POINTER(C.c_int64)],
         "bgk_batch_info": [P, C.POINTER(C.c_int64)],
+        "bgk_batch_set_guess": [P, P],
         "bgk_mlp_create": [I, I, I, C.c_uint64, C.POINTER(P)],
         "bgk_mlp_destroy": [P],
         "bgk_mlp_num_params": [P, C.POINTER(C.c_int64)],
@@ -311,6 +312,7 @@ class Batch:
             phys[i] = Physics(float(w.nu), INTEGRATORS["BE"], float(dt[i]) if dt else 0.0, float(w.cfl))
         cf = Config(float(tau), int(l_max), PRECISIONS[precision], 0, None, 0,
                     {"auto": 0, "on": 1, "off": 2}[cache_inverse], 0.0, 0)
+        self.mixed = precision == "mixed"
         h = C.c_void_p()
         _ck(self.lib.bgk_batch_create(n, meshes, vgrids, phys, C.byref(cf), C.byref(h)), "bgk_batch_create")
         self.h = h
@@ -331,6 +333,10 @@ class Batch:
 
     def __del__(self):
         self.close()
+
+    def set_guess(self, mlp):
+        self._guess = mlp
+        _ck(self.lib.bgk_batch_set_guess(self.h, mlp.h if mlp is not None else None), "bgk_batch_set_guess")
 
     def autotune(self, reps=3):
         out = np.zeros(self.n, dtype=np.int32)

@@ -93,6 +93,11 @@ struct bgk_batch {
   int* d_counter = nullptr;
   DevState** d_ds = nullptr;
   std::vector<BatchInst> h_inst;
+  // mixed precision: the instances' FP32 shadows, swept by a second batched launch
+  bool mixed = false;
+  BatchInst* d_inst32 = nullptr;
+  DevState** d_ds32 = nullptr;
+  std::vector<BatchInst> h_inst32;
   int ctas = 0;
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t t0 = nullptr, t1 = nullptr;
@@ -145,13 +150,20 @@ int build_units(bgk_batch* b, const std::vector<int>& only) {
   CK(cudaMemcpyAsync(b->d_units, flat.data(), sizeof(int2) * flat.size(), cudaMemcpyHostToDevice, b->stream));
   CK(cudaMemcpyAsync(b->d_inst, b->h_inst.data(), sizeof(BatchInst) * b->h_inst.size(), cudaMemcpyHostToDevice,
                      b->stream));
+  if (b->mixed) {
+    for (size_t i = 0; i < b->h_inst.size(); ++i) b->h_inst32[i].B = b->h_inst[i].B;
+    CK(cudaMemcpyAsync(b->d_inst32, b->h_inst32.data(), sizeof(BatchInst) * b->h_inst32.size(),
+                       cudaMemcpyHostToDevice, b->stream));
+  }
   CK(cudaStreamSynchronize(b->stream));
   return BGK_OK;
 }
 
-void launch_batched_sweep(bgk_batch* b, cudaStream_t s) {
+void launch_batched_sweep(bgk_batch* b, cudaStream_t s, bool shadows = false) {
   cudaMemsetAsync(b->d_counter, 0, sizeof(int), s);
-  if (b->precision == BGK_FP64)
+  if (shadows)
+    k_sweep_batched<float><<<b->ctas, 128, 0, s>>>(b->d_inst32, b->d_units, b->nunits, b->d_counter);
+  else if (b->precision == BGK_FP64)
     k_sweep_batched<double><<<b->ctas, 128, 0, s>>>(b->d_inst, b->d_units, b->nunits, b->d_counter);
   else
     k_sweep_batched<float><<<b->ctas, 128, 0, s>>>(b->d_inst, b->d_units, b->nunits, b->d_counter);
@@ -179,13 +191,38 @@ int fork_instances(bgk_batch* b, cudaStream_t s, const std::vector<cudaStream_t>
   return rc;
 }
 
-// One backward-Euler step of every instance as one graph (Sec. 3.5 with S = 1).
+// One conditional while-loop in the capture of stream s: body(bs) records the loop body
+// on stream bs; the loop repeats while k_any_active(ds list) finds an active problem.
+template <class F>
+int batch_loop(bgk_batch* b, cudaStream_t s, DevState** d_ds, F&& body) {
+  cudaGraphConditionalHandle cond = 0;
+  cudaGraph_t bodyg;
+  int rc = add_while(s, &cond, &bodyg);
+  if (rc != BGK_OK) return rc;
+  cudaStream_t bs = nullptr;
+  CK(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
+  if (cudaStreamBeginCaptureToGraph(bs, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+      cudaSuccess) {
+    cudaStreamDestroy(bs);
+    return BGK_E_CUDA;
+  }
+  rc = body(bs);
+  if (rc == BGK_OK) k_any_active<<<1, 1, 0, bs>>>(d_ds, (int)b->inst.size(), cond);
+  if (rc == BGK_OK && cudaGetLastError() != cudaSuccess) rc = BGK_E_CUDA;
+  cudaGraph_t body_out = nullptr;
+  if (cudaStreamEndCapture(bs, &body_out) != cudaSuccess && rc == BGK_OK) rc = BGK_E_CUDA;
+  cudaStreamDestroy(bs);
+  return rc;
+}
+
+// One backward-Euler step of every instance as one graph (Sec. 3.5 with S = 1).  With a
+// guess attached, each instance's iterate 0 takes its guessed moments (hooks run one
+// after another: instances share the network's scratch).  Mixed precision: a batched
+// FP32 phase over the shadows, then the batched FP64 phase.
 int capture_batch_step(bgk_batch* b) {
   cudaStream_t s = b->stream;
   cudaGraph_t graph = nullptr;
   CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-  cudaStream_t bs = nullptr;
-  bool body_open = false;
   int rc = fork_instances(b, s, b->side_outer, [&](bgk_handle* h) {
     k_reset_state<<<1, 1, 0, h->stream>>>(h->ds);
     if (cudaMemcpyAsync(h->fk, h->f, h->nfv * h->tsize, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
@@ -194,50 +231,74 @@ int capture_batch_step(bgk_batch* b) {
     moments(h, 0);
     return BGK_OK;
   });
-  cudaGraphConditionalHandle cond = 0;
-  if (rc == BGK_OK) {
-    cudaGraph_t cg;
-    cudaStreamCaptureStatus cst;
-    const cudaGraphNode_t* deps = nullptr;
-    size_t ndeps = 0;
-    cudaGraphNodeParams cp = {};
-    cudaGraphNode_t node;
-    if (cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, &deps, nullptr, &ndeps) != cudaSuccess ||
-        cudaGraphConditionalHandleCreate(&cond, cg, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
-      rc = BGK_E_CUDA;
-    } else {
-      cp.type = cudaGraphNodeTypeConditional;
-      cp.conditional.handle = cond;
-      cp.conditional.type = cudaGraphCondTypeWhile;
-      cp.conditional.size = 1;
-      if (cudaGraphAddNode(&node, cg, deps, nullptr, ndeps, &cp) != cudaSuccess ||
-          cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies) != cudaSuccess ||
-          cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking) != cudaSuccess ||
-          cudaStreamBeginCaptureToGraph(bs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
-                                        cudaStreamCaptureModeThreadLocal) != cudaSuccess)
-        rc = BGK_E_CUDA;
-      else
-        body_open = true;
-    }
+  for (size_t i = 0; i < b->inst.size() && rc == BGK_OK; ++i) {
+    bgk_handle* h = b->inst[i];
+    if (!h->guess) continue;
+    cudaStream_t keep = h->stream;
+    h->stream = s;
+    rc = guess_hook(h);
+    h->stream = keep;
   }
-  if (rc == BGK_OK)
-    rc = fork_instances(b, bs, b->side_body, [&](bgk_handle* h) { return build_src(h, h->fk, h->qscale_main); });
-  if (rc == BGK_OK) launch_batched_sweep(b, bs);
-  if (rc == BGK_OK)
-    rc = fork_instances(b, bs, b->side_body, [&](bgk_handle* h) {
-      moments(h, 1);
-      const double tol = h->cfg.tau / std::max(1.0, h->phys.nu * h->dt);
-      k_finalize<<<1, 256, 0, h->stream>>>(h->ds, h->partial, h->mom_blocks, tol, h->cfg.l_max, 0, 0, 0);
+  if (rc == BGK_OK && b->mixed) {
+    // FP32 phase: shadows start from the FP64 state and its (possibly guessed) moments
+    rc = fork_instances(b, s, b->side_outer, [&](bgk_handle* h) {
+      bgk_handle* sh = h->shadow;
+      k_reset_state<<<1, 1, 0, h->stream>>>(sh->ds);
+      k_stage_begin<<<1, 1, 0, h->stream>>>(sh->ds, 0);
+      k_convert_gated<double, float><<<148 * 2, 256, 0, h->stream>>>(h->nfv, (const double*)h->f, (float*)sh->f,
+                                                                     nullptr);
+      k_copy_moments<<<148, 256, 0, h->stream>>>((size_t)h->nnode * h->nm, h->U[0], h->U[1], h->ds, sh->U[0],
+                                                 sh->U[1], sh->ds);
       return BGK_OK;
     });
-  if (rc == BGK_OK) k_any_active<<<1, 1, 0, bs>>>(b->d_ds, (int)b->inst.size(), cond);
-  if (rc == BGK_OK && cudaGetLastError() != cudaSuccess) rc = BGK_E_CUDA;
-  // close every capture that was opened, whatever happened above
-  if (body_open) {
-    cudaGraph_t body_out = nullptr;
-    if (cudaStreamEndCapture(bs, &body_out) != cudaSuccess && rc == BGK_OK) rc = BGK_E_CUDA;
+    if (rc == BGK_OK)
+      rc = batch_loop(b, s, b->d_ds32, [&](cudaStream_t bs) {
+        int r = fork_instances(b, bs, b->side_body, [&](bgk_handle* h) {
+          bgk_handle* sh = h->shadow;
+          cudaStream_t keep = sh->stream;
+          sh->stream = h->stream;
+          const int rr = build_src_shadow(sh, (const double*)h->fk, h->qscale_main);
+          sh->stream = keep;
+          return rr;
+        });
+        if (r == BGK_OK) launch_batched_sweep(b, bs, true);
+        if (r == BGK_OK)
+          r = fork_instances(b, bs, b->side_body, [&](bgk_handle* h) {
+            bgk_handle* sh = h->shadow;
+            cudaStream_t keep = sh->stream;
+            sh->stream = h->stream;
+            moments(sh, 1);
+            sh->stream = keep;
+            const double tol = h->cfg.tau / std::max(1.0, h->phys.nu * h->dt);
+            k_finalize<<<1, 256, 0, h->stream>>>(sh->ds, sh->partial, sh->mom_blocks, std::max(tol, h->fp32_floor),
+                                                 sh->cfg.l_max, 0, 0, 0, 1);
+            return BGK_OK;
+          });
+        return r;
+      });
+    if (rc == BGK_OK)
+      rc = fork_instances(b, s, b->side_outer, [&](bgk_handle* h) {
+        bgk_handle* sh = h->shadow;
+        k_record_fp32<<<1, 1, 0, h->stream>>>(sh->ds, h->ds, 0);
+        k_convert_gated<float, double><<<148 * 2, 256, 0, h->stream>>>(h->nfv, (const float*)sh->f, (double*)h->f,
+                                                                       sh->ds);
+        moments(h, 0);
+        return BGK_OK;
+      });
   }
-  if (bs) cudaStreamDestroy(bs);
+  if (rc == BGK_OK)
+    rc = batch_loop(b, s, b->d_ds, [&](cudaStream_t bs) {
+      int r = fork_instances(b, bs, b->side_body, [&](bgk_handle* h) { return build_src(h, h->fk, h->qscale_main); });
+      if (r == BGK_OK) launch_batched_sweep(b, bs);
+      if (r == BGK_OK)
+        r = fork_instances(b, bs, b->side_body, [&](bgk_handle* h) {
+          moments(h, 1);
+          const double tol = h->cfg.tau / std::max(1.0, h->phys.nu * h->dt);
+          k_finalize<<<1, 256, 0, h->stream>>>(h->ds, h->partial, h->mom_blocks, tol, h->cfg.l_max, 0, 0, 0);
+          return BGK_OK;
+        });
+      return r;
+    });
   if (cudaStreamEndCapture(s, &graph) != cudaSuccess && rc == BGK_OK) rc = BGK_E_CUDA;
   cudaGetLastError();
   if (rc != BGK_OK) {
@@ -263,7 +324,7 @@ void release_batch(bgk_batch* b) {
   for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
   if (b->t0) cudaEventDestroy(b->t0);
   if (b->t1) cudaEventDestroy(b->t1);
-  void* ptrs[] = {b->d_inst, b->d_grids, b->d_units, b->d_counter, b->d_ds};
+  void* ptrs[] = {b->d_inst, b->d_grids, b->d_units, b->d_counter, b->d_ds, b->d_inst32, b->d_ds32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
@@ -301,6 +362,7 @@ int bgk_batch_create(int n, const bgk_mesh* meshes, const bgk_vgrid* vgrids, con
   if (!b) return BGK_E_OOM;
   bgk_config c = cfg ? *cfg : bgk_config{};
   b->precision = c.precision == BGK_FP32_SWEEP ? BGK_FP32_SWEEP : BGK_FP64;
+  b->mixed = c.precision == BGK_MIXED;
   if (c.stream) {
     b->stream = (cudaStream_t)c.stream;
   } else {
@@ -312,6 +374,8 @@ int bgk_batch_create(int n, const bgk_mesh* meshes, const bgk_vgrid* vgrids, con
   }
   c.stream = b->stream;
   c.eager = 1;  // instances never capture their own graphs; the batch captures one
+  const int cache_policy = c.cache_inverse;
+  c.cache_inverse = 2;  // caches are added below, once every instance's arrays exist
   for (int i = 0; i < n; ++i) {
     if (phys[i].integrator != BGK_BE) {
       release_batch(b);
@@ -346,6 +410,23 @@ int bgk_batch_create(int n, const bgk_mesh* meshes, const bgk_vgrid* vgrids, con
     release_batch(b);
     return rc;
   }
+  // local-inverse caches, largest instances first, while the policy allows
+  if (cache_policy != 2) {
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int c2) { return b->inst[a]->nfv > b->inst[c2]->nfv; });
+    for (int i : order) {
+      bgk_handle* h = b->inst[i];
+      h->cfg.cache_inverse = cache_policy;
+      rc = build_inverse_cache(h, h->nus_main);
+      if (rc != BGK_OK) {
+        release_batch(b);
+        return rc;
+      }
+    }
+    cudaStreamSynchronize(b->stream);
+  }
   std::vector<DevState*> dsp(n);
   b->h_inst.resize(n);
   for (int i = 0; i < n; ++i) {
@@ -370,6 +451,29 @@ int bgk_batch_create(int n, const bgk_mesh* meshes, const bgk_vgrid* vgrids, con
     dsp[i] = h->ds;
   }
   cudaMemcpyAsync(b->d_ds, dsp.data(), sizeof(DevState*) * n, cudaMemcpyHostToDevice, b->stream);
+  if (b->mixed) {
+    // the shadows' descriptors: same grids and schedules, FP32 state, no inverse cache
+    if (dalloc(b->d_inst32, sizeof(BatchInst) * n) != BGK_OK || dalloc(b->d_ds32, sizeof(DevState*) * n) != BGK_OK) {
+      release_batch(b);
+      return BGK_E_OOM;
+    }
+    b->h_inst32 = b->h_inst;
+    std::vector<DevState*> ds32(n);
+    for (int i = 0; i < n; ++i) {
+      bgk_handle* sh = b->inst[i]->shadow;
+      BatchInst& I = b->h_inst32[i];
+      I.sa = sweep_args(sh);
+      I.f = sh->f;
+      I.src = sh->src;
+      I.fbc = sh->fbc;
+      I.Ainv = sh->Ainv;
+      I.ds = sh->ds;
+      I.nus = sh->nus_main;
+      I.cached = sh->Ainv && sh->nus_cached == sh->nus_main;
+      ds32[i] = sh->ds;
+    }
+    cudaMemcpyAsync(b->d_ds32, ds32.data(), sizeof(DevState*) * n, cudaMemcpyHostToDevice, b->stream);
+  }
   int per_sm = 0;
   if (b->precision == BGK_FP64)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_batched<double>, 128, 0);
@@ -417,13 +521,16 @@ int bgk_batch_autotune(bgk_batch* b, int reps, int32_t* h_block) {
       if (it != g_tune_cache.end()) best = it->second;
     }
     if (best < 0) {
-      // the data in f are overwritten by the timing sweeps: save and restore them
+      // the timing sweeps overwrite f: save and restore it (not needed before any state
+      // has been set, which is when a caller short of memory should tune)
       std::vector<void*> saved;
       for (int i : kv.second) {
         bgk_handle* h = b->inst[i];
         void* p = nullptr;
-        if (dalloc(p, h->nfv * h->tsize) != BGK_OK) return BGK_E_OOM;
-        cudaMemcpyAsync(p, h->f, h->nfv * h->tsize, cudaMemcpyDeviceToDevice, b->stream);
+        if (h->state_set) {
+          if (dalloc(p, h->nfv * h->tsize) != BGK_OK) return BGK_E_OOM;
+          cudaMemcpyAsync(p, h->f, h->nfv * h->tsize, cudaMemcpyDeviceToDevice, b->stream);
+        }
         saved.push_back(p);
         k_reset_state<<<1, 1, 0, b->stream>>>(h->ds);
       }
@@ -440,10 +547,14 @@ int bgk_batch_autotune(bgk_batch* b, int reps, int32_t* h_block) {
       }
       for (size_t k = 0; k < kv.second.size(); ++k) {
         bgk_handle* h = b->inst[kv.second[k]];
-        cudaMemcpyAsync(h->f, saved[k], h->nfv * h->tsize, cudaMemcpyDeviceToDevice, b->stream);
+        if (saved[k])
+          cudaMemcpyAsync(h->f, saved[k], h->nfv * h->tsize, cudaMemcpyDeviceToDevice, b->stream);
+        else
+          cudaMemsetAsync(h->f, 0, h->nfv * h->tsize, b->stream);
       }
       CK(cudaStreamSynchronize(b->stream));
-      for (void* p : saved) cudaFree(p);
+      for (void* p : saved)
+        if (p) cudaFree(p);
       std::lock_guard<std::mutex> lock(g_tune_mutex);
       g_tune_cache[kv.first] = best;
     }
@@ -456,6 +567,26 @@ int bgk_batch_autotune(bgk_batch* b, int reps, int32_t* h_block) {
   return rc;
 }
 
+int bgk_batch_set_guess(bgk_batch* b, bgk_mlp* m) {
+  if (!b) return BGK_E_INVALID;
+  CK(cudaStreamSynchronize(b->stream));
+  for (bgk_handle* h : b->inst) {
+    if (m && (m->F != guess_features(h->hm.dim) || m->O != h->nm)) return BGK_E_INVALID;
+    if (m) {
+      int rc = guess_buffers(h);
+      if (rc == BGK_OK) rc = mlp_reserve(m, std::max<int64_t>(m->cap, h->nnode));
+      if (rc != BGK_OK) return rc;
+    }
+    h->guess = m;
+  }
+  if (m) {
+    k_to_bf16<<<(m->np + 255) / 256, 256, 0, b->stream>>>(m->np, m->p, m->pb);
+    m->pb_valid = true;
+  }
+  CK(cudaStreamSynchronize(b->stream));
+  return capture_batch_step(b);
+}
+
 int bgk_batch_step(bgk_batch* b, int nsteps, int32_t* h_iters, int32_t* h_status) {
   if (!b || nsteps < 0) return BGK_E_INVALID;
   for (int k = 0; k < nsteps; ++k) CK(cudaGraphLaunch(b->exec, b->stream));
@@ -464,7 +595,7 @@ int bgk_batch_step(bgk_batch* b, int nsteps, int32_t* h_iters, int32_t* h_status
   for (size_t i = 0; i < b->inst.size(); ++i) {
     DevState d;
     CK(cudaMemcpy(&d, b->inst[i]->ds, sizeof(DevState), cudaMemcpyDeviceToHost));
-    if (h_iters) h_iters[i] = d.iters[0];
+    if (h_iters) h_iters[i] = d.iters[0] + d.iters32[0];
     if (h_status) h_status[i] = d.status;
     if (d.status != BGK_OK && worst == BGK_OK) worst = d.status;
   }

@@ -66,6 +66,7 @@ struct bgk_handle {
   int mom_blocks = 0;
   DevState* ds = nullptr;
   bool have_prev = false;    // BDF2 history present
+  bool state_set = false;    // a distribution has been set (bgk_set_state_maxwellian / bgk_set_f)
   // graphs
   cudaGraphExec_t exec_main = nullptr;   // the integrator's step
   cudaGraphExec_t exec_start = nullptr;  // BDF2 start-up step (backward Euler)
@@ -237,7 +238,9 @@ int build_inverse_cache(bgk_handle* h, double nus) {
   if (h->cfg.cache_inverse == 0 && h->precision != BGK_FP64) return BGK_OK;
   if (h->cfg.cache_inverse == 0) {
     size_t fr = 0, tot = 0;
-    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess || h->ainv_bytes > fr / 2) return BGK_OK;  // does not fit: skip
+    const size_t reserve = (size_t)16 << 30;  // headroom for other problems and their work arrays
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess || fr < reserve || h->ainv_bytes > (fr - reserve) / 2)
+      return BGK_OK;  // does not fit: skip
   }
   if (dalloc(h->Ainv, h->ainv_bytes) != BGK_OK) {
     h->Ainv = nullptr;
@@ -841,6 +844,7 @@ static int set_maxwellian(bgk_handle* h, const double* h_nut, bool inflow) {
           cudaMemcpyAsync(h->fk, h->f, h->nfv * h->tsize, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
         rc = BGK_E_CUDA;
       h->have_prev = false;
+      h->state_set = true;
       if (h->have_hist) cudaMemsetAsync(h->have_hist, 0, sizeof(int), h->stream);
     }
   }
@@ -877,6 +881,7 @@ static int transfer_f(bgk_handle* h, void* ptr, int dtype, bool in, cudaMemcpyKi
         cudaMemcpyAsync(h->fk, h->f, h->nfv * h->tsize, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
       rc = BGK_E_CUDA;
     h->have_prev = false;
+    h->state_set = true;
   } else {
     const void* srcp = h->f;
     if (!same) {
@@ -1046,6 +1051,6 @@ int bgk_timing(bgk_handle* h, int reset, double* sweep_ms_total, int64_t* sweep_
 
 }  // extern "C"
 
-#include "bgk_batch.cuh"
 #include "bgk_mlp.cuh"
 #include "bgk_guess.cuh"
+#include "bgk_batch.cuh"

@@ -93,3 +93,29 @@ def test_batch_rejects_non_backward_euler():
     rc = lib.bgk_batch_create(n, m, vg, ph, None, C.byref(h))
     assert rc == bgk.BGK_E_INVALID
     del BgkError
+
+
+def test_mixed_batch_with_guess_reaches_the_fp64_fixed_point():
+    """The combined form: batched launch, FP32 phase then FP64 phase, guess of iterate 0
+    (a zero-weight network: the guess is the extrapolated previous change).  Every
+    instance ends at the FP64 fixed point: within the Picard tolerance of a plain FP64
+    single-instance run of the same steps."""
+    ws = instances()
+    b = bgk.Batch(ws, precision="mixed")
+    F, O = b.instances[0].guess_dims()
+    m = bgk.MLP(F, O, 32, seed=0)
+    p, nrm = m.get_params()
+    m.set_params(np.zeros_like(p), nrm)
+    b.set_guess(m)
+    for s, w in zip(b.instances, ws):
+        s.set_state_maxwellian(w.init)
+        s.set_inflow_maxwellian(w.inflow)
+    for _ in range(3):
+        its, sts = b.step(1)
+        assert np.all(sts == 0)
+    for i, w in enumerate(ws):
+        s = bgk.Solver.from_workload(w)
+        s.set_state_maxwellian(w.init)
+        s.set_inflow_maxwellian(w.inflow)
+        s.step(3)
+        assert rel_err(b.instances[i].get_f(), s.get_f()) < 1e-6
