@@ -247,6 +247,8 @@ int capture_batch_step(bgk_batch* b) {
       k_stage_begin<<<1, 1, 0, h->stream>>>(sh->ds, 0);
       k_convert_gated<double, float><<<148 * 2, 256, 0, h->stream>>>(h->nfv, (const double*)h->f, (float*)sh->f,
                                                                      nullptr);
+      k_convert_gated<double, float><<<148 * 2, 256, 0, h->stream>>>(h->nfv, (const double*)h->fk, (float*)sh->fk,
+                                                                     nullptr);
       k_copy_moments<<<148, 256, 0, h->stream>>>((size_t)h->nnode * h->nm, h->U[0], h->U[1], h->ds, sh->U[0],
                                                  sh->U[1], sh->ds);
       return BGK_OK;
@@ -257,7 +259,7 @@ int capture_batch_step(bgk_batch* b) {
           bgk_handle* sh = h->shadow;
           cudaStream_t keep = sh->stream;
           sh->stream = h->stream;
-          const int rr = build_src_shadow(sh, (const double*)h->fk, h->qscale_main);
+          const int rr = build_src_shadow(sh, (const float*)sh->fk, h->qscale_main);
           sh->stream = keep;
           return rr;
         });

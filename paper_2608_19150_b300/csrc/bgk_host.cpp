@@ -228,6 +228,12 @@ int build_vgrid(int dim, int N, int kv, double L, VGrid& g) {
     }
     for (int p = 0; p < n; ++p) g.lag[k][p] = c[p];
   }
+  for (int cl = 0; cl <= g.ncl; ++cl) g.bnd_f[cl] = (float)(-L + cl * g.h);
+  for (int cl = 0; cl < g.ncl; ++cl) g.mid_f[cl] = (float)(-L + (cl + 0.5) * g.h);
+  for (int m = 0; m < N; ++m) g.iw_f[m] = (float)(1.0 / g.w[m]);
+  for (int k = 0; k <= kMaxKv; ++k)
+    for (int p = 0; p <= kMaxKv; ++p) g.lag_f[k][p] = (float)g.lag[k][p];
+  g.hh_f = (float)(0.5 * g.h);
   return BGK_OK;
 }
 

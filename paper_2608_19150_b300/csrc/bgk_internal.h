@@ -23,6 +23,12 @@ struct VGrid {
   // Lagrange basis of one velocity cell in its local variable xi in [-1, 1]:
   // l_k(xi) = sum_p lag[k][p] xi^p  (same for every cell of the uniform grid).
   double lag[kMaxKv + 1][kMaxKv + 1];
+  // the same grid constants as floats, for projections computed in FP32
+  float bnd_f[kMaxN1D + 1];   // cell boundaries -L + c h
+  float mid_f[kMaxN1D];       // cell midpoints
+  float iw_f[kMaxN1D];        // 1 / w_m
+  float lag_f[kMaxKv + 1][kMaxKv + 1];
+  float hh_f;                 // h / 2
 };
 
 // Geometry of the mesh as the sweep needs it (Sec. 3.1 / 3.3).  Per cell: the d+1

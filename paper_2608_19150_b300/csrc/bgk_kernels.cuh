@@ -57,11 +57,34 @@ __device__ __forceinline__ uint32_t face_code(const double* __restrict__ G, cons
 // l_m the Lagrange basis of node m on its velocity cell, extended polynomially beyond
 // [-L, L] on the first and last cells.  Exact up to rounding via erfc and the Gaussian
 // partial-moment recurrence, in arithmetic R; writes scale * c[m] to out[m * stride].
+// grid constants in the projection's arithmetic type (floats precomputed on the host)
+template <typename R>
+struct GridVals;
+template <>
+struct GridVals<double> {
+  const VGrid& g;
+  __device__ double bnd(int c) const { return -g.L + c * g.h; }
+  __device__ double mid(int c) const { return -g.L + (c + 0.5) * g.h; }
+  __device__ double iw(int m) const { return 1.0 / g.w[m]; }
+  __device__ double lag(int k, int p) const { return g.lag[k][p]; }
+  __device__ double hh() const { return 0.5 * g.h; }
+};
+template <>
+struct GridVals<float> {
+  const VGrid& g;
+  __device__ float bnd(int c) const { return g.bnd_f[c]; }
+  __device__ float mid(int c) const { return g.mid_f[c]; }
+  __device__ float iw(int m) const { return g.iw_f[m]; }
+  __device__ float lag(int k, int p) const { return g.lag_f[k][p]; }
+  __device__ float hh() const { return g.hh_f; }
+};
+
 template <typename R, typename TO>
 __device__ __forceinline__ void proj_factors_t(const VGrid& g, R u, R theta, TO* out, size_t stride, R scale) {
   const R rs2 = (R)0.70710678118654752440, rs2pi = (R)0.39894228040143267794;
   const R sig = sqrt(theta), isig = R(1) / sig;
-  const R hh = (R)(0.5 * g.h);
+  const GridVals<R> gv{g};
+  const R hh = gv.hh();
   R tprev = -(R)INFINITY, phiprev = 0, Eprev = 0;
   for (int cl = 0; cl < g.ncl; ++cl) {
     R tb, phib, Eb;
@@ -70,7 +93,7 @@ __device__ __forceinline__ void proj_factors_t(const VGrid& g, R u, R theta, TO*
       phib = 0;
       Eb = 0;
     } else {
-      tb = ((R)(-g.L + (cl + 1) * g.h) - u) * isig;
+      tb = (gv.bnd(cl + 1) - u) * isig;
       phib = rs2pi * exp(R(-0.5) * tb * tb);
       Eb = R(0.5) * erfc(fabs(tb) * rs2);
     }
@@ -92,7 +115,7 @@ __device__ __forceinline__ void proj_factors_t(const VGrid& g, R u, R theta, TO*
       I[k] = (R)(k - 1) * I[k - 2] + (isinf(ta) ? R(0) : ap * phia) - (isinf(tb) ? R(0) : bp * phib);
     }
     // local variable xi = (v - mid)/(h/2) = alpha + beta t
-    const R mid = (R)(-g.L + (cl + 0.5) * g.h);
+    const R mid = gv.mid(cl);
     const R alpha = (u - mid) / hh, beta = sig / hh;
     R J[kMaxKv + 1];  // J_p = int phi (alpha + beta t)^p dt
     R binom[kMaxKv + 1] = {1, 0, 0, 0, 0};
@@ -111,9 +134,9 @@ __device__ __forceinline__ void proj_factors_t(const VGrid& g, R u, R theta, TO*
     }
     for (int k = 0; k < g.np; ++k) {
       R sacc = 0;
-      for (int p = 0; p < g.np; ++p) sacc += (R)g.lag[k][p] * J[p];
+      for (int p = 0; p < g.np; ++p) sacc += gv.lag(k, p) * J[p];
       const int m = cl * g.np + k;
-      out[(size_t)m * stride] = (TO)(scale * sacc / (R)g.w[m]);
+      out[(size_t)m * stride] = (TO)(scale * sacc * gv.iw(m));
     }
     tprev = tb;
     phiprev = phib;
@@ -536,6 +559,7 @@ __device__ __forceinline__ void lu_solve(T (&A)[N][N], T (&b)[N]) {
 // Sweep schedule of one ordinate, as the kernels see it.
 struct SweepArgs {
   const double* geo;
+  const float* geof;   // the same geometry as floats (FP32 sweeps)
   int gs;
   const int32_t* nbr;
   const uint64_t* perm;
@@ -708,9 +732,9 @@ __device__ __forceinline__ void fetch_item(const SweepArgs& sa, const uint32_t* 
 #pragma unroll
   for (int a = 0; a < E::NDOF; ++a) it.src[a] = sj[(size_t)c * E::NDOF + a];
   if constexpr (REG) {
-    const double* Gc = sa.geo + (size_t)c * sa.gs;
+    const float* Gc = sa.geof + (size_t)c * sa.gs;
 #pragma unroll
-    for (int q = 0; q <= E::NF * E::D; ++q) it.geo[q] = (T)Gc[q];
+    for (int q = 0; q <= E::NF * E::D; ++q) it.geo[q] = Gc[q];
   }
 }
 

@@ -40,6 +40,7 @@ struct bgk_handle {
   bool own_stream = false;
   // device geometry and schedule
   double* geo = nullptr;
+  float* geof = nullptr;     // FP32 copy of geo (FP32 sweeps)
   int32_t* nbr = nullptr;
   int32_t* nbr_face = nullptr;
   uint64_t* perm = nullptr;
@@ -187,6 +188,7 @@ void launch_moments(bgk_handle* h, int mode) {
 SweepArgs sweep_args(const bgk_handle* h) {
   SweepArgs a;
   a.geo = h->geo;
+  a.geof = h->geof;
   a.gs = h->hm.geo_stride;
   a.nbr = h->nbr;
   a.perm = h->perm;
@@ -314,12 +316,13 @@ int build_src(bgk_handle* h, const void* qsrc, double qscale) {
   return h->precision == BGK_FP64 ? build_src_t<double>(h, qsrc, qscale) : build_src_t<float>(h, qsrc, qscale);
 }
 
-// FP32 source of the shadow problem with the FP64 stage source q of the main problem.
-int build_src_shadow(bgk_handle* sh, const double* q64, double qscale) {
+// FP32 source of the shadow problem; q32 is the main problem's stage source q converted
+// to FP32 once per stage (held in the shadow's fk array, which the shadow does not use).
+int build_src_shadow(bgk_handle* sh, const float* q32, double qscale) {
   k_factors<float><<<(sh->nnode + 127) / 128, 128, 0, sh->stream>>>(sh->g, sh->nnode, sh->U[0], sh->U[1], sh->ds,
                                                                    sh->phys.nu, (float*)sh->cf);
-  k_source<float, double><<<148 * 16, 256, 0, sh->stream>>>(sh->g, sh->nnode, (const float*)sh->cf, q64,
-                                                            (float)qscale, (float*)sh->src, sh->ds);
+  k_source<float, float><<<148 * 16, 256, 0, sh->stream>>>(sh->g, sh->nnode, (const float*)sh->cf, q32,
+                                                           (float)qscale, (float*)sh->src, sh->ds);
   return cudaGetLastError() == cudaSuccess ? BGK_OK : BGK_E_CUDA;
 }
 
@@ -353,6 +356,7 @@ int shadow_phase(bgk_handle* h, int st, const void* qsrc, double qscale, double 
   k_reset_state<<<1, 1, 0, s>>>(sh->ds);
   k_stage_begin<<<1, 1, 0, s>>>(sh->ds, st);
   k_convert_gated<double, float><<<blk, thr, 0, s>>>(h->nfv, (const double*)h->f, (float*)sh->f, nullptr);
+  k_convert_gated<double, float><<<blk, thr, 0, s>>>(h->nfv, (const double*)qsrc, (float*)sh->fk, nullptr);
   k_copy_moments<<<148, 256, 0, s>>>((size_t)h->nnode * h->nm, h->U[0], h->U[1], h->ds, sh->U[0], sh->U[1], sh->ds);
   const double tol32 = std::max(tol, h->fp32_floor);
   cudaStream_t keep = sh->stream;
@@ -365,7 +369,7 @@ int shadow_phase(bgk_handle* h, int st, const void* qsrc, double qscale, double 
     CK(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
     CK(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     sh->stream = bs;
-    rc = build_src_shadow(sh, (const double*)qsrc, qscale);
+    rc = build_src_shadow(sh, (const float*)sh->fk, qscale);
     launch_sweep_any(sh, nus);
     moments(sh, 1);
     k_finalize<<<1, 256, 0, bs>>>(sh->ds, sh->partial, sh->mom_blocks, tol32, sh->cfg.l_max, st, cond, 1, 1);
@@ -377,7 +381,7 @@ int shadow_phase(bgk_handle* h, int st, const void* qsrc, double qscale, double 
   } else {
     sh->stream = s;
     for (;;) {
-      int rc = build_src_shadow(sh, (const double*)qsrc, qscale);
+      int rc = build_src_shadow(sh, (const float*)sh->fk, qscale);
       if (rc != BGK_OK) {
         sh->stream = keep;
         return rc;
@@ -594,7 +598,7 @@ void release(bgk_handle* h) {
   h->shadow = nullptr;
   if (h->exec_main) cudaGraphExecDestroy(h->exec_main);
   if (h->exec_start) cudaGraphExecDestroy(h->exec_start);
-  void* ptrs[] = {h->gX, h->gY, h->Uhist, h->have_hist,
+  void* ptrs[] = {h->gX, h->gY, h->Uhist, h->have_hist, h->geof,
                   h->geo, h->nbr, h->nbr_face, h->perm, h->bnode, h->glist, h->lvl, h->ngen, h->nproc, h->Ainv, h->f, h->fk,
                   h->fprev, h->src, h->fbc, h->q, h->F[0], h->F[1], h->F[2], h->U[0], h->U[1], h->partial, h->cf,
                   h->ds};
@@ -693,6 +697,7 @@ int bgk_create(const bgk_mesh* mesh, const bgk_vgrid* vg, const bgk_physics* phy
     if (rc == BGK_OK) rc = r;
   };
   A(dalloc(h->geo, sizeof(double) * hm.geo.size()));
+  A(dalloc(h->geof, sizeof(float) * hm.geo.size()));
   A(dalloc(h->nbr, sizeof(int32_t) * hm.nbr.size()));
   A(dalloc(h->nbr_face, sizeof(int32_t) * hm.nbr_face.size()));
   A(dalloc(h->perm, sizeof(uint64_t) * n));
@@ -725,6 +730,11 @@ int bgk_create(const bgk_mesh* mesh, const bgk_vgrid* vg, const bgk_physics* phy
   }
   cudaStream_t s = h->stream;
   CK(cudaMemcpyAsync(h->geo, hm.geo.data(), sizeof(double) * hm.geo.size(), cudaMemcpyHostToDevice, s));
+  {
+    std::vector<float> gf(hm.geo.begin(), hm.geo.end());
+    CK(cudaMemcpyAsync(h->geof, gf.data(), sizeof(float) * gf.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+  }
   CK(cudaMemcpyAsync(h->nbr, hm.nbr.data(), sizeof(int32_t) * hm.nbr.size(), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(h->nbr_face, hm.nbr_face.data(), sizeof(int32_t) * hm.nbr_face.size(), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(h->perm, hm.perm.data(), sizeof(uint64_t) * n, cudaMemcpyHostToDevice, s));
