@@ -330,6 +330,8 @@ static int build_geometry(orc_t *o) {
     if (j - i > 2) { free(keys); return ORC_E_INVALID; } /* non-manifold */
     if (j - i == 2) {
       size_t a = (size_t)keys[i].cell * nf + keys[i].face, b = (size_t)keys[i + 1].cell * nf + keys[i + 1].face;
+      /* the two cells must lie on opposite sides of the shared face (else they overlap) */
+      if (o->orient[a] == o->orient[b]) { free(keys); return ORC_E_INVALID; }
       o->nbr[a] = keys[i + 1].cell; o->nbr_face[a] = keys[i + 1].face;
       o->nbr[b] = keys[i].cell; o->nbr_face[b] = keys[i].face;
     }

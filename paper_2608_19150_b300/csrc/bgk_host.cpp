@@ -124,6 +124,11 @@ int build_host_mesh(const bgk_mesh* m, HostMesh& hm) {
         int c2 = it->second.first, f2 = it->second.second;
         if (c2 == c) return BGK_E_INVALID;
         if (hm.nbr[(size_t)c2 * 4 + f2] != INT32_MIN) return BGK_E_INVALID;  // non-manifold
+        // the two outward normals of a shared face are opposite unless the cells overlap
+        const double* G2 = hm.geo.data() + (size_t)c2 * hm.geo_stride + f2 * d;
+        double dn = 0.0;
+        for (int al = 0; al < d; ++al) dn += G[f * d + al] * G2[al];
+        if (!(dn < 0.0)) return BGK_E_INVALID;  // folded
         hm.nbr[(size_t)c * 4 + f] = c2;
         hm.nbr_face[(size_t)c * 4 + f] = f2;
         hm.nbr[(size_t)c2 * 4 + f2] = c;
