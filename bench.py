@@ -204,6 +204,21 @@ def max_over_ranks(x, world):
     return float(t.item())
 
 
+def sum_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_throughput(units, elapsed_max, world):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return sum_over_ranks(float(units), world) / elapsed_max
+
+
 def run_reference(args):
     """The reference arm: the CPU oracle as it stands, each step one oracle sweep over a
     bounded sample of the workload's ordinates (rank 0 only)."""
@@ -333,7 +348,7 @@ def run_ours(args):
     for _ in range(args.warmup):
         s.step(1)
     el_max, sweeps, iters, launches, clk = timed_steps(s, args.steps, world, local)
-    value = world * dof * sweeps / el_max   # equal work per rank (replicas)
+    value = job_throughput(dof * sweeps, el_max, world)
     # end to end through the C ABI with host buffers: f^k in from pinned host memory,
     # moments out to host, every step
     f_host = torch.empty(dof, dtype=torch.float64 if fdt == np.float64 else torch.float32, pin_memory=True)
@@ -348,7 +363,7 @@ def run_ours(args):
         e2e_sweeps += sum(list(st.iterations)[:st.n_stages]) + sum(list(st.iterations_fp32)[:st.n_stages])
         s.lib.bgk_get_moments(s.h, U.ctypes.data_as(bgk.C.c_void_p))
     el_e2e = max_over_ranks(time.perf_counter() - t0, world)
-    e2e = {"value": world * dof * e2e_sweeps / el_e2e, "unit": UNIT,
+    e2e = {"value": job_throughput(dof * e2e_sweeps, el_e2e, world), "unit": UNIT,
            "h2d_bytes_per_step": int(f_host.numel() * f_host.element_size()), "d2h_bytes_per_step": int(U.nbytes)}
     dt = s.dt
     s.close()
@@ -362,7 +377,7 @@ def run_ours(args):
         for _ in range(args.warmup):
             p.step(1)
         pe, psw, pit, _, pclk = timed_steps(p, args.steps, world, local)
-        plain = {"ms_per_step": 1e3 * pe / args.steps, "value": world * dof * psw / pe, "picard_iterations": pit,
+        plain = {"ms_per_step": 1e3 * pe / args.steps, "value": job_throughput(dof * psw, pe, world), "picard_iterations": pit,
                  "clocks": pclk}
         p.close()
         del p
@@ -461,7 +476,7 @@ def run_batched(args):
     plain = None
     if args.compare_fp64:
         pb, _, _, _, pupd, pit, pel, pclk = run("fp64", False)
-        plain = {"ms_per_step": 1e3 * pel / args.steps, "value": world * pupd / pel,
+        plain = {"ms_per_step": 1e3 * pel / args.steps, "value": job_throughput(pupd, pel, world),
                  "picard_iterations_per_instance": pit, "clocks": pclk}
         pb.close()
         del pb
@@ -482,7 +497,7 @@ def run_batched(args):
     hbm_peak = float(peaks.get("hbm_gbs", 6400.0))
     if rank != 0:
         return
-    line = {"metric": METRIC, "value": world * upd / el_max, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+    line = {"metric": METRIC, "value": job_throughput(upd, el_max, world), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * el_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp64": "f64", "fp32": "f32", "mixed": "f32 sweeps then f64 (mixed)"}[args.precision],
@@ -580,11 +595,12 @@ def run_learned(args):
             s.close()
         per_run.append(row)
     clk = clocks.stop()
+    value = job_throughput(dof * res["learned"][0], max_over_ranks(res["learned"][1], world), world)
     if rank != 0:
         return
     ms_plain = 1e3 * res["plain"][1] / res["plain"][2]
     ms_learn = 1e3 * res["learned"][1] / res["learned"][2]
-    line = {"metric": METRIC, "value": dof * res["learned"][0] / res["learned"][1], "unit": UNIT, "n_gpus": world,
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": 1, "ms_per_step": ms_learn, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
             "config": {"workload": "learned initial guess, 2D-2V: %dx%d squares (%d P1 triangles), 32x32 velocities, "
