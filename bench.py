@@ -328,6 +328,16 @@ def sweep_roofline(w, precision, reps, peaks):
     return r
 
 
+def state_errors(f, U, f_ref, U_ref, d):
+    """Relative differences after the same steps from the same state: f in the max norm,
+    each moment (n, n u, E) in the l2 norm over nodes (momentum relative to max(|n u|, |n|))."""
+    nrm = np.linalg.norm
+    return {"f_max_rel": float(np.abs(f - f_ref).max() / np.abs(f_ref).max()),
+            "n_l2_rel": float(nrm(U[:, 0] - U_ref[:, 0]) / nrm(U_ref[:, 0])),
+            "nu_l2_rel": float(nrm(U[:, 1:1 + d] - U_ref[:, 1:1 + d]) / max(nrm(U_ref[:, 1:1 + d]), nrm(U_ref[:, 0]))),
+            "E_l2_rel": float(nrm(U[:, -1] - U_ref[:, -1]) / nrm(U_ref[:, -1]))}
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_init(args)
@@ -349,6 +359,7 @@ def run_ours(args):
         s.step(1)
     el_max, sweeps, iters, launches, clk = timed_steps(s, args.steps, world, local)
     value = job_throughput(dof * sweeps, el_max, world)
+    f_end, U_end = s.get_f(np.float64), s.get_moments()
     # end to end through the C ABI with host buffers: f^k in from pinned host memory,
     # moments out to host, every step
     f_host = torch.empty(dof, dtype=torch.float64 if fdt == np.float64 else torch.float32, pin_memory=True)
@@ -378,7 +389,8 @@ def run_ours(args):
             p.step(1)
         pe, psw, pit, _, pclk = timed_steps(p, args.steps, world, local)
         plain = {"ms_per_step": 1e3 * pe / args.steps, "value": job_throughput(dof * psw, pe, world), "picard_iterations": pit,
-                 "clocks": pclk}
+                 "clocks": pclk,
+                 "error_vs_plain_fp64": state_errors(f_end, U_end, p.get_f(np.float64), p.get_moments(), p.dim)}
         p.close()
         del p
     # the sweep kernels, event-timed on their own stream

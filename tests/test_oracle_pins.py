@@ -6,6 +6,7 @@ graph algorithms, dense numpy solves), closed forms, and invariants the paper st
 """
 import itertools
 import math
+import os
 
 import mpmath
 import networkx as nx
@@ -14,6 +15,8 @@ import pytest
 
 from oracle.oracle import Oracle, tableau
 from paper_2608_19150_b300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
 def small_square(n=4, seed=0, kx=1, n1d=8, kv=3, L=6.0):
@@ -435,9 +438,14 @@ def test_discrete_conservation_law_backward_euler():
 # -------------------------------------------------------------- DIRK tableaus (App. A)
 def test_tableaus_match_printed_digits_and_order_conditions():
     A, b, c = tableau("DIRK3")
-    printed = [[0.435867, 0, 0], [0.282067, 0.435867, 0], [1.208497, -0.644363, 0.435867]]
-    np.testing.assert_allclose(A, printed, atol=5e-7)
-    np.testing.assert_allclose(c, [0.435867, 0.717933, 1.0], atol=5e-7)
+    rows = [ln.split("|") for ln in open(os.path.join(GOLDEN, "dirk3_tableau_printed.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    c_pr = [float(r[0]) for r in rows[:3]]
+    A_pr = [[float(x) for x in r[1].split()] for r in rows[:3]]
+    b_pr = [float(x) for x in rows[3][1].split()]
+    np.testing.assert_allclose(A, A_pr, atol=5e-7)
+    np.testing.assert_allclose(c, c_pr, atol=5e-7)
+    np.testing.assert_allclose(b, b_pr, atol=5e-7)
     np.testing.assert_allclose(b, A[-1], atol=1e-15)
     assert abs(b.sum() - 1) < 1e-14 and abs(b @ c - 0.5) < 1e-14
     assert abs(b @ c ** 2 - 1 / 3) < 1e-14 and abs(b @ A @ c - 1 / 6) < 1e-14
