@@ -257,20 +257,25 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def launches_per_step(st, guess=False):
-    """Kernels one step launches (graph nodes of kernel type), from its statistics."""
+def launches_per_step(st, guess=False, main_fp32=False):
+    """Kernels one step launches (graph nodes of kernel type), from its statistics.  FP32
+    sweeps form their source themselves (factors, sweep, moments, test per iteration);
+    FP64 iterations add the source pass."""
     n = 1
+    per_main = 4 if main_fp32 else 5
     for k in range(st.n_stages):
         n += 2 + (k > 0) + (k < st.n_stages - 1)          # stage set-up, moments, stage combines
         n += 9 if guess else 0
         if st.iterations_fp32[k]:
-            n += 7 + 5 * st.iterations_fp32[k]            # FP32 phase
-        n += 5 * st.iterations[k]                         # factors, source, sweep, moments, test
+            n += 7 + 4 * st.iterations_fp32[k]            # FP32 phase
+        n += per_main * st.iterations[k]
     return n
 
 
-def timed_steps(s, steps, world, local, guess=False):
-    """Run `steps` steps of solver s (already warmed up) timed on the device clock."""
+def timed_steps(s, steps, world, local, tstream, guess=False, main_fp32=False):
+    """Run `steps` steps of solver s (already warmed up; created on torch stream tstream),
+    each bracketed by CUDA events on that stream; the time is the sum of the steps'
+    device times (the statistics read between steps is not inside any bracket)."""
     import torch
     s.synchronize()
     sweeps0 = s.last_stats().total_sweeps
@@ -278,15 +283,21 @@ def timed_steps(s, steps, world, local, guess=False):
     barrier(world)
     clocks.start()
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    iters, launches = [], 0
+    iters, launches, el = [], 0, 0.0
     for _ in range(steps):
-        st = s.step(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(tstream)
+        s.step_async(1)
+        e1.record(tstream)
+        st = s.last_stats()
+        if st.status != 0:
+            raise RuntimeError("step failed with status %d" % st.status)
+        e1.synchronize()
+        el += e0.elapsed_time(e1) * 1e-3
         iters.append({"fp64": list(st.iterations)[:st.n_stages], "fp32": list(st.iterations_fp32)[:st.n_stages]})
-        launches += launches_per_step(st, guess)
+        launches += launches_per_step(st, guess, main_fp32)
     s.synchronize()
     torch.cuda.synchronize()
-    el = time.perf_counter() - t0
     barrier(world)
     clk = clocks.stop()
     sweeps = s.last_stats().total_sweeps - sweeps0
@@ -349,7 +360,9 @@ def run_ours(args):
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except OSError:
         pass
-    s = bgk.Solver.from_workload(w, precision=args.precision, eager=args.eager, cache_inverse=args.cache)
+    tstream = torch.cuda.Stream()
+    s = bgk.Solver.from_workload(w, precision=args.precision, eager=args.eager, cache_inverse=args.cache,
+                                 stream=tstream.cuda_stream)
     s.set_state_maxwellian(w.init)
     s.set_inflow_maxwellian(w.inflow)
     dof = s.nv * s.nnode
@@ -357,7 +370,8 @@ def run_ours(args):
     f0 = s.get_f(fdt)
     for _ in range(args.warmup):
         s.step(1)
-    el_max, sweeps, iters, launches, clk = timed_steps(s, args.steps, world, local)
+    el_max, sweeps, iters, launches, clk = timed_steps(s, args.steps, world, local, tstream,
+                                                       main_fp32=args.precision == "fp32")
     value = job_throughput(dof * sweeps, el_max, world)
     f_end, U_end = s.get_f(np.float64), s.get_moments()
     # end to end through the C ABI with host buffers: f^k in from pinned host memory,
@@ -382,12 +396,12 @@ def run_ours(args):
     # the plain FP64 path on the same steps, for the comparison the metric asks for
     plain = None
     if args.precision != "fp64":
-        p = bgk.Solver.from_workload(w, precision="fp64")
+        p = bgk.Solver.from_workload(w, precision="fp64", stream=tstream.cuda_stream)
         p.set_f(f0.astype(np.float64))
         p.set_inflow_maxwellian(w.inflow)
         for _ in range(args.warmup):
             p.step(1)
-        pe, psw, pit, _, pclk = timed_steps(p, args.steps, world, local)
+        pe, psw, pit, _, pclk = timed_steps(p, args.steps, world, local, tstream)
         plain = {"ms_per_step": 1e3 * pe / args.steps, "value": job_throughput(dof * psw, pe, world), "picard_iterations": pit,
                  "clocks": pclk,
                  "error_vs_plain_fp64": state_errors(f_end, U_end, p.get_f(np.float64), p.get_moments(), p.dim)}

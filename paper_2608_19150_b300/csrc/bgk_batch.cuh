@@ -30,10 +30,12 @@ struct BatchInst {
 template <typename T, class E>
 __device__ __noinline__ void batch_sweep_one(const BatchInst& I, int j, int tid, int nt, const NamedBarrier& bar) {
   if (I.cached)
-    sweep_ordinate<E, T, true>(I.sa, *I.g, j, (T)I.nus, (const T*)I.src, (const T*)I.fbc, (const T*)I.Ainv,
+    sweep_ordinate<E, T, true>(I.sa, *I.g, j, (T)I.nus, SrcArgs<T>{(const T*)I.src, nullptr, nullptr, T(0)},
+                               (const T*)I.fbc, (const T*)I.Ainv,
                                (T*)I.f, tid, nt, bar);
   else
-    sweep_ordinate<E, T, false>(I.sa, *I.g, j, (T)I.nus, (const T*)I.src, (const T*)I.fbc, nullptr, (T*)I.f, tid,
+    sweep_ordinate<E, T, false>(I.sa, *I.g, j, (T)I.nus, SrcArgs<T>{(const T*)I.src, nullptr, nullptr, T(0)},
+                                (const T*)I.fbc, nullptr, (T*)I.f, tid,
                                 nt, bar);
 }
 
@@ -390,6 +392,9 @@ int bgk_batch_create(int n, const bgk_mesh* meshes, const bgk_vgrid* vgrids, con
       release_batch(b);
       return rc;
     }
+    // the batched sweep reads a precomputed src
+    h->fuse_src = false;
+    if (h->shadow) h->shadow->fuse_src = false;
     b->inst.push_back(h);
   }
   const int ns = std::min(8, n);

@@ -79,8 +79,11 @@ struct GridVals<float> {
   __device__ float hh() const { return g.hh_f; }
 };
 
-template <typename R, typename TO>
-__device__ __forceinline__ void proj_factors_t(const VGrid& g, R u, R theta, TO* out, size_t stride, R scale) {
+// KV: the velocity degree k_v as a compile-time constant, so the per-cell arrays below
+// stay in registers (proj_factors_t dispatches on g.kv).
+template <typename R, typename TO, int KV>
+__device__ __forceinline__ void proj_factors_kv(const VGrid& g, R u, R theta, TO* out, size_t stride, R scale) {
+  constexpr int NP = KV + 1;
   const R rs2 = (R)0.70710678118654752440, rs2pi = (R)0.39894228040143267794;
   const R sig = sqrt(theta), isig = R(1) / sig;
   const GridVals<R> gv{g};
@@ -98,7 +101,7 @@ __device__ __forceinline__ void proj_factors_t(const VGrid& g, R u, R theta, TO*
       Eb = R(0.5) * erfc(fabs(tb) * rs2);
     }
     const R ta = tprev, phia = phiprev, Ea = Eprev;
-    R I[kMaxKv + 1];
+    R I[KV + 1];
     // I_0 = Phi(tb) - Phi(ta) from the tails that avoid cancellation
     if (ta >= 0)
       I[0] = Ea - Eb;
@@ -107,9 +110,10 @@ __device__ __forceinline__ void proj_factors_t(const VGrid& g, R u, R theta, TO*
     else
       I[0] = (R(1) - Eb) - Ea;
     // I_k = int t^k phi: I_1 = phi(a) - phi(b); I_k = (k-1) I_{k-2} + a^{k-1}phi(a) - b^{k-1}phi(b)
-    if (g.kv >= 1) I[1] = phia - phib;
+    if (KV >= 1) I[1] = phia - phib;
     R ap = 1, bp = 1;
-    for (int k = 2; k <= g.kv; ++k) {
+#pragma unroll
+    for (int k = 2; k <= KV; ++k) {
       ap = isinf(ta) ? R(0) : ap * ta;
       bp = isinf(tb) ? R(0) : bp * tb;
       I[k] = (R)(k - 1) * I[k - 2] + (isinf(ta) ? R(0) : ap * phia) - (isinf(tb) ? R(0) : bp * phib);
@@ -117,30 +121,49 @@ __device__ __forceinline__ void proj_factors_t(const VGrid& g, R u, R theta, TO*
     // local variable xi = (v - mid)/(h/2) = alpha + beta t
     const R mid = gv.mid(cl);
     const R alpha = (u - mid) / hh, beta = sig / hh;
-    R J[kMaxKv + 1];  // J_p = int phi (alpha + beta t)^p dt
-    R binom[kMaxKv + 1] = {1, 0, 0, 0, 0};
-    for (int p = 0; p <= g.kv; ++p) {
+    R J[KV + 1];  // J_p = int phi (alpha + beta t)^p dt
+    R binom[KV + 1];
+    binom[0] = 1;
+#pragma unroll
+    for (int q = 1; q <= KV; ++q) binom[q] = 0;
+#pragma unroll
+    for (int p = 0; p <= KV; ++p) {
       if (p > 0)
+#pragma unroll
         for (int q = p; q >= 1; --q) binom[q] += binom[q - 1];
-      R apow[kMaxKv + 1];
+      R apow[KV + 1];
       apow[0] = 1;
+#pragma unroll
       for (int q = 1; q <= p; ++q) apow[q] = apow[q - 1] * alpha;
       R sacc = 0, ab = 1;
+#pragma unroll
       for (int q = 0; q <= p; ++q) {
         sacc += binom[q] * apow[p - q] * ab * I[q];
         ab *= beta;
       }
       J[p] = sacc;
     }
-    for (int k = 0; k < g.np; ++k) {
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
       R sacc = 0;
-      for (int p = 0; p < g.np; ++p) sacc += gv.lag(k, p) * J[p];
-      const int m = cl * g.np + k;
+#pragma unroll
+      for (int p = 0; p < NP; ++p) sacc += gv.lag(k, p) * J[p];
+      const int m = cl * NP + k;
       out[(size_t)m * stride] = (TO)(scale * sacc * gv.iw(m));
     }
     tprev = tb;
     phiprev = phib;
     Eprev = Eb;
+  }
+}
+
+template <typename R, typename TO>
+__device__ __forceinline__ void proj_factors_t(const VGrid& g, R u, R theta, TO* out, size_t stride, R scale) {
+  switch (g.kv) {
+    case 1: proj_factors_kv<R, TO, 1>(g, u, theta, out, stride, scale); break;
+    case 2: proj_factors_kv<R, TO, 2>(g, u, theta, out, stride, scale); break;
+    case 3: proj_factors_kv<R, TO, 3>(g, u, theta, out, stride, scale); break;
+    default: proj_factors_kv<R, TO, 4>(g, u, theta, out, stride, scale); break;
   }
 }
 
@@ -221,20 +244,58 @@ __global__ void k_maxwell(VGrid g, int npos, int nm, const double* __restrict__ 
 template <typename T>
 struct InnerSums;
 
-template <>
-struct InnerSums<double> {
-  double s[3] = {0, 0, 0};
-  __device__ __forceinline__ void add(const VGrid& g, int m, double f) {
-    s[0] = fma(g.w[m], f, s[0]);
-    s[1] = fma(g.wx[m], f, s[1]);
-    s[2] = fma(g.wxx[m], f, s[2]);
+// Both storage types are summed with FP32 error-free transformations (TwoProd by FMA,
+// TwoSum; the compensated dot product of Ogita, Rump and Oishi), which on B300 run on
+// the FP32 pipes at ~58x the FP64 rate: the weights are float pairs wh + wl, FP32 data
+// enter as f, FP64 data as a float pair fh + fl split with integer operations.  The
+// sums keep ~2^-47 relative accuracy (FP64 rounding is 2^-53; the tolerance of the
+// Picard criterion is 1e-8).
+
+// Split a double into floats hi + lo with integer operations only: hi = sign, exponent
+// and the leading 23 stored mantissa bits; lo = the remaining 29 bits rounded to float.
+// |f - hi - lo| <= 2^-47 |f| for 2^-126 <= |f| < 2^128; smaller magnitudes contribute
+// at most 2^-97 absolute; larger ones and non-finite values convert directly.
+__device__ __forceinline__ void split_double(double f, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(f);
+  const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7ffu);
+  const int ef = e - 1023 + 127;  // biased float exponent of hi
+  if (ef >= 255) {
+    hi = (float)f;
+    lo = 0.f;
+    return;
   }
-  __device__ __forceinline__ double get(int k) const { return s[k]; }
-};
+  if (ef <= 0) {
+    hi = __int_as_float((int)sign);
+    lo = hi;
+    return;
+  }
+  const unsigned long long m = b & 0xfffffffffffffull;  // 52 stored mantissa bits
+  hi = __int_as_float((int)(sign | ((unsigned int)ef << 23) | (unsigned int)(m >> 29)));
+  // lo = (m mod 2^29) * 2^(e - 1075)
+  const int pe = e - 1075 + 127;  // biased exponent of 2^(e - 1075)
+  const float r = (float)(unsigned int)(m & 0x1fffffffu);
+  const float sc = pe >= 1 ? __int_as_float(pe << 23) : 0.f;
+  lo = __int_as_float(__float_as_int(r * sc) | (int)sign);
+}
 
 template <>
 struct InnerSums<float> {
   float hi[3] = {0.f, 0.f, 0.f}, lo[3] = {0.f, 0.f, 0.f};
+  // accumulate (wh + wl)(fh + fl) for the three weights of point m
+  __device__ __forceinline__ void add2(const VGrid& g, int m, float fh, float fl) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float wh = g.wh[k][m], wl = g.wl[k][m];
+      const float p = wh * fh;
+      const float ep = fmaf(wh, fh, -p) + fmaf(wh, fl, wl * fh);  // p + ep = (wh + wl)(fh + fl) - wl fl
+      const float t = hi[k] + p;                                  // TwoSum(hi, p)
+      const float z = t - hi[k];
+      const float es = (hi[k] - (t - z)) + (p - z);
+      hi[k] = t;
+      lo[k] += es + ep;
+    }
+  }
   __device__ __forceinline__ void add(const VGrid& g, int m, float f) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -249,6 +310,17 @@ struct InnerSums<float> {
     }
   }
   __device__ __forceinline__ double get(int k) const { return (double)hi[k] + (double)lo[k]; }
+};
+
+template <>
+struct InnerSums<double> {
+  InnerSums<float> S;
+  __device__ __forceinline__ void add(const VGrid& g, int m, double f) {
+    float fh, fl;
+    split_double(f, fh, fl);
+    S.add2(g, m, fh, fl);
+  }
+  __device__ __forceinline__ double get(int k) const { return S.get(k); }
 };
 
 // Velocity moments U_i = sum_j w_j (1, v_j, |v_j|^2/2) f_{j,i} (Eq. moments), FP64
@@ -303,7 +375,9 @@ __global__ void k_moments(VGrid g, const T* __restrict__ f, int nnode, double* U
   const int cur = ds->it & 1;
   double* Uw = (mode == 0) ? (cur == 0 ? U0 : U1) : (cur == 0 ? U1 : U0);
   if (i < nnode)
-    for (int m = 0; m < nm; ++m) Uw[(size_t)i * nm + m] = acc[m];
+#pragma unroll
+    for (int m = 0; m < 5; ++m)
+      if (m < nm) Uw[(size_t)i * nm + m] = acc[m];
   if (mode == 0) return;
   // partial sums for the convergence measure
   const double* Uo = cur == 0 ? U0 : U1;
@@ -312,11 +386,14 @@ __global__ void k_moments(VGrid g, const T* __restrict__ f, int nnode, double* U
     const double* o = Uo + (size_t)i * nm;
     r[0] = (acc[0] - o[0]) * (acc[0] - o[0]);
     r[1] = o[0] * o[0];
-    for (int a = 0; a < g.dim; ++a) {
-      r[2] += (acc[1 + a] - o[1 + a]) * (acc[1 + a] - o[1 + a]);
-      r[3] += o[1 + a] * o[1 + a];
-    }
-    r[4] = (acc[nm - 1] - o[nm - 1]) * (acc[nm - 1] - o[nm - 1]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (a < g.dim) {
+        r[2] += (acc[1 + a] - o[1 + a]) * (acc[1 + a] - o[1 + a]);
+        r[3] += o[1 + a] * o[1 + a];
+      }
+    const double aE = g.dim == 2 ? acc[3] : acc[4];
+    r[4] = (aE - o[nm - 1]) * (aE - o[nm - 1]);
     r[5] = o[nm - 1] * o[nm - 1];
   }
   __shared__ double red[6][32];
@@ -350,10 +427,12 @@ __global__ void k_factors(VGrid g, int nnode, const double* __restrict__ U0, con
   const double* Un = (((ds->it & 1) == 0) ? U0 : U1) + (size_t)i * nm;
   const double n = Un[0];
   double u[3] = {0, 0, 0}, u2 = 0.0;
-  for (int a = 0; a < g.dim; ++a) {
-    u[a] = Un[1 + a] / n;
-    u2 += u[a] * u[a];
-  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    if (a < g.dim) {
+      u[a] = Un[1 + a] / n;
+      u2 += u[a] * u[a];
+    }
   double th = (2.0 * Un[1 + g.dim] / n - u2) / g.dim;
   double scale = coef * n;
   if (!(n > 0.0) || !(th > 0.0) || !isfinite(n) || !isfinite(th)) {
@@ -362,9 +441,11 @@ __global__ void k_factors(VGrid g, int nnode, const double* __restrict__ U0, con
     th = 1.0;
     u[0] = u[1] = u[2] = 0.0;
   }
-  for (int a = 0; a < g.dim; ++a)
-    proj_factors_t<T, T>(g, (T)u[a], (T)th, cf + (size_t)a * g.N * nnode + i, (size_t)nnode,
-                         (T)(a == 0 ? scale : 1.0));
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    if (a < g.dim)
+      proj_factors_t<T, T>(g, (T)u[a], (T)th, cf + (size_t)a * g.N * nnode + i, (size_t)nnode,
+                           (T)(a == 0 ? scale : 1.0));
 }
 
 // src[j][i] = prod_a cf[a][j_a][i] + qscale * q[j][i]  (nu M^l + q of Eq. bgk-ss-picard)
@@ -672,6 +753,10 @@ __device__ __forceinline__ void cp_async_bytes(void* smem, const void* gmem, int
   else
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
 }
+// Asynchronous prefetch of `bytes` (a multiple of 16, 16-byte aligned) into L2.
+__device__ __forceinline__ void prefetch_l2_bulk(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
@@ -713,28 +798,133 @@ struct PrefetchSlots {
 // item's copy can be loaded while the current item is processed.
 // REG: the item also carries its geometry (converted to T), loaded one item ahead in
 // registers (FP32 sweeps; FP64 sweeps are bound by FP64 arithmetic, not by latency).
-template <class E, typename T, bool REG = false>
+// FUSED: the item carries the stage source q and the Maxwellian factors of its nodes
+// instead of src, and the solve forms src = prod_a cf[a][j_a] + qscale q itself (the
+// product of k_source, in the same order), so no src array is written or read.
+template <class E, typename T, bool REG = false, bool FUSED = false>
 struct SweepItem {
   uint32_t e;
   int4 nb;
   uint64_t pm;
-  T src[E::NDOF];
+  T src[E::NDOF];  // src, or q when FUSED
   T geo[REG ? E::NF * E::D + 1 : 1];
+  T c1[FUSED ? E::NDOF : 1], c2[FUSED ? E::NDOF : 1], c3[(FUSED && E::D == 3) ? E::NDOF : 1];
 };
 
-template <class E, typename T, bool REG>
+// Source of one sweep launch: src = nu M^l + qscale q precomputed (src), or its factors
+// (FUSED: cf[a][m][node] of k_factors, q and qscale).
+template <typename T>
+struct SrcArgs {
+  const T* src;
+  const T* cf;
+  const T* q;
+  T qscale;
+};
+
+// Per-ordinate pointers of the source: sj = src or q; c1..c3 the factor rows of j's
+// velocity indices (j lexicographic, last dimension fastest).
+template <typename T>
+struct SrcRows {
+  const T* sj;
+  const T* c1;
+  const T* c2;
+  const T* c3;
+};
+
+template <typename T, bool FUSED>
+__device__ __forceinline__ SrcRows<T> src_rows(const SrcArgs<T>& sr, const VGrid& g, int j, int nnode) {
+  SrcRows<T> r{};
+  if constexpr (FUSED) {
+    r.sj = sr.q + (size_t)j * nnode;
+    if (g.dim == 2) {
+      r.c1 = sr.cf + (size_t)(j / g.N) * nnode;
+      r.c2 = sr.cf + (size_t)(g.N + j % g.N) * nnode;
+    } else {
+      r.c1 = sr.cf + (size_t)(j / (g.N * g.N)) * nnode;
+      r.c2 = sr.cf + (size_t)(g.N + (j / g.N) % g.N) * nnode;
+      r.c3 = sr.cf + (size_t)(2 * g.N + j % g.N) * nnode;
+    }
+  } else {
+    r.sj = sr.src + (size_t)j * nnode;
+  }
+  return r;
+}
+
+// Load the N values of T at p with the widest vector loads that p's alignment (ALIGN
+// bytes, a compile-time fact of the layout) allows.
+// (the vector types are read as such and unpacked by value: no type-punned stores into v)
+template <typename T, int N, int ALIGN>
+__device__ __forceinline__ void load_vec(const T* __restrict__ p, T (&v)[N]) {
+  constexpr int BYTES = N * (int)sizeof(T);
+  if constexpr (sizeof(T) == 4 && ALIGN % 16 == 0 && BYTES % 16 == 0) {
+#pragma unroll
+    for (int q = 0; q < N / 4; ++q) {
+      const float4 t = reinterpret_cast<const float4*>(p)[q];
+      v[4 * q] = t.x;
+      v[4 * q + 1] = t.y;
+      v[4 * q + 2] = t.z;
+      v[4 * q + 3] = t.w;
+    }
+  } else if constexpr (sizeof(T) == 4 && ALIGN % 8 == 0 && BYTES % 8 == 0) {
+#pragma unroll
+    for (int q = 0; q < N / 2; ++q) {
+      const float2 t = reinterpret_cast<const float2*>(p)[q];
+      v[2 * q] = t.x;
+      v[2 * q + 1] = t.y;
+    }
+  } else if constexpr (sizeof(T) == 8 && ALIGN % 16 == 0 && BYTES % 16 == 0) {
+#pragma unroll
+    for (int q = 0; q < N / 2; ++q) {
+      const double2 t = reinterpret_cast<const double2*>(p)[q];
+      v[2 * q] = t.x;
+      v[2 * q + 1] = t.y;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < N; ++q) v[q] = p[q];
+  }
+}
+
+// alignment in bytes of a cell's node values (cell * NDOF * sizeof(T) from a 256-byte
+// aligned array whose ordinate rows are NDOF * n_cells values long)
+template <class E, typename T>
+__host__ __device__ constexpr int cell_align() {
+  return (E::NDOF * (int)sizeof(T)) % 16 == 0 ? 16 : (E::NDOF * (int)sizeof(T)) % 8 == 0 ? 8 : 4;
+}
+
+template <class E, typename T, bool REG, bool FUSED>
 __device__ __forceinline__ void fetch_item(const SweepArgs& sa, const uint32_t* __restrict__ gl,
-                                           const T* __restrict__ sj, int k, SweepItem<E, T, REG>& it) {
+                                           const SrcRows<T>& rw, int k, SweepItem<E, T, REG, FUSED>& it) {
   it.e = gl[k];
   const int c = (int)(it.e & kCellMask);
   it.nb = *reinterpret_cast<const int4*>(sa.nbr + (size_t)c * 4);
   it.pm = sa.perm[c];
-#pragma unroll
-  for (int a = 0; a < E::NDOF; ++a) it.src[a] = sj[(size_t)c * E::NDOF + a];
+  const size_t o = (size_t)c * E::NDOF;
+  constexpr int AL = cell_align<E, T>();
+  load_vec<T, E::NDOF, AL>(rw.sj + o, it.src);
+  if constexpr (FUSED) {
+    load_vec<T, E::NDOF, AL>(rw.c1 + o, it.c1);
+    load_vec<T, E::NDOF, AL>(rw.c2 + o, it.c2);
+    if constexpr (E::D == 3) load_vec<T, E::NDOF, AL>(rw.c3 + o, it.c3);
+  }
   if constexpr (REG) {
     const float* Gc = sa.geof + (size_t)c * sa.gs;
 #pragma unroll
     for (int q = 0; q <= E::NF * E::D; ++q) it.geo[q] = Gc[q];
+  }
+}
+
+// FUSED: replace q by src = prod c + qscale q (as k_source forms it) once the item
+// becomes the current one, so only src stays live while it waits to be solved.
+template <class E, typename T, bool REG, bool FUSED>
+__device__ __forceinline__ void resolve_src(SweepItem<E, T, REG, FUSED>& it, T qscale) {
+  if constexpr (FUSED) {
+#pragma unroll
+    for (int a = 0; a < E::NDOF; ++a) {
+      T m = it.c1[a] * it.c2[a];
+      if constexpr (E::D == 3) m = m * it.c3[a];
+      it.src[a] = fma(qscale, it.src[a], m);
+    }
   }
 }
 
@@ -762,9 +952,9 @@ struct NamedBarrier {
 // otherwise the matrix is assembled and factorised in place.  The schedule entry, the
 // neighbour ids, the node permutation and src of the thread's next item are loaded
 // before the current item is solved (they are not written during the sweep).
-template <class E, typename T, bool CACHED, class Bar, bool PF = false>
+template <class E, typename T, bool CACHED, class Bar, bool PF = false, bool FUSED = false>
 __device__ __forceinline__ void sweep_ordinate(const SweepArgs& sa, const VGrid& g, int j, T nus,
-                                               const T* __restrict__ src, const T* __restrict__ fbc,
+                                               const SrcArgs<T>& sr, const T* __restrict__ fbc,
                                                const T* __restrict__ Ainv, T* f, int tid, int nt, const Bar& bar,
                                                unsigned char* pf_smem = nullptr) {
   constexpr int ND = E::NDOF, NF = E::NF, FD = E::FD;
@@ -776,18 +966,19 @@ __device__ __forceinline__ void sweep_ordinate(const SweepArgs& sa, const VGrid&
   const T* Aj = CACHED ? Ainv + (size_t)j * sa.ncell * ainv_stride<E, T>() : nullptr;
   const int G = sa.ngen[j];
   T* fj = f + (size_t)j * sa.nnode;
-  const T* sj = src + (size_t)j * sa.nnode;
+  const SrcRows<T> rw = src_rows<T, FUSED>(sr, g, j, sa.nnode);
   const T* bj = fbc + (size_t)j * sa.nbface * FD;
   int lo = lv[0], hi = G > 0 ? lv[1] : lv[0];
   int k = lo + tid;
   constexpr bool REG = !PF && sizeof(T) == 4;
-  SweepItem<E, T, REG> cur, nxt;
+  SweepItem<E, T, REG, FUSED> cur, nxt;
   bool have = k < hi;
   // prefetch slots (PF): item data of cur in slot `slot`, of nxt in slot ^ 1
   const PrefetchSlots<E, T> pfs{pf_smem, nt, tid, sa.gs};
   int slot = 0;
   if (have) {
-    fetch_item<E, T, REG>(sa, gl, sj, k, cur);
+    fetch_item<E, T, REG, FUSED>(sa, gl, rw, k, cur);
+    resolve_src(cur, sr.qscale);
     if (PF) pfs.issue(slot, sa.geo, Aj, (int)(cur.e & kCellMask), k);
   }
   int kpend = -1;
@@ -803,7 +994,10 @@ __device__ __forceinline__ void sweep_ordinate(const SweepArgs& sa, const VGrid&
         kn = -1;
       }
       if (kn >= 0) {
-        fetch_item<E, T, REG>(sa, gl, sj, kn, nxt);
+        // the next item's cached inverse streams from HBM into L2 while this one is solved
+        if constexpr (CACHED && !PF) prefetch_l2_bulk(Aj + (size_t)kn * ainv_stride<E, T>(),
+                                                      ainv_stride<E, T>() * (uint32_t)sizeof(T));
+        fetch_item<E, T, REG, FUSED>(sa, gl, rw, kn, nxt);
         if (PF) pfs.issue(slot ^ 1, sa.geo, Aj, (int)(nxt.e & kCellMask), kn);
       }
       if (PF) {
@@ -815,14 +1009,16 @@ __device__ __forceinline__ void sweep_ordinate(const SweepArgs& sa, const VGrid&
       // ---- solve item k
       const int c = (int)(cur.e & kCellMask);
       const uint32_t code = cur.e >> kCellBits;
+      // face rates r_i (all faces for the assembly; with a cached inverse only the inflow
+      // faces' |r_i| are needed and are formed below, face by face)
       T r[NF];
-      unsigned outm;
-      if constexpr (REG)
-        face_rates_t<E, T>(cur.geo, code, v0, v1, v2, r, outm);
-      else if (PF)
-        face_rates<E, T>(pfs.geo(slot), code, v0, v1, v2, r, outm);
-      else
-        face_rates<E, T>(sa.geo + (size_t)c * sa.gs, code, v0, v1, v2, r, outm);
+      unsigned outm = 0;
+      if constexpr (!CACHED) {
+        if constexpr (REG)
+          face_rates_t<E, T>(cur.geo, code, v0, v1, v2, r, outm);
+        else
+          face_rates<E, T>(sa.geo + (size_t)c * sa.gs, code, v0, v1, v2, r, outm);
+      }
       T b[ND];
       E::mass(cur.src, b);
       const int nbs[4] = {cur.nb.x, cur.nb.y, cur.nb.z, cur.nb.w};
@@ -838,16 +1034,31 @@ __device__ __forceinline__ void sweep_ordinate(const SweepArgs& sa, const VGrid&
 #pragma unroll
           for (int kk = 0; kk < FD; ++kk) y[kk] = bj[(size_t)(-nb - 1) * FD + kk];
         }
-        E::inflow(i, -r[i], y, b);
+        T ci;
+        if constexpr (CACHED) {
+          // |v . N_i| / |K| of inflow face i, as face_rates forms it
+          if constexpr (REG) {
+            T sf = v0 * cur.geo[i * E::D] + v1 * cur.geo[i * E::D + 1];
+            if (E::D == 3) sf += v2 * cur.geo[i * E::D + 2];
+            ci = fabs(sf) * cur.geo[NF * E::D];
+          } else {
+            const double* Gc = PF ? pfs.geo(slot) : sa.geo + (size_t)c * sa.gs;
+            T sf = v0 * (T)Gc[i * E::D] + v1 * (T)Gc[i * E::D + 1];
+            if (E::D == 3) sf += v2 * (T)Gc[i * E::D + 2];
+            ci = fabs(sf) * (T)Gc[NF * E::D];
+          }
+        } else {
+          ci = -r[i];
+        }
+        E::inflow(i, ci, y, b);
       }
       T x[ND];
       if (CACHED) {
         // the inverse is 16-byte aligned and padded: read it with 128-bit loads
         constexpr int AS = ainv_stride<E, T>(), NV = AS * (int)sizeof(T) / 16;
         T Ar[AS];
-        const uint4* Av = reinterpret_cast<const uint4*>(PF ? pfs.ainv(slot) : Aj + (size_t)k * AS);
-#pragma unroll
-        for (int q = 0; q < NV; ++q) reinterpret_cast<uint4*>(Ar)[q] = Av[q];
+        static_assert(AS * (int)sizeof(T) == NV * 16, "padded inverse");
+        load_vec<T, AS, 16>(PF ? pfs.ainv(slot) : Aj + (size_t)k * AS, Ar);
 #pragma unroll
         for (int a = 0; a < ND; ++a) {
           T s = T(0);
@@ -867,6 +1078,7 @@ __device__ __forceinline__ void sweep_ordinate(const SweepArgs& sa, const VGrid&
       // ---- advance
       if (same) {
         cur = nxt;
+        resolve_src(cur, sr.qscale);
         k = kn;
         slot ^= 1;
       } else {
@@ -874,6 +1086,7 @@ __device__ __forceinline__ void sweep_ordinate(const SweepArgs& sa, const VGrid&
         kpend = kn;
         if (kn >= 0) {
           cur = nxt;
+          resolve_src(cur, sr.qscale);
           slot ^= 1;
         }
       }
@@ -888,7 +1101,8 @@ __device__ __forceinline__ void sweep_ordinate(const SweepArgs& sa, const VGrid&
       k = lo + tid;
       have = gg + 1 < G && k < hi;
       if (have) {
-        fetch_item<E, T, REG>(sa, gl, sj, k, cur);
+        fetch_item<E, T, REG, FUSED>(sa, gl, rw, k, cur);
+        resolve_src(cur, sr.qscale);
         if (PF) pfs.issue(slot, sa.geo, Aj, (int)(cur.e & kCellMask), k);
       }
     }
@@ -900,14 +1114,14 @@ __device__ __forceinline__ void sweep_ordinate(const SweepArgs& sa, const VGrid&
 // One sweep of every ordinate of one problem: one CTA per ordinate.  PF: the cached
 // local inverse and the geometry of each thread's next cell are copied to shared memory
 // asynchronously while the current cell is solved (dynamic shared memory).
-template <class E, typename T, bool CACHED, bool PF = false>
-__global__ void __launch_bounds__(256) k_sweep(SweepArgs sa, VGrid g, T nus, const T* __restrict__ src,
+template <class E, typename T, bool CACHED, bool PF = false, bool FUSED = false>
+__global__ void __launch_bounds__(256) k_sweep(SweepArgs sa, VGrid g, T nus, SrcArgs<T> sr,
                                                const T* __restrict__ fbc, const T* __restrict__ Ainv, T* f,
                                                const DevState* ds) {
   extern __shared__ __align__(16) unsigned char pf_smem[];
   if (ds && (ds->status != BGK_OK || ds->done)) return;
-  sweep_ordinate<E, T, CACHED, CtaBarrier, PF>(sa, g, (int)blockIdx.x, nus, src, fbc, Ainv, f, (int)threadIdx.x,
-                                               (int)blockDim.x, CtaBarrier(), pf_smem);
+  sweep_ordinate<E, T, CACHED, CtaBarrier, PF, FUSED>(sa, g, (int)blockIdx.x, nus, sr, fbc, Ainv, f,
+                                                      (int)threadIdx.x, (int)blockDim.x, CtaBarrier(), pf_smem);
 }
 
 // out = a_k * fk + a_f * f + sum_r cF[r] * F[r]   (stage bookkeeping of Sec. 3.5)

@@ -64,6 +64,11 @@ struct bgk_handle {
   double* U[2] = {nullptr, nullptr};
   double* partial = nullptr;
   void* cf = nullptr;        // Maxwellian factors [dim][N][node] of the current iterate
+  // FP32 sweeps without a local-inverse cache form src = nu M + qscale q inside the sweep
+  // from cf and q (no src pass); build_src then only records q and qscale for the launch
+  bool fuse_src = false;
+  const void* fused_q = nullptr;
+  double fused_qscale = 0.0;
   int mom_blocks = 0;
   DevState* ds = nullptr;
   bool have_prev = false;    // BDF2 history present
@@ -211,15 +216,24 @@ template <class E, typename T>
 void launch_sweep_t(bgk_handle* h, double nus) {
   const bool cached = h->Ainv && nus == h->nus_cached;
   const size_t pf = prefetch_smem<E, T>(h);
+  const SrcArgs<T> sr{(const T*)h->src, nullptr, nullptr, T(0)};
+  if constexpr (sizeof(T) == 4) {
+    if (h->fuse_src) {
+      const SrcArgs<T> fr{nullptr, (const T*)h->cf, (const T*)h->fused_q, (T)h->fused_qscale};
+      k_sweep<E, T, false, false, true><<<h->g.nv, h->sweep_threads, 0, h->stream>>>(
+          sweep_args(h), h->g, (T)nus, fr, (const T*)h->fbc, nullptr, (T*)h->f, h->ds);
+      return;
+    }
+  }
   if (cached && h->cfg.prefetch == 1 && pf <= 96 * 1024)
     k_sweep<E, T, true, true><<<h->g.nv, h->sweep_threads, pf, h->stream>>>(
-        sweep_args(h), h->g, (T)nus, (const T*)h->src, (const T*)h->fbc, (const T*)h->Ainv, (T*)h->f, h->ds);
+        sweep_args(h), h->g, (T)nus, sr, (const T*)h->fbc, (const T*)h->Ainv, (T*)h->f, h->ds);
   else if (cached)
     k_sweep<E, T, true><<<h->g.nv, h->sweep_threads, 0, h->stream>>>(
-        sweep_args(h), h->g, (T)nus, (const T*)h->src, (const T*)h->fbc, (const T*)h->Ainv, (T*)h->f, h->ds);
+        sweep_args(h), h->g, (T)nus, sr, (const T*)h->fbc, (const T*)h->Ainv, (T*)h->f, h->ds);
   else
     k_sweep<E, T, false><<<h->g.nv, h->sweep_threads, 0, h->stream>>>(
-        sweep_args(h), h->g, (T)nus, (const T*)h->src, (const T*)h->fbc, nullptr, (T*)h->f, h->ds);
+        sweep_args(h), h->g, (T)nus, sr, (const T*)h->fbc, nullptr, (T*)h->f, h->ds);
 }
 
 template <class E, typename T>
@@ -303,12 +317,18 @@ void moments(bgk_handle* h, int mode) {
 }
 
 // src = nu * M(U[it&1]) + qscale * qsrc: per-node factors, then a streaming product
+// (fused sweeps: the factors only; the sweep forms src from them, qsrc and qscale)
 template <typename T>
 int build_src_t(bgk_handle* h, const void* qsrc, double qscale) {
   k_factors<T><<<(h->nnode + 127) / 128, 128, 0, h->stream>>>(h->g, h->nnode, h->U[0], h->U[1], h->ds, h->phys.nu,
                                                               (T*)h->cf);
-  k_source<T><<<148 * 16, 256, 0, h->stream>>>(h->g, h->nnode, (const T*)h->cf, (const T*)qsrc, (T)qscale, (T*)h->src,
-                                               h->ds);
+  if (h->fuse_src) {
+    h->fused_q = qsrc;
+    h->fused_qscale = qscale;
+  } else {
+    k_source<T><<<148 * 16, 256, 0, h->stream>>>(h->g, h->nnode, (const T*)h->cf, (const T*)qsrc, (T)qscale,
+                                                 (T*)h->src, h->ds);
+  }
   return cudaGetLastError() == cudaSuccess ? BGK_OK : BGK_E_CUDA;
 }
 
@@ -319,11 +339,7 @@ int build_src(bgk_handle* h, const void* qsrc, double qscale) {
 // FP32 source of the shadow problem; q32 is the main problem's stage source q converted
 // to FP32 once per stage (held in the shadow's fk array, which the shadow does not use).
 int build_src_shadow(bgk_handle* sh, const float* q32, double qscale) {
-  k_factors<float><<<(sh->nnode + 127) / 128, 128, 0, sh->stream>>>(sh->g, sh->nnode, sh->U[0], sh->U[1], sh->ds,
-                                                                   sh->phys.nu, (float*)sh->cf);
-  k_source<float, float><<<148 * 16, 256, 0, sh->stream>>>(sh->g, sh->nnode, (const float*)sh->cf, q32,
-                                                           (float)qscale, (float*)sh->src, sh->ds);
-  return cudaGetLastError() == cudaSuccess ? BGK_OK : BGK_E_CUDA;
+  return build_src_t<float>(sh, q32, qscale);
 }
 
 // Conditional while-node appended to the capture of stream s; returns the body graph.
@@ -772,6 +788,7 @@ int bgk_create(const bgk_mesh* mesh, const bgk_vgrid* vg, const bgk_physics* phy
     h->nus_main = phys->nu + 1.0 / (h->dt * ass);
     h->qscale_main = 1.0 / (h->dt * ass);
     rc = build_inverse_cache(h, h->nus_main);
+    h->fuse_src = h->precision == BGK_FP32_SWEEP && !h->Ainv && h->cfg.prefetch != 1;
   }
   if (rc == BGK_OK && h->cfg.precision == BGK_MIXED) {
     // the FP32 shadow: same mesh, grid, physics and stream; no graphs of its own

@@ -245,3 +245,42 @@ def test_mixed_precision_reaches_the_fp64_fixed_point(integ):
     s32.set_inflow_maxwellian(w.inflow)
     s32.step(2)
     assert rel_err(s32.get_f(), f) > rel_err(s.get_f(), f)
+
+
+@pytest.mark.parametrize("name", ["p2_tri", "p1_tet_cycles"])
+def test_fp32_fused_source_equals_source_pass(name):
+    """FP32 sweeps without a cache form src = nu M + q scale inside the sweep; the result
+    matches the separate source pass to FP32 rounding (the two kernels are compiled
+    separately and may contract the local solve's products into FMAs differently)."""
+    from paper_2608_19150_b300 import bgk
+    w = workloads()[name]
+    out = []
+    for prefetch in (False, True):   # prefetch=True keeps the separate source pass
+        s = bgk.Solver.from_workload(w, precision="fp32", cache_inverse="off", prefetch=prefetch, tau=1e-6)
+        s.set_state_maxwellian(w.init)
+        s.set_inflow_maxwellian(w.inflow)
+        s.sweep(0.0, 0.0)
+        f1 = s.get_f(np.float32)
+        st = s.step(1)
+        out.append((f1, s.get_f(np.float32), list(st.iterations)))
+    assert rel_err(out[0][0], out[1][0].astype(np.float64)) < 2e-6
+    assert rel_err(out[0][1], out[1][1].astype(np.float64)) < 2e-5
+
+
+def test_fp64_storage_moments_split_sums():
+    """FP64 data are summed as float pairs with compensated FP32 arithmetic; the moments
+    must match the oracle's FP64 sums of the same data (seeded, signs and magnitudes
+    spread over 1e-30 .. 1e3) to 1e-13."""
+    w = small_shock_tube(n=8, kx=2, n_v=16, integrator="BE")
+    s, o = make_pair(w)
+    f0 = o.maxwellian(w.init)
+    r = synth.splitmix64_uniform(91, 2 * f0.size).reshape((2,) + f0.shape)
+    f = f0 * (0.5 + r[0]) * 10.0 ** np.floor(4 * r[1] - 1)
+    f[:, ::97] *= -1.0
+    f[3, :50] = 10.0 ** np.linspace(-30, -20, 50)
+    s.set_f(f)
+    U = s.get_moments()
+    Uo = o.moments(f)
+    assert rel_err(U, Uo) < 1e-13
+    for m in range(U.shape[1]):
+        assert np.abs(U[:, m] - Uo[:, m]).max() <= 1e-13 * np.abs(Uo[:, m]).max() + 1e-300
