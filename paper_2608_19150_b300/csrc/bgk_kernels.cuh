@@ -892,10 +892,11 @@ __host__ __device__ constexpr int cell_align() {
   return (E::NDOF * (int)sizeof(T)) % 16 == 0 ? 16 : (E::NDOF * (int)sizeof(T)) % 8 == 0 ? 8 : 4;
 }
 
+// Loads of an item whose schedule entry e is already known.
 template <class E, typename T, bool REG, bool FUSED>
-__device__ __forceinline__ void fetch_item(const SweepArgs& sa, const uint32_t* __restrict__ gl,
-                                           const SrcRows<T>& rw, int k, SweepItem<E, T, REG, FUSED>& it) {
-  it.e = gl[k];
+__device__ __forceinline__ void fetch_item_e(const SweepArgs& sa, uint32_t e, const SrcRows<T>& rw,
+                                             SweepItem<E, T, REG, FUSED>& it) {
+  it.e = e;
   const int c = (int)(it.e & kCellMask);
   it.nb = *reinterpret_cast<const int4*>(sa.nbr + (size_t)c * 4);
   it.pm = sa.perm[c];
@@ -912,6 +913,12 @@ __device__ __forceinline__ void fetch_item(const SweepArgs& sa, const uint32_t* 
 #pragma unroll
     for (int q = 0; q <= E::NF * E::D; ++q) it.geo[q] = Gc[q];
   }
+}
+
+template <class E, typename T, bool REG, bool FUSED>
+__device__ __forceinline__ void fetch_item(const SweepArgs& sa, const uint32_t* __restrict__ gl,
+                                           const SrcRows<T>& rw, int k, SweepItem<E, T, REG, FUSED>& it) {
+  fetch_item_e<E, T, REG, FUSED>(sa, gl[k], rw, it);
 }
 
 // FUSED: replace q by src = prod c + qscale q (as k_source forms it) once the item
@@ -968,38 +975,58 @@ __device__ __forceinline__ void sweep_ordinate(const SweepArgs& sa, const VGrid&
   T* fj = f + (size_t)j * sa.nnode;
   const SrcRows<T> rw = src_rows<T, FUSED>(sr, g, j, sa.nnode);
   const T* bj = fbc + (size_t)j * sa.nbface * FD;
-  int lo = lv[0], hi = G > 0 ? lv[1] : lv[0];
-  int k = lo + tid;
   constexpr bool REG = !PF && sizeof(T) == 4;
   SweepItem<E, T, REG, FUSED> cur, nxt;
-  bool have = k < hi;
   // prefetch slots (PF): item data of cur in slot `slot`, of nxt in slot ^ 1
   const PrefetchSlots<E, T> pfs{pf_smem, nt, tid, sa.gs};
   int slot = 0;
-  if (have) {
+  // The thread's items are the positions lv[g] + tid + m nt of each generation g, in
+  // order.  The one being solved (k), the next (kn: its data is loaded while k is
+  // solved) and the one after (kn2: its schedule entry is loaded while k is solved), so
+  // no load of item data waits on the entry load before it.
+  auto seek = [&](int g2, int& kq, int& gq) {
+    for (; g2 < G; ++g2) {
+      const int k2 = lv[g2] + tid;
+      if (k2 < lv[g2 + 1]) {
+        kq = k2;
+        gq = g2;
+        return;
+      }
+    }
+    kq = -1;
+    gq = G;
+  };
+  auto advance = [&](int kq, int gq, int& kr, int& gr) {
+    if (kq < 0) {
+      kr = -1;
+      gr = G;
+    } else if (kq + nt < lv[gq + 1]) {
+      kr = kq + nt;
+      gr = gq;
+    } else {
+      seek(gq + 1, kr, gr);
+    }
+  };
+  int k, gk, kn, gn, kn2, gn2;
+  seek(0, k, gk);
+  advance(k, gk, kn, gn);
+  advance(kn, gn, kn2, gn2);
+  if (k >= 0) {
     fetch_item<E, T, REG, FUSED>(sa, gl, rw, k, cur);
     resolve_src(cur, sr.qscale);
     if (PF) pfs.issue(slot, sa.geo, Aj, (int)(cur.e & kCellMask), k);
   }
-  int kpend = -1;
+  uint32_t en = kn >= 0 ? gl[kn] : 0u;
   for (int gg = 0; gg < G; ++gg) {
-    while (have) {
-      // prefetch the thread's next item: same generation, else the next generation
-      int kn = k + nt;
-      bool same = kn < hi;
-      if (!same && gg + 1 < G) {
-        kn = hi + tid;
-        if (kn >= lv[gg + 2]) kn = -1;
-      } else if (!same) {
-        kn = -1;
-      }
+    while (k >= 0 && gk == gg) {
       if (kn >= 0) {
         // the next item's cached inverse streams from HBM into L2 while this one is solved
         if constexpr (CACHED && !PF) prefetch_l2_bulk(Aj + (size_t)kn * ainv_stride<E, T>(),
                                                       ainv_stride<E, T>() * (uint32_t)sizeof(T));
-        fetch_item<E, T, REG, FUSED>(sa, gl, rw, kn, nxt);
+        fetch_item_e<E, T, REG, FUSED>(sa, en, rw, nxt);
         if (PF) pfs.issue(slot ^ 1, sa.geo, Aj, (int)(nxt.e & kCellMask), kn);
       }
+      const uint32_t en2 = kn2 >= 0 ? gl[kn2] : 0u;
       if (PF) {
         if (kn >= 0)
           cp_async_wait<1>();
@@ -1056,15 +1083,18 @@ __device__ __forceinline__ void sweep_ordinate(const SweepArgs& sa, const VGrid&
       if (CACHED) {
         // the inverse is 16-byte aligned and padded: read it with 128-bit loads
         constexpr int AS = ainv_stride<E, T>(), NV = AS * (int)sizeof(T) / 16;
-        T Ar[AS];
         static_assert(AS * (int)sizeof(T) == NV * 16, "padded inverse");
-        load_vec<T, AS, 16>(PF ? pfs.ainv(slot) : Aj + (size_t)k * AS, Ar);
+        const T* Ap = PF ? pfs.ainv(slot) : Aj + (size_t)k * AS;
+        {
+          T Ar[AS];
+          load_vec<T, AS, 16>(Ap, Ar);
 #pragma unroll
-        for (int a = 0; a < ND; ++a) {
-          T s = T(0);
+          for (int a = 0; a < ND; ++a) {
+            T s = T(0);
 #pragma unroll
-          for (int bb = 0; bb < ND; ++bb) s += Ar[a * ND + bb] * b[bb];
-          x[a] = s;
+            for (int bb = 0; bb < ND; ++bb) s += Ar[a * ND + bb] * b[bb];
+            x[a] = s;
+          }
         }
       } else {
         T A[ND][ND];
@@ -1076,37 +1106,19 @@ __device__ __forceinline__ void sweep_ordinate(const SweepArgs& sa, const VGrid&
 #pragma unroll
       for (int a = 0; a < ND; ++a) fj[(size_t)c * ND + a] = x[a];
       // ---- advance
-      if (same) {
+      if (kn >= 0) {
         cur = nxt;
         resolve_src(cur, sr.qscale);
-        k = kn;
         slot ^= 1;
-      } else {
-        have = false;
-        kpend = kn;
-        if (kn >= 0) {
-          cur = nxt;
-          resolve_src(cur, sr.qscale);
-          slot ^= 1;
-        }
       }
+      k = kn;
+      gk = gn;
+      kn = kn2;
+      gn = gn2;
+      en = en2;
+      advance(kn, gn, kn2, gn2);
     }
     bar.sync();
-    lo = hi;
-    hi = gg + 1 < G ? lv[gg + 2] : hi;
-    if (kpend >= 0) {
-      k = kpend;
-      have = true;
-    } else {
-      k = lo + tid;
-      have = gg + 1 < G && k < hi;
-      if (have) {
-        fetch_item<E, T, REG, FUSED>(sa, gl, rw, k, cur);
-        resolve_src(cur, sr.qscale);
-        if (PF) pfs.issue(slot, sa.geo, Aj, (int)(cur.e & kCellMask), k);
-      }
-    }
-    kpend = -1;
   }
   if (PF) cp_async_wait<0>();
 }
