@@ -619,7 +619,11 @@ __device__ __forceinline__ void lu_solve(T (&A)[N][N], T (&b)[N]) {
   T inv[N];
 #pragma unroll
   for (int k = 0; k < N; ++k) {
-    inv[k] = T(1) / A[k][k];
+    // FP32 sweeps take the fast reciprocal (2 ulp): the FP32 phase is refined in FP64
+    if constexpr (sizeof(T) == 4)
+      inv[k] = __fdividef(1.0f, A[k][k]);
+    else
+      inv[k] = T(1) / A[k][k];
 #pragma unroll
     for (int i = k + 1; i < N; ++i) {
       const T l = A[i][k] * inv[k];
@@ -1049,18 +1053,25 @@ __device__ __forceinline__ void sweep_ordinate(const SweepArgs& sa, const VGrid&
       T b[ND];
       E::mass(cur.src, b);
       const int nbs[4] = {cur.nb.x, cur.nb.y, cur.nb.z, cur.nb.w};
+      // upwind traces of all faces in one round of loads (no branch between them): an
+      // inflow face reads its neighbour's values (or the boundary data), any other face
+      // reads this cell's own old values, which are not used
+      T y[NF][FD];
+#pragma unroll
+      for (int i = 0; i < NF; ++i) {
+        const bool in = ((code >> (2 * i)) & 3u) == 2u;
+        const int nb = nbs[i];
+#pragma unroll
+        for (int kk = 0; kk < FD; ++kk) {
+          const T* p = !in ? fj + (size_t)c * ND
+                           : (nb >= 0 ? fj + (size_t)nb * ND + (int)((cur.pm >> (16 * i + 4 * kk)) & 15u)
+                                      : bj + (size_t)(-nb - 1) * FD + kk);
+          y[i][kk] = *p;
+        }
+      }
 #pragma unroll
       for (int i = 0; i < NF; ++i) {
         if (((code >> (2 * i)) & 3u) != 2u) continue;
-        const int nb = nbs[i];
-        T y[FD];
-        if (nb >= 0) {
-#pragma unroll
-          for (int kk = 0; kk < FD; ++kk) y[kk] = fj[(size_t)nb * ND + (int)((cur.pm >> (16 * i + 4 * kk)) & 15u)];
-        } else {
-#pragma unroll
-          for (int kk = 0; kk < FD; ++kk) y[kk] = bj[(size_t)(-nb - 1) * FD + kk];
-        }
         T ci;
         if constexpr (CACHED) {
           // |v . N_i| / |K| of inflow face i, as face_rates forms it
@@ -1077,7 +1088,7 @@ __device__ __forceinline__ void sweep_ordinate(const SweepArgs& sa, const VGrid&
         } else {
           ci = -r[i];
         }
-        E::inflow(i, ci, y, b);
+        E::inflow(i, ci, y[i], b);
       }
       T x[ND];
       if (CACHED) {
