@@ -420,7 +420,7 @@ def run_ours(args):
     roofline = dict(rl[dom])
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w, 400, dt)
+        cpu = cpu_baseline(w, 1024, dt)
     if rank != 0:
         return
     ms = 1e3 * el_max / args.steps

@@ -324,19 +324,24 @@ struct InnerSums<double> {
 };
 
 // Velocity moments U_i = sum_j w_j (1, v_j, |v_j|^2/2) f_{j,i} (Eq. moments), FP64
-// accuracy for either storage type.  mode 0: write U[it&1].  mode 1: write
-// U[(it+1)&1] and per-block partial sums of |dU_m|^2 and |U_old,m|^2, m = 0, 1, 2,
-// for the criterion of Eq. (convergence-criteria).
+// accuracy for either storage type.  A block covers 32 nodes; its 4 warps split the
+// outermost velocity index into 4 ranges (more loads in flight per node) and their
+// partial sums are added in a fixed order.  mode 0: write U[it&1].  mode 1: write
+// U[(it+1)&1] and per-block partial sums of |dU_m|^2 and |U_old,m|^2, m = 0, 1, 2, for
+// the criterion of Eq. (convergence-criteria).  Launch: 128 threads, ceil(nnode/32) blocks.
 template <typename T>
-__global__ void k_moments(VGrid g, const T* __restrict__ f, int nnode, double* U0, double* U1, const DevState* ds,
-                          int mode, double* __restrict__ partial) {
+__global__ void __launch_bounds__(128) k_moments(VGrid g, const T* __restrict__ f, int nnode, double* U0,
+                                                 double* U1, const DevState* ds, int mode,
+                                                 double* __restrict__ partial) {
   if (ds->status != BGK_OK || ds->done) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31, part = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + lane;
   const int nm = g.dim + 2;
+  const int ja = part * g.N / 4, jb = (part + 1) * g.N / 4;
   double acc[5] = {0, 0, 0, 0, 0};
   if (i < nnode) {
     if (g.dim == 2) {
-      for (int j0 = 0; j0 < g.N; ++j0) {
+      for (int j0 = ja; j0 < jb; ++j0) {
         InnerSums<T> S;
         const T* fr = f + (size_t)j0 * g.N * nnode + i;
 #pragma unroll 8
@@ -349,7 +354,7 @@ __global__ void k_moments(VGrid g, const T* __restrict__ f, int nnode, double* U
         acc[3] += 0.5 * w0 * (x0 * x0 * s0 + s2);
       }
     } else {
-      for (int j0 = 0; j0 < g.N; ++j0) {
+      for (int j0 = ja; j0 < jb; ++j0) {
         double t0 = 0, t1 = 0, t2 = 0, t3 = 0;
         for (int j1 = 0; j1 < g.N; ++j1) {
           InnerSums<T> S;
@@ -372,6 +377,13 @@ __global__ void k_moments(VGrid g, const T* __restrict__ f, int nnode, double* U
       }
     }
   }
+  __shared__ double accp[4][5][32];
+#pragma unroll
+  for (int m = 0; m < 5; ++m) accp[part][m][lane] = acc[m];
+  __syncthreads();
+  if (part != 0) return;
+#pragma unroll
+  for (int m = 0; m < 5; ++m) acc[m] = ((accp[0][m][lane] + accp[1][m][lane]) + accp[2][m][lane]) + accp[3][m][lane];
   const int cur = ds->it & 1;
   double* Uw = (mode == 0) ? (cur == 0 ? U0 : U1) : (cur == 0 ? U1 : U0);
   if (i < nnode)
@@ -379,7 +391,7 @@ __global__ void k_moments(VGrid g, const T* __restrict__ f, int nnode, double* U
     for (int m = 0; m < 5; ++m)
       if (m < nm) Uw[(size_t)i * nm + m] = acc[m];
   if (mode == 0) return;
-  // partial sums for the convergence measure
+  // partial sums for the convergence measure (warp 0 of the block)
   const double* Uo = cur == 0 ? U0 : U1;
   double r[6] = {0, 0, 0, 0, 0, 0};
   if (i < nnode) {
@@ -396,19 +408,11 @@ __global__ void k_moments(VGrid g, const T* __restrict__ f, int nnode, double* U
     r[4] = (aE - o[nm - 1]) * (aE - o[nm - 1]);
     r[5] = o[nm - 1] * o[nm - 1];
   }
-  __shared__ double red[6][32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
     double x = r[k];
     for (int o2 = 16; o2 > 0; o2 >>= 1) x += __shfl_down_sync(0xffffffffu, x, o2);
-    if (lane == 0) red[k][warp] = x;
-  }
-  __syncthreads();
-  if (threadIdx.x < 6) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[threadIdx.x][w];
-    partial[(size_t)blockIdx.x * 6 + threadIdx.x] = s;
+    if (lane == 0) partial[(size_t)blockIdx.x * 6 + k] = x;
   }
 }
 

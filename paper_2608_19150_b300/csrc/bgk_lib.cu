@@ -707,7 +707,7 @@ int bgk_create(const bgk_mesh* mesh, const bgk_vgrid* vg, const bgk_physics* phy
   const size_t n = hm.ncell, nv = h->g.nv;
   const size_t fb = h->nfv * h->tsize;
   const size_t fbcb = nv * (size_t)hm.nbface * hm.fd * h->tsize;
-  h->mom_blocks = (h->nnode + 127) / 128;
+  h->mom_blocks = (h->nnode + 31) / 32;  // k_moments: 32 nodes per block
   rc = BGK_OK;
   auto A = [&](int r) {
     if (rc == BGK_OK) rc = r;
