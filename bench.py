@@ -43,8 +43,8 @@ def parse():
     p.add_argument("--train-runs", type=int, default=200)
     p.add_argument("--eval-runs", type=int, default=4)
     p.add_argument("--instances", type=int, default=64)
-    p.add_argument("--guess", action="store_true", help="batched: train and attach the learned guess")
-    p.add_argument("--compare-fp64", action="store_true", help="batched: also time the plain FP64 batch")
+    p.add_argument("--no-guess", action="store_true", help="batched: without the learned guess")
+    p.add_argument("--no-compare", action="store_true", help="batched: skip the plain FP64 batch")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cache", default="auto", choices=["auto", "on", "off"],
                    help="local-inverse cache of the sweep")
@@ -304,7 +304,16 @@ def timed_steps(s, steps, world, local, tstream, guess=False, main_fp32=False):
     return max_over_ranks(el, world), sweeps, iters, launches, clk
 
 
-def sweep_roofline(w, precision, reps, peaks):
+# DRAM bytes (read + write) per sweep launch at the 64x64 shock tube with 32x32 velocities,
+# from the ncu captures summarised in profiles/ (the same kernels as timed here); a launch
+# of the n x n workload moves (n / 64)^2 times as much (traffic grows with the cells).
+PROFILED_TRAFFIC = {
+    "fp64": (3.750e9, "profiles/sweep_fp64_cached_shock_tube_64_p2_v32.md"),
+    "fp32": (0.631e9, "profiles/sweep_fp32_fused_shock_tube_64_p2_v32.md"),
+}
+
+
+def sweep_roofline(w, precision, reps, peaks, n_side=None, n_v=None):
     """Event-timed sweep kernel of the given precision on its own handle (first-stage
     coefficient, local-inverse cache as in the step) and its roofline entry."""
     from paper_2608_19150_b300 import bgk
@@ -326,12 +335,18 @@ def sweep_roofline(w, precision, reps, peaks):
         fl = sweep_flops_per_item(cached)
         tf = fl * s.nv * s.ncell / (sweep_ms * 1e-3) / 1e12
         r = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-             "frac": tf / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "k_sweep<ElemP2Tri,double,%d>" % cached,
+             "frac": tf / FP64_PEAK_TFLOPS, "traffic": None,
+             "kernel": "k_sweep<ElemP2Tri,double,%s>" % ("cached" if cached else "uncached"),
              "flops_per_local_solve": fl, "peak_source": "nominal B300 FP64 rate (measured FMA probe 1.125)"}
     else:
         r = {"bound": "hbm", "achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_gbs / hbm_peak,
-             "traffic": None, "kernel": "k_sweep<ElemP2Tri,float,%d>" % cached,
+             "traffic": None,
+             "kernel": "k_sweep<ElemP2Tri,float,%s>" % ("cached" if cached else "uncached,fused source"),
              "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+    profiled = PROFILED_TRAFFIC.get(precision)
+    if profiled and n_side and n_v == 32 and (precision == "fp32" or cached):
+        r["traffic"] = profiled[0] * (n_side / 64.0) ** 2
+        r["traffic_source"] = profiled[1] + " (scaled from 64x64 by the cell count)"
     r.update({"sweep_ms": sweep_ms, "dof_per_launch": dof, "algorithmic_bytes_per_dof": 2 * tsz,
               "hbm_achieved_gbs": hbm_gbs, "hbm_frac": hbm_gbs / hbm_peak,
               "local_inverse_cache_gb": s.cache_bytes / 1e9})
@@ -408,9 +423,9 @@ def run_ours(args):
         p.close()
         del p
     # the sweep kernels, event-timed on their own stream
-    rl = {"fp64": sweep_roofline(w, "fp64", args.sweep_reps, peaks)}
+    rl = {"fp64": sweep_roofline(w, "fp64", args.sweep_reps, peaks, args.n_side, args.n_v)}
     if args.precision != "fp64":
-        rl["fp32"] = sweep_roofline(w, "fp32", args.sweep_reps, peaks)
+        rl["fp32"] = sweep_roofline(w, "fp32", args.sweep_reps, peaks, args.n_side, args.n_v)
     # dominant kernel of the timed step: the sweep precision that used the most time
     n64 = sum(sum(i["fp64"]) for i in iters)
     n32 = sum(sum(i["fp32"]) for i in iters)
@@ -448,7 +463,8 @@ def run_batched(args):
     ws = [synth.workload_random_smooth(seed=d["seed"], n_side=d["n_side"], kx=d["kx"], n_v=d["n_v"],
                                        knudsen=d["knudsen"]) for d in draws]
     mlp, guess_info = None, None
-    if args.guess:
+    use_guess = not args.no_guess
+    if use_guess:
         # guess network trained on seeded small runs drawn like the batch (other seeds)
         from paper_2608_19150_b300 import guess as G
         t0 = time.perf_counter()
@@ -468,9 +484,11 @@ def run_batched(args):
                       "loss_first": float(losses[:20].mean()), "loss_last": float(losses[-50:].mean())}
         del X, Y
 
+    tstream = torch.cuda.Stream()
+
     def run(precision, use_guess):
         t0 = time.perf_counter()
-        b = bgk.Batch(ws, precision=precision, cache_inverse=args.cache, l_max=3000)
+        b = bgk.Batch(ws, precision=precision, cache_inverse=args.cache, l_max=3000, stream=tstream.cuda_stream)
         setup = time.perf_counter() - t0
         t0 = time.perf_counter()
         blocks = b.autotune(reps=2)          # before any state is set: nothing to save
@@ -487,26 +505,29 @@ def run_batched(args):
         barrier(world)
         clocks.start()
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        upd = 0.0
+        upd, el = 0.0, 0.0
         iters = []
         for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(tstream)
             it, st = b.step(1)
+            e1.record(tstream)
+            e1.synchronize()
+            el += e0.elapsed_time(e1) * 1e-3
             upd += float((dofs * it).sum())
             iters.append(it.tolist())
         torch.cuda.synchronize()
-        el = time.perf_counter() - t0
         clk = clocks.stop()
         return b, blocks, setup, tune_s, upd, iters, max_over_ranks(el, world), clk
 
     plain = None
-    if args.compare_fp64:
+    if not args.no_compare:
         pb, _, _, _, pupd, pit, pel, pclk = run("fp64", False)
         plain = {"ms_per_step": 1e3 * pel / args.steps, "value": job_throughput(pupd, pel, world),
                  "picard_iterations_per_instance": pit, "clocks": pclk}
         pb.close()
         del pb
-    b, blocks, setup, tune_s, upd, iters, el_max, clk = run(args.precision, args.guess)
+    b, blocks, setup, tune_s, upd, iters, el_max, clk = run(args.precision, use_guess)
     b.timing(reset=True)
     for _ in range(args.sweep_reps):
         b.sweep()
@@ -599,20 +620,27 @@ def run_learned(args):
         w = _learned_workload(2000 + k, n_full)
         row = {"knudsen": w.knudsen}
         for name in ("plain", "learned"):
-            s = bgk.Solver.from_workload(w, precision=args.precision, l_max=2000)
+            tstream = torch.cuda.Stream()
+            s = bgk.Solver.from_workload(w, precision=args.precision, l_max=2000, stream=tstream.cuda_stream)
             s.set_state_maxwellian(w.init)
             s.set_inflow_maxwellian(w.inflow)
             if name == "learned":
                 s.set_guess(m)
             s.step(1)                                  # BDF2 start-up step (backward Euler), untimed
             torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            its = 0
+            its, el = 0, 0.0
             for _ in range(args.steps):
-                st = s.step(1)
-                its += st.iterations[0]
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(tstream)
+                s.step_async(1)
+                e1.record(tstream)
+                st = s.last_stats()
+                if st.status != 0:
+                    raise RuntimeError("step failed with status %d" % st.status)
+                e1.synchronize()
+                el += e0.elapsed_time(e1) * 1e-3
+                its += st.iterations[0] + st.iterations_fp32[0]
             torch.cuda.synchronize()
-            el = time.perf_counter() - t0
             res[name][0] += its
             res[name][1] += el
             res[name][2] += args.steps
@@ -628,7 +656,9 @@ def run_learned(args):
     ms_learn = 1e3 * res["learned"][1] / res["learned"][2]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": 1, "ms_per_step": ms_learn, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
+            "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp32": "f32", "mixed": "f32 sweeps then f64 (mixed)"}[args.precision],
+            "data": "synthetic",
             "config": {"workload": "learned initial guess, 2D-2V: %dx%d squares (%d P1 triangles), 32x32 velocities, "
                                    "BDF2, CFL 10, Kn log-uniform 1e-4..1 per run; MLP 4 layers x 128 (FP32 training, "
                                    "BF16 inference)" % (n_full, n_full, 2 * n_full * n_full),

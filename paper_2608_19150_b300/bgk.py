@@ -296,7 +296,7 @@ class Solver:
 class Batch:
     """Many independent backward-Euler problems advanced together (bgk_batch_*)."""
 
-    def __init__(self, workloads, precision="fp64", tau=1e-8, l_max=1000, cache_inverse="auto", dt=None):
+    def __init__(self, workloads, precision="fp64", tau=1e-8, l_max=1000, cache_inverse="auto", dt=None, stream=None):
         self.lib = load()
         n = len(workloads)
         self._keep = []
@@ -310,7 +310,7 @@ class Batch:
             meshes[i] = Mesh(w.mesh.dim, w.kx, xyz.shape[0], _ptr(xyz), cells.shape[0], _ptr(cells))
             vgrids[i] = VGrid(float(w.L), int(w.n_v), int(w.k_v))
             phys[i] = Physics(float(w.nu), INTEGRATORS["BE"], float(dt[i]) if dt else 0.0, float(w.cfl))
-        cf = Config(float(tau), int(l_max), PRECISIONS[precision], 0, None, 0,
+        cf = Config(float(tau), int(l_max), PRECISIONS[precision], 0, C.c_void_p(stream) if stream else None, 0,
                     {"auto": 0, "on": 1, "off": 2}[cache_inverse], 0.0, 0)
         self.mixed = precision == "mixed"
         h = C.c_void_p()

@@ -324,20 +324,27 @@ struct InnerSums<double> {
 };
 
 // Velocity moments U_i = sum_j w_j (1, v_j, |v_j|^2/2) f_{j,i} (Eq. moments), FP64
-// accuracy for either storage type.  A block covers 32 nodes; its 4 warps split the
-// outermost velocity index into 4 ranges (more loads in flight per node) and their
-// partial sums are added in a fixed order.  mode 0: write U[it&1].  mode 1: write
-// U[(it+1)&1] and per-block partial sums of |dU_m|^2 and |U_old,m|^2, m = 0, 1, 2, for
-// the criterion of Eq. (convergence-criteria).  Launch: 128 threads, ceil(nnode/32) blocks.
+// accuracy for either storage type.  A block of 128 threads covers 128 / PARTS nodes;
+// PARTS thread groups split the outermost velocity index into ranges (more loads in
+// flight per node for the costlier FP64 data) and their partial sums are added in a
+// fixed order.  mode 0: write U[it&1].  mode 1: write U[(it+1)&1] and per-block partial
+// sums of |dU_m|^2 and |U_old,m|^2, m = 0, 1, 2, for the criterion of Eq.
+// (convergence-criteria).  Launch: 128 threads, ceil(nnode * PARTS / 128) blocks.
+template <typename T>
+struct MomentParts {
+  static constexpr int value = sizeof(T) == 8 ? 4 : 1;
+};
+
 template <typename T>
 __global__ void __launch_bounds__(128) k_moments(VGrid g, const T* __restrict__ f, int nnode, double* U0,
                                                  double* U1, const DevState* ds, int mode,
                                                  double* __restrict__ partial) {
   if (ds->status != BGK_OK || ds->done) return;
-  const int lane = threadIdx.x & 31, part = threadIdx.x >> 5;
-  const int i = blockIdx.x * 32 + lane;
+  constexpr int PARTS = MomentParts<T>::value, NPB = 128 / PARTS;
+  const int nl = threadIdx.x % NPB, part = threadIdx.x / NPB;
+  const int i = blockIdx.x * NPB + nl;
   const int nm = g.dim + 2;
-  const int ja = part * g.N / 4, jb = (part + 1) * g.N / 4;
+  const int ja = part * g.N / PARTS, jb = (part + 1) * g.N / PARTS;
   double acc[5] = {0, 0, 0, 0, 0};
   if (i < nnode) {
     if (g.dim == 2) {
@@ -377,24 +384,32 @@ __global__ void __launch_bounds__(128) k_moments(VGrid g, const T* __restrict__ 
       }
     }
   }
-  __shared__ double accp[4][5][32];
+  if constexpr (PARTS > 1) {
+    __shared__ double accp[PARTS][5][NPB];
 #pragma unroll
-  for (int m = 0; m < 5; ++m) accp[part][m][lane] = acc[m];
-  __syncthreads();
-  if (part != 0) return;
+    for (int m = 0; m < 5; ++m) accp[part][m][nl] = acc[m];
+    __syncthreads();
+    if (part == 0)
 #pragma unroll
-  for (int m = 0; m < 5; ++m) acc[m] = ((accp[0][m][lane] + accp[1][m][lane]) + accp[2][m][lane]) + accp[3][m][lane];
+      for (int m = 0; m < 5; ++m) {
+        double t = accp[0][m][nl];
+#pragma unroll
+        for (int q = 1; q < PARTS; ++q) t += accp[q][m][nl];
+        acc[m] = t;
+      }
+  }
+  const bool owner = part == 0 && i < nnode;
   const int cur = ds->it & 1;
   double* Uw = (mode == 0) ? (cur == 0 ? U0 : U1) : (cur == 0 ? U1 : U0);
-  if (i < nnode)
+  if (owner)
 #pragma unroll
     for (int m = 0; m < 5; ++m)
       if (m < nm) Uw[(size_t)i * nm + m] = acc[m];
   if (mode == 0) return;
-  // partial sums for the convergence measure (warp 0 of the block)
+  // partial sums for the convergence measure over the block's nodes
   const double* Uo = cur == 0 ? U0 : U1;
   double r[6] = {0, 0, 0, 0, 0, 0};
-  if (i < nnode) {
+  if (owner) {
     const double* o = Uo + (size_t)i * nm;
     r[0] = (acc[0] - o[0]) * (acc[0] - o[0]);
     r[1] = o[0] * o[0];
@@ -408,12 +423,18 @@ __global__ void __launch_bounds__(128) k_moments(VGrid g, const T* __restrict__ 
     r[4] = (aE - o[nm - 1]) * (aE - o[nm - 1]);
     r[5] = o[nm - 1] * o[nm - 1];
   }
+  __shared__ double red[6][4];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
     double x = r[k];
     for (int o2 = 16; o2 > 0; o2 >>= 1) x += __shfl_down_sync(0xffffffffu, x, o2);
-    if (lane == 0) partial[(size_t)blockIdx.x * 6 + k] = x;
+    if (lane == 0) red[k][warp] = x;
   }
+  __syncthreads();
+  if (threadIdx.x < 6)
+    partial[(size_t)blockIdx.x * 6 + threadIdx.x] =
+        ((red[threadIdx.x][0] + red[threadIdx.x][1]) + red[threadIdx.x][2]) + red[threadIdx.x][3];
 }
 
 // Projected-Maxwellian factors of every node from the current moments U[it & 1]:

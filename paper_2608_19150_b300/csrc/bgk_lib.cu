@@ -707,7 +707,8 @@ int bgk_create(const bgk_mesh* mesh, const bgk_vgrid* vg, const bgk_physics* phy
   const size_t n = hm.ncell, nv = h->g.nv;
   const size_t fb = h->nfv * h->tsize;
   const size_t fbcb = nv * (size_t)hm.nbface * hm.fd * h->tsize;
-  h->mom_blocks = (h->nnode + 31) / 32;  // k_moments: 32 nodes per block
+  // k_moments: 128 / MomentParts nodes per block of 128 threads
+  h->mom_blocks = h->precision == BGK_FP64 ? (h->nnode + 31) / 32 : (h->nnode + 127) / 128;
   rc = BGK_OK;
   auto A = [&](int r) {
     if (rc == BGK_OK) rc = r;
