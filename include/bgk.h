@@ -147,6 +147,24 @@ int bgk_get_generations(bgk_handle* h, int j, int32_t* h_gen, int* n_gen);
  * For parity tests and sweep benchmarks; a step does not use this entry point. */
 int bgk_sweep(bgk_handle* h, double nu_s, double q_scale);
 
+/* Ordinate shards (Sec. 4: the sweeps of different ordinates are independent given the
+ * Maxwellian of the current moments and the lagged values; the one coupling per Picard
+ * iteration is the sum over ordinates in Eq. moments).  A sharded iteration over S parts of
+ * the ordinates is: every part computes its partial moments, the parts' partial moments
+ * are summed in a fixed order (an allreduce across devices), and every part sweeps its
+ * ordinates with the summed moments.
+ *   bgk_sweep_range: one sweep of the ordinates [j_begin, j_end) with the source built
+ *     from the moments d_U (device, [node][d+2], the summed moments of the current
+ *     iterate) and the handle's stage source, as bgk_sweep (nu_s, q_scale <= 0: the step's
+ *     first-stage values).  Ordinates outside the range are not touched.  Returns
+ *     BGK_E_NONPHYSICAL if d_U has n <= 0 or theta <= 0 somewhere.
+ *   bgk_moments_range_device: the partial moments of the current f over the ordinates
+ *     [j_begin, j_end) into d_U (device, [node][d+2]); j_begin and j_end must be multiples
+ *     of N^(d-1) (whole values of the outermost velocity index), else BGK_E_INVALID.
+ *     The parts' partial moments add up to bgk_get_moments_device. */
+int bgk_sweep_range(bgk_handle* h, int j_begin, int j_end, const double* d_U, double nu_s, double q_scale);
+int bgk_moments_range_device(bgk_handle* h, int j_begin, int j_end, double* d_U);
+
 /* Advance nsteps implicit steps (Sec. 3.5 stages, Sec. 4 Picard loop to tolerance).
  * Each step runs as one CUDA graph with one conditional while-loop per stage.  st may
  * be NULL.  Errors: BGK_E_NOCONV, BGK_E_NONPHYSICAL, BGK_E_CUDA. */

@@ -78,6 +78,8 @@ def load(path: str = LIB_PATH):
         "bgk_get_velocity": [P, V, V],
         "bgk_get_generations": [P, I, V, C.POINTER(I)],
         "bgk_sweep": [P, D, D],
+        "bgk_sweep_range": [P, I, I, V, D, D],
+        "bgk_moments_range_device": [P, I, I, V],
         "bgk_step": [P, I, C.POINTER(Stats)],
         "bgk_step_async": [P, I],
         "bgk_last_stats": [P, C.POINTER(Stats)],
@@ -251,6 +253,16 @@ class Solver:
 
     def sweep(self, nu_s, q_scale):
         _ck(self.lib.bgk_sweep(self.h, float(nu_s), float(q_scale)), "bgk_sweep")
+
+    def sweep_range(self, j_begin, j_end, U_ptr, nu_s=0.0, q_scale=0.0):
+        """One sweep of ordinates [j_begin, j_end) with the moments at device pointer U_ptr."""
+        _ck(self.lib.bgk_sweep_range(self.h, int(j_begin), int(j_end), C.c_void_p(U_ptr), float(nu_s),
+                                     float(q_scale)), "bgk_sweep_range")
+
+    def moments_range_device(self, j_begin, j_end, U_ptr):
+        """Partial moments of ordinates [j_begin, j_end) into the device buffer at U_ptr."""
+        _ck(self.lib.bgk_moments_range_device(self.h, int(j_begin), int(j_end), C.c_void_p(U_ptr)),
+            "bgk_moments_range_device")
 
     def step(self, nsteps=1):
         st = Stats()

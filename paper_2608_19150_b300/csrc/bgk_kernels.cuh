@@ -437,6 +437,48 @@ __global__ void __launch_bounds__(128) k_moments(VGrid g, const T* __restrict__ 
         ((red[threadIdx.x][0] + red[threadIdx.x][1]) + red[threadIdx.x][2]) + red[threadIdx.x][3];
 }
 
+// Partial moments over the ordinates whose outermost velocity index lies in [ja, jb) (one
+// shard of an ordinate-sharded sweep): out[i][m] = sum over those j of w_j e_m(v_j) f_j,i.
+// The shards' partial moments add up to Eq. (moments).
+template <typename T>
+__global__ void k_moments_range(VGrid g, const T* __restrict__ f, int nnode, int ja, int jb,
+                                double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nnode) return;
+  const int nm = g.dim + 2;
+  const size_t inner = g.dim == 2 ? (size_t)g.N : (size_t)g.N * g.N;  // ordinates per outer index
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (int j0 = ja; j0 < jb; ++j0) {
+    double t0 = 0, t1 = 0, t2 = 0, t3 = 0;
+    const int nmid = g.dim == 2 ? 1 : g.N;
+    for (int j1 = 0; j1 < nmid; ++j1) {
+      InnerSums<T> S;
+      const T* fr = f + ((size_t)j0 * inner + (size_t)j1 * g.N) * nnode + i;
+      for (int j2 = 0; j2 < g.N; ++j2) S.add(g, j2, fr[(size_t)j2 * nnode]);
+      const double s0 = S.get(0), s1 = S.get(1), s2 = S.get(2);
+      const double w1 = g.dim == 2 ? 1.0 : g.w[j1], x1 = g.dim == 2 ? 0.0 : g.x[j1];
+      t0 += w1 * s0;
+      t1 += w1 * x1 * s0;
+      t2 += w1 * s1;
+      t3 += w1 * (x1 * x1 * s0 + s2);
+    }
+    const double w0 = g.w[j0], x0 = g.x[j0];
+    acc[0] += w0 * t0;
+    acc[1] += w0 * x0 * t0;
+    if (g.dim == 2) {
+      acc[2] += w0 * t2;
+      acc[3] += 0.5 * w0 * (x0 * x0 * t0 + t3);
+    } else {
+      acc[2] += w0 * t1;
+      acc[3] += w0 * t2;
+      acc[4] += 0.5 * w0 * (x0 * x0 * t0 + t3);
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < 5; ++m)
+    if (m < nm) out[(size_t)i * nm + m] = acc[m];
+}
+
 // Projected-Maxwellian factors of every node from the current moments U[it & 1]:
 // cf[a][m][i] = c_a[m](u_i, theta_i) (App. B), with coef * n_i folded into a = 0.  The
 // moments and primitive variables are FP64; the projection runs in the storage type T
@@ -1162,13 +1204,14 @@ __device__ __forceinline__ void sweep_ordinate(const SweepArgs& sa, const VGrid&
 // One sweep of every ordinate of one problem: one CTA per ordinate.  PF: the cached
 // local inverse and the geometry of each thread's next cell are copied to shared memory
 // asynchronously while the current cell is solved (dynamic shared memory).
+// (ordinates jofs + blockIdx.x: all of them, or one shard's range)
 template <class E, typename T, bool CACHED, bool PF = false, bool FUSED = false>
 __global__ void __launch_bounds__(256) k_sweep(SweepArgs sa, VGrid g, T nus, SrcArgs<T> sr,
                                                const T* __restrict__ fbc, const T* __restrict__ Ainv, T* f,
-                                               const DevState* ds) {
+                                               const DevState* ds, int jofs) {
   extern __shared__ __align__(16) unsigned char pf_smem[];
   if (ds && (ds->status != BGK_OK || ds->done)) return;
-  sweep_ordinate<E, T, CACHED, CtaBarrier, PF, FUSED>(sa, g, (int)blockIdx.x, nus, sr, fbc, Ainv, f,
+  sweep_ordinate<E, T, CACHED, CtaBarrier, PF, FUSED>(sa, g, jofs + (int)blockIdx.x, nus, sr, fbc, Ainv, f,
                                                       (int)threadIdx.x, (int)blockDim.x, CtaBarrier(), pf_smem);
 }
 

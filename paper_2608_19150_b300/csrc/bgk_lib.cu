@@ -213,27 +213,27 @@ size_t prefetch_smem(const bgk_handle* h) {
 }
 
 template <class E, typename T>
-void launch_sweep_t(bgk_handle* h, double nus) {
+void launch_sweep_t(bgk_handle* h, double nus, int jb, int je) {
   const bool cached = h->Ainv && nus == h->nus_cached;
   const size_t pf = prefetch_smem<E, T>(h);
   const SrcArgs<T> sr{(const T*)h->src, nullptr, nullptr, T(0)};
   if constexpr (sizeof(T) == 4) {
     if (h->fuse_src) {
       const SrcArgs<T> fr{nullptr, (const T*)h->cf, (const T*)h->fused_q, (T)h->fused_qscale};
-      k_sweep<E, T, false, false, true><<<h->g.nv, h->sweep_threads, 0, h->stream>>>(
-          sweep_args(h), h->g, (T)nus, fr, (const T*)h->fbc, nullptr, (T*)h->f, h->ds);
+      k_sweep<E, T, false, false, true><<<je - jb, h->sweep_threads, 0, h->stream>>>(
+          sweep_args(h), h->g, (T)nus, fr, (const T*)h->fbc, nullptr, (T*)h->f, h->ds, jb);
       return;
     }
   }
   if (cached && h->cfg.prefetch == 1 && pf <= 96 * 1024)
-    k_sweep<E, T, true, true><<<h->g.nv, h->sweep_threads, pf, h->stream>>>(
-        sweep_args(h), h->g, (T)nus, sr, (const T*)h->fbc, (const T*)h->Ainv, (T*)h->f, h->ds);
+    k_sweep<E, T, true, true><<<je - jb, h->sweep_threads, pf, h->stream>>>(
+        sweep_args(h), h->g, (T)nus, sr, (const T*)h->fbc, (const T*)h->Ainv, (T*)h->f, h->ds, jb);
   else if (cached)
-    k_sweep<E, T, true><<<h->g.nv, h->sweep_threads, 0, h->stream>>>(
-        sweep_args(h), h->g, (T)nus, sr, (const T*)h->fbc, (const T*)h->Ainv, (T*)h->f, h->ds);
+    k_sweep<E, T, true><<<je - jb, h->sweep_threads, 0, h->stream>>>(
+        sweep_args(h), h->g, (T)nus, sr, (const T*)h->fbc, (const T*)h->Ainv, (T*)h->f, h->ds, jb);
   else
-    k_sweep<E, T, false><<<h->g.nv, h->sweep_threads, 0, h->stream>>>(
-        sweep_args(h), h->g, (T)nus, sr, (const T*)h->fbc, nullptr, (T*)h->f, h->ds);
+    k_sweep<E, T, false><<<je - jb, h->sweep_threads, 0, h->stream>>>(
+        sweep_args(h), h->g, (T)nus, sr, (const T*)h->fbc, nullptr, (T*)h->f, h->ds, jb);
 }
 
 template <class E, typename T>
@@ -275,20 +275,22 @@ int build_inverse_cache(bgk_handle* h, double nus) {
 }
 
 template <typename T>
-void launch_sweep(bgk_handle* h, double nus) {
+void launch_sweep(bgk_handle* h, double nus, int jb, int je) {
   if (h->hm.dim == 3)
-    launch_sweep_t<ElemP1Tet, T>(h, nus);
+    launch_sweep_t<ElemP1Tet, T>(h, nus, jb, je);
   else if (h->hm.kx == 2)
-    launch_sweep_t<ElemP2Tri, T>(h, nus);
+    launch_sweep_t<ElemP2Tri, T>(h, nus, jb, je);
   else
-    launch_sweep_t<ElemP1Tri, T>(h, nus);
+    launch_sweep_t<ElemP1Tri, T>(h, nus, jb, je);
 }
 
-void launch_sweep_any(bgk_handle* h, double nus) {
+// one sweep over the ordinates [jb, je) (all of them by default)
+void launch_sweep_any(bgk_handle* h, double nus, int jb = 0, int je = -1) {
+  if (je < 0) je = h->g.nv;
   if (h->precision == BGK_FP64)
-    launch_sweep<double>(h, nus);
+    launch_sweep<double>(h, nus, jb, je);
   else
-    launch_sweep<float>(h, nus);
+    launch_sweep<float>(h, nus, jb, je);
 }
 
 template <typename T>
@@ -1007,6 +1009,43 @@ int bgk_sweep(bgk_handle* h, double nu_s, double q_scale) {
   DevState st;
   CK(cudaMemcpy(&st, h->ds, sizeof(DevState), cudaMemcpyDeviceToHost));
   return st.err ? BGK_E_NONPHYSICAL : BGK_OK;
+}
+
+int bgk_sweep_range(bgk_handle* h, int j_begin, int j_end, const double* d_U, double nu_s, double q_scale) {
+  if (!h || !d_U || j_begin < 0 || j_end > h->g.nv || j_begin >= j_end) return BGK_E_INVALID;
+  if (nu_s <= 0.0) nu_s = h->nus_main;
+  if (q_scale <= 0.0) q_scale = h->qscale_main;
+  k_reset_state<<<1, 1, 0, h->stream>>>(h->ds);
+  DevState st;
+  CK(cudaMemcpyAsync(&st, h->ds, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  // the given moments become the current iterate's (U[it & 1]) for the source
+  CK(cudaMemcpyAsync(h->U[st.it & 1], d_U, sizeof(double) * h->nnode * h->nm, cudaMemcpyDeviceToDevice,
+                     h->stream));
+  int rc = build_src(h, h->fk, q_scale);
+  if (rc != BGK_OK) return rc;
+  launch_sweep_any(h, nu_s, j_begin, j_end);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(&st, h->ds, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return st.err ? BGK_E_NONPHYSICAL : BGK_OK;
+}
+
+int bgk_moments_range_device(bgk_handle* h, int j_begin, int j_end, double* d_U) {
+  if (!h || !d_U) return BGK_E_INVALID;
+  const int inner = h->g.dim == 2 ? h->g.N : h->g.N * h->g.N;  // ordinates per outermost index
+  if (j_begin < 0 || j_end > h->g.nv || j_begin >= j_end || j_begin % inner != 0 || j_end % inner != 0)
+    return BGK_E_INVALID;
+  const int blk = (h->nnode + 127) / 128;
+  if (h->precision == BGK_FP64)
+    k_moments_range<double><<<blk, 128, 0, h->stream>>>(h->g, (const double*)h->f, h->nnode, j_begin / inner,
+                                                        j_end / inner, d_U);
+  else
+    k_moments_range<float><<<blk, 128, 0, h->stream>>>(h->g, (const float*)h->f, h->nnode, j_begin / inner,
+                                                       j_end / inner, d_U);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->stream));
+  return BGK_OK;
 }
 
 int bgk_step_async(bgk_handle* h, int nsteps) {
