@@ -36,10 +36,11 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default="mixed", choices=["fp64", "fp32", "mixed"])
-    p.add_argument("--n-side", type=int, default=128)
-    p.add_argument("--n-v", type=int, default=32)
+    p.add_argument("--n-side", type=int, default=None,
+                   help="cells per side (shock_tube 128, bump3d 24, learned 256)")
+    p.add_argument("--n-v", type=int, default=None, help="velocity points per dimension (32; bump3d 16)")
     p.add_argument("--sweep-reps", type=int, default=5)
-    p.add_argument("--workload", default="shock_tube", choices=["shock_tube", "batched", "learned"])
+    p.add_argument("--workload", default="shock_tube", choices=["shock_tube", "bump3d", "batched", "learned"])
     p.add_argument("--train-runs", type=int, default=200)
     p.add_argument("--eval-runs", type=int, default=4)
     p.add_argument("--instances", type=int, default=64)
@@ -50,24 +51,47 @@ def parse():
                    help="local-inverse cache of the sweep")
     p.add_argument("--eager", action="store_true",
                    help="launch each step's kernels from a host loop instead of one CUDA graph (profiling)")
-    return p.parse_args()
+    a = p.parse_args()
+    if a.n_side is None:
+        a.n_side = {"bump3d": 24, "learned": 256}.get(a.workload, 128)
+    if a.n_v is None:
+        a.n_v = 16 if a.workload == "bump3d" else 32
+    return a
 
 
 def workload(args):
     from paper_2608_19150_b300 import synth
+    if args.workload == "bump3d":
+        return synth.workload_3d_bump(n_side=args.n_side, seed=2, n_v=args.n_v, k_v=3, L=6.0, knudsen=1e-2,
+                                      integrator="BE", cfl=8.0)
     return synth.workload_shock_tube(n_side=args.n_side, seed=1, kx=2, n_v=args.n_v, k_v=3, L=8.0, knudsen=1e-3,
                                      integrator="DIRK3", cfl=10.0)
 
 
+def elem_of(w):
+    """(name of the element tables, dofs per cell, velocity dimension) of a workload."""
+    if w.mesh.dim == 3:
+        return "p1tet", 4, 3
+    return ("p2tri", 6, 2) if w.kx == 2 else ("p1tri", 3, 2)
+
+
 def config(w, args, extra=None):
-    c = {"workload": "2D-2V shock tube, %dx%d squares (%d P2 triangles), %dx%d velocities on [-8,8]^2, DIRK3, "
-                     "Kn 1e-3, CFL 10, tau 1e-8" % (args.n_side, args.n_side, w.mesh.n_cells, args.n_v, args.n_v),
-         "n_cells": w.mesh.n_cells, "dof_per_sweep": int(w.mesh.n_cells * 6 * args.n_v ** 2),
+    _, nd, dv = elem_of(w)
+    dof = int(w.mesh.n_cells * nd * args.n_v ** dv)
+    if w.mesh.dim == 3:
+        name = ("3D-3V Gaussian bump, %d^3 cubes (%d P1 tetrahedra), %d^3 velocities on [-6,6]^3, backward Euler, "
+                "Kn 1e-2, CFL 8, tau 1e-8" % (args.n_side, w.mesh.n_cells, args.n_v))
+        integ = "BE"
+    else:
+        name = ("2D-2V shock tube, %dx%d squares (%d P2 triangles), %dx%d velocities on [-8,8]^2, DIRK3, "
+                "Kn 1e-3, CFL 10, tau 1e-8" % (args.n_side, args.n_side, w.mesh.n_cells, args.n_v, args.n_v))
+        integ = "DIRK3"
+    c = {"workload": name,
+         "n_cells": w.mesh.n_cells, "dof_per_sweep": dof,
          "precision": {"fp64": "FP64 sweeps", "fp32": "FP32 sweeps, FP64-accurate moments",
                        "mixed": "FP32 sweeps to the FP32 floor, then FP64 sweeps; FP64 moments"}[args.precision],
-         "integrator": "DIRK3",
-         "l2": "inputs larger than L2 (f %.2f GB per array)" % (w.mesh.n_cells * 6 * args.n_v ** 2 *
-                                                                 (4 if args.precision == "fp32" else 8) / 1e9),
+         "integrator": integ,
+         "l2": "inputs larger than L2 (f %.2f GB per array)" % (dof * (4 if args.precision == "fp32" else 8) / 1e9),
          "parallelism": "replicas", "launch": "eager host loop" if args.eager else
          "one CUDA graph per step, conditional while-node per stage"}
     if extra:
@@ -76,30 +100,31 @@ def config(w, args, extra=None):
 
 
 # --------------------------------------------------------------------- flop count
-def sweep_flops_per_item(cached):
-    """Floating-point operations of one local solve of the P2 kernel, counted from the
-    generated reference tables (multiply and add each count one) with the average face mix
-    of a triangle: 1.5 outflow and 1.5 inflow faces.  cached: right-hand side plus one
-    6x6 matrix-vector product with the stored inverse."""
+def sweep_flops_per_item(cached, kind="p2tri"):
+    """Floating-point operations of one local solve, counted from the generated reference
+    tables (multiply and add each count one) with the average face mix of the simplex: half
+    the faces outflow, half inflow.  cached: right-hand side plus one matrix-vector product
+    with the stored inverse."""
     sys.path.insert(0, os.path.join(ROOT, "paper_2608_19150_b300", "csrc"))
     import gen_tables as gt
-    d, nd, nf, Mh, Dd, Eh, fn = gt.tables("p2tri")
+    d, nd, nf, Mh, Dd, Eh, fn = gt.tables(kind)
+    half = nf / 2.0
     fl = 0.0
     fl += nf * (2 * d - 1 + 2)                     # s_i = v . N_i, |s_i| * (1/|K|)
     if cached:
         fl += sum(2 * sum(1 for b in range(nd) if Mh[a][b] != 0) - 1 for a in range(nd))
-        fl += 1.5 * sum(2 * sum(1 for k in range(len(fn[0])) if Eh[0][a][fn[0][k]] != 0) + 1
-                        for a in range(nd) if any(Eh[0][a][fn[0][k]] != 0 for k in range(len(fn[0]))))
+        fl += half * sum(2 * sum(1 for k in range(len(fn[0])) if Eh[0][a][fn[0][k]] != 0) + 1
+                         for a in range(nd) if any(Eh[0][a][fn[0][k]] != 0 for k in range(len(fn[0]))))
         return fl + nd * (2 * nd - 1)
     for a in range(nd):
         for b in range(nd):
             t = (Mh[a][b] != 0) + sum(Dd[i][a][b] != 0 for i in range(nf))
             fl += max(0, 2 * t - 1)
     nnzE = sum(1 for a in range(nd) for b in range(nd) if Eh[0][a][b] != 0)
-    fl += 1.5 * 2 * nnzE                           # outflow face terms
+    fl += half * 2 * nnzE                          # outflow face terms
     fl += sum(2 * sum(1 for b in range(nd) if Mh[a][b] != 0) - 1 for a in range(nd))
-    fl += 1.5 * sum(2 * sum(1 for k in range(len(fn[0])) if Eh[0][a][fn[0][k]] != 0) + 1
-                    for a in range(nd) if any(Eh[0][a][fn[0][k]] != 0 for k in range(len(fn[0]))))
+    fl += half * sum(2 * sum(1 for k in range(len(fn[0])) if Eh[0][a][fn[0][k]] != 0) + 1
+                     for a in range(nd) if any(Eh[0][a][fn[0][k]] != 0 for k in range(len(fn[0]))))
     for k in range(nd):                            # LU without pivoting + substitution
         fl += 1 + (nd - k - 1) * (1 + 2 * (nd - k - 1) + 2)
     for i in range(nd):
@@ -232,7 +257,7 @@ def run_reference(args):
     j0 = (o.nv - n_ord) // 2
     js = np.arange(j0, j0 + n_ord, dtype=np.int32)
     o.build_dags_for(js)
-    dt = 10.0 * o.dt_explicit()
+    dt = w.cfl * o.dt_explicit()
     f0 = o.maxwellian_rows(w.init, js)
     fbc = o.maxwellian_rows(w.inflow, js)
     A, _, _ = tableau(w.integrator)
@@ -331,20 +356,22 @@ def sweep_roofline(w, precision, reps, peaks, n_side=None, n_v=None):
     hbm_gbs = 2 * tsz * dof / (sweep_ms * 1e-3) / 1e9
     hbm_peak = float(peaks.get("hbm_gbs", 6400.0))
     cached = s.cache_bytes > 0
+    kind = elem_of(w)[0]
+    ename = {"p2tri": "ElemP2Tri", "p1tri": "ElemP1Tri", "p1tet": "ElemP1Tet"}[kind]
     if precision == "fp64":
-        fl = sweep_flops_per_item(cached)
+        fl = sweep_flops_per_item(cached, kind)
         tf = fl * s.nv * s.ncell / (sweep_ms * 1e-3) / 1e12
         r = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
              "frac": tf / FP64_PEAK_TFLOPS, "traffic": None,
-             "kernel": "k_sweep<ElemP2Tri,double,%s>" % ("cached" if cached else "uncached"),
+             "kernel": "k_sweep<%s,double,%s>" % (ename, "cached" if cached else "uncached"),
              "flops_per_local_solve": fl, "peak_source": "nominal B300 FP64 rate (measured FMA probe 1.125)"}
     else:
         r = {"bound": "hbm", "achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_gbs / hbm_peak,
              "traffic": None,
-             "kernel": "k_sweep<ElemP2Tri,float,%s>" % ("cached" if cached else "uncached,fused source"),
+             "kernel": "k_sweep<%s,float,%s>" % (ename, "cached" if cached else "uncached,fused source"),
              "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
     profiled = PROFILED_TRAFFIC.get(precision)
-    if profiled and n_side and n_v == 32 and (precision == "fp32" or cached):
+    if profiled and kind == "p2tri" and n_side and n_v == 32 and (precision == "fp32" or cached):
         r["traffic"] = profiled[0] * (n_side / 64.0) ** 2
         r["traffic_source"] = profiled[1] + " (scaled from 64x64 by the cell count)"
     r.update({"sweep_ms": sweep_ms, "dof_per_launch": dof, "algorithmic_bytes_per_dof": 2 * tsz,
@@ -435,7 +462,7 @@ def run_ours(args):
     roofline = dict(rl[dom])
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w, 1024, dt)
+        cpu = cpu_baseline(w, 1024 if w.mesh.dim == 2 else 256, dt)
     if rank != 0:
         return
     ms = 1e3 * el_max / args.steps
