@@ -284,3 +284,24 @@ def test_fp64_storage_moments_split_sums():
     assert rel_err(U, Uo) < 1e-13
     for m in range(U.shape[1]):
         assert np.abs(U[:, m] - Uo[:, m]).max() <= 1e-13 * np.abs(Uo[:, m]).max() + 1e-300
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("k_v,n_v", [(1, 12), (2, 12), (4, 15)])
+def test_every_velocity_degree(k_v, n_v, precision):
+    """The projection is specialised per velocity degree k_v (1..4): the projected
+    Maxwellian, its moments and one BE step against the oracle for each degree."""
+    w = synth.workload_p1_square(n_side=6, n_v=n_v, k_v=k_v, knudsen=0.05, integrator="BE")
+    s, o = make_pair(w, precision=precision, tau=1e-8 if precision == "fp64" else 1e-6)
+    s.set_state_maxwellian(w.init)
+    s.set_inflow_maxwellian(w.inflow)
+    f0 = o.maxwellian(w.init)
+    tol = FP64_TOL if precision == "fp64" else 2e-6
+    assert rel_err(s.get_f(), f0) < tol
+    assert rel_err(s.get_moments(), o.moments(f0)) < (FP64_TOL if precision == "fp64" else 1e-6)
+    if precision == "fp64":
+        o.set_physics(w.nu, s.dt, "BE", 1e-8, 1000)
+        st = s.step(1)
+        f1, it, meas, status = o.step(f0, o.maxwellian(w.inflow))
+        assert status == 0 and st.iterations[0] == it[0]
+        assert rel_err(s.get_f(), f1) < FP64_TOL
