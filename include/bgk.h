@@ -34,7 +34,8 @@ enum {
   BGK_E_OOM = 3,          /* device allocation failed */
   BGK_E_NOCONV = 4,       /* Picard iteration reached l_max without meeting the criterion */
   BGK_E_NONPHYSICAL = 5,  /* n <= 0, theta <= 0 or a non-finite moment was met */
-  BGK_E_TIMEOUT = 6       /* a bounded device-side wait ran out */
+  BGK_E_TIMEOUT = 6,      /* a bounded device-side wait ran out */
+  BGK_E_IO = 7            /* a checkpoint file could not be written or read, or does not match */
 };
 
 enum { BGK_BE = 0, BGK_DIRK2 = 1, BGK_DIRK3 = 2, BGK_BSTABLE2 = 3, BGK_BDF2 = 4 };
@@ -138,6 +139,27 @@ int bgk_get_velocity(const bgk_handle* h, double* h_v, double* h_w);
 /* Generation of every cell for ordinate j (host int32 [n_cells]); returns the count of
  * generations in *n_gen.  Bit-exact definition: longest path from a source (Sec. 4.1). */
 int bgk_get_generations(bgk_handle* h, int j, int32_t* h_gen, int* n_gen);
+
+/* Lagged edges of ordinate j's sweep graph (Sec. 4.1: the DFS back edges removed to break
+ * cycles; their upwind values are taken from the previous Picard iterate).  Writes up to
+ * `cap` pairs (upwind cell, downwind cell) to h_edges ([n][2], host) and their number to
+ * *n_lagged (the total, also when it exceeds cap).  An inflow face is lagged exactly when
+ * its upwind cell does not have a smaller generation. */
+int bgk_get_lagged_edges(bgk_handle* h, int j, int32_t* h_edges, int cap, int* n_lagged);
+
+/* Checkpoint / resume.  bgk_save writes the time-stepping state -- f^n, f^{n-1} when the
+ * BDF2 history is present, the step count, and the learned guess's moment history when a
+ * network is attached -- to the file `path` (raw little-endian binary behind a header that
+ * records the problem's sizes, velocity grid, nu, dt, storage type and a hash of the mesh
+ * geometry).  bgk_load reads such a file into a handle created for the same problem (same
+ * mesh, grid, nu, dt, integrator and storage precision; else BGK_E_IO) and replaces its
+ * state: the next bgk_step is bit-identical to the one the saving handle would take.
+ * Returns BGK_E_IO when the file cannot be written/read or does not match. */
+int bgk_save(bgk_handle* h, const char* path);
+int bgk_load(bgk_handle* h, const char* path);
+/* Steps taken since the state was last set or loaded (bgk_set_*, bgk_load restores the
+ * saved count) and the corresponding time steps * dt. */
+int bgk_get_time(const bgk_handle* h, int64_t* steps, double* t);
 
 /* One transport sweep of the Picard iteration, Eq. (bgk-ss-picard): f <- solution with
  * the Maxwellian of the current moments, source q = q_scale * f_q and collision nu_s.

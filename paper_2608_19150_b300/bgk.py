@@ -14,7 +14,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libbgk_b300.so")
 
-BGK_OK, BGK_E_INVALID, BGK_E_CUDA, BGK_E_OOM, BGK_E_NOCONV, BGK_E_NONPHYSICAL, BGK_E_TIMEOUT = range(7)
+BGK_OK, BGK_E_INVALID, BGK_E_CUDA, BGK_E_OOM, BGK_E_NOCONV, BGK_E_NONPHYSICAL, BGK_E_TIMEOUT, BGK_E_IO = range(8)
 INTEGRATORS = {"BE": 0, "DIRK2": 1, "DIRK3": 2, "BSTABLE2": 3, "BDF2": 4}
 PRECISIONS = {"fp64": 0, "fp32": 1, "mixed": 2}
 DTYPES = {np.dtype(np.float64): 0, np.dtype(np.float32): 1}
@@ -77,6 +77,10 @@ def load(path: str = LIB_PATH):
         "bgk_get_moments_device": [P, V],
         "bgk_get_velocity": [P, V, V],
         "bgk_get_generations": [P, I, V, C.POINTER(I)],
+        "bgk_get_lagged_edges": [P, I, V, I, C.POINTER(I)],
+        "bgk_save": [P, C.c_char_p],
+        "bgk_load": [P, C.c_char_p],
+        "bgk_get_time": [P, C.POINTER(C.c_int64), C.POINTER(D)],
         "bgk_sweep": [P, D, D],
         "bgk_sweep_range": [P, I, I, V, D, D],
         "bgk_moments_range_device": [P, I, I, V],
@@ -250,6 +254,27 @@ class Solver:
         n = C.c_int()
         _ck(self.lib.bgk_get_generations(self.h, int(j), _ptr(gen), C.byref(n)), "bgk_get_generations")
         return gen, n.value
+
+    def lagged_edges(self, j):
+        """[(upwind cell, downwind cell)] of ordinate j's lagged (cycle-breaking) edges."""
+        n = C.c_int()
+        _ck(self.lib.bgk_get_lagged_edges(self.h, int(j), None, 0, C.byref(n)), "bgk_get_lagged_edges")
+        e = np.empty((max(n.value, 1), 2), dtype=np.int32)
+        _ck(self.lib.bgk_get_lagged_edges(self.h, int(j), _ptr(e), n.value, C.byref(n)), "bgk_get_lagged_edges")
+        return e[:n.value]
+
+    def save(self, path):
+        _ck(self.lib.bgk_save(self.h, os.fsencode(path)), "bgk_save")
+
+    def load(self, path):
+        _ck(self.lib.bgk_load(self.h, os.fsencode(path)), "bgk_load")
+
+    def time(self):
+        """(steps since the state was set or loaded, the time they span)"""
+        n = C.c_int64()
+        t = C.c_double()
+        _ck(self.lib.bgk_get_time(self.h, C.byref(n), C.byref(t)), "bgk_get_time")
+        return n.value, t.value
 
     def sweep(self, nu_s, q_scale):
         _ck(self.lib.bgk_sweep(self.h, float(nu_s), float(q_scale)), "bgk_sweep")

@@ -73,6 +73,7 @@ struct bgk_handle {
   DevState* ds = nullptr;
   bool have_prev = false;    // BDF2 history present
   bool state_set = false;    // a distribution has been set (bgk_set_state_maxwellian / bgk_set_f)
+  int64_t steps = 0;         // steps taken since the state was set or loaded
   // graphs
   cudaGraphExec_t exec_main = nullptr;   // the integrator's step
   cudaGraphExec_t exec_start = nullptr;  // BDF2 start-up step (backward Euler)
@@ -643,6 +644,7 @@ const char* bgk_status_string(int status) {
     case BGK_E_NOCONV: return "Picard iteration did not converge within l_max";
     case BGK_E_NONPHYSICAL: return "non-physical moments (n <= 0, theta <= 0 or non-finite)";
     case BGK_E_TIMEOUT: return "bounded device wait ran out";
+    case BGK_E_IO: return "checkpoint file could not be written or read, or does not match the problem";
     default: return "unknown status";
   }
 }
@@ -877,6 +879,7 @@ static int set_maxwellian(bgk_handle* h, const double* h_nut, bool inflow) {
         rc = BGK_E_CUDA;
       h->have_prev = false;
       h->state_set = true;
+      h->steps = 0;
       if (h->have_hist) cudaMemsetAsync(h->have_hist, 0, sizeof(int), h->stream);
     }
   }
@@ -914,6 +917,7 @@ static int transfer_f(bgk_handle* h, void* ptr, int dtype, bool in, cudaMemcpyKi
       rc = BGK_E_CUDA;
     h->have_prev = false;
     h->state_set = true;
+    h->steps = 0;
   } else {
     const void* srcp = h->f;
     if (!same) {
@@ -991,6 +995,172 @@ int bgk_get_generations(bgk_handle* h, int j, int32_t* h_gen, int* n_gen) {
   return BGK_OK;
 }
 
+int bgk_get_lagged_edges(bgk_handle* h, int j, int32_t* h_edges, int cap, int* n_lagged) {
+  if (!h || j < 0 || j >= h->g.nv || !n_lagged || cap < 0 || (cap > 0 && !h_edges)) return BGK_E_INVALID;
+  const int n = h->hm.ncell;
+  std::vector<uint32_t> gl(n);
+  std::vector<int32_t> lv(n + 1), gen(n, 0);
+  std::vector<uint32_t> code(n, 0);
+  int32_t G = 0;
+  CK(cudaMemcpyAsync(gl.data(), h->glist + (size_t)j * n, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(lv.data(), h->lvl + (size_t)j * (n + 1), sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost,
+                     h->stream));
+  CK(cudaMemcpyAsync(&G, h->ngen + j, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  for (int g = 0; g < G; ++g)
+    for (int k = lv[g]; k < lv[g + 1]; ++k) {
+      gen[gl[k] & kCellMask] = g;
+      code[gl[k] & kCellMask] = gl[k] >> kCellBits;
+    }
+  int cnt = 0;
+  for (int c = 0; c < n; ++c)
+    for (int f = 0; f < h->hm.nf; ++f) {
+      const int nb = h->hm.nbr[(size_t)c * 4 + f];
+      if (((code[c] >> (2 * f)) & 3u) != 2u || nb < 0 || gen[nb] < gen[c]) continue;
+      if (cnt < cap) {
+        h_edges[2 * cnt] = nb;
+        h_edges[2 * cnt + 1] = c;
+      }
+      ++cnt;
+    }
+  *n_lagged = cnt;
+  return BGK_OK;
+}
+
+}  // extern "C"
+
+namespace {
+// checkpoint file header (little-endian, as written by bgk_save)
+struct CkptHeader {
+  char magic[8];
+  int32_t version, dtype, dim, kx, ncell, ndof, nv, npoints, kv, integrator, have_prev, have_hist;
+  int64_t nnode, nfv, steps;
+  double L, nu, dt;
+  uint64_t mesh_hash;
+};
+
+uint64_t fnv1a(uint64_t h, const void* p, size_t n) {
+  const unsigned char* b = (const unsigned char*)p;
+  for (size_t i = 0; i < n; ++i) {
+    h ^= b[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+CkptHeader ckpt_header(const bgk_handle* h) {
+  CkptHeader c;
+  std::memset(&c, 0, sizeof(c));
+  std::memcpy(c.magic, "BGKCKPT1", 8);
+  c.version = 1;
+  c.dtype = h->tsize == 8 ? BGK_DTYPE_F64 : BGK_DTYPE_F32;
+  c.dim = h->hm.dim;
+  c.kx = h->hm.kx;
+  c.ncell = h->hm.ncell;
+  c.ndof = h->hm.ndof;
+  c.nv = h->g.nv;
+  c.npoints = h->g.N;
+  c.kv = h->g.kv;
+  c.integrator = h->phys.integrator;
+  c.nnode = h->nnode;
+  c.nfv = (int64_t)h->nfv;
+  c.L = h->g.L;
+  c.nu = h->phys.nu;
+  c.dt = h->dt;
+  uint64_t hs = 1469598103934665603ull;
+  hs = fnv1a(hs, h->hm.geo.data(), sizeof(double) * h->hm.geo.size());
+  hs = fnv1a(hs, h->hm.nbr.data(), sizeof(int32_t) * h->hm.nbr.size());
+  c.mesh_hash = hs;
+  return c;
+}
+
+// copy n bytes between a device array and a file through a bounded host buffer
+bool ckpt_stream(FILE* fp, void* dev, size_t n, bool write, cudaStream_t s) {
+  const size_t chunk = (size_t)64 << 20;
+  std::vector<unsigned char> buf(std::min(chunk, std::max<size_t>(n, 1)));
+  for (size_t off = 0; off < n; off += chunk) {
+    const size_t m = std::min(chunk, n - off);
+    if (write) {
+      if (cudaMemcpyAsync(buf.data(), (unsigned char*)dev + off, m, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess || std::fwrite(buf.data(), 1, m, fp) != m)
+        return false;
+    } else {
+      if (std::fread(buf.data(), 1, m, fp) != m ||
+          cudaMemcpyAsync((unsigned char*)dev + off, buf.data(), m, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess)
+        return false;
+    }
+  }
+  return true;
+}
+}  // namespace
+
+extern "C" {
+
+int bgk_save(bgk_handle* h, const char* path) {
+  if (!h || !path || !h->state_set) return BGK_E_INVALID;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return BGK_E_CUDA;
+  CkptHeader c = ckpt_header(h);
+  c.have_prev = h->have_prev ? 1 : 0;
+  int hist = 0;
+  if (h->have_hist && h->Uhist &&
+      cudaMemcpy(&hist, h->have_hist, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return BGK_E_CUDA;
+  c.have_hist = hist ? 1 : 0;
+  c.steps = h->steps;
+  FILE* fp = std::fopen(path, "wb");
+  if (!fp) return BGK_E_IO;
+  bool ok = std::fwrite(&c, sizeof(c), 1, fp) == 1;
+  const size_t fb = h->nfv * h->tsize;
+  ok = ok && ckpt_stream(fp, h->f, fb, true, h->stream);
+  if (ok && c.have_prev) ok = ckpt_stream(fp, h->fprev, fb, true, h->stream);
+  if (ok && c.have_hist) ok = ckpt_stream(fp, h->Uhist, sizeof(double) * h->nnode * h->nm, true, h->stream);
+  ok = (std::fclose(fp) == 0) && ok;
+  return ok ? BGK_OK : BGK_E_IO;
+}
+
+int bgk_load(bgk_handle* h, const char* path) {
+  if (!h || !path) return BGK_E_INVALID;
+  FILE* fp = std::fopen(path, "rb");
+  if (!fp) return BGK_E_IO;
+  CkptHeader c;
+  const CkptHeader want = ckpt_header(h);
+  bool ok = std::fread(&c, sizeof(c), 1, fp) == 1 && std::memcmp(c.magic, want.magic, 8) == 0 &&
+            c.version == want.version && c.dtype == want.dtype && c.dim == want.dim && c.kx == want.kx &&
+            c.ncell == want.ncell && c.ndof == want.ndof && c.nv == want.nv && c.npoints == want.npoints &&
+            c.kv == want.kv && c.integrator == want.integrator && c.nnode == want.nnode && c.nfv == want.nfv &&
+            c.L == want.L && c.nu == want.nu && c.dt == want.dt && c.mesh_hash == want.mesh_hash;
+  const size_t fb = h->nfv * h->tsize;
+  ok = ok && ckpt_stream(fp, h->f, fb, false, h->stream);
+  if (ok && c.have_prev) ok = ckpt_stream(fp, h->fprev, fb, false, h->stream);
+  if (ok && c.have_hist) {
+    // the guess history is restored when this handle has a network attached
+    if (h->Uhist && h->have_hist) {
+      ok = ckpt_stream(fp, h->Uhist, sizeof(double) * h->nnode * h->nm, false, h->stream);
+      const int one = 1;
+      ok = ok && cudaMemcpy(h->have_hist, &one, sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
+    }
+  } else if (ok && h->have_hist) {
+    ok = cudaMemset(h->have_hist, 0, sizeof(int)) == cudaSuccess;
+  }
+  std::fclose(fp);
+  if (!ok) return BGK_E_IO;
+  if (cudaMemcpyAsync(h->fk, h->f, fb, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return BGK_E_CUDA;
+  h->have_prev = c.have_prev != 0;
+  h->state_set = true;
+  h->steps = c.steps;
+  return BGK_OK;
+}
+
+int bgk_get_time(const bgk_handle* h, int64_t* steps, double* t) {
+  if (!h) return BGK_E_INVALID;
+  if (steps) *steps = h->steps;
+  if (t) *t = (double)h->steps * h->dt;
+  return BGK_OK;
+}
+
 int bgk_sweep(bgk_handle* h, double nu_s, double q_scale) {
   if (!h) return BGK_E_INVALID;
   if (nu_s <= 0.0) nu_s = h->nus_main;
@@ -1065,6 +1235,7 @@ int bgk_step_async(bgk_handle* h, int nsteps) {
       CK(cudaMemcpyAsync(h->fprev, h->fk, h->nfv * h->tsize, cudaMemcpyDeviceToDevice, h->stream));
       h->have_prev = true;
     }
+    h->steps += 1;
   }
   return BGK_OK;
 }
