@@ -25,10 +25,24 @@ struct BatchInst {
   int B;       // ordinates per CTA
   int cached;  // local inverses available for nus
   int nv;
+  // FP32 instances without an inverse cache form their source in the sweep (as the
+  // single-problem FP32 sweep does): Maxwellian factors cf, stage source q and its scale
+  int fused;
+  const void* cf;
+  const void* q;
+  double qscale;
 };
 
 template <typename T, class E>
 __device__ __noinline__ void batch_sweep_one(const BatchInst& I, int j, int tid, int nt, const NamedBarrier& bar) {
+  if constexpr (sizeof(T) == 4) {
+    if (I.fused) {
+      sweep_ordinate<E, T, false, NamedBarrier, false, true>(
+          I.sa, *I.g, j, (T)I.nus, SrcArgs<T>{nullptr, (const T*)I.cf, (const T*)I.q, (T)I.qscale},
+          (const T*)I.fbc, nullptr, (T*)I.f, tid, nt, bar);
+      return;
+    }
+  }
   if (I.cached)
     sweep_ordinate<E, T, true>(I.sa, *I.g, j, (T)I.nus, SrcArgs<T>{(const T*)I.src, nullptr, nullptr, T(0)},
                                (const T*)I.fbc, (const T*)I.Ainv,
@@ -39,8 +53,10 @@ __device__ __noinline__ void batch_sweep_one(const BatchInst& I, int j, int tid,
                                 nt, bar);
 }
 
+// (at most 128 registers: four CTAs per SM; the dispatch's calls keep more state on the
+// stack, which costs less than the residency it buys: 64-instance FP64 sweep 293 -> 252 ms)
 template <typename T>
-__global__ void __launch_bounds__(128) k_sweep_batched(const BatchInst* __restrict__ inst,
+__global__ void __launch_bounds__(128, 4) k_sweep_batched(const BatchInst* __restrict__ inst,
                                                        const int2* __restrict__ units, int nunits, int* counter) {
   __shared__ int s_unit;
   for (;;) {
@@ -392,9 +408,6 @@ int bgk_batch_create(int n, const bgk_mesh* meshes, const bgk_vgrid* vgrids, con
       release_batch(b);
       return rc;
     }
-    // the batched sweep reads a precomputed src
-    h->fuse_src = false;
-    if (h->shadow) h->shadow->fuse_src = false;
     b->inst.push_back(h);
   }
   const int ns = std::min(8, n);
@@ -434,6 +447,9 @@ int bgk_batch_create(int n, const bgk_mesh* meshes, const bgk_vgrid* vgrids, con
     }
     cudaStreamSynchronize(b->stream);
   }
+  // FP32 instances without a cache form their source in the sweep (set at creation, before
+  // the caches existed: settle it now)
+  for (bgk_handle* h : b->inst) h->fuse_src = h->precision == BGK_FP32_SWEEP && !h->Ainv;
   std::vector<DevState*> dsp(n);
   b->h_inst.resize(n);
   for (int i = 0; i < n; ++i) {
@@ -451,6 +467,10 @@ int bgk_batch_create(int n, const bgk_mesh* meshes, const bgk_vgrid* vgrids, con
     I.type = inst_type(h);
     I.cached = h->Ainv && h->nus_cached == h->nus_main;
     I.nv = h->g.nv;
+    I.fused = h->fuse_src ? 1 : 0;
+    I.cf = h->cf;
+    I.q = h->fk;
+    I.qscale = h->qscale_main;
     // default tile: one ordinate per CTA when generations are wide, more when narrow
     const int width = h->hm.ncell / std::max(1, h->Gmax);
     I.B = width >= 96 ? 1 : (width >= 48 ? 2 : 4);
@@ -477,6 +497,11 @@ int bgk_batch_create(int n, const bgk_mesh* meshes, const bgk_vgrid* vgrids, con
       I.ds = sh->ds;
       I.nus = sh->nus_main;
       I.cached = sh->Ainv && sh->nus_cached == sh->nus_main;
+      // the shadow's stage source is the main q converted to FP32 into its fk
+      I.fused = sh->fuse_src ? 1 : 0;
+      I.cf = sh->cf;
+      I.q = sh->fk;
+      I.qscale = b->inst[i]->qscale_main;
       ds32[i] = sh->ds;
     }
     cudaMemcpyAsync(b->d_ds32, ds32.data(), sizeof(DevState*) * n, cudaMemcpyHostToDevice, b->stream);
