@@ -40,7 +40,9 @@ def parse():
                    help="cells per side (shock_tube 128, bump3d 24, learned 256)")
     p.add_argument("--n-v", type=int, default=None, help="velocity points per dimension (32; bump3d 16)")
     p.add_argument("--sweep-reps", type=int, default=5)
-    p.add_argument("--workload", default="shock_tube", choices=["shock_tube", "bump3d", "batched", "learned"])
+    p.add_argument("--workload", default="shock_tube", choices=["shock_tube", "bump3d", "strip", "batched", "learned"])
+    p.add_argument("--sweep-mode", default="auto", choices=["auto", "tgs", "ts"],
+                   help="sweep algorithm: generation sweep (tgs), one thread per ordinate (ts), or automatic")
     p.add_argument("--train-runs", type=int, default=200)
     p.add_argument("--eval-runs", type=int, default=4)
     p.add_argument("--instances", type=int, default=64)
@@ -53,7 +55,7 @@ def parse():
                    help="launch each step's kernels from a host loop instead of one CUDA graph (profiling)")
     a = p.parse_args()
     if a.n_side is None:
-        a.n_side = {"bump3d": 24, "learned": 256}.get(a.workload, 128)
+        a.n_side = {"bump3d": 24, "learned": 256, "strip": 4096}.get(a.workload, 128)
     if a.n_v is None:
         a.n_v = 16 if a.workload == "bump3d" else 32
     return a
@@ -64,6 +66,9 @@ def workload(args):
     if args.workload == "bump3d":
         return synth.workload_3d_bump(n_side=args.n_side, seed=2, n_v=args.n_v, k_v=3, L=6.0, knudsen=1e-2,
                                       integrator="BE", cfl=8.0)
+    if args.workload == "strip":
+        return synth.workload_strip(nx=args.n_side, ny=2, seed=5, kx=1, n_v=args.n_v, k_v=3, L=6.0, knudsen=1e-2,
+                                    integrator="BE", cfl=10.0)
     return synth.workload_shock_tube(n_side=args.n_side, seed=1, kx=2, n_v=args.n_v, k_v=3, L=8.0, knudsen=1e-3,
                                      integrator="DIRK3", cfl=10.0)
 
@@ -82,6 +87,10 @@ def config(w, args, extra=None):
         name = ("3D-3V Gaussian bump, %d^3 cubes (%d P1 tetrahedra), %d^3 velocities on [-6,6]^3, backward Euler, "
                 "Kn 1e-2, CFL 8, tau 1e-8" % (args.n_side, w.mesh.n_cells, args.n_v))
         integ = "BE"
+    elif args.workload == "strip":
+        name = ("2D-2V smooth quasi-1D problem on a %dx2 strip (%d P1 triangles), %dx%d velocities on [-6,6]^2, "
+                "backward Euler, Kn 1e-2, CFL 10, tau 1e-8" % (args.n_side, w.mesh.n_cells, args.n_v, args.n_v))
+        integ = "BE"
     else:
         name = ("2D-2V shock tube, %dx%d squares (%d P2 triangles), %dx%d velocities on [-8,8]^2, DIRK3, "
                 "Kn 1e-3, CFL 10, tau 1e-8" % (args.n_side, args.n_side, w.mesh.n_cells, args.n_v, args.n_v))
@@ -93,7 +102,7 @@ def config(w, args, extra=None):
          "integrator": integ,
          "l2": "inputs larger than L2 (f %.2f GB per array)" % (dof * (4 if args.precision == "fp32" else 8) / 1e9),
          "parallelism": "replicas", "launch": "eager host loop" if args.eager else
-         "one CUDA graph per step, conditional while-node per stage"}
+         "one CUDA graph per step, conditional while-node per stage", "sweep_mode": args.sweep_mode}
     if extra:
         c.update(extra)
     return c
@@ -338,11 +347,11 @@ PROFILED_TRAFFIC = {
 }
 
 
-def sweep_roofline(w, precision, reps, peaks, n_side=None, n_v=None):
+def sweep_roofline(w, precision, reps, peaks, n_side=None, n_v=None, sweep_mode="auto"):
     """Event-timed sweep kernel of the given precision on its own handle (first-stage
     coefficient, local-inverse cache as in the step) and its roofline entry."""
     from paper_2608_19150_b300 import bgk
-    s = bgk.Solver.from_workload(w, precision=precision)
+    s = bgk.Solver.from_workload(w, precision=precision, sweep_mode=sweep_mode)
     s.set_state_maxwellian(w.init)
     s.set_inflow_maxwellian(w.inflow)
     s.sweep(0.0, 0.0)
@@ -358,23 +367,25 @@ def sweep_roofline(w, precision, reps, peaks, n_side=None, n_v=None):
     cached = s.cache_bytes > 0
     kind = elem_of(w)[0]
     ename = {"p2tri": "ElemP2Tri", "p1tri": "ElemP1Tri", "p1tet": "ElemP1Tet"}[kind]
+    kname = "k_sweep_ts" if s.sweep_mode == "ts" else "k_sweep"
     if precision == "fp64":
         fl = sweep_flops_per_item(cached, kind)
         tf = fl * s.nv * s.ncell / (sweep_ms * 1e-3) / 1e12
         r = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
              "frac": tf / FP64_PEAK_TFLOPS, "traffic": None,
-             "kernel": "k_sweep<%s,double,%s>" % (ename, "cached" if cached else "uncached"),
+             "kernel": "%s<%s,double,%s>" % (kname, ename, "cached" if cached else "uncached"),
              "flops_per_local_solve": fl, "peak_source": "nominal B300 FP64 rate (measured FMA probe 1.125)"}
     else:
         r = {"bound": "hbm", "achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_gbs / hbm_peak,
              "traffic": None,
-             "kernel": "k_sweep<%s,float,%s>" % (ename, "cached" if cached else "uncached,fused source"),
+             "kernel": "%s<%s,float,%s>" % (kname, ename, "cached" if cached else "uncached,fused source"),
              "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
     profiled = PROFILED_TRAFFIC.get(precision)
-    if profiled and kind == "p2tri" and n_side and n_v == 32 and (precision == "fp32" or cached):
+    if profiled and kind == "p2tri" and kname == "k_sweep" and n_side and n_v == 32 and (precision == "fp32" or cached):
         r["traffic"] = profiled[0] * (n_side / 64.0) ** 2
         r["traffic_source"] = profiled[1] + " (scaled from 64x64 by the cell count)"
-    r.update({"sweep_ms": sweep_ms, "dof_per_launch": dof, "algorithmic_bytes_per_dof": 2 * tsz,
+    r.update({"sweep_ms": sweep_ms, "sweep_mode": s.sweep_mode, "dof_per_launch": dof,
+              "algorithmic_bytes_per_dof": 2 * tsz,
               "hbm_achieved_gbs": hbm_gbs, "hbm_frac": hbm_gbs / hbm_peak,
               "local_inverse_cache_gb": s.cache_bytes / 1e9})
     s.close()
@@ -404,7 +415,7 @@ def run_ours(args):
         pass
     tstream = torch.cuda.Stream()
     s = bgk.Solver.from_workload(w, precision=args.precision, eager=args.eager, cache_inverse=args.cache,
-                                 stream=tstream.cuda_stream)
+                                 stream=tstream.cuda_stream, sweep_mode=args.sweep_mode)
     s.set_state_maxwellian(w.init)
     s.set_inflow_maxwellian(w.inflow)
     dof = s.nv * s.nnode
@@ -438,7 +449,7 @@ def run_ours(args):
     # the plain FP64 path on the same steps, for the comparison the metric asks for
     plain = None
     if args.precision != "fp64":
-        p = bgk.Solver.from_workload(w, precision="fp64", stream=tstream.cuda_stream)
+        p = bgk.Solver.from_workload(w, precision="fp64", stream=tstream.cuda_stream, sweep_mode=args.sweep_mode)
         p.set_f(f0.astype(np.float64))
         p.set_inflow_maxwellian(w.inflow)
         for _ in range(args.warmup):
@@ -450,9 +461,9 @@ def run_ours(args):
         p.close()
         del p
     # the sweep kernels, event-timed on their own stream
-    rl = {"fp64": sweep_roofline(w, "fp64", args.sweep_reps, peaks, args.n_side, args.n_v)}
+    rl = {"fp64": sweep_roofline(w, "fp64", args.sweep_reps, peaks, args.n_side, args.n_v, args.sweep_mode)}
     if args.precision != "fp64":
-        rl["fp32"] = sweep_roofline(w, "fp32", args.sweep_reps, peaks, args.n_side, args.n_v)
+        rl["fp32"] = sweep_roofline(w, "fp32", args.sweep_reps, peaks, args.n_side, args.n_v, args.sweep_mode)
     # dominant kernel of the timed step: the sweep precision that used the most time
     n64 = sum(sum(i["fp64"]) for i in iters)
     n32 = sum(sum(i["fp32"]) for i in iters)

@@ -42,7 +42,10 @@ class Physics(C.Structure):
 class Config(C.Structure):
     _fields_ = [("tau", C.c_double), ("l_max", C.c_int), ("precision", C.c_int), ("block_threads", C.c_int),
                 ("stream", C.c_void_p), ("eager", C.c_int),
-                ("cache_inverse", C.c_int), ("fp32_floor", C.c_double), ("prefetch", C.c_int)]
+                ("cache_inverse", C.c_int), ("fp32_floor", C.c_double), ("prefetch", C.c_int),
+                ("sweep_mode", C.c_int)]
+
+SWEEP_MODES = {"auto": 0, "tgs": 1, "ts": 2}
 
 
 class Stats(C.Structure):
@@ -154,7 +157,8 @@ class Solver:
     """Handle of one problem on the current CUDA device (thin wrapper of bgk_create)."""
 
     def __init__(self, dim, kx, xyz, cells, n_v, k_v, L, nu, integrator="BE", dt=0.0, cfl=10.0, tau=1e-8,
-                 l_max=1000, precision="fp64", block_threads=0, stream=None, eager=False, cache_inverse="auto", fp32_floor=0.0, prefetch=False):
+                 l_max=1000, precision="fp64", block_threads=0, stream=None, eager=False, cache_inverse="auto", fp32_floor=0.0, prefetch=False,
+                 sweep_mode="auto"):
         self.lib = load()
         self._xyz = np.ascontiguousarray(xyz, dtype=np.float64)
         self._cells = np.ascontiguousarray(cells, dtype=np.int32)
@@ -163,14 +167,16 @@ class Solver:
         ph = Physics(float(nu), INTEGRATORS[integrator], float(dt), float(cfl))
         cf = Config(float(tau), int(l_max), PRECISIONS[precision], int(block_threads),
                     C.c_void_p(stream) if stream else None, int(bool(eager)),
-                    {"auto": 0, "on": 1, "off": 2}[cache_inverse], float(fp32_floor), 1 if prefetch else 0)
+                    {"auto": 0, "on": 1, "off": 2}[cache_inverse], float(fp32_floor), 1 if prefetch else 0,
+                    SWEEP_MODES[sweep_mode])
         h = C.c_void_p()
         _ck(self.lib.bgk_create(C.byref(m), C.byref(vg), C.byref(ph), C.byref(cf), C.byref(h)), "bgk_create")
         self.h = h
-        sz = (C.c_int64 * 9)()
+        sz = (C.c_int64 * 10)()
         _ck(self.lib.bgk_sizes(self.h, sz), "bgk_sizes")
         (self.nv, self.nnode, self.ndof, self.ncell, self.dim, self.gmax, self.lagged, self.cache_bytes,
-         self.sweep_threads) = (int(x) for x in sz)
+         self.sweep_threads, mode) = (int(x) for x in sz)
+        self.sweep_mode = {1: "tgs", 2: "ts"}[mode]
         self.precision = precision
         self.fdtype = np.float32 if precision == "fp32" else np.float64
 
@@ -187,10 +193,11 @@ class Solver:
         self.lib = load()
         self.h = handle
         self._owner = owner
-        sz = (C.c_int64 * 9)()
+        sz = (C.c_int64 * 10)()
         _ck(self.lib.bgk_sizes(self.h, sz), "bgk_sizes")
         (self.nv, self.nnode, self.ndof, self.ncell, self.dim, self.gmax, self.lagged, self.cache_bytes,
-         self.sweep_threads) = (int(x) for x in sz)
+         self.sweep_threads, mode) = (int(x) for x in sz)
+        self.sweep_mode = {1: "tgs", 2: "ts"}[mode]
         self.precision = precision
         self.fdtype = np.float32 if precision == "fp32" else np.float64
         return self
@@ -348,7 +355,7 @@ class Batch:
             vgrids[i] = VGrid(float(w.L), int(w.n_v), int(w.k_v))
             phys[i] = Physics(float(w.nu), INTEGRATORS["BE"], float(dt[i]) if dt else 0.0, float(w.cfl))
         cf = Config(float(tau), int(l_max), PRECISIONS[precision], 0, C.c_void_p(stream) if stream else None, 0,
-                    {"auto": 0, "on": 1, "off": 2}[cache_inverse], 0.0, 0)
+                    {"auto": 0, "on": 1, "off": 2}[cache_inverse], 0.0, 0, 0)
         self.mixed = precision == "mixed"
         h = C.c_void_p()
         _ck(self.lib.bgk_batch_create(n, meshes, vgrids, phys, C.byref(cf), C.byref(h)), "bgk_batch_create")

@@ -1011,6 +1011,10 @@ __device__ __forceinline__ void resolve_src(SweepItem<E, T, REG, FUSED>& it, T q
 struct CtaBarrier {
   __device__ __forceinline__ void sync() const { __syncthreads(); }
 };
+// No barrier: a single thread sweeps its ordinate alone (TS).
+struct NoBarrier {
+  __device__ __forceinline__ void sync() const {}
+};
 struct NamedBarrier {
   int id, count;
   __device__ __forceinline__ void sync() const {
@@ -1204,6 +1208,20 @@ __device__ __forceinline__ void sweep_ordinate(const SweepArgs& sa, const VGrid&
 // One sweep of every ordinate of one problem: one CTA per ordinate.  PF: the cached
 // local inverse and the geometry of each thread's next cell are copied to shared memory
 // asynchronously while the current cell is solved (dynamic shared memory).
+// Topological sweep (TS, Sec. 4.1): one thread per ordinate walks that ordinate's whole
+// schedule alone, cell after cell in generation order, with no barrier; the concurrent
+// work is the number of ordinates (the generation sweep's is ordinates x generation
+// width).  Same operations per cell as the generation sweep.
+template <class E, typename T, bool CACHED, bool FUSED = false>
+__global__ void __launch_bounds__(64) k_sweep_ts(SweepArgs sa, VGrid g, T nus, SrcArgs<T> sr,
+                                                 const T* __restrict__ fbc, const T* __restrict__ Ainv, T* f,
+                                                 const DevState* ds, int jb, int je) {
+  if (ds && (ds->status != BGK_OK || ds->done)) return;
+  const int j = jb + (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (j >= je) return;
+  sweep_ordinate<E, T, CACHED, NoBarrier, false, FUSED>(sa, g, j, nus, sr, fbc, Ainv, f, 0, 1, NoBarrier());
+}
+
 // (ordinates jofs + blockIdx.x: all of them, or one shard's range)
 template <class E, typename T, bool CACHED, bool PF = false, bool FUSED = false>
 __global__ void __launch_bounds__(256) k_sweep(SweepArgs sa, VGrid g, T nus, SrcArgs<T> sr,

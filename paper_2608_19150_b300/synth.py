@@ -84,6 +84,35 @@ def square_mesh(n: int, seed: int, jitter: float = 0.2) -> Mesh:
     return Mesh(2, xyz, cells, n_side=n, seed=seed)
 
 
+def rect_mesh(nx: int, ny: int, seed: int, jitter: float = 0.2) -> Mesh:
+    """[0, 1] x [0, ny/nx]: nx x ny squares of side h = 1/nx, each cut into two triangles
+    along a seeded diagonal, interior vertices jittered as in square_mesh (a strip when
+    ny << nx)."""
+    h = 1.0 / nx
+    ii, jj = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1), indexing="ij")
+    xyz = np.stack([ii.ravel() * h, jj.ravel() * h], axis=1).astype(np.float64)
+    vid = lambda i, j: i * (ny + 1) + j  # noqa: E731
+    nvert = (nx + 1) * (ny + 1)
+    r = splitmix64_uniform(seed, 2 * nvert + nx * ny)
+    jit = (2.0 * r[: 2 * nvert].reshape(-1, 2) - 1.0) * (jitter * h)
+    interior = (ii.ravel() > 0) & (ii.ravel() < nx) & (jj.ravel() > 0) & (jj.ravel() < ny)
+    xyz[interior] += jit[interior]
+    diag = r[2 * nvert:] < 0.5
+    cells = np.empty((2 * nx * ny, 3), dtype=np.int32)
+    k = 0
+    for i in range(nx):
+        for j in range(ny):
+            a, b, c, d = vid(i, j), vid(i + 1, j), vid(i + 1, j + 1), vid(i, j + 1)
+            if diag[i * ny + j]:
+                cells[k] = (a, b, c)
+                cells[k + 1] = (a, c, d)
+            else:
+                cells[k] = (a, b, d)
+                cells[k + 1] = (b, c, d)
+            k += 2
+    return Mesh(2, xyz, cells, n_side=nx, seed=seed, meta={"ny": ny})
+
+
 # Kuhn (Freudenthal) split of the unit cube into 6 tetrahedra sharing the main
 # diagonal from corner 0 to corner 7; corners are indexed by bits (x, y, z).
 _KUHN = [(0, 1, 3, 7), (0, 3, 2, 7), (0, 2, 6, 7), (0, 6, 4, 7), (0, 4, 5, 7), (0, 5, 1, 7)]
@@ -182,6 +211,21 @@ def workload_p1_square(n_side=16, seed=0, n_v=16, k_v=3, L=6.0, knudsen=1e-2,
     inflow = _pack(np.ones_like(n), u, np.ones_like(n))
     return Workload("2d2v_p1_smooth_%dx%d_v%d" % (n_side, n_side, n_v), mesh, 1, n_v, k_v, L,
                     knudsen, integrator, cfl, init, inflow)
+
+
+def workload_strip(nx=1024, ny=2, seed=5, kx=1, n_v=32, k_v=3, L=6.0, knudsen=1e-2,
+                   integrator="BE", cfl=10.0) -> Workload:
+    """Quasi-1D smooth problem on a strip of nx x ny squares (narrow sweep generations):
+    n = 1 + 0.2 sin(2 pi x), u = 0, theta = 1 + 0.1 cos(2 pi x); inflow Maxwellian (1, 0, 1)."""
+    mesh = rect_mesh(nx, ny, seed, 0.2)
+    x = node_coords(mesh, kx).reshape(-1, 2)
+    n = 1.0 + 0.2 * np.sin(2 * np.pi * x[:, 0])
+    th = 1.0 + 0.1 * np.cos(2 * np.pi * x[:, 0])
+    u = np.zeros_like(x)
+    init = _pack(n, u, th)
+    inflow = _pack(np.ones_like(n), u, np.ones_like(n))
+    return Workload("2d2v_strip_p%d_%dx%d_v%d" % (kx, nx, ny, n_v), mesh, kx, n_v, k_v, L, knudsen,
+                    integrator, cfl, init, inflow)
 
 
 def workload_shock_tube(n_side=128, seed=1, kx=2, n_v=32, k_v=3, L=8.0, knudsen=1e-3,

@@ -1,0 +1,54 @@
+"""The two sweep algorithms (Sec. 4.1): TS (one thread per ordinate walks its whole
+schedule) and TGS (a CTA per ordinate walks the generations, the cells of a generation in
+parallel) do the same operations per cell in a valid topological order.  They agree to
+rounding (the two kernels are compiled separately and may contract the local assembly's
+products into FMAs differently; with the local-inverse cache the results are identical):
+one sweep and two steps, FP64 with and without the cache, FP32, mixed, triangles P1/P2 and
+tetrahedra with cycles.  The default is TGS, also on a strip (narrow generations), where TS
+was measured 8x slower."""
+import numpy as np
+import pytest
+
+from paper_2608_19150_b300 import bgk, synth
+
+from gpu_common import rel_err, small_shock_tube, twisted_workload
+
+pytestmark = pytest.mark.gpu
+
+
+def _cases():
+    return {"p2_tri": small_shock_tube(n=8, kx=2, n_v=16, integrator="DIRK3"),
+            "p1_strip": synth.workload_strip(nx=48, ny=2, n_v=16, integrator="BDF2"),
+            "p1_tet": twisted_workload(3, 8)}
+
+
+@pytest.mark.parametrize("precision,cache", [("fp64", "on"), ("fp64", "off"), ("fp32", "off"), ("mixed", "auto")])
+@pytest.mark.parametrize("name", ["p2_tri", "p1_strip", "p1_tet"])
+def test_ts_equals_tgs(name, precision, cache):
+    w = _cases()[name]
+    tau = 1e-6 if precision == "fp32" else 1e-8
+    out = []
+    for mode in ("tgs", "ts"):
+        s = bgk.Solver.from_workload(w, precision=precision, cache_inverse=cache, sweep_mode=mode, tau=tau)
+        assert s.sweep_mode == mode
+        s.set_state_maxwellian(w.init)
+        s.set_inflow_maxwellian(w.inflow)
+        s.sweep(0.0, 0.0)
+        f1 = s.get_f(s.fdtype)
+        s.set_state_maxwellian(w.init)
+        st = s.step(2)
+        out.append((f1, s.get_f(s.fdtype), list(st.iterations), list(st.iterations_fp32)))
+    if precision == "fp64" and cache == "on":
+        np.testing.assert_array_equal(out[0][0], out[1][0])
+        np.testing.assert_array_equal(out[0][1], out[1][1])
+    tol = 2e-6 if precision == "fp32" else 1e-12
+    assert rel_err(out[1][0], out[0][0].astype(np.float64)) < tol
+    assert rel_err(out[1][1], out[0][1].astype(np.float64)) < tol
+    if precision == "fp64":
+        assert out[0][2] == out[1][2]
+
+
+def test_default_is_tgs():
+    strip = bgk.Solver.from_workload(synth.workload_strip(nx=256, ny=1, n_v=16))
+    square = bgk.Solver.from_workload(small_shock_tube(n=16, kx=2, n_v=16))
+    assert strip.sweep_mode == "tgs" and square.sweep_mode == "tgs"
