@@ -39,6 +39,7 @@ enum {
 };
 
 enum { BGK_BE = 0, BGK_DIRK2 = 1, BGK_DIRK3 = 2, BGK_BSTABLE2 = 3, BGK_BDF2 = 4 };
+enum { BGK_COLL_MAXWELLIAN = 0, BGK_COLL_LINEAR = 1 };
 /* BGK_FP64: FP64 storage and sweeps.  BGK_FP32_SWEEP: FP32 storage and sweeps, moments
  * and Maxwellian parameters to FP64 accuracy; it stalls at FP32 rounding (~1e-7 in the
  * moment change).  BGK_MIXED: FP64 state; each stage first runs FP32 sweeps until the
@@ -71,6 +72,10 @@ typedef struct {
   int integrator;     /* BGK_BE, BGK_DIRK2, BGK_DIRK3, BGK_BSTABLE2, BGK_BDF2 */
   double dt;          /* time step; if <= 0, dt = cfl * dt_e (explicit bound of Sec. 5) */
   double cfl;
+  int collision;      /* BGK_COLL_MAXWELLIAN (0): nu (M[f] - f) with the projected Maxwellian
+                         (App. B); BGK_COLL_LINEAR (1): the simplified, linear Maxwellian
+                         N_h = n / |V| at every ordinate, |V| = (2L)^d (Eq. linear-Maxwellian,
+                         Prop. Linear Stability); it conserves mass only */
 } bgk_physics;
 
 /* Solver configuration. */
@@ -130,6 +135,10 @@ int bgk_set_state_maxwellian(bgk_handle* h, const double* h_nut);
 /* Inflow boundary data: projected Maxwellian of the nodal states (host [n_nodes][d+2]),
  * used at nodes of boundary faces with v.n < 0 (Eq. bgk-bc, inflow condition). */
 int bgk_set_inflow_maxwellian(bgk_handle* h, const double* h_nut);
+/* Inflow boundary data f^bc of Eq. bgk-bc given directly: host FP64 [n_ordinates][n_nodes]
+ * (values at nodes not on a boundary face are ignored).  Copied; the caller keeps h_f.
+ * BGK_E_INVALID on a null argument. */
+int bgk_set_inflow(bgk_handle* h, const double* h_f);
 /* Raw distribution in or out, host buffers [n_ordinates][n_nodes] of dtype. */
 int bgk_set_f(bgk_handle* h, const void* h_f, int dtype);
 int bgk_get_f(bgk_handle* h, void* h_f, int dtype);

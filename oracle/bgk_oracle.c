@@ -81,6 +81,7 @@ typedef struct {
   /* physics */
   double nu, dt, tau;
   int integrator, lmax;
+  int collision; /* 0: projected Maxwellian; 1: simplified Maxwellian N_h = n / |V| */
 } orc_t;
 
 /* ------------------------------------------------------------------ velocity grid */
@@ -980,9 +981,21 @@ static int picard(orc_t *o, double *f, const double *q, const double *fbc, doubl
   *status = ORC_E_NOCONV;
   for (l = 0; l < lmax; ++l) {
     int bad = 0;
-    for (int i = 0; i < o->nnode; ++i) bad |= primitive(o->dim, Uo + (size_t)i * nm, nut + (size_t)i * nm);
-    if (bad) { *status = ORC_E_NONPHYSICAL; break; }
-    orc_maxwellian(o, nut, Mn);
+    if (o->collision == 1) {
+      /* Eq. linear-Maxwellian: the same value n / |V| at every ordinate, |V| = (2L)^d */
+      double vol = 1.0;
+      for (int al = 0; al < o->dim; ++al) vol *= 2.0 * o->L;
+      for (int i = 0; i < o->nnode; ++i) {
+        double n = Uo[(size_t)i * nm];
+        if (!(n > 0.0) || !isfinite(n)) bad = 1;
+        for (int j = 0; j < o->nv; ++j) Mn[(size_t)j * o->nnode + i] = n / vol;
+      }
+      if (bad) { *status = ORC_E_NONPHYSICAL; break; }
+    } else {
+      for (int i = 0; i < o->nnode; ++i) bad |= primitive(o->dim, Uo + (size_t)i * nm, nut + (size_t)i * nm);
+      if (bad) { *status = ORC_E_NONPHYSICAL; break; }
+      orc_maxwellian(o, nut, Mn);
+    }
     sweep(o, f, Mn, q, fbc, nu, nu_s, fnew);
     moments(o, fnew, Un);
     *meas = orc_conv_measure(o, Un, Uo);
@@ -998,6 +1011,10 @@ static int picard(orc_t *o, double *f, const double *q, const double *fbc, doubl
 void orc_set_physics(orc_t *o, double nu, double dt, int integrator, double tau, int lmax) {
   o->nu = nu; o->dt = dt; o->integrator = integrator; o->tau = tau; o->lmax = lmax;
 }
+
+/* Collision model: 0 = the projected Maxwellian (App. B), 1 = the simplified Maxwellian of
+ * Eq. linear-Maxwellian (Prop. Linear Stability). */
+void orc_set_collision(orc_t *o, int kind) { o->collision = kind; }
 
 /* Advance one time step (Sec. 3.5 + Sec. 4).  f: in f^k, out f^{k+1}.  fprev: f^{k-1}
  * (BDF2 only; NULL -> backward Euler start).  fbc: boundary values [j][cell][node].

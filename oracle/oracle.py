@@ -9,7 +9,8 @@ and the readings taken where the paper is silent).  This wrapper only marshals a
 
 Parity status per function (pins live in ``tests/test_oracle_pins.py``):
   velocity grid, element matrices, projection, moments, sweep graph / generations,
-  one sweep, one time step (BE, DIRK2, DIRK3, B-stable DIRK2, BDF2): pinned.
+  one sweep, one time step (BE, DIRK2, DIRK3, B-stable DIRK2, BDF2), the simplified
+  Maxwellian collision model: pinned.
 """
 from __future__ import annotations
 
@@ -72,6 +73,7 @@ def _load():
         lib.orc_conv_measure.restype = C.c_double
         lib.orc_conv_measure.argtypes = [P, dp, dp]
         lib.orc_set_physics.argtypes = [P, C.c_double, C.c_double, C.c_int, C.c_double, C.c_int]
+        lib.orc_set_collision.argtypes = [P, C.c_int]
         lib.orc_step.restype = C.c_int
         lib.orc_step.argtypes = [P, dp, C.c_void_p, dp, ip, dp]
         _lib = lib
@@ -220,6 +222,10 @@ class Oracle:
     def set_physics(self, nu, dt, integrator="BE", tau=1e-8, lmax=1000):
         self.integrator = integrator
         self.lib.orc_set_physics(self.h, float(nu), float(dt), INTEGRATORS[integrator], float(tau), int(lmax))
+
+    def set_collision(self, kind):
+        """'maxwellian' (App. B projection) or 'linear' (Eq. linear-Maxwellian: n / |V|)."""
+        self.lib.orc_set_collision(self.h, {"maxwellian": 0, "linear": 1}[kind])
 
     def step(self, f, fbc, fprev=None):
         """One time step in place on a copy; returns (f_next, iters per stage, measures, status)."""

@@ -36,7 +36,11 @@ class VGrid(C.Structure):
 
 
 class Physics(C.Structure):
-    _fields_ = [("nu", C.c_double), ("integrator", C.c_int), ("dt", C.c_double), ("cfl", C.c_double)]
+    _fields_ = [("nu", C.c_double), ("integrator", C.c_int), ("dt", C.c_double), ("cfl", C.c_double),
+                ("collision", C.c_int)]
+
+
+COLLISIONS = {"maxwellian": 0, "linear": 1}
 
 
 class Config(C.Structure):
@@ -72,6 +76,7 @@ def load(path: str = LIB_PATH):
         "bgk_get_dt": [P, C.POINTER(D)],
         "bgk_set_state_maxwellian": [P, V],
         "bgk_set_inflow_maxwellian": [P, V],
+        "bgk_set_inflow": [P, V],
         "bgk_set_f": [P, V, I],
         "bgk_get_f": [P, V, I],
         "bgk_set_f_device": [P, V, I],
@@ -158,13 +163,13 @@ class Solver:
 
     def __init__(self, dim, kx, xyz, cells, n_v, k_v, L, nu, integrator="BE", dt=0.0, cfl=10.0, tau=1e-8,
                  l_max=1000, precision="fp64", block_threads=0, stream=None, eager=False, cache_inverse="auto", fp32_floor=0.0, prefetch=False,
-                 sweep_mode="auto"):
+                 sweep_mode="auto", collision="maxwellian"):
         self.lib = load()
         self._xyz = np.ascontiguousarray(xyz, dtype=np.float64)
         self._cells = np.ascontiguousarray(cells, dtype=np.int32)
         m = Mesh(dim, kx, self._xyz.shape[0], _ptr(self._xyz), self._cells.shape[0], _ptr(self._cells))
         vg = VGrid(float(L), int(n_v), int(k_v))
-        ph = Physics(float(nu), INTEGRATORS[integrator], float(dt), float(cfl))
+        ph = Physics(float(nu), INTEGRATORS[integrator], float(dt), float(cfl), COLLISIONS[collision])
         cf = Config(float(tau), int(l_max), PRECISIONS[precision], int(block_threads),
                     C.c_void_p(stream) if stream else None, int(bool(eager)),
                     {"auto": 0, "on": 1, "off": 2}[cache_inverse], float(fp32_floor), 1 if prefetch else 0,
@@ -226,6 +231,11 @@ class Solver:
     def set_inflow_maxwellian(self, nut):
         nut = np.ascontiguousarray(nut, dtype=np.float64)
         _ck(self.lib.bgk_set_inflow_maxwellian(self.h, _ptr(nut)), "bgk_set_inflow_maxwellian")
+
+    def set_inflow(self, f):
+        """Inflow data f^bc as nodal values [nv, nnode] (FP64)."""
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        _ck(self.lib.bgk_set_inflow(self.h, _ptr(f)), "bgk_set_inflow")
 
     def set_f(self, f):
         f = np.ascontiguousarray(f)

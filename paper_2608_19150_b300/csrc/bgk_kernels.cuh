@@ -484,15 +484,29 @@ __global__ void k_moments_range(VGrid g, const T* __restrict__ f, int nnode, int
 // moments and primitive variables are FP64; the projection runs in the storage type T
 // (FP64 for FP64 states, FP32 for FP32 sweeps, whose source is FP32 anyway).
 // Non-physical moments set the error flag (the stage loop then stops).
+// linear != 0: the simplified Maxwellian N_h = n / |V| at every ordinate (Eq.
+// linear-Maxwellian): cf[0][m] = coef n / (2L)^d, cf[a > 0][m] = 1.
 template <typename T>
 __global__ void k_factors(VGrid g, int nnode, const double* __restrict__ U0, const double* __restrict__ U1,
-                          DevState* ds, double coef, T* __restrict__ cf) {
+                          DevState* ds, double coef, T* __restrict__ cf, int linear) {
   if (ds->status != BGK_OK || ds->done) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nnode) return;
   const int nm = g.dim + 2;
   const double* Un = (((ds->it & 1) == 0) ? U0 : U1) + (size_t)i * nm;
   const double n = Un[0];
+  if (linear) {
+    double vol = 1.0;
+    for (int a = 0; a < g.dim; ++a) vol *= 2.0 * g.L;
+    double val = coef * n / vol;
+    if (!(n > 0.0) || !isfinite(n)) {
+      atomicOr(&ds->err, 1);
+      val = 0.0;
+    }
+    for (int a = 0; a < g.dim; ++a)
+      for (int m = 0; m < g.N; ++m) cf[((size_t)a * g.N + m) * nnode + i] = (T)(a == 0 ? val : 1.0);
+    return;
+  }
   double u[3] = {0, 0, 0}, u2 = 0.0;
 #pragma unroll
   for (int a = 0; a < 3; ++a)
@@ -1273,6 +1287,17 @@ __global__ void k_record_fp32(const DevState* __restrict__ sh, DevState* main, i
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     main->iters32[st] = sh->stage_it;
     main->total_sweeps += sh->stage_it;
+  }
+}
+
+// Inflow data from nodal values: fbc[j][p] = fn[j][bnode[p]] (boundary-face positions p).
+template <typename T>
+__global__ void k_gather_inflow(int nv, int npos, int nnode, const double* __restrict__ fn,
+                                const int32_t* __restrict__ bnode, T* __restrict__ fbc) {
+  const size_t n = (size_t)nv * npos;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t j = i / npos, p = i - j * npos;
+    fbc[i] = (T)fn[j * nnode + bnode[p]];
   }
 }
 

@@ -343,7 +343,7 @@ void moments(bgk_handle* h, int mode) {
 template <typename T>
 int build_src_t(bgk_handle* h, const void* qsrc, double qscale) {
   k_factors<T><<<(h->nnode + 127) / 128, 128, 0, h->stream>>>(h->g, h->nnode, h->U[0], h->U[1], h->ds, h->phys.nu,
-                                                              (T*)h->cf);
+                                                              (T*)h->cf, h->phys.collision == BGK_COLL_LINEAR);
   if (h->fuse_src) {
     h->fused_q = qsrc;
     h->fused_qscale = qscale;
@@ -693,7 +693,8 @@ int bgk_create(const bgk_mesh* mesh, const bgk_vgrid* vg, const bgk_physics* phy
   if (h->cfg.l_max <= 0) h->cfg.l_max = 1000;
   h->precision = h->cfg.precision == BGK_FP32_SWEEP ? BGK_FP32_SWEEP : BGK_FP64;  // BGK_MIXED: FP64 + shadow
   h->tsize = h->precision == BGK_FP64 ? 8 : 4;
-  if (phys->integrator < BGK_BE || phys->integrator > BGK_BDF2 || !(phys->nu >= 0.0)) {
+  if (phys->integrator < BGK_BE || phys->integrator > BGK_BDF2 || !(phys->nu >= 0.0) ||
+      (phys->collision != BGK_COLL_MAXWELLIAN && phys->collision != BGK_COLL_LINEAR)) {
     delete h;
     return BGK_E_INVALID;
   }
@@ -915,6 +916,34 @@ int bgk_set_state_maxwellian(bgk_handle* h, const double* h_nut) { return set_ma
 int bgk_set_inflow_maxwellian(bgk_handle* h, const double* h_nut) {
   int rc = set_maxwellian(h, h_nut, true);
   if (rc == BGK_OK && h && h->shadow) rc = set_maxwellian(h->shadow, h_nut, true);
+  return rc;
+}
+
+static int set_inflow_nodal(bgk_handle* h, const double* h_f) {
+  if (!h || !h_f) return BGK_E_INVALID;
+  const int npos = h->hm.nbface * h->hm.fd;
+  if (npos == 0) return BGK_OK;
+  double* dfn = nullptr;
+  if (dalloc(dfn, sizeof(double) * h->nfv) != BGK_OK) return BGK_E_OOM;
+  int rc = BGK_OK;
+  if (cudaMemcpyAsync(dfn, h_f, sizeof(double) * h->nfv, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+    rc = BGK_E_CUDA;
+  if (rc == BGK_OK) {
+    const int thr = 256, blk = 148 * 4;
+    if (h->precision == BGK_FP64)
+      k_gather_inflow<double><<<blk, thr, 0, h->stream>>>(h->g.nv, npos, h->nnode, dfn, h->bnode, (double*)h->fbc);
+    else
+      k_gather_inflow<float><<<blk, thr, 0, h->stream>>>(h->g.nv, npos, h->nnode, dfn, h->bnode, (float*)h->fbc);
+    if (cudaGetLastError() != cudaSuccess) rc = BGK_E_CUDA;
+  }
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) rc = BGK_E_CUDA;
+  cudaFree(dfn);
+  return rc;
+}
+
+int bgk_set_inflow(bgk_handle* h, const double* h_f) {
+  int rc = set_inflow_nodal(h, h_f);
+  if (rc == BGK_OK && h->shadow) rc = set_inflow_nodal(h->shadow, h_f);
   return rc;
 }
 

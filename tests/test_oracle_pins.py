@@ -405,6 +405,63 @@ def test_l2_stability_free_streaming_zero_inflow():
         prev = cur
 
 
+@pytest.mark.parametrize("integ", ["BE", "BSTABLE2", "DIRK3"])
+def test_linear_maxwellian_constant_state_is_steady(integ):
+    """Eq. linear-Maxwellian: N_h = n / |V| with |V| = (2L)^d.  A state constant in x and v
+    with the same constant as inflow is an exact steady state (transport vanishes and
+    N_h equals the state); a wrong |V| or moment breaks it."""
+    m, o = small_square(4, n1d=8)
+    c = 0.37
+    f = np.full((o.nv, o.nnode), c)
+    o.set_collision("linear")
+    o.set_physics(1000.0, 0.05, integ, tau=1e-13, lmax=200)
+    f1, it, meas, st = o.step(f, f.copy())
+    assert st == 0
+    np.testing.assert_allclose(f1, c, rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("integ", ["BE", "BSTABLE2"])
+def test_l2_stability_linear_maxwellian_zero_inflow(integ):
+    """Prop. (Linear Stability), case (ii): with the simplified Maxwellian, nu = 1000 and
+    zero inflow, B-stable integrators do not let ||f||_{L2(X x V)} grow."""
+    m, o = small_square(4, n1d=8)
+    w = synth.workload_p1_square(n_side=4, n_v=8)
+    f = o.maxwellian(w.init)
+    _, wt, _, _ = o.velocity()
+    Ms = [o.cell(c)["M"] for c in range(o.ncell)]
+
+    def l2(f):
+        return sum(wt[j] * sum(f[j, c * 3:(c + 1) * 3] @ Ms[c] @ f[j, c * 3:(c + 1) * 3] for c in range(o.ncell))
+                   for j in range(o.nv))
+    o.set_collision("linear")
+    o.set_physics(1000.0, 0.002, integ, tau=1e-13, lmax=1000)
+    prev = l2(f)
+    for _ in range(3):
+        f, it, meas, st = o.step(f, np.zeros_like(f))
+        assert st == 0
+        cur = l2(f)
+        assert cur <= prev * (1 + 1e-12)
+        prev = cur
+
+
+def test_linear_maxwellian_collision_conserves_mass_only():
+    """The simplified collision term sum_j w_j (N_h - f_j) has zero density moment (the
+    quadrature integrates 1 exactly: sum_j w_j = |V|) but not zero momentum or energy."""
+    m, o = small_square(3, n1d=8)
+    w = synth.workload_p1_square(n_side=3, n_v=8)
+    nut = w.init.copy()
+    nut[:, 1] = 0.3
+    f = o.maxwellian(nut)
+    v, wt, _, _ = o.velocity()
+    U = o.moments(f)
+    N = U[:, 0] / (2 * o.L) ** 2
+    coll = N[None, :] - f
+    E = np.concatenate([np.ones((o.nv, 1)), v, 0.5 * (v * v).sum(1, keepdims=True)], axis=1)
+    dU = E.T @ (wt[:, None] * coll)
+    assert np.abs(dU[0]).max() < 1e-14 * np.abs(U[:, 0]).max()
+    assert np.abs(dU[1]).max() > 1e-3
+
+
 def test_discrete_conservation_law_backward_euler():
     """Eq. (discrete-cons): after a converged BE step the change of int U equals minus dt
     times the net boundary flux sum_j w_j e_j (v_j.n) f_hat over dX (interior faces cancel)."""
