@@ -40,6 +40,10 @@ enum {
 
 enum { BGK_BE = 0, BGK_DIRK2 = 1, BGK_DIRK3 = 2, BGK_BSTABLE2 = 3, BGK_BDF2 = 4 };
 enum { BGK_COLL_MAXWELLIAN = 0, BGK_COLL_LINEAR = 1 };
+/* Boundary conditions of Sec. 4.2 on the sides of a box domain.  INFLOW: given data g
+ * (bgk_set_inflow_maxwellian / bgk_set_inflow).  BOUNCE_BACK: f^bc(x, v) = f(x, -v).
+ * REFLECT: f^bc(x, v) = f(x, R_n v), R_n v = v - 2 (v.n) n (specular). */
+enum { BGK_BC_INFLOW = 0, BGK_BC_BOUNCE_BACK = 1, BGK_BC_REFLECT = 2 };
 /* BGK_FP64: FP64 storage and sweeps.  BGK_FP32_SWEEP: FP32 storage and sweeps, moments
  * and Maxwellian parameters to FP64 accuracy; it stalls at FP32 rounding (~1e-7 in the
  * moment change).  BGK_MIXED: FP64 state; each stage first runs FP32 sweeps until the
@@ -76,6 +80,16 @@ typedef struct {
                          (App. B); BGK_COLL_LINEAR (1): the simplified, linear Maxwellian
                          N_h = n / |V| at every ordinate, |V| = (2L)^d (Eq. linear-Maxwellian,
                          Prop. Linear Stability); it conserves mass only */
+  int walls[6];       /* boundary condition per side of the box, BGK_BC_*, in the order
+                         x-, x+, y-, y+, z-, z+ (the first 2d are read).  A boundary face
+                         belongs to side (a, +/-) when its unit outward normal is +/-e_a
+                         (other components below 1e-10 of its length); faces with any
+                         other normal stay INFLOW.  BOUNCE_BACK and REFLECT couple ordinate
+                         j to its mirror (-v_j, or v_j with component a negated; both are
+                         grid points of the symmetric velocity grid) and read the mirror's
+                         trace from the previous Picard iterate f^l (lagged, Sec. 4.2), so
+                         the wall data are refreshed before every sweep.  All zero: inflow
+                         everywhere. */
 } bgk_physics;
 
 /* Solver configuration. */
@@ -194,7 +208,9 @@ int bgk_sweep(bgk_handle* h, double nu_s, double q_scale);
  *     from the moments d_U (device, [node][d+2], the summed moments of the current
  *     iterate) and the handle's stage source, as bgk_sweep (nu_s, q_scale <= 0: the step's
  *     first-stage values).  Ordinates outside the range are not touched.  Returns
- *     BGK_E_NONPHYSICAL if d_U has n <= 0 or theta <= 0 somewhere.
+ *     BGK_E_NONPHYSICAL if d_U has n <= 0 or theta <= 0 somewhere, BGK_E_INVALID if the
+ *     problem has bounce-back or reflecting walls (their mirror ordinates may lie in
+ *     another part; the shards exchange no boundary data).
  *   bgk_moments_range_device: the partial moments of the current f over the ordinates
  *     [j_begin, j_end) into d_U (device, [node][d+2]); j_begin and j_end must be multiples
  *     of N^(d-1) (whole values of the outermost velocity index), else BGK_E_INVALID.

@@ -82,6 +82,10 @@ typedef struct {
   double nu, dt, tau;
   int integrator, lmax;
   int collision; /* 0: projected Maxwellian; 1: simplified Maxwellian N_h = n / |V| */
+  /* wall boundary conditions (Sec. 4.2); NULL: inflow everywhere */
+  int *wmirror;  /* [cell][face]: -1 inflow face, else the table row of mirror[] to use */
+  int *mirror;   /* [1 + dim][nv]: row 0 = index of -v_j, row 1 + a = index of v_j with
+                    component a negated (R_n v_j for n = +/-e_a) */
 } orc_t;
 
 /* ------------------------------------------------------------------ velocity grid */
@@ -642,7 +646,7 @@ static void dense_solve(int n, double *A, double *b) {
  * fnew = f^{l+1}; Mn = nodal Maxwellian; q = stage source; fbc = boundary values,
  * all [j][cell][node]. */
 static void sweep_ordinate(const orc_t *o, int j, const double *fold, const double *Mn, const double *q,
-                           const double *fbc, double nu, double nu_s, double *fnew) {
+                           const double *fbc, double nu, double nu_s, double *fnew, const double *fall) {
   int d = o->dim, nd = o->ndof, nf = o->nface;
   {
     const double *v = o->v + (size_t)j * d;
@@ -680,7 +684,11 @@ static void sweep_ordinate(const orc_t *o, int j, const double *fold, const doub
           double y[MAXDOF] = {0};
           for (int k = 0; k < o->fdof; ++k) {
             int bb = o->face_nodes[f * o->fdof + k]; /* nodes off the face have zero face mass */
-            if (nb < 0) y[bb] = fbc[base + (size_t)c * nd + bb];
+            if (nb < 0 && o->wmirror && o->wmirror[cf] >= 0) {
+              /* wall: the mirror ordinate's interior trace at the same node, from f^l */
+              int jm = o->mirror[(size_t)o->wmirror[cf] * o->nv + j];
+              y[bb] = fall[(size_t)jm * o->nnode + (size_t)c * nd + bb];
+            } else if (nb < 0) y[bb] = fbc[base + (size_t)c * nd + bb];
             else {
               size_t iu = base + (size_t)nb * nd + o->nbr_node[cf * MAXDOF + bb];
               y[bb] = lag[cf] ? fold[iu] : fnew[iu];
@@ -701,7 +709,7 @@ static void sweep_range(const orc_t *o, const double *fold, const double *Mn, co
   size_t nn = (size_t)o->nnode;
   for (int j = j0; j < j1; ++j)
     sweep_ordinate(o, j, fold + (size_t)j * nn, Mn + (size_t)j * nn, q + (size_t)j * nn, fbc + (size_t)j * nn, nu,
-                   nu_s, fnew + (size_t)j * nn);
+                   nu_s, fnew + (size_t)j * nn, fold);
 }
 
 static void sweep(const orc_t *o, const double *fold, const double *Mn, const double *q, const double *fbc,
@@ -717,6 +725,7 @@ void orc_destroy(orc_t *o) {
   free(o->vol); free(o->M); free(o->G); free(o->Fm); free(o->ncan); free(o->orient); free(o->unit_n);
   free(o->farea); free(o->nbr); free(o->nbr_face); free(o->nbr_node); free(o->face_nodes);
   free(o->gen); free(o->order); free(o->lagged); free(o->ngen);
+  free(o->wmirror); free(o->mirror);
   free(o);
 }
 
@@ -893,13 +902,15 @@ void orc_maxwellian_rows(const orc_t *o, const double *nut, const int *js, int n
 }
 
 /* One sweep for the listed ordinates only; all arrays hold just those rows
- * ([nj][nnode]); the graphs must have been built. */
+ * ([nj][nnode]); the graphs must have been built.  Inflow boundaries only (a wall needs
+ * the mirror ordinates' rows): with walls set it does nothing. */
 void orc_sweep_rows(const orc_t *o, const int *js, int nj, const double *fold, const double *Mn, const double *q,
                     const double *fbc, double nu, double nu_s, double *fnew) {
   size_t nn = (size_t)o->nnode;
+  if (o->wmirror) return;
   for (int r = 0; r < nj; ++r)
     sweep_ordinate(o, js[r], fold + (size_t)r * nn, Mn + (size_t)r * nn, q + (size_t)r * nn, fbc + (size_t)r * nn, nu,
-                   nu_s, fnew + (size_t)r * nn);
+                   nu_s, fnew + (size_t)r * nn, NULL);
 }
 
 /* explicit time-step bound (Sec. 5): dt_e = (1/d) (1/(2 kx + 1)) h_min / max_j |v_j|,
@@ -1015,6 +1026,62 @@ void orc_set_physics(orc_t *o, double nu, double dt, int integrator, double tau,
 /* Collision model: 0 = the projected Maxwellian (App. B), 1 = the simplified Maxwellian of
  * Eq. linear-Maxwellian (Prop. Linear Stability). */
 void orc_set_collision(orc_t *o, int kind) { o->collision = kind; }
+
+/* Boundary conditions of Sec. 4.2 per side of a box: kinds[2a + s] for the side whose unit
+ * outward normal is -e_a (s = 0) or +e_a (s = 1); 0 inflow, 1 bounce-back
+ * f^bc(x, v) = f(x, -v), 2 reflection f^bc(x, v) = f(x, R_n v), R_n v = v - 2 (v.n) n.
+ * A face is on a side when its unit normal's other components are below 1e-10.  The
+ * mirror ordinate of each transform is found by searching the grid for the transformed
+ * velocity (the paper assumes it is a grid point; ORC_E_INVALID if it is not, within
+ * 1e-12 L).  Walls read the mirror's trace from the previous Picard iterate (lagged). */
+int orc_set_walls(orc_t *o, const int *kinds) {
+  int d = o->dim, nf = o->nface, any = 0;
+  free(o->wmirror); free(o->mirror);
+  o->wmirror = NULL; o->mirror = NULL;
+  for (int k = 0; k < 2 * d; ++k) {
+    if (kinds[k] < 0 || kinds[k] > 2) return ORC_E_INVALID;
+    if (kinds[k]) any = 1;
+  }
+  if (!any) return ORC_OK;
+  int *mir = malloc(sizeof(int) * (size_t)(1 + d) * o->nv);
+  for (int t = 0; t <= d; ++t)
+    for (int j = 0; j < o->nv; ++j) {
+      double tv[3];
+      for (int al = 0; al < d; ++al) {
+        double vj = o->v[(size_t)j * d + al];
+        tv[al] = (t == 0 || t == 1 + al) ? -vj : vj;
+      }
+      int found = -1;
+      for (int jj = 0; jj < o->nv && found < 0; ++jj) {
+        double dmax = 0.0;
+        for (int al = 0; al < d; ++al) {
+          double e = fabs(o->v[(size_t)jj * d + al] - tv[al]);
+          if (e > dmax) dmax = e;
+        }
+        if (dmax <= 1e-12 * o->L) found = jj;
+      }
+      if (found < 0) { free(mir); return ORC_E_INVALID; }
+      mir[(size_t)t * o->nv + j] = found;
+    }
+  int *wm = malloc(sizeof(int) * (size_t)o->ncell * nf);
+  for (int cf = 0; cf < o->ncell * nf; ++cf) {
+    wm[cf] = -1;
+    if (o->nbr[cf] >= 0) continue;
+    const double *un = o->unit_n + (size_t)cf * d;
+    for (int al = 0; al < d; ++al) {
+      int aligned = 1;
+      for (int be = 0; be < d; ++be)
+        if (be != al && !(fabs(un[be]) <= 1e-10)) aligned = 0;
+      if (!aligned) continue;
+      int kind = kinds[2 * al + (un[al] > 0.0 ? 1 : 0)];
+      if (kind == 1) wm[cf] = 0;
+      else if (kind == 2) wm[cf] = 1 + al;
+    }
+  }
+  o->wmirror = wm;
+  o->mirror = mir;
+  return ORC_OK;
+}
 
 /* Advance one time step (Sec. 3.5 + Sec. 4).  f: in f^k, out f^{k+1}.  fprev: f^{k-1}
  * (BDF2 only; NULL -> backward Euler start).  fbc: boundary values [j][cell][node].

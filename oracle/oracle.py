@@ -10,7 +10,7 @@ and the readings taken where the paper is silent).  This wrapper only marshals a
 Parity status per function (pins live in ``tests/test_oracle_pins.py``):
   velocity grid, element matrices, projection, moments, sweep graph / generations,
   one sweep, one time step (BE, DIRK2, DIRK3, B-stable DIRK2, BDF2), the simplified
-  Maxwellian collision model: pinned.
+  Maxwellian collision model, bounce-back and reflecting walls: pinned.
 """
 from __future__ import annotations
 
@@ -74,6 +74,8 @@ def _load():
         lib.orc_conv_measure.argtypes = [P, dp, dp]
         lib.orc_set_physics.argtypes = [P, C.c_double, C.c_double, C.c_int, C.c_double, C.c_int]
         lib.orc_set_collision.argtypes = [P, C.c_int]
+        lib.orc_set_walls.restype = C.c_int
+        lib.orc_set_walls.argtypes = [P, ip]
         lib.orc_step.restype = C.c_int
         lib.orc_step.argtypes = [P, dp, C.c_void_p, dp, ip, dp]
         _lib = lib
@@ -226,6 +228,16 @@ class Oracle:
     def set_collision(self, kind):
         """'maxwellian' (App. B projection) or 'linear' (Eq. linear-Maxwellian: n / |V|)."""
         self.lib.orc_set_collision(self.h, {"maxwellian": 0, "linear": 1}[kind])
+
+    def set_walls(self, walls):
+        """Sec. 4.2 boundary conditions per box side: {"x-"|"x+"|"y-"|"y+"|"z-"|"z+":
+        "inflow"|"bounce_back"|"reflect"}; sides not named stay inflow."""
+        sides = ("x-", "x+", "y-", "y+", "z-", "z+")
+        kinds = {"inflow": 0, "bounce_back": 1, "reflect": 2}
+        k = np.array([kinds[walls.get(sd, "inflow")] for sd in sides], dtype=np.int32)
+        st = self.lib.orc_set_walls(self.h, k)
+        if st != 0:
+            raise ValueError("orc_set_walls: status %d" % st)
 
     def step(self, f, fbc, fprev=None):
         """One time step in place on a copy; returns (f_next, iters per stage, measures, status)."""

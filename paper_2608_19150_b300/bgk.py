@@ -37,10 +37,12 @@ class VGrid(C.Structure):
 
 class Physics(C.Structure):
     _fields_ = [("nu", C.c_double), ("integrator", C.c_int), ("dt", C.c_double), ("cfl", C.c_double),
-                ("collision", C.c_int)]
+                ("collision", C.c_int), ("walls", C.c_int * 6)]
 
 
 COLLISIONS = {"maxwellian": 0, "linear": 1}
+WALLS = {"inflow": 0, "bounce_back": 1, "reflect": 2}
+SIDES = ("x-", "x+", "y-", "y+", "z-", "z+")
 
 
 class Config(C.Structure):
@@ -163,13 +165,16 @@ class Solver:
 
     def __init__(self, dim, kx, xyz, cells, n_v, k_v, L, nu, integrator="BE", dt=0.0, cfl=10.0, tau=1e-8,
                  l_max=1000, precision="fp64", block_threads=0, stream=None, eager=False, cache_inverse="auto", fp32_floor=0.0, prefetch=False,
-                 sweep_mode="auto", collision="maxwellian"):
+                 sweep_mode="auto", collision="maxwellian", walls=None):
         self.lib = load()
         self._xyz = np.ascontiguousarray(xyz, dtype=np.float64)
         self._cells = np.ascontiguousarray(cells, dtype=np.int32)
         m = Mesh(dim, kx, self._xyz.shape[0], _ptr(self._xyz), self._cells.shape[0], _ptr(self._cells))
         vg = VGrid(float(L), int(n_v), int(k_v))
-        ph = Physics(float(nu), INTEGRATORS[integrator], float(dt), float(cfl), COLLISIONS[collision])
+        wl = (C.c_int * 6)(*[WALLS[(walls or {}).get(side, "inflow")] for side in SIDES])
+        if walls and set(walls) - set(SIDES):
+            raise KeyError("unknown side in walls: %s" % sorted(set(walls) - set(SIDES)))
+        ph = Physics(float(nu), INTEGRATORS[integrator], float(dt), float(cfl), COLLISIONS[collision], wl)
         cf = Config(float(tau), int(l_max), PRECISIONS[precision], int(block_threads),
                     C.c_void_p(stream) if stream else None, int(bool(eager)),
                     {"auto": 0, "on": 1, "off": 2}[cache_inverse], float(fp32_floor), 1 if prefetch else 0,

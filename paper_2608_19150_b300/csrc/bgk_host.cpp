@@ -145,6 +145,22 @@ int build_host_mesh(const bgk_mesh* m, HostMesh& hm) {
       if (hm.nbr[(size_t)c * 4 + f] == INT32_MIN) hm.nbr[(size_t)c * 4 + f] = -(++nb);
   hm.nbface = nb;
   hm.bnode.assign((size_t)nb * hm.fd, 0);
+  hm.bside.assign((size_t)nb, -1);
+  for (int c = 0; c < hm.ncell; ++c)
+    for (int f = 0; f < hm.nf; ++f) {
+      const int n2 = hm.nbr[(size_t)c * 4 + f];
+      if (n2 >= 0) continue;
+      const double* N = hm.geo.data() + (size_t)c * hm.geo_stride + f * d;
+      double len = 0.0;
+      for (int al = 0; al < d; ++al) len += N[al] * N[al];
+      len = std::sqrt(len);
+      for (int al = 0; al < d; ++al) {
+        bool aligned = true;
+        for (int be = 0; be < d; ++be)
+          if (be != al && !(std::fabs(N[be]) <= 1e-10 * len)) aligned = false;
+        if (aligned) hm.bside[(size_t)(-n2 - 1)] = (int8_t)(2 * al + (N[al] > 0.0 ? 1 : 0));
+      }
+    }
   for (int c = 0; c < hm.ncell; ++c) {
     const int* cv = CV + (size_t)c * nv;
     uint64_t pm = 0;

@@ -41,6 +41,8 @@ struct HostMesh {
   std::vector<uint64_t> perm;     // [cell]: 16 bits per face, 4 bits per face-local node:
                                   //   the neighbour's local node matching face node k
   std::vector<int32_t> bnode;     // [bface][fd]: node index (cell*ndof+local) of face node k
+  std::vector<int8_t> bside;      // [bface]: side 2a + (n_a > 0) of the box when the unit
+                                  //   outward normal is +/-e_a, else -1
   double min_vol = 0.0;
 };
 

@@ -1290,6 +1290,32 @@ __global__ void k_record_fp32(const DevState* __restrict__ sh, DevState* main, i
   }
 }
 
+// Wall boundary data of Sec. 4.2, refreshed before every sweep from the current iterate
+// f^l: at boundary-face position p of a wall face, fbc[j][p] = f[j'][bnode[p]] with j' the
+// mirror ordinate (wall code 1: -v_j, every velocity index i -> N-1-i; code 2+a: R_n v_j
+// for the normal +/-e_a, index a mirrored).  Positions of inflow faces (code 0) keep
+// their given data.  The 1D grid is symmetric about 0, so the mirrored index holds the
+// mirrored velocity.
+template <typename T>
+__global__ void k_wall_bc(VGrid g, int npos, int fd, int nnode, const T* __restrict__ f,
+                          const int32_t* __restrict__ bnode, const int8_t* __restrict__ wall,
+                          T* __restrict__ fbc) {
+  const size_t n = (size_t)g.nv * npos;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(i / npos), p = (int)(i - (size_t)j * npos);
+    const int w = wall[p / fd];
+    if (w == 0) continue;
+    int jm = 0, stride = 1, jj = j;  // velocity component d-1 varies fastest in j
+    for (int a = g.dim - 1; a >= 0; --a) {
+      const int ia = jj % g.N;
+      jj /= g.N;
+      jm += ((w == 1 || w == 2 + a) ? g.N - 1 - ia : ia) * stride;
+      stride *= g.N;
+    }
+    fbc[i] = f[(size_t)jm * nnode + bnode[p]];
+  }
+}
+
 // Inflow data from nodal values: fbc[j][p] = fn[j][bnode[p]] (boundary-face positions p).
 template <typename T>
 __global__ void k_gather_inflow(int nv, int npos, int nnode, const double* __restrict__ fn,

@@ -46,6 +46,8 @@ struct bgk_handle {
   int32_t* nbr_face = nullptr;
   uint64_t* perm = nullptr;
   int32_t* bnode = nullptr;
+  int8_t* wall = nullptr;    // [bface] wall code: 0 inflow, 1 bounce-back, 2 + a reflection across e_a
+  bool has_walls = false;
   uint32_t* glist = nullptr;
   int32_t* lvl = nullptr;
   int32_t* ngen = nullptr;
@@ -342,6 +344,12 @@ void moments(bgk_handle* h, int mode) {
 // (fused sweeps: the factors only; the sweep forms src from them, qsrc and qscale)
 template <typename T>
 int build_src_t(bgk_handle* h, const void* qsrc, double qscale) {
+  if (h->has_walls) {
+    const int npos = h->hm.nbface * h->hm.fd;
+    const int blocks = std::min<size_t>(148 * 8, ((size_t)h->g.nv * npos + 255) / 256);
+    k_wall_bc<T><<<blocks, 256, 0, h->stream>>>(h->g, npos, h->hm.fd, h->nnode, (const T*)h->f, h->bnode, h->wall,
+                                                (T*)h->fbc);
+  }
   k_factors<T><<<(h->nnode + 127) / 128, 128, 0, h->stream>>>(h->g, h->nnode, h->U[0], h->U[1], h->ds, h->phys.nu,
                                                               (T*)h->cf, h->phys.collision == BGK_COLL_LINEAR);
   if (h->fuse_src) {
@@ -641,7 +649,7 @@ void release(bgk_handle* h) {
   h->shadow = nullptr;
   if (h->exec_main) cudaGraphExecDestroy(h->exec_main);
   if (h->exec_start) cudaGraphExecDestroy(h->exec_start);
-  void* ptrs[] = {h->gX, h->gY, h->Uhist, h->have_hist, h->geof,
+  void* ptrs[] = {h->gX, h->gY, h->Uhist, h->have_hist, h->geof, h->wall,
                   h->geo, h->nbr, h->nbr_face, h->perm, h->bnode, h->glist, h->lvl, h->ngen, h->nproc, h->Ainv, h->f, h->fk,
                   h->fprev, h->src, h->fbc, h->q, h->F[0], h->F[1], h->F[2], h->U[0], h->U[1], h->partial, h->cf,
                   h->ds};
@@ -698,6 +706,11 @@ int bgk_create(const bgk_mesh* mesh, const bgk_vgrid* vg, const bgk_physics* phy
     delete h;
     return BGK_E_INVALID;
   }
+  for (int k = 0; k < 2 * h->hm.dim; ++k)
+    if (phys->walls[k] != BGK_BC_INFLOW && phys->walls[k] != BGK_BC_BOUNCE_BACK && phys->walls[k] != BGK_BC_REFLECT) {
+      delete h;
+      return BGK_E_INVALID;
+    }
   // time step: given, or cfl * dt_e with dt_e = (1/d)(1/(2k+1)) h_min / max_j |v_j| (Sec. 5)
   if (phys->dt > 0.0) {
     h->dt = phys->dt;
@@ -786,6 +799,25 @@ int bgk_create(const bgk_mesh* mesh, const bgk_vgrid* vg, const bgk_physics* phy
   CK(cudaMemcpyAsync(h->perm, hm.perm.data(), sizeof(uint64_t) * n, cudaMemcpyHostToDevice, s));
   if (!hm.bnode.empty())
     CK(cudaMemcpyAsync(h->bnode, hm.bnode.data(), sizeof(int32_t) * hm.bnode.size(), cudaMemcpyHostToDevice, s));
+  {
+    // wall code per boundary face from the side it lies on (Sec. 4.2 boundary conditions)
+    std::vector<int8_t> code(hm.nbface, 0);
+    for (int b = 0; b < hm.nbface; ++b) {
+      const int side = hm.bside[b];
+      if (side < 0) continue;
+      const int kind = phys->walls[side];
+      code[b] = kind == BGK_BC_BOUNCE_BACK ? 1 : kind == BGK_BC_REFLECT ? (int8_t)(2 + side / 2) : 0;
+      if (code[b]) h->has_walls = true;
+    }
+    if (h->has_walls) {
+      if (dalloc(h->wall, hm.nbface) != BGK_OK) {
+        release(h);
+        return BGK_E_OOM;
+      }
+      CK(cudaMemcpyAsync(h->wall, code.data(), hm.nbface, cudaMemcpyHostToDevice, s));
+      CK(cudaStreamSynchronize(s));
+    }
+  }
   CK(cudaMemsetAsync(h->ds, 0, sizeof(DevState), s));
   CK(cudaMemsetAsync(h->f, 0, fb, s));
   CK(cudaMemsetAsync(h->fk, 0, fb, s));
@@ -1236,7 +1268,7 @@ int bgk_sweep(bgk_handle* h, double nu_s, double q_scale) {
 }
 
 int bgk_sweep_range(bgk_handle* h, int j_begin, int j_end, const double* d_U, double nu_s, double q_scale) {
-  if (!h || !d_U || j_begin < 0 || j_end > h->g.nv || j_begin >= j_end) return BGK_E_INVALID;
+  if (!h || !d_U || j_begin < 0 || j_end > h->g.nv || j_begin >= j_end || h->has_walls) return BGK_E_INVALID;
   if (nu_s <= 0.0) nu_s = h->nus_main;
   if (q_scale <= 0.0) q_scale = h->qscale_main;
   k_reset_state<<<1, 1, 0, h->stream>>>(h->ds);

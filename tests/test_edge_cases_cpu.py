@@ -11,13 +11,13 @@ from oracle.oracle import Oracle
 from paper_2608_19150_b300 import bgk, synth
 
 
-def _create(dim, kx, xyz, cells, n1d=8, kv=3, L=6.0, integ="BE"):
+def _create(dim, kx, xyz, cells, n1d=8, kv=3, L=6.0, integ="BE", collision=0, walls=(0,) * 6):
     lib = bgk.load()
     xyz = np.ascontiguousarray(xyz, dtype=np.float64)
     cells = np.ascontiguousarray(cells, dtype=np.int32)
     m = bgk.Mesh(dim, kx, xyz.shape[0], bgk._ptr(xyz), cells.shape[0], bgk._ptr(cells))
     vg = bgk.VGrid(L, n1d, kv)
-    ph = bgk.Physics(1.0, bgk.INTEGRATORS[integ], 0.0, 10.0)
+    ph = bgk.Physics(1.0, bgk.INTEGRATORS[integ], 0.0, 10.0, collision, (C.c_int * 6)(*walls))
     h = C.c_void_p()
     rc = lib.bgk_create(C.byref(m), C.byref(vg), C.byref(ph), None, C.byref(h))
     return rc
@@ -48,6 +48,11 @@ def test_invalid_problems_are_rejected_before_any_device_work():
     xyz = np.array([[0, 0], [1, 0], [1, 1], [0, 1]], dtype=np.float64)
     cells = np.array([[0, 1, 2], [0, 2, 3], [0, 1, 3]], dtype=np.int32)  # three triangles overlap
     assert _create(2, 1, xyz, cells) == bgk.BGK_E_INVALID
+    # unknown collision model or boundary kind (only the first 2d wall entries are read)
+    assert _create(2, 1, m.xyz, m.cells, collision=2) == bgk.BGK_E_INVALID
+    assert _create(2, 1, m.xyz, m.cells, walls=(0, 0, 3, 0, 0, 0)) == bgk.BGK_E_INVALID
+    assert _create(2, 1, m.xyz, m.cells, walls=(0, -1, 0, 0, 0, 0)) == bgk.BGK_E_INVALID
+    assert _create(3, 1, c.xyz, c.cells, walls=(0, 0, 0, 0, 0, 9)) == bgk.BGK_E_INVALID
     # and the oracle refuses the same bad inputs
     with pytest.raises(ValueError):
         Oracle(2, 1, m.xyz, bad, 8, 3, 6.0)
