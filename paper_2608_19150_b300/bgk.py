@@ -160,6 +160,14 @@ def moments_measure_noalloc(L, n_points, k_v, dim, n_nodes, f_ptr, dtype, U_old_
         "bgk_moments_measure_noalloc")
 
 
+def _wall_kinds(walls):
+    """{side: kind} (sides "x-".."z+", kinds of WALLS; unnamed sides inflow) -> int[6]."""
+    walls = walls or {}
+    if set(walls) - set(SIDES):
+        raise KeyError("unknown side in walls: %s" % sorted(set(walls) - set(SIDES)))
+    return (C.c_int * 6)(*[WALLS[walls.get(side, "inflow")] for side in SIDES])
+
+
 class Solver:
     """Handle of one problem on the current CUDA device (thin wrapper of bgk_create)."""
 
@@ -171,10 +179,8 @@ class Solver:
         self._cells = np.ascontiguousarray(cells, dtype=np.int32)
         m = Mesh(dim, kx, self._xyz.shape[0], _ptr(self._xyz), self._cells.shape[0], _ptr(self._cells))
         vg = VGrid(float(L), int(n_v), int(k_v))
-        wl = (C.c_int * 6)(*[WALLS[(walls or {}).get(side, "inflow")] for side in SIDES])
-        if walls and set(walls) - set(SIDES):
-            raise KeyError("unknown side in walls: %s" % sorted(set(walls) - set(SIDES)))
-        ph = Physics(float(nu), INTEGRATORS[integrator], float(dt), float(cfl), COLLISIONS[collision], wl)
+        ph = Physics(float(nu), INTEGRATORS[integrator], float(dt), float(cfl), COLLISIONS[collision],
+                     _wall_kinds(walls))
         cf = Config(float(tau), int(l_max), PRECISIONS[precision], int(block_threads),
                     C.c_void_p(stream) if stream else None, int(bool(eager)),
                     {"auto": 0, "on": 1, "off": 2}[cache_inverse], float(fp32_floor), 1 if prefetch else 0,
@@ -355,7 +361,8 @@ class Solver:
 class Batch:
     """Many independent backward-Euler problems advanced together (bgk_batch_*)."""
 
-    def __init__(self, workloads, precision="fp64", tau=1e-8, l_max=1000, cache_inverse="auto", dt=None, stream=None):
+    def __init__(self, workloads, precision="fp64", tau=1e-8, l_max=1000, cache_inverse="auto", dt=None, stream=None,
+                 walls=None):
         self.lib = load()
         n = len(workloads)
         self._keep = []
@@ -368,7 +375,8 @@ class Batch:
             self._keep += [xyz, cells]
             meshes[i] = Mesh(w.mesh.dim, w.kx, xyz.shape[0], _ptr(xyz), cells.shape[0], _ptr(cells))
             vgrids[i] = VGrid(float(w.L), int(w.n_v), int(w.k_v))
-            phys[i] = Physics(float(w.nu), INTEGRATORS["BE"], float(dt[i]) if dt else 0.0, float(w.cfl))
+            phys[i] = Physics(float(w.nu), INTEGRATORS["BE"], float(dt[i]) if dt else 0.0, float(w.cfl), 0,
+                              _wall_kinds(walls))
         cf = Config(float(tau), int(l_max), PRECISIONS[precision], 0, C.c_void_p(stream) if stream else None, 0,
                     {"auto": 0, "on": 1, "off": 2}[cache_inverse], 0.0, 0, 0)
         self.mixed = precision == "mixed"

@@ -48,6 +48,26 @@ def test_batch_matches_single_instances(precision, cache):
         assert rel_err(b.instances[i].get_f(), s.get_f()) < tol
 
 
+def test_batch_with_walls_matches_single_instances():
+    """Walls (Sec. 4.2) inside the batched persistent sweep: each instance refreshes its
+    own wall data before the shared sweep launch."""
+    ws = instances()
+    walls = {"x+": "bounce_back", "y-": "reflect", "y+": "reflect"}
+    b = bgk.Batch(ws, walls=walls)
+    for s, w in zip(b.instances, ws):
+        s.set_state_maxwellian(w.init)
+        s.set_inflow_maxwellian(w.inflow)
+    its, sts = b.step(2)
+    assert np.all(sts == 0)
+    for i, w in enumerate(ws):
+        s = bgk.Solver.from_workload(w, walls=walls)
+        s.set_state_maxwellian(w.init)
+        s.set_inflow_maxwellian(w.inflow)
+        st = s.step(2)
+        assert st.iterations[0] == its[i]
+        assert rel_err(b.instances[i].get_f(), s.get_f()) < 1e-13
+
+
 def test_batch_against_oracle_and_autotune_keeps_results():
     ws = instances()
     b = bgk.Batch(ws)
