@@ -26,6 +26,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "sweep DOF-updates/s; time per implicit step to 1e-8 residual vs plain FP64"
 UNIT = "DOF-updates/s"
+WALL_NOTE = ("; wall faces read as inflow data in the sampled sweep (the mirror rows are not in the sample; "
+             "a wall read costs the same per face)")
+# Sec. 4.2 wall sets for the single-problem workloads (sides without an entry: inflow)
+WALL_SETS = {"none": None,
+             "channel": {"y-": "reflect", "y+": "reflect"},
+             "closed_reflect": {sd: "reflect" for sd in ("x-", "x+", "y-", "y+", "z-", "z+")},
+             "closed_bounce_back": {sd: "bounce_back" for sd in ("x-", "x+", "y-", "y+", "z-", "z+")}}
 FP64_PEAK_TFLOPS = 1.25   # nominal B300 FP64 rate (no tensor path); see the design notes
 
 
@@ -43,6 +50,8 @@ def parse():
     p.add_argument("--workload", default="shock_tube", choices=["shock_tube", "bump3d", "strip", "batched", "learned"])
     p.add_argument("--sweep-mode", default="auto", choices=["auto", "tgs", "ts"],
                    help="sweep algorithm: generation sweep (tgs), one thread per ordinate (ts), or automatic")
+    p.add_argument("--walls", default="none", choices=sorted(WALL_SETS),
+                   help="Sec. 4.2 walls: channel = reflecting walls at y = 0, 1 (single-problem workloads)")
     p.add_argument("--train-runs", type=int, default=200)
     p.add_argument("--eval-runs", type=int, default=4)
     p.add_argument("--instances", type=int, default=64)
@@ -95,6 +104,8 @@ def config(w, args, extra=None):
         name = ("2D-2V shock tube, %dx%d squares (%d P2 triangles), %dx%d velocities on [-8,8]^2, DIRK3, "
                 "Kn 1e-3, CFL 10, tau 1e-8" % (args.n_side, args.n_side, w.mesh.n_cells, args.n_v, args.n_v))
         integ = "DIRK3"
+    if getattr(args, "walls", "none") != "none":
+        name += ", walls: " + ", ".join("%s %s" % kv for kv in sorted(WALL_SETS[args.walls].items()))
     c = {"workload": name,
          "n_cells": w.mesh.n_cells, "dof_per_sweep": dof,
          "precision": {"fp64": "FP64 sweeps", "fp32": "FP32 sweeps, FP64-accurate moments",
@@ -286,27 +297,28 @@ def run_reference(args):
             "config": config(w, args, {"sample": "each step: one oracle sweep over %d of %d ordinates of the "
                                                  "full mesh" % (n_ord, o.nv), "precision": "FP64 CPU oracle"}),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "%d ordinates x %d cells x 6 nodes per step" % (n_ord, o.ncell)},
+                             "sample": "%d ordinates x %d cells x 6 nodes per step%s" % (n_ord, o.ncell, WALL_NOTE
+                                                                                       if args.walls != "none" else "")},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def launches_per_step(st, guess=False, main_fp32=False):
+def launches_per_step(st, guess=False, main_fp32=False, walls=False):
     """Kernels one step launches (graph nodes of kernel type), from its statistics.  FP32
     sweeps form their source themselves (factors, sweep, moments, test per iteration);
-    FP64 iterations add the source pass."""
+    FP64 iterations add the source pass; walls add their refresh to every iteration."""
     n = 1
-    per_main = 4 if main_fp32 else 5
+    per_main = (4 if main_fp32 else 5) + bool(walls)
     for k in range(st.n_stages):
         n += 2 + (k > 0) + (k < st.n_stages - 1)          # stage set-up, moments, stage combines
         n += 9 if guess else 0
         if st.iterations_fp32[k]:
-            n += 7 + 4 * st.iterations_fp32[k]            # FP32 phase
+            n += 7 + (4 + bool(walls)) * st.iterations_fp32[k]   # FP32 phase
         n += per_main * st.iterations[k]
     return n
 
 
-def timed_steps(s, steps, world, local, tstream, guess=False, main_fp32=False):
+def timed_steps(s, steps, world, local, tstream, guess=False, main_fp32=False, walls=False):
     """Run `steps` steps of solver s (already warmed up; created on torch stream tstream),
     each bracketed by CUDA events on that stream; the time is the sum of the steps'
     device times (the statistics read between steps is not inside any bracket)."""
@@ -329,7 +341,7 @@ def timed_steps(s, steps, world, local, tstream, guess=False, main_fp32=False):
         e1.synchronize()
         el += e0.elapsed_time(e1) * 1e-3
         iters.append({"fp64": list(st.iterations)[:st.n_stages], "fp32": list(st.iterations_fp32)[:st.n_stages]})
-        launches += launches_per_step(st, guess, main_fp32)
+        launches += launches_per_step(st, guess, main_fp32, walls)
     s.synchronize()
     torch.cuda.synchronize()
     barrier(world)
@@ -414,8 +426,9 @@ def run_ours(args):
     except OSError:
         pass
     tstream = torch.cuda.Stream()
+    walls = WALL_SETS[args.walls]
     s = bgk.Solver.from_workload(w, precision=args.precision, eager=args.eager, cache_inverse=args.cache,
-                                 stream=tstream.cuda_stream, sweep_mode=args.sweep_mode)
+                                 stream=tstream.cuda_stream, sweep_mode=args.sweep_mode, walls=walls)
     s.set_state_maxwellian(w.init)
     s.set_inflow_maxwellian(w.inflow)
     dof = s.nv * s.nnode
@@ -424,7 +437,7 @@ def run_ours(args):
     for _ in range(args.warmup):
         s.step(1)
     el_max, sweeps, iters, launches, clk = timed_steps(s, args.steps, world, local, tstream,
-                                                       main_fp32=args.precision == "fp32")
+                                                       main_fp32=args.precision == "fp32", walls=bool(walls))
     value = job_throughput(dof * sweeps, el_max, world)
     f_end, U_end = s.get_f(np.float64), s.get_moments()
     # end to end through the C ABI with host buffers: f^k in from pinned host memory,
@@ -449,12 +462,13 @@ def run_ours(args):
     # the plain FP64 path on the same steps, for the comparison the metric asks for
     plain = None
     if args.precision != "fp64":
-        p = bgk.Solver.from_workload(w, precision="fp64", stream=tstream.cuda_stream, sweep_mode=args.sweep_mode)
+        p = bgk.Solver.from_workload(w, precision="fp64", stream=tstream.cuda_stream, sweep_mode=args.sweep_mode,
+                                     walls=walls)
         p.set_f(f0.astype(np.float64))
         p.set_inflow_maxwellian(w.inflow)
         for _ in range(args.warmup):
             p.step(1)
-        pe, psw, pit, _, pclk = timed_steps(p, args.steps, world, local, tstream)
+        pe, psw, pit, _, pclk = timed_steps(p, args.steps, world, local, tstream, walls=bool(walls))
         plain = {"ms_per_step": 1e3 * pe / args.steps, "value": job_throughput(dof * psw, pe, world), "picard_iterations": pit,
                  "clocks": pclk,
                  "error_vs_plain_fp64": state_errors(f_end, U_end, p.get_f(np.float64), p.get_moments(), p.dim)}
@@ -474,6 +488,8 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, 1024 if w.mesh.dim == 2 else 256, dt)
+        if walls:
+            cpu["sample"] += WALL_NOTE
     if rank != 0:
         return
     ms = 1e3 * el_max / args.steps
