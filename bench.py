@@ -52,6 +52,8 @@ def parse():
                    help="sweep algorithm: generation sweep (tgs), one thread per ordinate (ts), or automatic")
     p.add_argument("--walls", default="none", choices=sorted(WALL_SETS),
                    help="Sec. 4.2 walls: channel = reflecting walls at y = 0, 1 (single-problem workloads)")
+    p.add_argument("--collision", default="maxwellian", choices=["maxwellian", "linear"],
+                   help="linear: the simplified Maxwellian n/|V| (single-problem workloads)")
     p.add_argument("--train-runs", type=int, default=200)
     p.add_argument("--eval-runs", type=int, default=4)
     p.add_argument("--instances", type=int, default=64)
@@ -104,6 +106,8 @@ def config(w, args, extra=None):
         name = ("2D-2V shock tube, %dx%d squares (%d P2 triangles), %dx%d velocities on [-8,8]^2, DIRK3, "
                 "Kn 1e-3, CFL 10, tau 1e-8" % (args.n_side, args.n_side, w.mesh.n_cells, args.n_v, args.n_v))
         integ = "DIRK3"
+    if getattr(args, "collision", "maxwellian") == "linear":
+        name += ", simplified Maxwellian n/|V|"
     if getattr(args, "walls", "none") != "none":
         name += ", walls: " + ", ".join("%s %s" % kv for kv in sorted(WALL_SETS[args.walls].items()))
     c = {"workload": name,
@@ -428,7 +432,8 @@ def run_ours(args):
     tstream = torch.cuda.Stream()
     walls = WALL_SETS[args.walls]
     s = bgk.Solver.from_workload(w, precision=args.precision, eager=args.eager, cache_inverse=args.cache,
-                                 stream=tstream.cuda_stream, sweep_mode=args.sweep_mode, walls=walls)
+                                 stream=tstream.cuda_stream, sweep_mode=args.sweep_mode, walls=walls,
+                                 collision=args.collision)
     s.set_state_maxwellian(w.init)
     s.set_inflow_maxwellian(w.inflow)
     dof = s.nv * s.nnode
@@ -463,7 +468,7 @@ def run_ours(args):
     plain = None
     if args.precision != "fp64":
         p = bgk.Solver.from_workload(w, precision="fp64", stream=tstream.cuda_stream, sweep_mode=args.sweep_mode,
-                                     walls=walls)
+                                     walls=walls, collision=args.collision)
         p.set_f(f0.astype(np.float64))
         p.set_inflow_maxwellian(w.inflow)
         for _ in range(args.warmup):
