@@ -109,7 +109,8 @@ def config(w, args, extra=None):
     if getattr(args, "collision", "maxwellian") == "linear":
         name += ", simplified Maxwellian n/|V|"
     if getattr(args, "walls", "none") != "none":
-        name += ", walls: " + ", ".join("%s %s" % kv for kv in sorted(WALL_SETS[args.walls].items()))
+        name += ", walls: " + ", ".join("%s %s" % kv for kv in sorted(WALL_SETS[args.walls].items())
+                                        if kv[0][0] in "xyz"[:w.mesh.dim])
     c = {"workload": name,
          "n_cells": w.mesh.n_cells, "dof_per_sweep": dof,
          "precision": {"fp64": "FP64 sweeps", "fp32": "FP32 sweeps, FP64-accurate moments",
