@@ -107,7 +107,10 @@ class Oracle:
 
     @classmethod
     def from_workload(cls, w):
-        return cls(w.mesh.dim, w.kx, w.mesh.xyz, w.mesh.cells, w.n_v, w.k_v, w.L)
+        o = cls(w.mesh.dim, w.kx, w.mesh.xyz, w.mesh.cells, w.n_v, w.k_v, w.L)
+        if getattr(w, "walls", None):
+            o.set_walls(w.walls)
+        return o
 
     def __del__(self):
         if getattr(self, "h", None):

@@ -199,6 +199,10 @@ class Solver:
     @classmethod
     def from_workload(cls, w, **kw):
         args = dict(integrator=w.integrator, cfl=w.cfl)
+        if getattr(w, "dt", 0.0) > 0.0:
+            args["dt"] = w.dt
+        if getattr(w, "walls", None):
+            args["walls"] = w.walls
         args.update(kw)
         return cls(w.mesh.dim, w.kx, w.mesh.xyz, w.mesh.cells, w.n_v, w.k_v, w.L, w.nu, **args)
 

@@ -188,6 +188,8 @@ class Workload:
     cfl: float
     init: np.ndarray         # [n_cells*n_nodes, dim+2]: n, u_1..u_d, theta per node
     inflow: np.ndarray       # same layout; used at nodes on inflow boundary faces
+    dt: float = 0.0          # time step; 0: from the CFL number
+    walls: dict = None       # Sec. 4.2 wall kinds per box side ({"y-": "reflect", ...}); None: inflow
 
     @property
     def nu(self) -> float:
@@ -242,6 +244,32 @@ def workload_shock_tube(n_side=128, seed=1, kx=2, n_v=32, k_v=3, L=8.0, knudsen=
     init = _pack(n, u, th)
     return Workload("2d2v_shock_tube_p%d_%dx%d_v%d" % (kx, n_side, n_side, n_v), mesh, kx, n_v,
                     k_v, L, knudsen, integrator, cfl, init, init.copy())
+
+
+SOD_STEPS = 85            # Sec. 5.1.1: 85 steps of 1.76e-3 to t = 0.15 (0.14960)
+
+
+def workload_sod_strip(nx=256, ny=6, kx=1, n_v=32, k_v=3, L=6.0, knudsen=1e-3, integrator="BE",
+                       dt=1.76e-3) -> Workload:
+    """The 1D Sod problem in a 2D strip (Sec. 5.1.1): X = [-1, 1] x [-3/128, 3/128], an
+    nx x ny uniform grid (each square cut into two triangles along a seeded diagonal; the
+    paper uses quadrilaterals), left half (n, u, theta) = (1, 0, 1), right half
+    (0.125, 0, 0.8) (pressures 1 and 0.1), reflecting walls at x_2 = +-3/128, the initial
+    states as inflow data at x_1 = -1 and 1, dt = 1.76e-3."""
+    m = rect_mesh(nx, ny, 7, jitter=0.0)
+    xyz = m.xyz.copy()
+    xyz[:, 0] = 2.0 * xyz[:, 0] - 1.0
+    xyz[:, 1] = 2.0 * xyz[:, 1] - ny / nx          # square cells of side 2/nx, centred on x_2 = 0
+    mesh = Mesh(2, xyz, m.cells, n_side=nx, seed=7, meta={"ny": ny})
+    xn = node_coords(mesh, kx)
+    cent = mesh.xyz[mesh.cells].mean(axis=1)[:, 0]
+    left = np.repeat((cent < 0.0)[:, None], xn.shape[1], axis=1).ravel()
+    n = np.where(left, 1.0, 0.125)
+    th = np.where(left, 1.0, 0.8)
+    u = np.zeros((n.size, 2))
+    init = _pack(n, u, th)
+    return Workload("2d2v_sod_strip_p%d_%dx%d_v%d" % (kx, nx, ny, n_v), mesh, kx, n_v, k_v, L, knudsen,
+                    integrator, 0.0, init, init.copy(), dt=dt, walls={"y-": "reflect", "y+": "reflect"})
 
 
 def workload_3d_bump(n_side=24, seed=2, n_v=16, k_v=3, L=6.0, knudsen=1e-2,

@@ -1,0 +1,82 @@
+"""The 1D Sod problem in a 2D strip (Sec. 5.1.1) on the GPU: 256 x 6 squares (triangulated),
+reflecting walls at x_2 = +-3/128, 85 steps of dt = 1.76e-3 to t = 0.1496.
+
+- Fluid limit (nu = 1000): the density along x_1 is compared with the exact Euler solution
+  for gamma = (d + 2)/d = 2 (the paper compares with an exact Riemann solver too).
+- Until the waves reach x_1 = +-1, the inflow data equal the interior state at both ends, so
+  the ends pass no net mass and the walls none either: total mass is conserved, and the
+  x_1-momentum grows by exactly (p_L - p_R) |wall-to-wall height| per unit time.
+- Picard iterations per step: nu = 1000 needs several times the iterations of nu = 1
+  (the paper's iteration table reports 5.5-5.8x for DIRK-1, 2.7-3.3x for DIRK-2).
+"""
+import numpy as np
+import pytest
+
+from euler_exact import sample
+from paper_2608_19150_b300 import bgk, synth
+
+pytestmark = pytest.mark.gpu
+
+RUNS = {}
+
+
+def _run(knudsen, integ, n_v=32, precision="fp64"):
+    key = (knudsen, integ, n_v, precision)
+    if key in RUNS:
+        return RUNS[key]
+    w = synth.workload_sod_strip(n_v=n_v, knudsen=knudsen, integrator=integ)
+    s = bgk.Solver.from_workload(w, precision=precision, l_max=3000)
+    s.set_state_maxwellian(w.init)
+    s.set_inflow_maxwellian(w.inflow)
+    U0 = s.get_moments()
+    its = []
+    for _ in range(synth.SOD_STEPS):
+        st = s.step(1)
+        its.append(int(sum(list(st.iterations)[:st.n_stages]) + sum(list(st.iterations_fp32)[:st.n_stages])))
+    RUNS[key] = (w, s, U0, s.get_moments(), np.array(its))
+    return RUNS[key]
+
+
+def _weights(w):
+    from oracle.oracle import Oracle
+    o = Oracle(w.mesh.dim, w.kx, w.mesh.xyz, w.mesh.cells, 4, 1, w.L)   # geometry only
+    return np.concatenate([o.cell(c)["M"].sum(axis=0) for c in range(o.ncell)])
+
+
+@pytest.mark.parametrize("integ", ["BE", "DIRK2"])
+def test_sod_fluid_limit_matches_exact_euler(integ):
+    w, s, U0, U, its = _run(1e-3, integ)
+    t = synth.SOD_STEPS * w.dt
+    x = synth.node_coords(w.mesh, w.kx).reshape(-1, 2)[:, 0]
+    ex = sample((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 2.0, x / t)
+    wt = _weights(w)
+    e_rho = np.sum(wt * np.abs(U[:, 0] - ex[:, 0])) / np.sum(wt * ex[:, 0])
+    u = U[:, 1] / U[:, 0]
+    e_u = np.sum(wt * np.abs(u - ex[:, 1])) / np.sum(wt)      # |u| ~ 1 in the star region
+    print("Sod nu=1000 %s: L1 density error %.4f, L1 velocity error %.4f" % (integ, e_rho, e_u))
+    assert e_rho < 0.03 and e_u < 0.05
+
+
+@pytest.mark.parametrize("knudsen", [1.0, 1e-3])
+def test_sod_conserves_mass_and_gains_end_pressure_momentum(knudsen):
+    w, s, U0, U, its = _run(knudsen, "BE")
+    wt = _weights(w)
+    t = synth.SOD_STEPS * w.dt
+    height = 2 * 6 / 256
+    m0, m1 = wt @ U0[:, 0], wt @ U[:, 0]
+    px = wt @ U[:, 1]
+    print("Sod nu=%g: mass change %.2e, x-momentum %.6f vs (p_L - p_R) H t = %.6f"
+          % (1 / knudsen, (m1 - m0) / m0, px, 0.9 * height * t))
+    assert abs(m1 - m0) < 1e-9 * m0
+    assert px == pytest.approx(0.9 * height * t, rel=1e-6)
+
+
+@pytest.mark.parametrize("integ", ["BE", "DIRK2"])
+def test_sod_iterations_grow_in_the_fluid_limit(integ):
+    rows = []
+    for kn in (1.0, 1e-3):
+        w, s, U0, U, its = _run(kn, integ)
+        rows.append(its)
+        print("Sod nu=%g %s: iterations per step min %d max %d avg %.2f tot %d"
+              % (1 / kn, integ, its.min(), its.max(), its.mean(), its.sum()))
+    assert rows[1].mean() > 2.0 * rows[0].mean()
