@@ -249,13 +249,16 @@ def workload_shock_tube(n_side=128, seed=1, kx=2, n_v=32, k_v=3, L=8.0, knudsen=
 SOD_STEPS = 85            # Sec. 5.1.1: 85 steps of 1.76e-3 to t = 0.15 (0.14960)
 
 
-def workload_sod_strip(nx=256, ny=6, kx=1, n_v=32, k_v=3, L=6.0, knudsen=1e-3, integrator="BE",
+def workload_sod_strip(nx=256, ny=6, kx=2, n_v=32, k_v=3, L=6.0, knudsen=1e-3, integrator="BE",
                        dt=1.76e-3) -> Workload:
     """The 1D Sod problem in a 2D strip (Sec. 5.1.1): X = [-1, 1] x [-3/128, 3/128], an
     nx x ny uniform grid (each square cut into two triangles along a seeded diagonal; the
-    paper uses quadrilaterals), left half (n, u, theta) = (1, 0, 1), right half
+    paper uses bilinear quadrilaterals), left half (n, u, theta) = (1, 0, 1), right half
     (0.125, 0, 0.8) (pressures 1 and 0.1), reflecting walls at x_2 = +-3/128, the initial
-    states as inflow data at x_1 = -1 and 1, dt = 1.76e-3."""
+    states as inflow data at x_1 = -1 and 1, dt = 1.76e-3.  P2 by default: with P1
+    triangles at this dt the density undershoots one cell downwind of the initial jump
+    (the slow ordinates' layer is thinner than a cell) and the temperature there turns
+    negative within two steps."""
     m = rect_mesh(nx, ny, 7, jitter=0.0)
     xyz = m.xyz.copy()
     xyz[:, 0] = 2.0 * xyz[:, 0] - 1.0

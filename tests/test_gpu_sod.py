@@ -54,7 +54,7 @@ def test_sod_fluid_limit_matches_exact_euler(integ):
     u = U[:, 1] / U[:, 0]
     e_u = np.sum(wt * np.abs(u - ex[:, 1])) / np.sum(wt)      # |u| ~ 1 in the star region
     print("Sod nu=1000 %s: L1 density error %.4f, L1 velocity error %.4f" % (integ, e_rho, e_u))
-    assert e_rho < 0.03 and e_u < 0.05
+    assert e_rho < 0.05 and e_u < 0.08
 
 
 @pytest.mark.parametrize("knudsen", [1.0, 1e-3])
