@@ -47,7 +47,9 @@ def parse():
                    help="cells per side (shock_tube 128, bump3d 24, learned 256)")
     p.add_argument("--n-v", type=int, default=None, help="velocity points per dimension (32; bump3d 16)")
     p.add_argument("--sweep-reps", type=int, default=5)
-    p.add_argument("--workload", default="shock_tube", choices=["shock_tube", "bump3d", "strip", "batched", "learned"])
+    p.add_argument("--workload", default="shock_tube", choices=["shock_tube", "bump3d", "strip", "sod", "batched", "learned"])
+    p.add_argument("--nu", type=float, default=1000.0, help="sod: collision frequency (the paper runs 1 and 1000)")
+    p.add_argument("--integrator", default="DIRK2", choices=["BE", "DIRK2"], help="sod: DIRK-1 or DIRK-2")
     p.add_argument("--sweep-mode", default="auto", choices=["auto", "tgs", "ts"],
                    help="sweep algorithm: generation sweep (tgs), one thread per ordinate (ts), or automatic")
     p.add_argument("--walls", default="none", choices=sorted(WALL_SETS),
@@ -66,7 +68,7 @@ def parse():
                    help="launch each step's kernels from a host loop instead of one CUDA graph (profiling)")
     a = p.parse_args()
     if a.n_side is None:
-        a.n_side = {"bump3d": 24, "learned": 256, "strip": 4096}.get(a.workload, 128)
+        a.n_side = {"bump3d": 24, "learned": 256, "strip": 4096, "sod": 256}.get(a.workload, 128)
     if a.n_v is None:
         a.n_v = 16 if a.workload == "bump3d" else 32
     return a
@@ -77,6 +79,9 @@ def workload(args):
     if args.workload == "bump3d":
         return synth.workload_3d_bump(n_side=args.n_side, seed=2, n_v=args.n_v, k_v=3, L=6.0, knudsen=1e-2,
                                       integrator="BE", cfl=8.0)
+    if args.workload == "sod":
+        return synth.workload_sod_strip(nx=args.n_side, ny=6, kx=2, n_v=args.n_v, k_v=3, L=6.0,
+                                        knudsen=1.0 / args.nu, integrator=args.integrator, dt=1.76e-3)
     if args.workload == "strip":
         return synth.workload_strip(nx=args.n_side, ny=2, seed=5, kx=1, n_v=args.n_v, k_v=3, L=6.0, knudsen=1e-2,
                                     integrator="BE", cfl=10.0)
@@ -98,6 +103,11 @@ def config(w, args, extra=None):
         name = ("3D-3V Gaussian bump, %d^3 cubes (%d P1 tetrahedra), %d^3 velocities on [-6,6]^3, backward Euler, "
                 "Kn 1e-2, CFL 8, tau 1e-8" % (args.n_side, w.mesh.n_cells, args.n_v))
         integ = "BE"
+    elif args.workload == "sod":
+        name = ("2D-2V Sod problem in a strip [-1,1]x[-3/128,3/128], %dx6 squares (%d P2 triangles), reflecting "
+                "walls at x2 = +-3/128, %dx%d velocities on [-6,6]^2, %s, nu %g, dt 1.76e-3, tau 1e-8"
+                % (args.n_side, w.mesh.n_cells, args.n_v, args.n_v, args.integrator, args.nu))
+        integ = args.integrator
     elif args.workload == "strip":
         name = ("2D-2V smooth quasi-1D problem on a %dx2 strip (%d P1 triangles), %dx%d velocities on [-6,6]^2, "
                 "backward Euler, Kn 1e-2, CFL 10, tau 1e-8" % (args.n_side, w.mesh.n_cells, args.n_v, args.n_v))
@@ -208,7 +218,8 @@ def cpu_baseline(w, n_ord, dt):
     """The oracle as it stands (single thread): one sweep of n_ord ordinates of the full
     mesh, on the sampled ordinates' own rows (graphs, Maxwellian, sweep)."""
     from oracle.oracle import Oracle, tableau
-    o = Oracle.from_workload(w)
+    # the sampled sweep reads wall faces as inflow data (the mirror rows are not sampled)
+    o = Oracle(w.mesh.dim, w.kx, w.mesh.xyz, w.mesh.cells, w.n_v, w.k_v, w.L)
     j0 = (o.nv - n_ord) // 2
     js = np.arange(j0, j0 + n_ord, dtype=np.int32)
     t0 = time.perf_counter()
@@ -277,12 +288,12 @@ def run_reference(args):
         return
     w = workload(args)
     from oracle.oracle import Oracle, tableau
-    o = Oracle.from_workload(w)
+    o = Oracle(w.mesh.dim, w.kx, w.mesh.xyz, w.mesh.cells, w.n_v, w.k_v, w.L)   # see cpu_baseline
     n_ord = 64
     j0 = (o.nv - n_ord) // 2
     js = np.arange(j0, j0 + n_ord, dtype=np.int32)
     o.build_dags_for(js)
-    dt = w.cfl * o.dt_explicit()
+    dt = w.dt if w.dt > 0 else w.cfl * o.dt_explicit()
     f0 = o.maxwellian_rows(w.init, js)
     fbc = o.maxwellian_rows(w.inflow, js)
     A, _, _ = tableau(w.integrator)
@@ -302,8 +313,9 @@ def run_reference(args):
             "config": config(w, args, {"sample": "each step: one oracle sweep over %d of %d ordinates of the "
                                                  "full mesh" % (n_ord, o.nv), "precision": "FP64 CPU oracle"}),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "%d ordinates x %d cells x 6 nodes per step%s" % (n_ord, o.ncell, WALL_NOTE
-                                                                                       if args.walls != "none" else "")},
+                             "sample": "%d ordinates x %d cells x %d nodes per step%s" % (
+                                 n_ord, o.ncell, o.nnode // o.ncell,
+                                 WALL_NOTE if (args.walls != "none" or w.walls) else "")},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -431,7 +443,7 @@ def run_ours(args):
     except OSError:
         pass
     tstream = torch.cuda.Stream()
-    walls = WALL_SETS[args.walls]
+    walls = WALL_SETS[args.walls] or w.walls
     s = bgk.Solver.from_workload(w, precision=args.precision, eager=args.eager, cache_inverse=args.cache,
                                  stream=tstream.cuda_stream, sweep_mode=args.sweep_mode, walls=walls,
                                  collision=args.collision)
