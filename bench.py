@@ -50,7 +50,7 @@ def parse():
     p.add_argument("--workload", default="shock_tube", choices=["shock_tube", "bump3d", "strip", "sod", "batched", "learned"])
     p.add_argument("--nu", type=float, default=1000.0, help="sod: collision frequency (the paper runs 1 and 1000)")
     p.add_argument("--integrator", default="DIRK2", choices=["BE", "DIRK2"], help="sod: DIRK-1 or DIRK-2")
-    p.add_argument("--sweep-mode", default="auto", choices=["auto", "tgs", "ts", "lanes"],
+    p.add_argument("--sweep-mode", default="auto", choices=["auto", "tgs", "ts"],
                    help="sweep algorithm: generation sweep (tgs), one thread per ordinate (ts), or automatic")
     p.add_argument("--walls", default="none", choices=sorted(WALL_SETS),
                    help="Sec. 4.2 walls: channel = reflecting walls at y = 0, 1 (single-problem workloads)")
@@ -396,7 +396,7 @@ def sweep_roofline(w, precision, reps, peaks, n_side=None, n_v=None, sweep_mode=
     cached = s.cache_bytes > 0
     kind = elem_of(w)[0]
     ename = {"p2tri": "ElemP2Tri", "p1tri": "ElemP1Tri", "p1tet": "ElemP1Tet"}[kind]
-    kname = {"ts": "k_sweep_ts", "lanes": "k_sweep_lanes"}.get(s.sweep_mode, "k_sweep")
+    kname = "k_sweep_ts" if s.sweep_mode == "ts" else "k_sweep"
     if precision == "fp64":
         fl = sweep_flops_per_item(cached, kind)
         tf = fl * s.nv * s.ncell / (sweep_ms * 1e-3) / 1e12

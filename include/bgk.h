@@ -110,13 +110,10 @@ typedef struct {
                          place (FP32 sweeps carry the next cell's geometry in registers) */
   int sweep_mode;     /* sweep algorithm (Sec. 4.1): 0 or 1 = TGS (a CTA per ordinate walks
                          the generations, the cells of a generation in parallel: the default),
-                         2 = TS (a thread per ordinate walks its whole schedule alone),
-                         3 = TGS in lane groups (4, 8 or 16 lanes of a warp per ordinate, after
-                         the mean generation width; several ordinates per warp, for narrow
-                         generations).  All give the same results up to rounding.  TS is
-                         slower on every mesh measured, strips with 1-2 cells per generation
-                         included (the CTA size of TGS follows the generation width and its
-                         barrier is per CTA) */
+                         2 = TS (a thread per ordinate walks its whole schedule alone).  Both
+                         give the same results up to rounding.  TS is slower on every mesh
+                         measured, strips with 1-2 cells per generation included (the CTA
+                         size of TGS follows the generation width and its barrier is per CTA) */
 } bgk_config;
 
 typedef struct {
@@ -141,8 +138,7 @@ int bgk_destroy(bgk_handle* h);
 /* Problem sizes: out[0]=n_ordinates, [1]=n_nodes, [2]=n_dof, [3]=n_cells, [4]=dim,
  * [5]=max generations over ordinates, [6]=lagged edges over all ordinates,
  * [7]=bytes of the local-inverse cache (0 if none), [8]=threads per sweep CTA,
- * [9]=sweep algorithm in use (1 TGS, 2 TS, 3 TGS in lane groups; [8] is then the lanes per
- * ordinate).  out holds 10 values. */
+ * [9]=sweep algorithm in use (1 TGS, 2 TS).  out holds 10 values. */
 int bgk_sizes(const bgk_handle* h, int64_t* out);
 /* Time step actually used (after the CFL rule). */
 int bgk_get_dt(const bgk_handle* h, double* dt);

@@ -51,7 +51,7 @@ class Config(C.Structure):
                 ("cache_inverse", C.c_int), ("fp32_floor", C.c_double), ("prefetch", C.c_int),
                 ("sweep_mode", C.c_int)]
 
-SWEEP_MODES = {"auto": 0, "tgs": 1, "ts": 2, "lanes": 3}
+SWEEP_MODES = {"auto": 0, "tgs": 1, "ts": 2}
 
 
 class Stats(C.Structure):
@@ -192,7 +192,7 @@ class Solver:
         _ck(self.lib.bgk_sizes(self.h, sz), "bgk_sizes")
         (self.nv, self.nnode, self.ndof, self.ncell, self.dim, self.gmax, self.lagged, self.cache_bytes,
          self.sweep_threads, mode) = (int(x) for x in sz)
-        self.sweep_mode = {1: "tgs", 2: "ts", 3: "lanes"}[mode]
+        self.sweep_mode = {1: "tgs", 2: "ts"}[mode]
         self.precision = precision
         self.fdtype = np.float32 if precision == "fp32" else np.float64
 
@@ -217,7 +217,7 @@ class Solver:
         _ck(self.lib.bgk_sizes(self.h, sz), "bgk_sizes")
         (self.nv, self.nnode, self.ndof, self.ncell, self.dim, self.gmax, self.lagged, self.cache_bytes,
          self.sweep_threads, mode) = (int(x) for x in sz)
-        self.sweep_mode = {1: "tgs", 2: "ts", 3: "lanes"}[mode]
+        self.sweep_mode = {1: "tgs", 2: "ts"}[mode]
         self.precision = precision
         self.fdtype = np.float32 if precision == "fp32" else np.float64
         return self

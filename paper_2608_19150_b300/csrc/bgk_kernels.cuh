@@ -1036,13 +1036,6 @@ struct NamedBarrier {
   }
 };
 
-// Barrier of a group of lanes inside one warp (lane-group sweep): __syncwarp over the
-// group's lanes, which also orders their memory accesses.
-struct LaneGroupBarrier {
-  unsigned mask;
-  __device__ __forceinline__ void sync() const { __syncwarp(mask); }
-};
-
 // One ordinate's transport sweep (Sec. 4, Eq. bgk-ss-picard) by a group of `nt` threads
 // (thread `tid` of the group) walking the ordinate's generations; the cells of one
 // generation are independent and share the group's threads.  For cell K and ordinate j
@@ -1241,26 +1234,6 @@ __global__ void __launch_bounds__(64) k_sweep_ts(SweepArgs sa, VGrid g, T nus, S
   const int j = jb + (int)(blockIdx.x * blockDim.x + threadIdx.x);
   if (j >= je) return;
   sweep_ordinate<E, T, CACHED, NoBarrier, false, FUSED>(sa, g, j, nus, sr, fbc, Ainv, f, 0, 1, NoBarrier());
-}
-
-// Generation sweep for narrow generations (a strip, a few cells per generation): groups
-// of LANES lanes (4, 8 or 16) inside each warp, one ordinate per group, 128 / LANES
-// ordinates per CTA.  Each group walks its ordinate's generations as the CTA-per-ordinate
-// kernel does and synchronises only its own lanes, so a warp carries several ordinates
-// instead of one ordinate with most of its lanes idle.  Ordinates [jb, je).
-template <class E, typename T, bool CACHED, int LANES, bool FUSED = false>
-__global__ void __launch_bounds__(128) k_sweep_lanes(SweepArgs sa, VGrid g, T nus, SrcArgs<T> sr,
-                                                     const T* __restrict__ fbc, const T* __restrict__ Ainv, T* f,
-                                                     const DevState* ds, int jb, int je) {
-  static_assert(LANES == 4 || LANES == 8 || LANES == 16, "lane groups divide a warp");
-  if (ds && (ds->status != BGK_OK || ds->done)) return;
-  constexpr int GPC = 128 / LANES;
-  const int grp = (int)threadIdx.x / LANES, lane = (int)threadIdx.x % LANES;
-  const int j = jb + (int)blockIdx.x * GPC + grp;
-  if (j >= je) return;
-  const unsigned mask = ((1u << LANES) - 1u) << (((int)threadIdx.x & 31) / LANES * LANES);
-  sweep_ordinate<E, T, CACHED, LaneGroupBarrier, false, FUSED>(sa, g, j, nus, sr, fbc, Ainv, f, lane, LANES,
-                                                               LaneGroupBarrier{mask});
 }
 
 // (ordinates jofs + blockIdx.x: all of them, or one shard's range)

@@ -37,7 +37,6 @@ struct bgk_handle {
   long lagged = 0;
   int sweep_threads = 128;
   bool sweep_ts = false;     // TS: one thread per ordinate (narrow generations)
-  int sweep_lanes = 0;       // > 0: lane-group TGS, this many lanes per ordinate (narrow generations)
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   // device geometry and schedule
@@ -217,46 +216,11 @@ size_t prefetch_smem(const bgk_handle* h) {
   return 2 * (size_t)h->sweep_threads * (h->hm.geo_stride * sizeof(double) + ainv_stride<E, T>() * sizeof(T));
 }
 
-template <class E, typename T, int LANES>
-void launch_sweep_lanes_n(bgk_handle* h, double nus, int jb, int je, bool cached) {
-  const int blk = (je - jb + 128 / LANES - 1) / (128 / LANES);
-  const SrcArgs<T> sr{(const T*)h->src, nullptr, nullptr, T(0)};
-  if constexpr (sizeof(T) == 4) {
-    if (h->fuse_src) {
-      const SrcArgs<T> fr{nullptr, (const T*)h->cf, (const T*)h->fused_q, (T)h->fused_qscale};
-      k_sweep_lanes<E, T, false, LANES, true><<<blk, 128, 0, h->stream>>>(sweep_args(h), h->g, (T)nus, fr,
-                                                                          (const T*)h->fbc, nullptr, (T*)h->f,
-                                                                          h->ds, jb, je);
-      return;
-    }
-  }
-  if (cached)
-    k_sweep_lanes<E, T, true, LANES><<<blk, 128, 0, h->stream>>>(sweep_args(h), h->g, (T)nus, sr, (const T*)h->fbc,
-                                                                 (const T*)h->Ainv, (T*)h->f, h->ds, jb, je);
-  else
-    k_sweep_lanes<E, T, false, LANES><<<blk, 128, 0, h->stream>>>(sweep_args(h), h->g, (T)nus, sr, (const T*)h->fbc,
-                                                                  nullptr, (T*)h->f, h->ds, jb, je);
-}
-
-template <class E, typename T>
-void launch_sweep_lanes(bgk_handle* h, double nus, int jb, int je, bool cached) {
-  if (h->sweep_lanes == 4)
-    launch_sweep_lanes_n<E, T, 4>(h, nus, jb, je, cached);
-  else if (h->sweep_lanes == 8)
-    launch_sweep_lanes_n<E, T, 8>(h, nus, jb, je, cached);
-  else
-    launch_sweep_lanes_n<E, T, 16>(h, nus, jb, je, cached);
-}
-
 template <class E, typename T>
 void launch_sweep_t(bgk_handle* h, double nus, int jb, int je) {
   const bool cached = h->Ainv && nus == h->nus_cached;
   const size_t pf = prefetch_smem<E, T>(h);
   const SrcArgs<T> sr{(const T*)h->src, nullptr, nullptr, T(0)};
-  if (h->sweep_lanes) {
-    launch_sweep_lanes<E, T>(h, nus, jb, je, cached);
-    return;
-  }
   if (h->sweep_ts) {
     const int thr = 64, blk = (je - jb + thr - 1) / thr;
     if constexpr (sizeof(T) == 4) {
@@ -675,11 +639,6 @@ int build_dags(bgk_handle* h) {
   // sweep algorithm: TGS unless TS is asked for (TS ran 8x slower even on a 4096 x 2 strip
   // with 1.4 cells per generation: its concurrency is one thread per ordinate)
   h->sweep_ts = h->cfg.sweep_mode == 2;
-  // lane groups: about the mean generation width in lanes, 4, 8 or 16
-  if (h->cfg.sweep_mode == 3) {
-    const double width = (double)n / std::max(1, h->Gmax);
-    h->sweep_lanes = width <= 4.0 ? 4 : width <= 8.0 ? 8 : 16;
-  }
   return BGK_OK;
 }
 
@@ -935,8 +894,8 @@ int bgk_sizes(const bgk_handle* h, int64_t* out) {
   out[5] = h->Gmax;
   out[6] = h->lagged;
   out[7] = h->Ainv ? (int64_t)h->ainv_bytes : 0;
-  out[8] = h->sweep_lanes ? h->sweep_lanes : h->sweep_threads;
-  out[9] = h->sweep_ts ? 2 : h->sweep_lanes ? 3 : 1;
+  out[8] = h->sweep_threads;
+  out[9] = h->sweep_ts ? 2 : 1;
   return BGK_OK;
 }
 

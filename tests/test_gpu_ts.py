@@ -52,29 +52,3 @@ def test_default_is_tgs():
     strip = bgk.Solver.from_workload(synth.workload_strip(nx=256, ny=1, n_v=16))
     square = bgk.Solver.from_workload(small_shock_tube(n=16, kx=2, n_v=16))
     assert strip.sweep_mode == "tgs" and square.sweep_mode == "tgs"
-
-
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("name", ["p1_strip", "p2_sod", "p2_tri"])
-def test_lane_groups_equal_cta_sweep(name, precision):
-    """Lane-group TGS (several ordinates per warp, each group of lanes synchronised by its
-    own __syncwarp) gives the CTA-per-ordinate results up to rounding, with walls too."""
-    from paper_2608_19150_b300 import bgk, synth
-    if name == "p1_strip":
-        w = synth.workload_strip(nx=256, ny=2, n_v=16)
-    elif name == "p2_sod":
-        w = synth.workload_sod_strip(nx=64, ny=6, n_v=16, knudsen=1.0)
-    else:
-        w = synth.workload_p1_square(n_side=8, n_v=16)
-    tau = 1e-8 if precision == "fp64" else 1e-6
-    out = {}
-    for mode in ("tgs", "lanes"):
-        s = bgk.Solver.from_workload(w, sweep_mode=mode, precision=precision, tau=tau)
-        assert s.sweep_mode == mode
-        s.set_state_maxwellian(w.init)
-        s.set_inflow_maxwellian(w.inflow)
-        st = s.step(2)
-        out[mode] = (s.get_f(), list(st.iterations))
-    assert out["lanes"][1] == out["tgs"][1]
-    err = np.abs(out["lanes"][0] - out["tgs"][0]).max() / np.abs(out["tgs"][0]).max()
-    assert err < (1e-13 if precision == "fp64" else 1e-5)
