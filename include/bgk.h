@@ -39,7 +39,7 @@ enum {
 };
 
 enum { BGK_BE = 0, BGK_DIRK2 = 1, BGK_DIRK3 = 2, BGK_BSTABLE2 = 3, BGK_BDF2 = 4 };
-enum { BGK_COLL_MAXWELLIAN = 0, BGK_COLL_LINEAR = 1 };
+enum { BGK_COLL_MAXWELLIAN = 0, BGK_COLL_LINEAR = 1, BGK_COLL_INTERP = 2 };
 /* Boundary conditions of Sec. 4.2 on the sides of a box domain.  INFLOW: given data g
  * (bgk_set_inflow_maxwellian / bgk_set_inflow).  BOUNCE_BACK: f^bc(x, v) = f(x, -v).
  * REFLECT: f^bc(x, v) = f(x, R_n v), R_n v = v - 2 (v.n) n (specular). */
@@ -79,7 +79,10 @@ typedef struct {
   int collision;      /* BGK_COLL_MAXWELLIAN (0): nu (M[f] - f) with the projected Maxwellian
                          (App. B); BGK_COLL_LINEAR (1): the simplified, linear Maxwellian
                          N_h = n / |V| at every ordinate, |V| = (2L)^d (Eq. linear-Maxwellian,
-                         Prop. Linear Stability); it conserves mass only */
+                         Prop. Linear Stability); it conserves mass only; BGK_COLL_INTERP (2):
+                         the Maxwellian of the current moments evaluated at the grid points
+                         (interpolation in velocity, the alternative Sec. 5.1.1 compares the
+                         projection with); it does not conserve the moments exactly */
   int walls[6];       /* boundary condition per side of the box, BGK_BC_*, in the order
                          x-, x+, y-, y+, z-, z+ (the first 2d are read).  A boundary face
                          belongs to side (a, +/-) when its unit outward normal is +/-e_a

@@ -81,7 +81,7 @@ typedef struct {
   /* physics */
   double nu, dt, tau;
   int integrator, lmax;
-  int collision; /* 0: projected Maxwellian; 1: simplified Maxwellian N_h = n / |V| */
+  int collision; /* 0: projected Maxwellian; 1: simplified Maxwellian N_h = n / |V|; 2: interpolated */
   /* wall boundary conditions (Sec. 4.2); NULL: inflow everywhere */
   int *wmirror;  /* [cell][face]: -1 inflow face, else the table row of mirror[] to use */
   int *mirror;   /* [1 + dim][nv]: row 0 = index of -v_j, row 1 + a = index of v_j with
@@ -1002,6 +1002,23 @@ static int picard(orc_t *o, double *f, const double *q, const double *fbc, doubl
         for (int j = 0; j < o->nv; ++j) Mn[(size_t)j * o->nnode + i] = n / vol;
       }
       if (bad) { *status = ORC_E_NONPHYSICAL; break; }
+    } else if (o->collision == 2) {
+      /* Sec. 5.1.1's alternative: the Maxwellian M_{n,u,theta} (Eq. Maxwellian) evaluated
+       * at each grid velocity v_j, n (2 pi theta)^(-d/2) exp(-|v_j - u|^2 / (2 theta)) */
+      for (int i = 0; i < o->nnode; ++i) bad |= primitive(o->dim, Uo + (size_t)i * nm, nut + (size_t)i * nm);
+      if (bad) { *status = ORC_E_NONPHYSICAL; break; }
+      for (int i = 0; i < o->nnode; ++i) {
+        const double *p = nut + (size_t)i * nm;
+        double th = p[1 + o->dim];
+        for (int j = 0; j < o->nv; ++j) {
+          double r2 = 0.0;
+          for (int al = 0; al < o->dim; ++al) {
+            double dv = o->v[(size_t)j * o->dim + al] - p[1 + al];
+            r2 += dv * dv;
+          }
+          Mn[(size_t)j * o->nnode + i] = p[0] * pow(2.0 * acos(-1.0) * th, -0.5 * o->dim) * exp(-r2 / (2.0 * th));
+        }
+      }
     } else {
       for (int i = 0; i < o->nnode; ++i) bad |= primitive(o->dim, Uo + (size_t)i * nm, nut + (size_t)i * nm);
       if (bad) { *status = ORC_E_NONPHYSICAL; break; }

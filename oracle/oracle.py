@@ -10,7 +10,8 @@ and the readings taken where the paper is silent).  This wrapper only marshals a
 Parity status per function (pins live in ``tests/test_oracle_pins.py``):
   velocity grid, element matrices, projection, moments, sweep graph / generations,
   one sweep, one time step (BE, DIRK2, DIRK3, B-stable DIRK2, BDF2), the simplified
-  Maxwellian collision model, bounce-back and reflecting walls: pinned.
+  Maxwellian collision model, the interpolated Maxwellian, bounce-back and reflecting
+  walls: pinned.
 """
 from __future__ import annotations
 
@@ -229,8 +230,9 @@ class Oracle:
         self.lib.orc_set_physics(self.h, float(nu), float(dt), INTEGRATORS[integrator], float(tau), int(lmax))
 
     def set_collision(self, kind):
-        """'maxwellian' (App. B projection) or 'linear' (Eq. linear-Maxwellian: n / |V|)."""
-        self.lib.orc_set_collision(self.h, {"maxwellian": 0, "linear": 1}[kind])
+        """'maxwellian' (App. B projection), 'linear' (Eq. linear-Maxwellian: n / |V|) or
+        'interpolated' (the Maxwellian's values at the grid points, Sec. 5.1.1)."""
+        self.lib.orc_set_collision(self.h, {"maxwellian": 0, "linear": 1, "interpolated": 2}[kind])
 
     def set_walls(self, walls):
         """Sec. 4.2 boundary conditions per box side: {"x-"|"x+"|"y-"|"y+"|"z-"|"z+":

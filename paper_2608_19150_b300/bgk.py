@@ -40,7 +40,7 @@ class Physics(C.Structure):
                 ("collision", C.c_int), ("walls", C.c_int * 6)]
 
 
-COLLISIONS = {"maxwellian": 0, "linear": 1}
+COLLISIONS = {"maxwellian": 0, "linear": 1, "interpolated": 2}
 WALLS = {"inflow": 0, "bounce_back": 1, "reflect": 2}
 SIDES = ("x-", "x+", "y-", "y+", "z-", "z+")
 

@@ -488,14 +488,14 @@ __global__ void k_moments_range(VGrid g, const T* __restrict__ f, int nnode, int
 // linear-Maxwellian): cf[0][m] = coef n / (2L)^d, cf[a > 0][m] = 1.
 template <typename T>
 __global__ void k_factors(VGrid g, int nnode, const double* __restrict__ U0, const double* __restrict__ U1,
-                          DevState* ds, double coef, T* __restrict__ cf, int linear) {
+                          DevState* ds, double coef, T* __restrict__ cf, int kind) {
   if (ds->status != BGK_OK || ds->done) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nnode) return;
   const int nm = g.dim + 2;
   const double* Un = (((ds->it & 1) == 0) ? U0 : U1) + (size_t)i * nm;
   const double n = Un[0];
-  if (linear) {
+  if (kind == BGK_COLL_LINEAR) {
     double vol = 1.0;
     for (int a = 0; a < g.dim; ++a) vol *= 2.0 * g.L;
     double val = coef * n / vol;
@@ -521,6 +521,17 @@ __global__ void k_factors(VGrid g, int nnode, const double* __restrict__ U0, con
     scale = 0.0;
     th = 1.0;
     u[0] = u[1] = u[2] = 0.0;
+  }
+  if (kind == BGK_COLL_INTERP) {
+    // the Maxwellian's values at the grid points (Sec. 5.1.1, the non-conservative
+    // alternative): one 1D Gaussian per dimension, n and coef in the first
+    const double rs = rsqrt(2.0 * 3.14159265358979323846 * th), h = 0.5 / th;
+    for (int a = 0; a < g.dim; ++a)
+      for (int m = 0; m < g.N; ++m) {
+        const double dv = g.x[m] - u[a];
+        cf[((size_t)a * g.N + m) * nnode + i] = (T)((a == 0 ? scale : 1.0) * rs * exp(-h * dv * dv));
+      }
+    return;
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a)

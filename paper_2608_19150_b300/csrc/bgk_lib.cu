@@ -351,7 +351,7 @@ int build_src_t(bgk_handle* h, const void* qsrc, double qscale) {
                                                 (T*)h->fbc);
   }
   k_factors<T><<<(h->nnode + 127) / 128, 128, 0, h->stream>>>(h->g, h->nnode, h->U[0], h->U[1], h->ds, h->phys.nu,
-                                                              (T*)h->cf, h->phys.collision == BGK_COLL_LINEAR);
+                                                              (T*)h->cf, h->phys.collision);
   if (h->fuse_src) {
     h->fused_q = qsrc;
     h->fused_qscale = qscale;
@@ -702,7 +702,8 @@ int bgk_create(const bgk_mesh* mesh, const bgk_vgrid* vg, const bgk_physics* phy
   h->precision = h->cfg.precision == BGK_FP32_SWEEP ? BGK_FP32_SWEEP : BGK_FP64;  // BGK_MIXED: FP64 + shadow
   h->tsize = h->precision == BGK_FP64 ? 8 : 4;
   if (phys->integrator < BGK_BE || phys->integrator > BGK_BDF2 || !(phys->nu >= 0.0) ||
-      (phys->collision != BGK_COLL_MAXWELLIAN && phys->collision != BGK_COLL_LINEAR)) {
+      (phys->collision != BGK_COLL_MAXWELLIAN && phys->collision != BGK_COLL_LINEAR &&
+       phys->collision != BGK_COLL_INTERP)) {
     delete h;
     return BGK_E_INVALID;
   }

@@ -159,3 +159,58 @@ def test_l2_decays_in_reflecting_box(model, integ):
         cur = l2(f)
         assert cur <= prev * (1 + 1e-12)
         prev = cur
+
+
+def _gauss_at_grid(v, n, u, th):
+    d = v.shape[1]
+    return n * (2 * np.pi * th) ** (-d / 2) * np.exp(-((v - u) ** 2).sum(1) / (2 * th))
+
+
+@pytest.mark.parametrize("n1d,kv", [(8, 3), (12, 2)])
+def test_interpolated_maxwellian_relaxation_in_closed_box(n1d, kv):
+    """Sec. 5.1.1's interpolated Maxwellian: in a closed reflecting box a uniform state
+    with even velocity dependence has no transport, so a converged backward-Euler step is
+    the pure relaxation f1 = (f0 + dt nu M[f1]) / (1 + dt nu), M[f1] the Maxwellian of f1's
+    discrete moments evaluated at the grid points (written out here with numpy)."""
+    m = synth.square_mesh(3, 0)
+    o = _oracle(m, n1d=n1d, kv=kv)
+    o.set_walls(ALL_REFLECT)
+    o.set_collision("interpolated")
+    v, wt, _, _ = o.velocity()
+    # f0: a uniform, even, non-Maxwellian distribution (two bumps)
+    g = np.exp(-((np.abs(v) - 1.0) ** 2).sum(1))
+    f0 = np.repeat(g[:, None], o.nnode, axis=1)
+    dt, nu = 0.05, 10.0
+    o.set_physics(nu, dt, "BE", tau=1e-14, lmax=500)
+    f1, it, meas, st = o.step(f0, np.zeros_like(f0))
+    assert st == 0
+    col = f1[:, 0]
+    assert np.abs(f1 - col[:, None]).max() < 1e-13 * col.max()     # stays uniform
+    n = wt @ col
+    E = wt @ (0.5 * (v * v).sum(1) * col)
+    th = 2 * E / n / v.shape[1]
+    M = _gauss_at_grid(v, n, np.zeros(v.shape[1]), th)
+    np.testing.assert_allclose(col, (g + dt * nu * M) / (1 + dt * nu), rtol=0, atol=1e-11 * col.max())
+
+
+def test_interpolation_is_not_conservative_and_projection_is():
+    """The reason the paper projects (App. B): on a coarse grid the interpolated Maxwellian
+    changes the mass of a closed box in a relaxation step, the projection does not; on a
+    finer grid the interpolation's defect shrinks."""
+    m = synth.square_mesh(3, 0)
+    defect = {}
+    for n1d, kv in ((8, 1), (16, 1)):
+        for kind in ("interpolated", "maxwellian"):
+            o = _oracle(m, n1d=n1d, kv=kv)
+            o.set_walls(ALL_REFLECT)
+            o.set_collision(kind)
+            v, wt, _, _ = o.velocity()
+            g = np.exp(-((np.abs(v) - 1.0) ** 2).sum(1))
+            f0 = np.repeat(g[:, None], o.nnode, axis=1)
+            o.set_physics(10.0, 0.05, "BE", tau=1e-14, lmax=500)
+            f1, it, meas, st = o.step(f0, np.zeros_like(f0))
+            assert st == 0
+            defect[(n1d, kind)] = abs(wt @ f1[:, 0] - wt @ g) / (wt @ g)
+    assert defect[(8, "maxwellian")] < 1e-12 and defect[(16, "maxwellian")] < 1e-12
+    assert defect[(8, "interpolated")] > 1e-4
+    assert defect[(16, "interpolated")] < 0.5 * defect[(8, "interpolated")]
