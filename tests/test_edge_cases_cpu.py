@@ -49,7 +49,7 @@ def test_invalid_problems_are_rejected_before_any_device_work():
     cells = np.array([[0, 1, 2], [0, 2, 3], [0, 1, 3]], dtype=np.int32)  # three triangles overlap
     assert _create(2, 1, xyz, cells) == bgk.BGK_E_INVALID
     # unknown collision model or boundary kind (only the first 2d wall entries are read)
-    assert _create(2, 1, m.xyz, m.cells, collision=2) == bgk.BGK_E_INVALID
+    assert _create(2, 1, m.xyz, m.cells, collision=3) == bgk.BGK_E_INVALID
     assert _create(2, 1, m.xyz, m.cells, walls=(0, 0, 3, 0, 0, 0)) == bgk.BGK_E_INVALID
     assert _create(2, 1, m.xyz, m.cells, walls=(0, -1, 0, 0, 0, 0)) == bgk.BGK_E_INVALID
     assert _create(3, 1, c.xyz, c.cells, walls=(0, 0, 0, 0, 0, 9)) == bgk.BGK_E_INVALID
