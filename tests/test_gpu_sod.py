@@ -85,3 +85,36 @@ def test_sod_iterations_grow_in_the_fluid_limit(integ):
         print("Sod nu=%g %s: iterations per step min %d max %d avg %.2f tot %d"
               % (1 / kn, integ, its.min(), its.max(), its.mean(), its.sum()))
     assert rows[1].mean() > 2.0 * rows[0].mean()
+
+
+def _density(knudsen, n_v, collision):
+    w = synth.workload_sod_strip(n_v=n_v, knudsen=knudsen, integrator="BE")
+    s = bgk.Solver.from_workload(w, precision="mixed", l_max=3000, collision=collision)
+    s.set_state_maxwellian(w.init)
+    s.set_inflow_maxwellian(w.inflow)
+    s.step(synth.SOD_STEPS)
+    n = s.get_moments()[:, 0]
+    s.close()
+    return w, n
+
+
+@pytest.mark.parametrize("knudsen", [1.0, 1e-3])
+def test_sod_projection_against_interpolation(knudsen):
+    """Sec. 5.1.1: L2 density errors of the projected and the interpolated Maxwellian as
+    the velocity grid is refined, against a projected run on 64x64 velocities (BE, 85
+    steps).  In the fluid limit the projection is markedly more accurate on coarse grids
+    (it keeps the collision invariants exactly); in the rarefied case both are close."""
+    w, ref = _density(knudsen, 64, "maxwellian")
+    wt = _weights(w)
+    nrm = np.sqrt(wt @ (ref * ref))
+    err = {}
+    for n_v in (8, 16, 32):
+        for col in ("maxwellian", "interpolated"):
+            _, n = _density(knudsen, n_v, col)
+            err[(n_v, col)] = np.sqrt(wt @ ((n - ref) ** 2)) / nrm
+    for n_v in (8, 16, 32):
+        print("Sod nu=%g n_v=%d: L2 density error projection %.3e interpolation %.3e"
+              % (1 / knudsen, n_v, err[(n_v, "maxwellian")], err[(n_v, "interpolated")]))
+    if knudsen < 1:
+        assert err[(8, "interpolated")] > 2 * err[(8, "maxwellian")]
+    assert err[(32, "maxwellian")] < err[(8, "maxwellian")]
