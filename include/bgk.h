@@ -54,12 +54,17 @@ enum { BGK_DTYPE_F64 = 0, BGK_DTYPE_F32 = 1 };
 
 /* Mesh of the spatial domain X (Sec. 3.1, Table 1): affine simplices, conforming. */
 typedef struct {
-  int dim;                      /* 2 (triangles) or 3 (tetrahedra) */
+  int dim;                      /* 2 (triangles or quadrilaterals) or 3 (tetrahedra) */
   int k_x;                      /* spatial degree: 1, or 2 for triangles */
   int n_vertices;
   const double* xyz;            /* host, [n_vertices][dim] */
   int n_cells;
-  const int32_t* cell_vertices; /* host, [n_cells][dim+1], positively oriented or not */
+  const int32_t* cell_vertices; /* host, [n_cells][dim+1] (simplices, either orientation) or
+                                   [n_cells][4] (quadrilaterals: vertices in order around the
+                                   cell, either direction) */
+  int shape;                    /* 0: simplices; 1: Q1 quadrilaterals (dim 2, k_x 1; Sec. 3.1's
+                                   bilinear element), which must be parallelograms (x0 + x2 =
+                                   x1 + x3 to 1e-12 of the cell size), else BGK_E_INVALID */
 } bgk_mesh;
 
 /* Velocity grid (Sec. 3.2): n_points per dimension on [-L, L], k_v+1 Gauss-Legendre

@@ -51,6 +51,7 @@ enum { INT_BE = 0, INT_DIRK2 = 1, INT_DIRK3 = 2, INT_BSTABLE2 = 3, INT_BDF2 = 4 
 
 typedef struct {
   int dim, kx, ndof, nface, fdof;
+  int quad, nvc; /* Q1 quadrilaterals (2D); vertices per cell */
   int nvert, ncell, nnode;
   const double *xyz_in;
   double *xyz;
@@ -233,23 +234,118 @@ static void sort_ints(int *v, int n) {
 
 /* global identity of local node a of cell c: vertex id, or sorted pair for a midpoint */
 static void node_identity(const orc_t *o, int c, int a, int *id2) {
-  const int *cv = o->cells + (size_t)c * (o->dim + 1);
-  if (a <= o->dim) { id2[0] = cv[a]; id2[1] = -1; return; }
+  const int *cv = o->cells + (size_t)c * o->nvc;
+  if (a < o->nvc) { id2[0] = cv[a]; id2[1] = -1; return; }
   int k = a - 3, l = (k + 1) % 3;
   int g0 = cv[k], g1 = cv[l];
   id2[0] = g0 < g1 ? g0 : g1; id2[1] = g0 < g1 ? g1 : g0;
 }
 
+/* Q1 quadrilateral (Sec. 3.1, the bilinear element): reference square [0,1]^2 with
+ * phi_0 = (1-s)(1-t), phi_1 = s(1-t), phi_2 = s t, phi_3 = (1-s) t at the vertices in cell
+ * order, the bilinear map x(s,t) = sum_a x_a phi_a(s,t) (any convex quadrilateral).
+ * M = int phi_a phi_b, G_al = int phi_b d_al phi_a with grad phi = J^-T grad_ref phi,
+ * integrated with 3x3 tensor Gauss-Legendre points: every integrand times |det J| is a
+ * polynomial of degree <= 3 in each of s and t, integrated exactly.  Face f is the
+ * straight edge from vertex f to vertex f+1 (mod 4); its mass matrix on the edge is
+ * integrated the same way in the edge parameter. */
+static void q1_phi(double s, double t, double *phi, double (*dphi)[2]) {
+  phi[0] = (1 - s) * (1 - t); phi[1] = s * (1 - t); phi[2] = s * t; phi[3] = (1 - s) * t;
+  dphi[0][0] = -(1 - t); dphi[0][1] = -(1 - s);
+  dphi[1][0] = 1 - t;    dphi[1][1] = -s;
+  dphi[2][0] = t;        dphi[2][1] = s;
+  dphi[3][0] = -t;       dphi[3][1] = 1 - s;
+}
+
+static int quad_cell_geometry(orc_t *o, int c, fkey_t *keys) {
+  const int nd = 4, nf = 4, d = 2;
+  const int *cv = o->cells + (size_t)c * 4;
+  double xg[3], wg[3];
+  gauss_legendre(3, xg, wg);
+  double *M = o->M + (size_t)c * nd * nd, *G = o->G + (size_t)c * d * nd * nd;
+  memset(M, 0, sizeof(double) * nd * nd);
+  memset(G, 0, sizeof(double) * d * nd * nd);
+  double vol = 0.0;
+  for (int qi = 0; qi < 3; ++qi)
+    for (int qj = 0; qj < 3; ++qj) {
+      double s = 0.5 * (xg[qi] + 1.0), t = 0.5 * (xg[qj] + 1.0), w = 0.25 * wg[qi] * wg[qj];
+      double phi[4], dphi[4][2], J[2][2] = {{0, 0}, {0, 0}};
+      q1_phi(s, t, phi, dphi);
+      for (int a = 0; a < 4; ++a)
+        for (int al = 0; al < 2; ++al)
+          for (int r = 0; r < 2; ++r) J[al][r] += o->xyz[(size_t)cv[a] * 2 + al] * dphi[a][r];
+      double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+      if (!(det > 0.0) && !(det < 0.0)) return ORC_E_INVALID;
+      double Ji[2][2] = {{J[1][1] / det, -J[0][1] / det}, {-J[1][0] / det, J[0][0] / det}};
+      double adet = fabs(det);
+      vol += w * adet;
+      double gphi[4][2];
+      for (int a = 0; a < 4; ++a)
+        for (int al = 0; al < 2; ++al) gphi[a][al] = dphi[a][0] * Ji[0][al] + dphi[a][1] * Ji[1][al];
+      for (int a = 0; a < nd; ++a)
+        for (int b = 0; b < nd; ++b) {
+          M[a * nd + b] += w * adet * phi[a] * phi[b];
+          for (int al = 0; al < d; ++al) G[((size_t)al * nd + a) * nd + b] += w * adet * phi[b] * gphi[a][al];
+        }
+    }
+  if (!(vol > 0.0)) return ORC_E_INVALID;
+  o->vol[c] = vol;
+  for (int f = 0; f < nf; ++f) {
+    int g[2] = {cv[f], cv[(f + 1) % 4]};
+    sort_ints(g, 2);
+    double N[3] = {0, 0, 0};
+    canon_normal(o, g, N);
+    double area = sqrt(N[0] * N[0] + N[1] * N[1]);
+    const double *xo = o->xyz + (size_t)cv[(f + 2) % 4] * 2, *x0 = o->xyz + (size_t)g[0] * 2;
+    double sd = (xo[0] - x0[0]) * N[0] + (xo[1] - x0[1]) * N[1];
+    int sg = sd < 0.0 ? 1 : -1;
+    size_t cf = (size_t)c * nf + f;
+    o->orient[cf] = sg;
+    o->farea[cf] = area;
+    for (int al = 0; al < d; ++al) {
+      o->ncan[cf * d + al] = N[al];
+      o->unit_n[cf * d + al] = sg * N[al] / area;
+    }
+    /* edge from vertex f to f+1: reference points (s, t)(e) along it, e in [0, 1] */
+    static const double e0[4][2] = {{0, 0}, {1, 0}, {1, 1}, {0, 1}};
+    double *Fm = o->Fm + cf * nd * nd;
+    memset(Fm, 0, sizeof(double) * nd * nd);
+    for (int q = 0; q < 3; ++q) {
+      double e = 0.5 * (xg[q] + 1.0), w = 0.5 * wg[q] * area;
+      const double *pa = e0[f], *pb = e0[(f + 1) % 4];
+      double phi[4], dphi[4][2];
+      q1_phi(pa[0] + e * (pb[0] - pa[0]), pa[1] + e * (pb[1] - pa[1]), phi, dphi);
+      for (int a = 0; a < nd; ++a)
+        for (int b = 0; b < nd; ++b) Fm[a * nd + b] += w * phi[a] * phi[b];
+    }
+    fkey_t *k = &keys[cf];
+    k->g[0] = g[0]; k->g[1] = g[1]; k->g[2] = -1;
+    k->cell = c; k->face = f;
+    o->nbr[cf] = -1; o->nbr_face[cf] = -1;
+  }
+  return ORC_OK;
+}
+
 static int build_geometry(orc_t *o) {
   int d = o->dim, nd = o->ndof, nf = o->nface;
-  /* local nodes on the face opposite vertex f */
+  /* local nodes on face f: simplices, the face opposite vertex f; quadrilaterals, the
+   * edge from vertex f to vertex f+1 */
   for (int f = 0; f < nf; ++f) {
     int m = 0;
+    if (o->quad) {
+      o->face_nodes[f * o->fdof] = f;
+      o->face_nodes[f * o->fdof + 1] = (f + 1) % 4;
+      continue;
+    }
     for (int a = 0; a <= d; ++a) if (a != f) o->face_nodes[f * o->fdof + m++] = a;
     if (o->kx == 2) o->face_nodes[f * o->fdof + m++] = 3 + (f + 1) % 3;
   }
   fkey_t *keys = malloc(sizeof(fkey_t) * (size_t)o->ncell * nf);
   for (int c = 0; c < o->ncell; ++c) {
+    if (o->quad) {
+      if (quad_cell_geometry(o, c, keys) != ORC_OK) { free(keys); return ORC_E_INVALID; }
+      continue;
+    }
     const int *cv = o->cells + (size_t)c * (d + 1);
     const double *x0 = o->xyz + (size_t)cv[0] * d;
     /* affine map x = x0 + J xi, J columns x_i - x0 */
@@ -729,22 +825,24 @@ void orc_destroy(orc_t *o) {
   free(o);
 }
 
-/* Build mesh geometry and the velocity grid.  n1d points per dimension, kv+1 Gauss
- * points per velocity cell, V = [-L, L]^dim. Returns NULL on invalid input. */
-orc_t *orc_create(int dim, int kx, int nvert, const double *xyz, int ncell, const int *cells, int n1d, int kv,
-                  double L) {
+/* Geometry and velocity grid of a simplex or (quad = 1) quadrilateral mesh. */
+static orc_t *create_impl(int dim, int kx, int quad, int nvert, const double *xyz, int ncell, const int *cells,
+                          int n1d, int kv, double L) {
   if ((dim != 2 && dim != 3) || (kx != 1 && kx != 2) || (kx == 2 && dim != 2)) return NULL;
+  if (quad && (dim != 2 || kx != 1)) return NULL;
   if (kv < 1 || kv > 4 || n1d % (kv + 1) != 0 || n1d > 64 || !(L > 0.0)) return NULL;
   orc_t *o = calloc(1, sizeof(orc_t));
   o->dim = dim; o->kx = kx; o->nvert = nvert; o->ncell = ncell;
-  o->ndof = kx == 1 ? dim + 1 : 6;
-  o->nface = dim + 1;
+  o->quad = quad;
+  o->nvc = quad ? 4 : dim + 1;
+  o->ndof = quad ? 4 : kx == 1 ? dim + 1 : 6;
+  o->nface = quad ? 4 : dim + 1;
   o->fdof = kx == 1 ? dim : 3;
   o->nnode = ncell * o->ndof;
   o->xyz = malloc(sizeof(double) * (size_t)nvert * dim);
   memcpy(o->xyz, xyz, sizeof(double) * (size_t)nvert * dim);
-  o->cells = malloc(sizeof(int) * (size_t)ncell * (dim + 1));
-  memcpy(o->cells, cells, sizeof(int) * (size_t)ncell * (dim + 1));
+  o->cells = malloc(sizeof(int) * (size_t)ncell * o->nvc);
+  memcpy(o->cells, cells, sizeof(int) * (size_t)ncell * o->nvc);
   o->n1d = n1d; o->kv = kv; o->L = L;
   o->nv = 1;
   for (int i = 0; i < dim; ++i) o->nv *= n1d;
@@ -783,13 +881,25 @@ orc_t *orc_create(int dim, int kx, int nvert, const double *xyz, int ncell, cons
   o->nbr_node = malloc(sizeof(int) * ncell * nf * MAXDOF);
   o->face_nodes = malloc(sizeof(int) * nf * o->fdof);
   for (int c = 0; c < ncell; ++c)
-    for (int k = 0; k <= dim; ++k) {
-      int g = cells[(size_t)c * (dim + 1) + k];
+    for (int k = 0; k < o->nvc; ++k) {
+      int g = cells[(size_t)c * o->nvc + k];
       if (g < 0 || g >= nvert) { orc_destroy(o); return NULL; }
     }
   if (build_geometry(o) != ORC_OK) { orc_destroy(o); return NULL; }
   o->nu = 0.0; o->dt = 1.0; o->tau = 1e-8; o->integrator = INT_BE; o->lmax = 1000;
   return o;
+}
+
+/* Build mesh geometry and the velocity grid.  n1d points per dimension, kv+1 Gauss
+ * points per velocity cell, V = [-L, L]^dim. Returns NULL on invalid input. */
+orc_t *orc_create(int dim, int kx, int nvert, const double *xyz, int ncell, const int *cells, int n1d, int kv,
+                  double L) {
+  return create_impl(dim, kx, 0, nvert, xyz, ncell, cells, n1d, kv, L);
+}
+
+/* The same on Q1 quadrilaterals: cells [ncell][4], vertices in order around each cell. */
+orc_t *orc_create_quad(int nvert, const double *xyz, int ncell, const int *cells, int n1d, int kv, double L) {
+  return create_impl(2, 1, 1, nvert, xyz, ncell, cells, n1d, kv, L);
 }
 
 int orc_info(const orc_t *o, int *out) {

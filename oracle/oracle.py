@@ -49,6 +49,8 @@ def _load():
         up = np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")
         lib.orc_create.restype = P
         lib.orc_create.argtypes = [C.c_int, C.c_int, C.c_int, dp, C.c_int, ip, C.c_int, C.c_int, C.c_double]
+        lib.orc_create_quad.restype = P
+        lib.orc_create_quad.argtypes = [C.c_int, dp, C.c_int, ip, C.c_int, C.c_int, C.c_double]
         lib.orc_destroy.argtypes = [P]
         lib.orc_info.argtypes = [P, ip]
         lib.orc_velocity.argtypes = [P, dp, dp, dp, dp]
@@ -98,7 +100,10 @@ class Oracle:
         self.dim, self.kx, self.n1d, self.kv, self.L = dim, kx, n1d, kv, L
         xyz = np.ascontiguousarray(xyz, dtype=np.float64)
         cells = np.ascontiguousarray(cells, dtype=np.int32)
-        self.h = self.lib.orc_create(dim, kx, xyz.shape[0], xyz, cells.shape[0], cells, n1d, kv, float(L))
+        if dim == 2 and cells.shape[1] == 4:       # Q1 quadrilaterals
+            self.h = self.lib.orc_create_quad(xyz.shape[0], xyz, cells.shape[0], cells, n1d, kv, float(L))
+        else:
+            self.h = self.lib.orc_create(dim, kx, xyz.shape[0], xyz, cells.shape[0], cells, n1d, kv, float(L))
         if not self.h:
             raise ValueError("oracle rejected the problem")
         info = np.zeros(5, dtype=np.int32)

@@ -28,7 +28,12 @@ class BgkError(RuntimeError):
 
 class Mesh(C.Structure):
     _fields_ = [("dim", C.c_int), ("k_x", C.c_int), ("n_vertices", C.c_int), ("xyz", C.c_void_p),
-                ("n_cells", C.c_int), ("cell_vertices", C.c_void_p)]
+                ("n_cells", C.c_int), ("cell_vertices", C.c_void_p), ("shape", C.c_int)]
+
+
+def _shape(dim, cells):
+    """0: simplices; 1: Q1 quadrilaterals (2D cells of four vertices)."""
+    return 1 if dim == 2 and cells.shape[1] == 4 else 0
 
 
 class VGrid(C.Structure):
@@ -177,7 +182,8 @@ class Solver:
         self.lib = load()
         self._xyz = np.ascontiguousarray(xyz, dtype=np.float64)
         self._cells = np.ascontiguousarray(cells, dtype=np.int32)
-        m = Mesh(dim, kx, self._xyz.shape[0], _ptr(self._xyz), self._cells.shape[0], _ptr(self._cells))
+        m = Mesh(dim, kx, self._xyz.shape[0], _ptr(self._xyz), self._cells.shape[0], _ptr(self._cells),
+                 _shape(dim, self._cells))
         vg = VGrid(float(L), int(n_v), int(k_v))
         ph = Physics(float(nu), INTEGRATORS[integrator], float(dt), float(cfl), COLLISIONS[collision],
                      _wall_kinds(walls))
@@ -377,7 +383,8 @@ class Batch:
             xyz = np.ascontiguousarray(w.mesh.xyz, dtype=np.float64)
             cells = np.ascontiguousarray(w.mesh.cells, dtype=np.int32)
             self._keep += [xyz, cells]
-            meshes[i] = Mesh(w.mesh.dim, w.kx, xyz.shape[0], _ptr(xyz), cells.shape[0], _ptr(cells))
+            meshes[i] = Mesh(w.mesh.dim, w.kx, xyz.shape[0], _ptr(xyz), cells.shape[0], _ptr(cells),
+                             _shape(w.mesh.dim, cells))
             vgrids[i] = VGrid(float(w.L), int(w.n_v), int(w.k_v))
             phys[i] = Physics(float(w.nu), INTEGRATORS["BE"], float(dt[i]) if dt else 0.0, float(w.cfl), 0,
                               _wall_kinds(walls))

@@ -21,7 +21,7 @@ struct BatchInst {
   const void* Ainv;
   const DevState* ds;
   double nus;
-  int type;    // 0 P1 triangle, 1 P2 triangle, 2 P1 tetrahedron
+  int type;    // 0 P1 triangle, 1 P2 triangle, 2 P1 tetrahedron, 3 Q1 parallelogram
   int B;       // ordinates per CTA
   int cached;  // local inverses available for nus
   int nv;
@@ -63,6 +63,8 @@ __global__ void __launch_bounds__(128, 4) k_sweep_batched(const BatchInst* __res
         batch_sweep_one<T, ElemP2Tri>(I, j, tid, nt, bar);
       else if (I.type == 0)
         batch_sweep_one<T, ElemP1Tri>(I, j, tid, nt, bar);
+      else if (I.type == 3)
+        batch_sweep_one<T, ElemQ1Quad>(I, j, tid, nt, bar);
       else
         batch_sweep_one<T, ElemP1Tet>(I, j, tid, nt, bar);
     }
@@ -120,7 +122,7 @@ void trace(const char* what, int i) {
   }
 }
 
-int inst_type(const bgk_handle* h) { return h->hm.dim == 3 ? 2 : (h->hm.kx == 2 ? 1 : 0); }
+int inst_type(const bgk_handle* h) { return h->hm.dim == 3 ? 2 : h->hm.quad ? 3 : (h->hm.kx == 2 ? 1 : 0); }
 
 // Class of an instance for the autotuner: element type, velocity points, cells (log2 bucket).
 uint64_t tune_key(const bgk_handle* h) {

@@ -19,7 +19,8 @@ int guess_buffers(bgk_handle* h) {
 // Features of the current moments U[it & 1] into gX, then U_hist <- U.
 void guess_features_launch(bgk_handle* h) {
   const int c = h->hm.ncell;
-  k_guess_features<<<(c + 127) / 128, 128, 0, h->stream>>>(h->hm.dim, h->hm.ndof, c, h->geo, h->hm.geo_stride,
+  k_guess_features<<<(c + 127) / 128, 128, 0, h->stream>>>(h->hm.dim, h->hm.ndof, h->hm.quad ? 1 : 0, c, h->geo,
+                                                          h->hm.geo_stride,
                                                            h->U[0], h->U[1], h->ds, h->Uhist, h->have_hist, h->dt,
                                                            h->phys.nu, h->gX);
   k_guess_history<<<148 * 4, 256, 0, h->stream>>>(h->nnode, h->nm, h->U[0], h->U[1], h->ds, h->Uhist, h->have_hist);

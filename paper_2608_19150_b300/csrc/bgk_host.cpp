@@ -51,17 +51,103 @@ struct FaceKey {
 };
 
 // identity of a local node: a vertex id, or the sorted vertex pair of an edge midpoint
-std::pair<int, int> node_id(const int* cv, int dim, int a) {
-  if (a <= dim) return {cv[a], -1};
+// (nvc: vertices per cell; every node of a Q1 quadrilateral is a vertex)
+std::pair<int, int> node_id(const int* cv, int nvc, int a) {
+  if (a < nvc) return {cv[a], -1};
   int k = a - 3, l = (k + 1) % 3;
   return {std::min(cv[k], cv[l]), std::max(cv[k], cv[l])};
 }
 
 }  // namespace
 
+int finish_host_mesh(const int32_t* CV, int nv, HostMesh& hm);
+
+// Q1 quadrilaterals (Sec. 3.1): four vertices per cell in order around it, nodes at the
+// vertices, face i the edge from vertex i to vertex i+1.  Only parallelograms: their
+// bilinear map is affine, so the local matrices are the reference tables combined with
+// the face normals (ElemQ1Quad); a cell with x0 + x2 != x1 + x3 is rejected.
+int build_host_mesh_quad(const bgk_mesh* m, HostMesh& hm) {
+  if (m->dim != 2 || m->k_x != 1) return BGK_E_INVALID;
+  if (m->n_cells <= 0 || m->n_vertices <= 0 || !m->xyz || !m->cell_vertices) return BGK_E_INVALID;
+  if (m->n_cells > (int)kCellMask) return BGK_E_INVALID;
+  const int d = 2, nv = 4;
+  hm.dim = 2;
+  hm.kx = 1;
+  hm.quad = true;
+  hm.nf = 4;
+  hm.ndof = 4;
+  hm.fd = 2;
+  hm.ncell = m->n_cells;
+  hm.nvert = m->n_vertices;
+  hm.geo_stride = 10;  // N_0 .. N_3, 1/|K|, padding
+  hm.geo.assign((size_t)hm.ncell * hm.geo_stride, 0.0);
+  hm.nbr.assign((size_t)hm.ncell * 4, INT32_MIN);
+  hm.nbr_face.assign((size_t)hm.ncell * 4, -1);
+  hm.perm.assign(hm.ncell, 0);
+  const double* X = m->xyz;
+  const int32_t* CV = m->cell_vertices;
+  std::map<FaceKey, std::pair<int, int>> open;
+  double min_vol = INFINITY;
+  for (int c = 0; c < hm.ncell; ++c) {
+    const int* cv = CV + (size_t)c * nv;
+    for (int a = 0; a < nv; ++a)
+      if (cv[a] < 0 || cv[a] >= hm.nvert) return BGK_E_INVALID;
+    const double* p[4];
+    for (int a = 0; a < 4; ++a) p[a] = X + 2 * (size_t)cv[a];
+    // parallelogram: x0 + x2 = x1 + x3 (relative to the longest edge)
+    double hmax = 0.0;
+    for (int a = 0; a < 4; ++a) {
+      const double ex = p[(a + 1) % 4][0] - p[a][0], ey = p[(a + 1) % 4][1] - p[a][1];
+      hmax = std::max(hmax, std::sqrt(ex * ex + ey * ey));
+    }
+    for (int al = 0; al < 2; ++al)
+      if (!(std::fabs(p[0][al] + p[2][al] - p[1][al] - p[3][al]) <= 1e-12 * hmax)) return BGK_E_INVALID;
+    const double vol = std::fabs((p[1][0] - p[0][0]) * (p[3][1] - p[0][1]) - (p[1][1] - p[0][1]) * (p[3][0] - p[0][0]));
+    if (!(vol > 0.0) || !std::isfinite(vol)) return BGK_E_INVALID;
+    min_vol = std::min(min_vol, vol);
+    double* G = hm.geo.data() + (size_t)c * hm.geo_stride;
+    G[hm.nf * d] = 1.0 / vol;
+    for (int f = 0; f < 4; ++f) {
+      int g[3] = {cv[f], cv[(f + 1) % 4], -1};
+      std::sort(g, g + 2);
+      double N[3] = {0, 0, 0};
+      canonical_normal(X, d, g, N);
+      // outward: a vertex off the face lies on the negative side
+      const int off = cv[(f + 2) % 4];
+      double sd = 0.0;
+      for (int al = 0; al < d; ++al) sd += (X[(size_t)off * d + al] - X[(size_t)g[0] * d + al]) * N[al];
+      if (sd == 0.0) return BGK_E_INVALID;
+      const double sg = sd < 0.0 ? 1.0 : -1.0;
+      for (int al = 0; al < d; ++al) G[f * d + al] = sg * N[al];
+      FaceKey key{{g[0], g[1], -1}};
+      auto it = open.find(key);
+      if (it == open.end()) {
+        open.emplace(key, std::make_pair(c, f));
+      } else {
+        int c2 = it->second.first, f2 = it->second.second;
+        if (c2 == c) return BGK_E_INVALID;
+        if (hm.nbr[(size_t)c2 * 4 + f2] != INT32_MIN) return BGK_E_INVALID;
+        const double* G2 = hm.geo.data() + (size_t)c2 * hm.geo_stride + f2 * d;
+        double dn = 0.0;
+        for (int al = 0; al < d; ++al) dn += G[f * d + al] * G2[al];
+        if (!(dn < 0.0)) return BGK_E_INVALID;
+        hm.nbr[(size_t)c * 4 + f] = c2;
+        hm.nbr_face[(size_t)c * 4 + f] = f2;
+        hm.nbr[(size_t)c2 * 4 + f2] = c;
+        hm.nbr_face[(size_t)c2 * 4 + f2] = f;
+        open.erase(it);
+      }
+    }
+  }
+  hm.min_vol = min_vol;
+  return finish_host_mesh(CV, nv, hm);
+}
+
 int build_host_mesh(const bgk_mesh* m, HostMesh& hm) {
   if (!m || (m->dim != 2 && m->dim != 3) || (m->k_x != 1 && m->k_x != 2) || (m->k_x == 2 && m->dim != 2))
     return BGK_E_INVALID;
+  if (m->shape != 0 && m->shape != 1) return BGK_E_INVALID;
+  if (m->shape == 1) return build_host_mesh_quad(m, hm);
   if (m->n_cells <= 0 || m->n_vertices <= 0 || !m->xyz || !m->cell_vertices) return BGK_E_INVALID;
   if (m->n_cells > (int)kCellMask) return BGK_E_INVALID;
   const int d = m->dim, nv = d + 1;
@@ -138,7 +224,13 @@ int build_host_mesh(const bgk_mesh* m, HostMesh& hm) {
     }
   }
   hm.min_vol = min_vol;
-  // boundary faces, numbered in (cell, face) order; node permutations across faces
+  return finish_host_mesh(CV, nv, hm);
+}
+
+// Boundary faces (numbered in (cell, face) order), their nodes and sides, and the node
+// permutations across interior faces.
+int finish_host_mesh(const int32_t* CV, int nv, HostMesh& hm) {
+  const int d = hm.dim;
   int nb = 0;
   for (int c = 0; c < hm.ncell; ++c)
     for (int f = 0; f < hm.nf; ++f)
@@ -167,16 +259,17 @@ int build_host_mesh(const bgk_mesh* m, HostMesh& hm) {
     for (int f = 0; f < hm.nf; ++f) {
       int n2 = hm.nbr[(size_t)c * 4 + f];
       for (int k = 0; k < hm.fd; ++k) {
-        int a = hm.kx == 1 ? (d == 2 ? ElemP1Tri::fn(f, k) : ElemP1Tet::fn(f, k)) : ElemP2Tri::fn(f, k);
+        int a = hm.quad ? ElemQ1Quad::fn(f, k)
+                        : hm.kx == 1 ? (d == 2 ? ElemP1Tri::fn(f, k) : ElemP1Tet::fn(f, k)) : ElemP2Tri::fn(f, k);
         if (n2 < 0) {
           hm.bnode[(size_t)(-n2 - 1) * hm.fd + k] = c * hm.ndof + a;
           continue;
         }
-        auto id = node_id(cv, d, a);
+        auto id = node_id(cv, nv, a);
         const int* cv2 = CV + (size_t)n2 * nv;
         int match = -1;
         for (int b = 0; b < hm.ndof; ++b)
-          if (node_id(cv2, d, b) == id) { match = b; break; }
+          if (node_id(cv2, nv, b) == id) { match = b; break; }
         if (match < 0) return BGK_E_INVALID;  // non-conforming
         pm |= (uint64_t)match << (16 * f + 4 * k);
       }

@@ -35,6 +35,7 @@ struct VGrid {
 // outward area-weighted face normals N_i (face i opposite vertex i) and 1/|K|.
 struct HostMesh {
   int dim = 0, kx = 0, ndof = 0, nf = 0, fd = 0, ncell = 0, nvert = 0, nbface = 0, geo_stride = 0;
+  bool quad = false;              // Q1 parallelograms (2D, 4 vertices per cell) instead of simplices
   std::vector<double> geo;        // [cell][geo_stride]: N_0 .. N_d (dim each), 1/|K|
   std::vector<int32_t> nbr;       // [cell][4]: neighbour id, or -(boundary face + 1)
   std::vector<int32_t> nbr_face;  // [cell][4]: face index of this face in the neighbour

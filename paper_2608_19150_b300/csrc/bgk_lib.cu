@@ -267,6 +267,7 @@ void launch_inverse_t(bgk_handle* h, double nus) {
 int build_inverse_cache(bgk_handle* h, double nus) {
   const bool f64s = h->precision == BGK_FP64;
   const int as = h->hm.dim == 3 ? (f64s ? ainv_stride<ElemP1Tet, double>() : ainv_stride<ElemP1Tet, float>())
+                 : h->hm.quad    ? (f64s ? ainv_stride<ElemQ1Quad, double>() : ainv_stride<ElemQ1Quad, float>())
                  : h->hm.kx == 2 ? (f64s ? ainv_stride<ElemP2Tri, double>() : ainv_stride<ElemP2Tri, float>())
                                  : (f64s ? ainv_stride<ElemP1Tri, double>() : ainv_stride<ElemP1Tri, float>());
   h->ainv_bytes = (size_t)h->g.nv * h->hm.ncell * as * h->tsize;
@@ -287,6 +288,8 @@ int build_inverse_cache(bgk_handle* h, double nus) {
   const bool f64 = h->precision == BGK_FP64;
   if (h->hm.dim == 3)
     f64 ? launch_inverse_t<ElemP1Tet, double>(h, nus) : launch_inverse_t<ElemP1Tet, float>(h, nus);
+  else if (h->hm.quad)
+    f64 ? launch_inverse_t<ElemQ1Quad, double>(h, nus) : launch_inverse_t<ElemQ1Quad, float>(h, nus);
   else if (h->hm.kx == 2)
     f64 ? launch_inverse_t<ElemP2Tri, double>(h, nus) : launch_inverse_t<ElemP2Tri, float>(h, nus);
   else
@@ -300,6 +303,8 @@ template <typename T>
 void launch_sweep(bgk_handle* h, double nus, int jb, int je) {
   if (h->hm.dim == 3)
     launch_sweep_t<ElemP1Tet, T>(h, nus, jb, je);
+  else if (h->hm.quad)
+    launch_sweep_t<ElemQ1Quad, T>(h, nus, jb, je);
   else if (h->hm.kx == 2)
     launch_sweep_t<ElemP2Tri, T>(h, nus, jb, je);
   else
@@ -589,7 +594,10 @@ int build_dags(bgk_handle* h) {
   const size_t smem = (size_t)((n + 3) / 4) * 4;
   if (smem > 200 * 1024) return BGK_E_INVALID;
   auto peel = [&](int nblk, const int32_t* jl, const uint8_t* lag) {
-    if (h->hm.dim == 2) {
+    if (h->hm.quad) {
+      k_peel<2, 4><<<nblk, threads, smem, h->stream>>>(h->geo, h->hm.geo_stride, h->nbr, h->nbr_face, n, h->g, jl, lag,
+                                                       h->glist, h->lvl, h->ngen, h->nproc);
+    } else if (h->hm.dim == 2) {
       k_peel<2, 3><<<nblk, threads, smem, h->stream>>>(h->geo, h->hm.geo_stride, h->nbr, h->nbr_face, n, h->g, jl, lag,
                                                        h->glist, h->lvl, h->ngen, h->nproc);
     } else {
@@ -830,6 +838,7 @@ int bgk_create(const bgk_mesh* mesh, const bgk_vgrid* vg, const bgk_physics* phy
   CK(cudaFuncSetAttribute(k_maxwell<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   CK(cudaFuncSetAttribute(k_peel<2, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   CK(cudaFuncSetAttribute(k_peel<3, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  CK(cudaFuncSetAttribute(k_peel<2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   CK(cudaFuncSetAttribute(k_sweep<ElemP1Tri, double, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           96 * 1024));
   CK(cudaFuncSetAttribute(k_sweep<ElemP2Tri, double, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -841,6 +850,10 @@ int bgk_create(const bgk_mesh* mesh, const bgk_vgrid* vg, const bgk_physics* phy
   CK(cudaFuncSetAttribute(k_sweep<ElemP2Tri, float, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           96 * 1024));
   CK(cudaFuncSetAttribute(k_sweep<ElemP1Tet, float, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          96 * 1024));
+  CK(cudaFuncSetAttribute(k_sweep<ElemQ1Quad, double, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          96 * 1024));
+  CK(cudaFuncSetAttribute(k_sweep<ElemQ1Quad, float, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           96 * 1024));
   rc = build_dags(h);
   if (rc == BGK_OK) {

@@ -32,7 +32,7 @@ __device__ __forceinline__ void prim_log(const double* U, int d, double* q) {
   q[1 + d] = log(fmax(th, 1e-300));
 }
 
-__global__ void k_guess_features(int d, int ndof, int ncell, const double* __restrict__ geo, int gs,
+__global__ void k_guess_features(int d, int ndof, int quad, int ncell, const double* __restrict__ geo, int gs,
                                  const double* __restrict__ U0, const double* __restrict__ U1,
                                  const DevState* __restrict__ ds, const double* __restrict__ Uhist,
                                  const int* __restrict__ have_hist, double dt, double nu, float* __restrict__ X) {
@@ -40,16 +40,26 @@ __global__ void k_guess_features(int d, int ndof, int ncell, const double* __res
   if (c >= ncell) return;
   const int nm = d + 2, F = guess_features(d);
   const double* U = ((ds->it & 1) == 0) ? U0 : U1;
+  const int nvx = quad ? 4 : d + 1;  // vertices (the first nodes of the cell)
   double qv[4][5];  // vertex values of q
-  for (int a = 0; a <= d; ++a) prim_log(U + (size_t)(c * ndof + a) * nm, d, qv[a]);
+  for (int a = 0; a < nvx; ++a) prim_log(U + (size_t)(c * ndof + a) * nm, d, qv[a]);
   const double* G = geo + (size_t)c * gs;
-  const double invK = G[(d + 1) * d];
+  const double invK = G[nvx * d];
   double grad[5][3] = {{0}};
-  for (int a = 0; a <= d; ++a)
-    for (int al = 0; al < d; ++al) {
-      const double gl = -G[a * d + al] * invK / d;
-      for (int m = 0; m < nm; ++m) grad[m][al] += qv[a][m] * gl;
-    }
+  if (quad) {
+    // mean gradient of the bilinear interpolant: (1/|K|) sum_faces N_f (q_f + q_f+1) / 2
+    for (int f = 0; f < 4; ++f)
+      for (int al = 0; al < d; ++al) {
+        const double gl = 0.5 * G[f * d + al] * invK;
+        for (int m = 0; m < nm; ++m) grad[m][al] += (qv[f][m] + qv[(f + 1) % 4][m]) * gl;
+      }
+  } else {
+    for (int a = 0; a <= d; ++a)
+      for (int al = 0; al < d; ++al) {
+        const double gl = -G[a * d + al] * invK / d;
+        for (int m = 0; m < nm; ++m) grad[m][al] += qv[a][m] * gl;
+      }
+  }
   const double lnd = log10(fmax(nu * dt, 1e-30));
   const bool hist = *have_hist != 0;
   for (int a = 0; a < ndof; ++a) {

@@ -11,7 +11,8 @@ is a fixed combination of |K| and s_i = v . N_i:
 with Mh = (1/|K|) int phi_a phi_b, Dd_i = (1/(d |K|)) int phi_b d phi_a / d l_i and
 Eh_i = (1/|F_i|) int_{F_i} phi_a phi_b.  This script integrates the products exactly
 with rational arithmetic (int over a k-simplex of prod l^e = k! |S| prod e! / (k+|e|)!)
-and writes them as constexpr doubles.  Run: python gen_tables.py > bgk_tables.h
+and writes them as constexpr doubles.  Q1 parallelograms: see q1_tables.
+Run: python gen_tables.py > bgk_tables.h
 """
 from fractions import Fraction as Fr
 from math import factorial
@@ -75,7 +76,69 @@ def integ(p, k, skip=None):
     return s
 
 
+def q1_tables():
+    """Q1 on a parallelogram K = x0 + J [0,1]^2, nodes at the vertices in cell order
+    (phi_0 = (1-s)(1-t), phi_1 = s(1-t), phi_2 = st, phi_3 = (1-s)t), face i from vertex i
+    to vertex i+1.  The area-weighted outward normal of the face s = 1 (face 1) is
+    N_1 = |K| J^-T e_s and that of t = 1 (face 2) is N_2 = |K| J^-T e_t, the opposite faces'
+    are their negatives, so v . grad phi = (s_1 d_s + s_2 d_t) phi / |K| with s_i = v . N_i:
+
+      -(1/|K|) int phi_b v.grad phi_a = -r_1 G_s[a][b] - r_2 G_t[a][b],   G_x = int_[0,1]^2 phi_b d_x phi_a
+
+    written symmetrically over the opposite faces (r_3 = -r_1, r_0 = -r_2):
+    Dd_1 = -G_s/2, Dd_3 = +G_s/2, Dd_2 = -G_t/2, Dd_0 = +G_t/2.  Mh = int phi_a phi_b over
+    the unit square, Eh_i the edge mass over the unit edge."""
+    # polynomials in (s, t) as {(p, q): coefficient}
+    one = {(0, 0): Fr(1)}
+    s_ = {(1, 0): Fr(1)}
+    t_ = {(0, 1): Fr(1)}
+    oms = {(0, 0): Fr(1), (1, 0): Fr(-1)}
+    omt = {(0, 0): Fr(1), (0, 1): Fr(-1)}
+    phi = [mul(oms, omt), mul(s_, omt), mul(s_, t_), mul(oms, t_)]
+    del one
+
+    def d(p, k):
+        r = {}
+        for e, c in p.items():
+            if e[k]:
+                e2 = list(e)
+                e2[k] -= 1
+                r[tuple(e2)] = r.get(tuple(e2), 0) + c * e[k]
+        return r
+
+    def sq(p):
+        return sum(c * Fr(1, (e[0] + 1) * (e[1] + 1)) for e, c in p.items())
+
+    def edge(p, i):
+        # face i: (0) t=0, s from 0 to 1; (1) s=1; (2) t=1; (3) s=0 -- integrate over the unit edge
+        tot = Fr(0)
+        for e, c in p.items():
+            if i == 0:
+                tot += c * (Fr(1, e[0] + 1) if e[1] == 0 else 0)
+            elif i == 1:
+                tot += c * Fr(1, e[1] + 1)
+            elif i == 2:
+                tot += c * Fr(1, e[0] + 1)
+            else:
+                tot += c * (Fr(1, e[1] + 1) if e[0] == 0 else 0)
+        return tot
+    nd = 4
+    Mh = [[sq(mul(phi[a], phi[b])) for b in range(nd)] for a in range(nd)]
+    Gs = [[sq(mul(phi[b], d(phi[a], 0))) for b in range(nd)] for a in range(nd)]
+    Gt = [[sq(mul(phi[b], d(phi[a], 1))) for b in range(nd)] for a in range(nd)]
+    half = Fr(1, 2)
+    Dd = [[[Gt[a][b] * half for b in range(nd)] for a in range(nd)],
+          [[-Gs[a][b] * half for b in range(nd)] for a in range(nd)],
+          [[-Gt[a][b] * half for b in range(nd)] for a in range(nd)],
+          [[Gs[a][b] * half for b in range(nd)] for a in range(nd)]]
+    Eh = [[[edge(mul(phi[a], phi[b]), i) for b in range(nd)] for a in range(nd)] for i in range(4)]
+    fn = [[i, (i + 1) % 4] for i in range(4)]
+    return 2, nd, 4, Mh, Dd, Eh, fn
+
+
 def tables(kind):
+    if kind == "q1quad":
+        return q1_tables()
     nv, phi = basis(kind)
     d = nv - 1
     nd = len(phi)
@@ -161,5 +224,5 @@ if __name__ == "__main__":
     print("#else")
     print("#define BGK_HD __host__ __device__")
     print("#endif")
-    for name, kind in (("ElemP1Tri", "p1tri"), ("ElemP2Tri", "p2tri"), ("ElemP1Tet", "p1tet")):
+    for name, kind in (("ElemP1Tri", "p1tri"), ("ElemP2Tri", "p2tri"), ("ElemP1Tet", "p1tet"), ("ElemQ1Quad", "q1quad")):
         print(emit(name, kind))

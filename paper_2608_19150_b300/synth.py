@@ -113,6 +113,23 @@ def rect_mesh(nx: int, ny: int, seed: int, jitter: float = 0.2) -> Mesh:
     return Mesh(2, xyz, cells, n_side=nx, seed=seed, meta={"ny": ny})
 
 
+def rect_quad_mesh(nx: int, ny: int, x0=0.0, x1=1.0, y0=0.0, y1=None, shear=0.0) -> Mesh:
+    """[x0, x1] x [y0, y1] as an nx x ny grid of Q1 quadrilaterals (vertices counter-
+    clockwise from the lower left); y1 defaults to a square-celled strip.  shear > 0 slants
+    every cell into a parallelogram: x += shear * (y - y0)."""
+    h = (x1 - x0) / nx
+    if y1 is None:
+        y1 = y0 + ny * h
+    xs, ys = np.linspace(x0, x1, nx + 1), np.linspace(y0, y1, ny + 1)
+    ii, jj = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1), indexing="ij")
+    xyz = np.stack([xs[ii.ravel()], ys[jj.ravel()]], axis=1).astype(np.float64)
+    xyz[:, 0] += shear * (xyz[:, 1] - y0)
+    vid = lambda i, j: i * (ny + 1) + j  # noqa: E731
+    cells = np.array([[vid(i, j), vid(i + 1, j), vid(i + 1, j + 1), vid(i, j + 1)]
+                      for i in range(nx) for j in range(ny)], dtype=np.int32)
+    return Mesh(2, xyz, cells, n_side=nx, meta={"ny": ny, "quad": True})
+
+
 # Kuhn (Freudenthal) split of the unit cube into 6 tetrahedra sharing the main
 # diagonal from corner 0 to corner 7; corners are indexed by bits (x, y, z).
 _KUHN = [(0, 1, 3, 7), (0, 3, 2, 7), (0, 2, 6, 7), (0, 6, 4, 7), (0, 4, 5, 7), (0, 5, 1, 7)]
@@ -167,7 +184,7 @@ def node_coords(mesh: Mesh, kx: int) -> np.ndarray:
     """Positions of the spatial DG nodes, [n_cells, n_nodes, dim], in the cell node order."""
     p = mesh.xyz[mesh.cells]
     if kx == 1:
-        return p.copy()
+        return p.copy()          # P1 simplices and Q1 quadrilaterals: the vertices
     if kx == 2 and mesh.dim == 2:
         mids = [(p[:, 0] + p[:, 1]) * 0.5, (p[:, 1] + p[:, 2]) * 0.5, (p[:, 2] + p[:, 0]) * 0.5]
         return np.concatenate([p, np.stack(mids, axis=1)], axis=1)
@@ -250,7 +267,7 @@ SOD_STEPS = 85            # Sec. 5.1.1: 85 steps of 1.76e-3 to t = 0.15 (0.14960
 
 
 def workload_sod_strip(nx=256, ny=6, kx=2, n_v=32, k_v=3, L=6.0, knudsen=1e-3, integrator="BE",
-                       dt=1.76e-3) -> Workload:
+                       dt=1.76e-3, quads=False) -> Workload:
     """The 1D Sod problem in a 2D strip (Sec. 5.1.1): X = [-1, 1] x [-3/128, 3/128], an
     nx x ny uniform grid (each square cut into two triangles along a seeded diagonal; the
     paper uses bilinear quadrilaterals), left half (n, u, theta) = (1, 0, 1), right half
@@ -258,12 +275,16 @@ def workload_sod_strip(nx=256, ny=6, kx=2, n_v=32, k_v=3, L=6.0, knudsen=1e-3, i
     states as inflow data at x_1 = -1 and 1, dt = 1.76e-3.  P2 by default: with P1
     triangles at this dt the density undershoots one cell downwind of the initial jump
     (the slow ordinates' layer is thinner than a cell) and the temperature there turns
-    negative within two steps."""
-    m = rect_mesh(nx, ny, 7, jitter=0.0)
-    xyz = m.xyz.copy()
-    xyz[:, 0] = 2.0 * xyz[:, 0] - 1.0
-    xyz[:, 1] = 2.0 * xyz[:, 1] - ny / nx          # square cells of side 2/nx, centred on x_2 = 0
-    mesh = Mesh(2, xyz, m.cells, n_side=nx, seed=7, meta={"ny": ny})
+    negative within two steps.  quads=True: the paper's Q1 quadrilaterals (k_x = 1)."""
+    if quads:
+        mesh = rect_quad_mesh(nx, ny, -1.0, 1.0, -ny / nx, ny / nx)
+        kx = 1
+    else:
+        m = rect_mesh(nx, ny, 7, jitter=0.0)
+        xyz = m.xyz.copy()
+        xyz[:, 0] = 2.0 * xyz[:, 0] - 1.0
+        xyz[:, 1] = 2.0 * xyz[:, 1] - ny / nx          # square cells of side 2/nx, centred on x_2 = 0
+        mesh = Mesh(2, xyz, m.cells, n_side=nx, seed=7, meta={"ny": ny})
     xn = node_coords(mesh, kx)
     cent = mesh.xyz[mesh.cells].mean(axis=1)[:, 0]
     left = np.repeat((cent < 0.0)[:, None], xn.shape[1], axis=1).ravel()
@@ -271,7 +292,8 @@ def workload_sod_strip(nx=256, ny=6, kx=2, n_v=32, k_v=3, L=6.0, knudsen=1e-3, i
     th = np.where(left, 1.0, 0.8)
     u = np.zeros((n.size, 2))
     init = _pack(n, u, th)
-    return Workload("2d2v_sod_strip_p%d_%dx%d_v%d" % (kx, nx, ny, n_v), mesh, kx, n_v, k_v, L, knudsen,
+    return Workload("2d2v_sod_strip_%s%d_%dx%d_v%d" % ("q" if quads else "p", kx, nx, ny, n_v), mesh, kx, n_v, k_v,
+                    L, knudsen,
                     integrator, 0.0, init, init.copy(), dt=dt, walls={"y-": "reflect", "y+": "reflect"})
 
 

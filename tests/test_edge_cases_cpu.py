@@ -53,6 +53,15 @@ def test_invalid_problems_are_rejected_before_any_device_work():
     assert _create(2, 1, m.xyz, m.cells, walls=(0, 0, 3, 0, 0, 0)) == bgk.BGK_E_INVALID
     assert _create(2, 1, m.xyz, m.cells, walls=(0, -1, 0, 0, 0, 0)) == bgk.BGK_E_INVALID
     assert _create(3, 1, c.xyz, c.cells, walls=(0, 0, 0, 0, 0, 9)) == bgk.BGK_E_INVALID
+    # quadrilaterals: a non-parallelogram cell; a quad with k_x = 2
+    lib = bgk.load()
+    q = np.array([[0, 0], [1.2, 0.1], [1.0, 0.9], [-0.1, 1.1]], dtype=np.float64)
+    qc = np.array([[0, 1, 2, 3]], dtype=np.int32)
+    for kx, xyz in ((1, q), (2, np.array([[0, 0], [1, 0], [1, 1], [0, 1]], dtype=np.float64))):
+        mq = bgk.Mesh(2, kx, 4, bgk._ptr(xyz), 1, bgk._ptr(qc), 1)
+        h = C.c_void_p()
+        assert lib.bgk_create(C.byref(mq), C.byref(bgk.VGrid(6.0, 8, 3)), C.byref(bgk.Physics(1.0, 0, 0.0, 10.0)),
+                              None, C.byref(h)) == bgk.BGK_E_INVALID
     # and the oracle refuses the same bad inputs
     with pytest.raises(ValueError):
         Oracle(2, 1, m.xyz, bad, 8, 3, 6.0)
