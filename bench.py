@@ -80,8 +80,8 @@ def workload(args):
         return synth.workload_3d_bump(n_side=args.n_side, seed=2, n_v=args.n_v, k_v=3, L=6.0, knudsen=1e-2,
                                       integrator="BE", cfl=8.0)
     if args.workload == "sod":
-        return synth.workload_sod_strip(nx=args.n_side, ny=6, kx=2, n_v=args.n_v, k_v=3, L=6.0,
-                                        knudsen=1.0 / args.nu, integrator=args.integrator, dt=1.76e-3)
+        return synth.workload_sod_strip(nx=args.n_side, ny=6, n_v=args.n_v, k_v=3, L=6.0, knudsen=1.0 / args.nu,
+                                        integrator=args.integrator, dt=1.76e-3, quads=True)
     if args.workload == "strip":
         return synth.workload_strip(nx=args.n_side, ny=2, seed=5, kx=1, n_v=args.n_v, k_v=3, L=6.0, knudsen=1e-2,
                                     integrator="BE", cfl=10.0)
@@ -93,6 +93,8 @@ def elem_of(w):
     """(name of the element tables, dofs per cell, velocity dimension) of a workload."""
     if w.mesh.dim == 3:
         return "p1tet", 4, 3
+    if w.mesh.cells.shape[1] == 4:
+        return "q1quad", 4, 2
     return ("p2tri", 6, 2) if w.kx == 2 else ("p1tri", 3, 2)
 
 
@@ -104,7 +106,7 @@ def config(w, args, extra=None):
                 "Kn 1e-2, CFL 8, tau 1e-8" % (args.n_side, w.mesh.n_cells, args.n_v))
         integ = "BE"
     elif args.workload == "sod":
-        name = ("2D-2V Sod problem in a strip [-1,1]x[-3/128,3/128], %dx6 squares (%d P2 triangles), reflecting "
+        name = ("2D-2V Sod problem in a strip [-1,1]x[-3/128,3/128], %dx6 Q1 quadrilaterals (%d cells), reflecting "
                 "walls at x2 = +-3/128, %dx%d velocities on [-6,6]^2, %s, nu %g, dt 1.76e-3, tau 1e-8"
                 % (args.n_side, w.mesh.n_cells, args.n_v, args.n_v, args.integrator, args.nu))
         integ = args.integrator

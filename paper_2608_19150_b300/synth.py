@@ -267,15 +267,15 @@ SOD_STEPS = 85            # Sec. 5.1.1: 85 steps of 1.76e-3 to t = 0.15 (0.14960
 
 
 def workload_sod_strip(nx=256, ny=6, kx=2, n_v=32, k_v=3, L=6.0, knudsen=1e-3, integrator="BE",
-                       dt=1.76e-3, quads=False) -> Workload:
+                       dt=1.76e-3, quads=True) -> Workload:
     """The 1D Sod problem in a 2D strip (Sec. 5.1.1): X = [-1, 1] x [-3/128, 3/128], an
-    nx x ny uniform grid (each square cut into two triangles along a seeded diagonal; the
-    paper uses bilinear quadrilaterals), left half (n, u, theta) = (1, 0, 1), right half
-    (0.125, 0, 0.8) (pressures 1 and 0.1), reflecting walls at x_2 = +-3/128, the initial
-    states as inflow data at x_1 = -1 and 1, dt = 1.76e-3.  P2 by default: with P1
-    triangles at this dt the density undershoots one cell downwind of the initial jump
-    (the slow ordinates' layer is thinner than a cell) and the temperature there turns
-    negative within two steps.  quads=True: the paper's Q1 quadrilaterals (k_x = 1)."""
+    nx x ny uniform grid of Q1 quadrilaterals as in the paper (quads=False: each square cut
+    into two triangles along a seeded diagonal, P_kx), left half (n, u, theta) = (1, 0, 1),
+    right half (0.125, 0, 0.8) (pressures 1 and 0.1), reflecting walls at x_2 = +-3/128,
+    the initial states as inflow data at x_1 = -1 and 1, dt = 1.76e-3.  On triangles use
+    P2: with P1 triangles at this dt the density undershoots one cell downwind of the
+    initial jump and the temperature there turns negative within two steps (Q1 and P2
+    stay physical)."""
     if quads:
         mesh = rect_quad_mesh(nx, ny, -1.0, 1.0, -ny / nx, ny / nx)
         kx = 1

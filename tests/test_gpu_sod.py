@@ -1,4 +1,5 @@
-"""The 1D Sod problem in a 2D strip (Sec. 5.1.1) on the GPU: 256 x 6 squares (triangulated),
+"""The 1D Sod problem in a 2D strip (Sec. 5.1.1) on the GPU: 256 x 6 Q1 quadrilaterals as in
+the paper (and P2 triangles for the fluid-limit comparison),
 reflecting walls at x_2 = +-3/128, 85 steps of dt = 1.76e-3 to t = 0.1496.
 
 - Fluid limit (nu = 1000): the density along x_1 is compared with the exact Euler solution
@@ -20,11 +21,11 @@ pytestmark = pytest.mark.gpu
 RUNS = {}
 
 
-def _run(knudsen, integ, n_v=32, precision="fp64"):
-    key = (knudsen, integ, n_v, precision)
+def _run(knudsen, integ, n_v=32, precision="fp64", quads=True):
+    key = (knudsen, integ, n_v, precision, quads)
     if key in RUNS:
         return RUNS[key]
-    w = synth.workload_sod_strip(n_v=n_v, knudsen=knudsen, integrator=integ)
+    w = synth.workload_sod_strip(n_v=n_v, knudsen=knudsen, integrator=integ, quads=quads)
     s = bgk.Solver.from_workload(w, precision=precision, l_max=3000)
     s.set_state_maxwellian(w.init)
     s.set_inflow_maxwellian(w.inflow)
@@ -43,9 +44,10 @@ def _weights(w):
     return np.concatenate([o.cell(c)["M"].sum(axis=0) for c in range(o.ncell)])
 
 
+@pytest.mark.parametrize("elements", ["q1", "p2"])
 @pytest.mark.parametrize("integ", ["BE", "DIRK2"])
-def test_sod_fluid_limit_matches_exact_euler(integ):
-    w, s, U0, U, its = _run(1e-3, integ)
+def test_sod_fluid_limit_matches_exact_euler(integ, elements):
+    w, s, U0, U, its = _run(1e-3, integ, quads=elements == "q1")
     t = synth.SOD_STEPS * w.dt
     x = synth.node_coords(w.mesh, w.kx).reshape(-1, 2)[:, 0]
     ex = sample((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 2.0, x / t)
@@ -53,7 +55,7 @@ def test_sod_fluid_limit_matches_exact_euler(integ):
     e_rho = np.sum(wt * np.abs(U[:, 0] - ex[:, 0])) / np.sum(wt * ex[:, 0])
     u = U[:, 1] / U[:, 0]
     e_u = np.sum(wt * np.abs(u - ex[:, 1])) / np.sum(wt)      # |u| ~ 1 in the star region
-    print("Sod nu=1000 %s: L1 density error %.4f, L1 velocity error %.4f" % (integ, e_rho, e_u))
+    print("Sod nu=1000 %s %s: L1 density error %.4f, L1 velocity error %.4f" % (elements, integ, e_rho, e_u))
     assert e_rho < 0.05 and e_u < 0.08
 
 
