@@ -397,7 +397,7 @@ def sweep_roofline(w, precision, reps, peaks, n_side=None, n_v=None, sweep_mode=
     hbm_peak = float(peaks.get("hbm_gbs", 6400.0))
     cached = s.cache_bytes > 0
     kind = elem_of(w)[0]
-    ename = {"p2tri": "ElemP2Tri", "p1tri": "ElemP1Tri", "p1tet": "ElemP1Tet"}[kind]
+    ename = {"p2tri": "ElemP2Tri", "p1tri": "ElemP1Tri", "p1tet": "ElemP1Tet", "q1quad": "ElemQ1Quad"}[kind]
     kname = "k_sweep_ts" if s.sweep_mode == "ts" else "k_sweep"
     if precision == "fp64":
         fl = sweep_flops_per_item(cached, kind)
