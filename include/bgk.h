@@ -68,7 +68,8 @@ typedef struct {
 } bgk_mesh;
 
 /* Velocity grid (Sec. 3.2): n_points per dimension on [-L, L], k_v+1 Gauss-Legendre
- * points in each of n_points/(k_v+1) uniform cells; nodal Q^{k_v} basis. */
+ * points in each of n_points/(k_v+1) uniform cells; nodal Q^{k_v} basis.  n_points <= 128
+ * (BGK_E_INVALID above). */
 typedef struct {
   double L;
   int n_points;

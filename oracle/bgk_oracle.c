@@ -668,7 +668,7 @@ static void project_1d(const orc_t *o, double u, double theta, double *c) {
 /* nodal discrete Maxwellian M_j = n prod_alpha c_alpha[j_alpha] (Sec. 3.3 + App. B) */
 static void maxwellian_at_node(const orc_t *o, const double *nut, double *out, size_t stride) {
   int d = o->dim, N = o->n1d;
-  double c[3][64];
+  double c[3][128];
   for (int al = 0; al < d; ++al) project_1d(o, nut[1 + al], nut[1 + d], c[al]);
   for (int j = 0; j < o->nv; ++j) {
     int jj = j, ja[3];
@@ -830,7 +830,7 @@ static orc_t *create_impl(int dim, int kx, int quad, int nvert, const double *xy
                           int n1d, int kv, double L) {
   if ((dim != 2 && dim != 3) || (kx != 1 && kx != 2) || (kx == 2 && dim != 2)) return NULL;
   if (quad && (dim != 2 || kx != 1)) return NULL;
-  if (kv < 1 || kv > 4 || n1d % (kv + 1) != 0 || n1d > 64 || !(L > 0.0)) return NULL;
+  if (kv < 1 || kv > 4 || n1d % (kv + 1) != 0 || n1d > 128 || !(L > 0.0)) return NULL;
   orc_t *o = calloc(1, sizeof(orc_t));
   o->dim = dim; o->kx = kx; o->nvert = nvert; o->ncell = ncell;
   o->quad = quad;
@@ -997,7 +997,7 @@ void orc_sweep_range(const orc_t *o, const double *fold, const double *Mn, const
  * out[r][node] for j = js[r], r < nj. */
 void orc_maxwellian_rows(const orc_t *o, const double *nut, const int *js, int nj, double *out) {
   int d = o->dim, N = o->n1d, nm = d + 2;
-  double c[3][64];
+  double c[3][128];
   for (int i = 0; i < o->nnode; ++i) {
     const double *p = nut + (size_t)i * nm;
     for (int al = 0; al < d; ++al) project_1d(o, p[1 + al], p[1 + d], c[al]);

@@ -8,7 +8,7 @@
 
 namespace bgk {
 
-constexpr int kMaxN1D = 64;   // velocity points per dimension
+constexpr int kMaxN1D = 128;  // velocity points per dimension (the paper runs up to 128)
 constexpr int kMaxKv = 4;     // velocity polynomial degree
 
 // Velocity grid of Sec. 3.2 (passed by value to kernels).

@@ -40,7 +40,7 @@ def test_invalid_problems_are_rejected_before_any_device_work():
     # velocity grid: points not a multiple of k_v + 1, k_v out of range, too many points
     assert _create(2, 1, m.xyz, m.cells, n1d=10, kv=3) == bgk.BGK_E_INVALID
     assert _create(2, 1, m.xyz, m.cells, n1d=12, kv=5) == bgk.BGK_E_INVALID
-    assert _create(2, 1, m.xyz, m.cells, n1d=68, kv=3) == bgk.BGK_E_INVALID
+    assert _create(2, 1, m.xyz, m.cells, n1d=132, kv=3) == bgk.BGK_E_INVALID
     assert _create(2, 1, m.xyz, m.cells, L=-1.0) == bgk.BGK_E_INVALID
     # empty mesh
     assert _create(2, 1, m.xyz, np.zeros((0, 3), dtype=np.int32)) == bgk.BGK_E_INVALID
