@@ -385,6 +385,8 @@ def sweep_roofline(w, precision, reps, peaks, n_side=None, n_v=None, sweep_mode=
     s = bgk.Solver.from_workload(w, precision=precision, sweep_mode=sweep_mode)
     s.set_state_maxwellian(w.init)
     s.set_inflow_maxwellian(w.inflow)
+    if sweep_mode == "auto":
+        s.autotune_sweep(2)
     s.sweep(0.0, 0.0)
     s.timing(reset=True)
     for _ in range(reps):
@@ -451,6 +453,8 @@ def run_ours(args):
                                  collision=args.collision)
     s.set_state_maxwellian(w.init)
     s.set_inflow_maxwellian(w.inflow)
+    tune = s.autotune_sweep(2) if args.sweep_mode == "auto" else None   # untimed set-up
+    chosen = s.sweep_mode
     dof = s.nv * s.nnode
     fdt = np.float32 if args.precision == "fp32" else np.float64
     f0 = s.get_f(fdt)
@@ -486,6 +490,8 @@ def run_ours(args):
                                      walls=walls, collision=args.collision)
         p.set_f(f0.astype(np.float64))
         p.set_inflow_maxwellian(w.inflow)
+        if args.sweep_mode == "auto":
+            p.autotune_sweep(2)
         for _ in range(args.warmup):
             p.step(1)
         pe, psw, pit, _, pclk = timed_steps(p, args.steps, world, local, tstream, walls=bool(walls))
@@ -520,6 +526,9 @@ def run_ours(args):
             "data": "synthetic", "config": config(w, args), "roofline": roofline, "rooflines": rl,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "picard_iterations": iters, "sweeps_timed": sweeps, "dt": dt}
+    if tune:
+        line["sweep_autotune_ms"] = tune
+        line["sweep_chosen"] = chosen
     if plain:
         line["plain_fp64"] = plain
         line["speedup_vs_plain_fp64"] = plain["ms_per_step"] / ms

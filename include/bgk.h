@@ -242,6 +242,15 @@ int bgk_synchronize(bgk_handle* h);
  * count since the last reset, recorded on the handle's stream. */
 int bgk_timing(bgk_handle* h, int reset, double* sweep_ms_total, int64_t* sweep_launches);
 
+/* Choose the sweep algorithm by measurement (Sec. 4.1: TS wins when generations are narrow
+ * and the ordinates many, TGS otherwise): times `reps` sweeps of each on the current state
+ * (which must have been set; it is restored) with the first stage's coefficients, keeps
+ * the faster and captures the step graphs again.  With BGK_MIXED the FP32 shadow chooses
+ * for itself the same way.  ms (may be NULL) receives 4 values: TGS and TS time per sweep
+ * of the main problem, then of the FP32 shadow (0 without one).  BGK_E_INVALID if no state
+ * was set or reps <= 0. */
+int bgk_autotune_sweep(bgk_handle* h, int reps, double* ms);
+
 /* ---- Batched instances ---------------------------------------------------------------
  * Many independent problems (own mesh, velocity grid, nu, dt; backward Euler) advanced
  * together.  Per Picard iteration the sweeps of all instances run as one persistent

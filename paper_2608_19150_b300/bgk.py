@@ -104,6 +104,7 @@ def load(path: str = LIB_PATH):
         "bgk_last_stats": [P, C.POINTER(Stats)],
         "bgk_synchronize": [P],
         "bgk_timing": [P, I, C.POINTER(D), C.POINTER(C.c_int64)],
+        "bgk_autotune_sweep": [P, I, V],
         "bgk_moments_measure_noalloc": [C.POINTER(VGrid), I, C.c_int64, V, I, V, V, V, V],
         "bgk_batch_create": [I, C.POINTER(Mesh), C.POINTER(VGrid), C.POINTER(Physics), C.POINTER(Config),
                              C.POINTER(P)],
@@ -343,6 +344,19 @@ class Solver:
 
     def synchronize(self):
         _ck(self.lib.bgk_synchronize(self.h), "bgk_synchronize")
+
+    def autotune_sweep(self, reps=3):
+        """Keep the faster of TGS and TS on the current state (bgk_autotune_sweep); returns
+        the per-sweep times in ms: {"tgs", "ts"} and, with an FP32 shadow, {"tgs32", "ts32"}."""
+        ms = np.zeros(4)
+        _ck(self.lib.bgk_autotune_sweep(self.h, int(reps), _ptr(ms)), "bgk_autotune_sweep")
+        sz = (C.c_int64 * 10)()
+        _ck(self.lib.bgk_sizes(self.h, sz), "bgk_sizes")
+        self.sweep_mode = {1: "tgs", 2: "ts"}[int(sz[9])]
+        out = {"tgs": float(ms[0]), "ts": float(ms[1])}
+        if ms[2] > 0:
+            out.update(tgs32=float(ms[2]), ts32=float(ms[3]))
+        return out
 
     def timing(self, reset=False):
         ms = C.c_double()

@@ -88,18 +88,8 @@ int bgk_set_guess(bgk_handle* h, bgk_mlp* m) {
   }
   h->guess = m;
   // the step graphs change shape: capture them again
-  if (!h->cfg.eager) {
-    if (h->exec_main) cudaGraphExecDestroy(h->exec_main);
-    if (h->exec_start) cudaGraphExecDestroy(h->exec_start);
-    h->exec_main = h->exec_start = nullptr;
-    int rc = enqueue_step(h, 0, &h->exec_main);
-    if (rc == BGK_OK && h->phys.integrator == BGK_BDF2) {
-      cudaGraphExec_t e0 = h->exec_main;
-      rc = enqueue_step(h, 1, &h->exec_main);
-      h->exec_start = e0;
-    }
-    if (rc != BGK_OK) return rc;
-  }
+  int rc = recapture_steps(h);
+  if (rc != BGK_OK) return rc;
   return BGK_OK;
 }
 

@@ -588,6 +588,62 @@ int enqueue_step(bgk_handle* h, int mode_bdf2, cudaGraphExec_t* exec_out) {
   return e == cudaSuccess ? BGK_OK : BGK_E_CUDA;
 }
 
+// Capture the step graphs again after a change of what a step launches (the learned
+// guess, the sweep algorithm); nothing to do in eager mode.
+int recapture_steps(bgk_handle* h) {
+  if (h->cfg.eager) return BGK_OK;
+  if (h->exec_main) cudaGraphExecDestroy(h->exec_main);
+  if (h->exec_start) cudaGraphExecDestroy(h->exec_start);
+  h->exec_main = h->exec_start = nullptr;
+  int rc = enqueue_step(h, 0, &h->exec_main);
+  if (rc == BGK_OK && h->phys.integrator == BGK_BDF2) {
+    cudaGraphExec_t e0 = h->exec_main;
+    rc = enqueue_step(h, 1, &h->exec_main);
+    h->exec_start = e0;
+  }
+  return rc;
+}
+
+// Mean time of `reps` sweeps of h in its current algorithm, with the first stage's
+// coefficients and the source of the current state (h->f is changed: callers restore it).
+int time_sweeps(bgk_handle* h, const void* qsrc, int reps, float* ms) {
+  k_reset_state<<<1, 1, 0, h->stream>>>(h->ds);
+  moments(h, 0);
+  int rc = build_src(h, qsrc, h->qscale_main);
+  if (rc != BGK_OK) return rc;
+  launch_sweep_any(h, h->nus_main);  // warm-up
+  CK(cudaEventRecord(h->ev0, h->stream));
+  for (int r = 0; r < reps; ++r) launch_sweep_any(h, h->nus_main);
+  CK(cudaEventRecord(h->ev1, h->stream));
+  CK(cudaGetLastError());
+  CK(cudaEventSynchronize(h->ev1));
+  CK(cudaEventElapsedTime(ms, h->ev0, h->ev1));
+  *ms /= reps;
+  return BGK_OK;
+}
+
+// TGS or TS for one handle: the faster of the two on its current state, which is restored.
+int choose_sweep(bgk_handle* h, const void* qsrc, int reps, float* t_tgs, float* t_ts) {
+  void* save = nullptr;
+  const size_t bytes = h->nfv * h->tsize;
+  if (dalloc(save, bytes) != BGK_OK) return BGK_E_OOM;
+  int rc = BGK_OK;
+  float t[2] = {0.f, 0.f};
+  if (cudaMemcpyAsync(save, h->f, bytes, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess) rc = BGK_E_CUDA;
+  for (int m = 0; m < 2 && rc == BGK_OK; ++m) {
+    h->sweep_ts = m == 1;
+    rc = time_sweeps(h, qsrc, reps, &t[m]);
+    if (rc == BGK_OK && cudaMemcpyAsync(h->f, save, bytes, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+      rc = BGK_E_CUDA;
+  }
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess && rc == BGK_OK) rc = BGK_E_CUDA;
+  cudaFree(save);
+  h->sweep_ts = rc == BGK_OK && t[1] < t[0];
+  if (t_tgs) *t_tgs = t[0];
+  if (t_ts) *t_ts = t[1];
+  return rc;
+}
+
 int build_dags(bgk_handle* h) {
   const int n = h->hm.ncell;
   const int threads = 256;
@@ -1374,6 +1430,25 @@ int bgk_synchronize(bgk_handle* h) {
   if (!h) return BGK_E_INVALID;
   CK(cudaStreamSynchronize(h->stream));
   return BGK_OK;
+}
+
+int bgk_autotune_sweep(bgk_handle* h, int reps, double* ms) {
+  if (!h || !h->state_set || reps <= 0) return BGK_E_INVALID;
+  float t[4] = {0.f, 0.f, 0.f, 0.f};
+  int rc = choose_sweep(h, h->fk, reps, &t[0], &t[1]);
+  if (rc == BGK_OK && h->shadow) {
+    // the FP32 shadow's own choice, on the FP32 copy of the state (its fk holds the
+    // stage source during a step; the state itself serves here)
+    bgk_handle* sh = h->shadow;
+    const int thr = 256, blk = 148 * 8;
+    k_convert<double, float><<<blk, thr, 0, h->stream>>>(h->nfv, (const double*)h->f, (float*)sh->f);
+    k_convert<double, float><<<blk, thr, 0, h->stream>>>(h->nfv, (const double*)h->f, (float*)sh->fk);
+    rc = choose_sweep(sh, sh->fk, reps, &t[2], &t[3]);
+  }
+  if (rc == BGK_OK) rc = recapture_steps(h);
+  if (ms)
+    for (int i = 0; i < 4; ++i) ms[i] = t[i];
+  return rc;
 }
 
 int bgk_timing(bgk_handle* h, int reset, double* sweep_ms_total, int64_t* sweep_launches) {

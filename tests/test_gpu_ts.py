@@ -52,3 +52,38 @@ def test_default_is_tgs():
     strip = bgk.Solver.from_workload(synth.workload_strip(nx=256, ny=1, n_v=16))
     square = bgk.Solver.from_workload(small_shock_tube(n=16, kx=2, n_v=16))
     assert strip.sweep_mode == "tgs" and square.sweep_mode == "tgs"
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_autotune_sweep_restores_state_and_steps_like_the_chosen_mode(precision):
+    """bgk_autotune_sweep times TGS and TS on the current state, keeps the faster, restores
+    the state and captures the step graphs again: a step afterwards equals a step of a
+    solver created with the chosen algorithm (up to rounding)."""
+    from paper_2608_19150_b300 import bgk, synth
+    w = synth.workload_sod_strip(nx=64, ny=6, n_v=16, knudsen=1.0)
+    s = bgk.Solver.from_workload(w, precision=precision)
+    s.set_state_maxwellian(w.init)
+    s.set_inflow_maxwellian(w.inflow)
+    f0 = s.get_f()
+    t = s.autotune_sweep(2)
+    assert t["tgs"] > 0 and t["ts"] > 0
+    assert s.sweep_mode == ("ts" if t["ts"] < t["tgs"] else "tgs")
+    np.testing.assert_array_equal(s.get_f(), f0)
+    st = s.step(2)
+    r = bgk.Solver.from_workload(w, precision=precision, sweep_mode=s.sweep_mode)
+    r.set_state_maxwellian(w.init)
+    r.set_inflow_maxwellian(w.inflow)
+    str_ = r.step(2)
+    if precision == "fp64":
+        assert list(st.iterations) == list(str_.iterations)
+        assert rel_err(s.get_f(), r.get_f()) < 1e-13
+    else:   # the FP32 shadow chose for itself: the same fixed point to the tolerance
+        assert rel_err(s.get_f(), r.get_f()) < 1e-6
+
+
+def test_autotune_needs_a_state():
+    from paper_2608_19150_b300 import bgk, synth
+    s = bgk.Solver.from_workload(synth.workload_p1_square(n_side=4, n_v=8))
+    with pytest.raises(bgk.BgkError) as e:
+        s.autotune_sweep()
+    assert e.value.status == bgk.BGK_E_INVALID
