@@ -120,9 +120,9 @@ typedef struct {
   int sweep_mode;     /* sweep algorithm (Sec. 4.1): 0 or 1 = TGS (a CTA per ordinate walks
                          the generations, the cells of a generation in parallel: the default),
                          2 = TS (a thread per ordinate walks its whole schedule alone).  Both
-                         give the same results up to rounding.  TS is slower on every mesh
-                         measured, strips with 1-2 cells per generation included (the CTA
-                         size of TGS follows the generation width and its barrier is per CTA) */
+                         give the same results up to rounding.  TS wins only on narrow
+                         domains with many ordinates (the Sod strip from 96x96 velocities);
+                         bgk_autotune_sweep chooses by measurement */
 } bgk_config;
 
 typedef struct {

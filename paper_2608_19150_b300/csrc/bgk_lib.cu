@@ -700,8 +700,9 @@ int build_dags(bgk_handle* h) {
     int t = (int)std::ceil(width / 32.0) * 32;
     h->sweep_threads = std::min(128, std::max(32, t));
   }
-  // sweep algorithm: TGS unless TS is asked for (TS ran 8x slower even on a 4096 x 2 strip
-  // with 1.4 cells per generation: its concurrency is one thread per ordinate)
+  // sweep algorithm: TGS unless TS is asked for or bgk_autotune_sweep measures it faster
+  // (TS's concurrency is one thread per ordinate: it wins only on narrow domains with many
+  // ordinates, e.g. the 256 x 6 Sod strip from 96 x 96 velocities)
   h->sweep_ts = h->cfg.sweep_mode == 2;
   return BGK_OK;
 }
