@@ -189,9 +189,11 @@ int bgk_get_lagged_edges(bgk_handle* h, int j, int32_t* h_edges, int cap, int* n
  * BDF2 history is present, the step count, and the learned guess's moment history when a
  * network is attached -- to the file `path` (raw little-endian binary behind a header that
  * records the problem's sizes, velocity grid, nu, dt, storage type and a hash of the mesh
- * geometry).  bgk_load reads such a file into a handle created for the same problem (same
- * mesh, grid, nu, dt, integrator and storage precision; else BGK_E_IO) and replaces its
- * state: the next bgk_step is bit-identical to the one the saving handle would take.
+ * geometry, the collision model and the wall kinds).  bgk_load reads such a file into a
+ * handle created for the same problem (same mesh, grid, nu, dt, integrator, collision
+ * model, walls and storage precision; else BGK_E_IO) and replaces its state: the next
+ * bgk_step is bit-identical to the one the saving handle would take, given the same inflow
+ * data (these are not in the file: set them on the loading handle).
  * Returns BGK_E_IO when the file cannot be written/read or does not match. */
 int bgk_save(bgk_handle* h, const char* path);
 int bgk_load(bgk_handle* h, const char* path);

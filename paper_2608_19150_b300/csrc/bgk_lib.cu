@@ -1206,8 +1206,8 @@ uint64_t fnv1a(uint64_t h, const void* p, size_t n) {
 CkptHeader ckpt_header(const bgk_handle* h) {
   CkptHeader c;
   std::memset(&c, 0, sizeof(c));
-  std::memcpy(c.magic, "BGKCKPT1", 8);
-  c.version = 1;
+  std::memcpy(c.magic, "BGKCKPT2", 8);
+  c.version = 2;
   c.dtype = h->tsize == 8 ? BGK_DTYPE_F64 : BGK_DTYPE_F32;
   c.dim = h->hm.dim;
   c.kx = h->hm.kx;
@@ -1225,6 +1225,9 @@ CkptHeader ckpt_header(const bgk_handle* h) {
   uint64_t hs = 1469598103934665603ull;
   hs = fnv1a(hs, h->hm.geo.data(), sizeof(double) * h->hm.geo.size());
   hs = fnv1a(hs, h->hm.nbr.data(), sizeof(int32_t) * h->hm.nbr.size());
+  // the collision model and the wall kinds decide the next step too
+  hs = fnv1a(hs, &h->phys.collision, sizeof(int));
+  hs = fnv1a(hs, h->phys.walls, sizeof(int) * 2 * (size_t)h->hm.dim);
   c.mesh_hash = hs;
   return c;
 }

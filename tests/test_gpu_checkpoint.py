@@ -57,6 +57,13 @@ def test_mismatched_or_broken_files_are_refused(tmp_path):
     with pytest.raises(bgk.BgkError) as e:
         c.load(path)
     assert e.value.status == bgk.BGK_E_IO
+    for kw in ({"collision": "linear"}, {"walls": {"y-": "reflect"}}):         # another model or walls
+        x = bgk.Solver.from_workload(w, **kw)
+        with pytest.raises(bgk.BgkError) as e:
+            x.load(path)
+        assert e.value.status == bgk.BGK_E_IO
+    same = bgk.Solver.from_workload(w)
+    same.load(path)
     with open(path, "r+b") as fh:                                               # truncated
         fh.truncate(os.path.getsize(path) // 2)
     d = bgk.Solver.from_workload(w)
