@@ -104,3 +104,35 @@ def test_trained_guess_saves_iterations_and_keeps_results():
         f0, f1 = res[0][1], res[1][1]
         assert np.abs(f0 - f1).max() <= 1e-6 * np.abs(f0).max()
     assert learned < plain, (learned, plain)
+
+
+def test_guess_features_on_quadrilaterals():
+    """The learned guess's cell gradients on Q1 parallelograms: the mean gradient of the
+    bilinear interpolant, which on a parallelogram is its gradient at the centre,
+    J^-T (d_s q, d_t q)(1/2, 1/2) -- written here with the reference map."""
+    import torch
+    m = synth.rect_quad_mesh(6, 4, shear=0.35)
+    x = synth.node_coords(m, 1).reshape(-1, 2)
+    n = 1.0 + 0.3 * np.sin(2 * np.pi * x[:, 0])
+    u = np.stack([0.2 * np.cos(np.pi * x[:, 1]), 0.1 * x[:, 0] * x[:, 1]], 1)
+    th = 1.0 + 0.2 * x[:, 1]
+    init = np.concatenate([n[:, None], u, th[:, None]], 1)
+    w = synth.Workload("quad", m, 1, 12, 2, 6.0, 0.05, "BE", 10.0, init, init.copy())
+    s = bgk.Solver.from_workload(w)
+    s.set_state_maxwellian(w.init)
+    F, O = s.guess_dims()
+    X = torch.zeros((s.nnode, F), dtype=torch.float32, device="cuda")
+    s.guess_features(X.data_ptr())
+    X = X.cpu().numpy()
+    U = s.get_moments()
+    d, nm = 2, 4
+    ux = U[:, 1:3] / U[:, :1]
+    for c in range(m.n_cells):
+        P = m.xyz[m.cells[c]]
+        J = np.stack([P[1] - P[0], P[3] - P[0]], 1)
+        for b in range(2):
+            qv = ux[c * 4:(c + 1) * 4, b]
+            g_ref = np.array([((qv[1] - qv[0]) + (qv[2] - qv[3])) / 2, ((qv[3] - qv[0]) + (qv[2] - qv[1])) / 2])
+            grad = np.linalg.solve(J.T, g_ref)
+            feat = X[c * 4:(c + 1) * 4, nm + d + b * d: nm + d + (b + 1) * d]
+            np.testing.assert_allclose(feat, np.tile(s.dt * grad, (4, 1)), rtol=1e-5, atol=1e-7)
