@@ -72,3 +72,78 @@ def test_fixed_order_sum_across_two_gloo_ranks():
 def test_sum_without_a_group_is_the_partial_itself():
     p = torch.arange(6, dtype=torch.float64)
     assert torch.equal(shard.sum_fixed_order(p), p)
+
+
+class _ToyShard:
+    """A stand-in for a solver shard with the same three calls, for the host control flow:
+    ordinates j in [jb, je) of a relaxation problem f_j <- (f_j^k + a M_j(U)) / (1 + a),
+    M_j(U) = (U_n + c v_j U_m) / J at every node (linear; it keeps the mass and feeds the
+    momentum back, so the loop converges geometrically, rate a c sum v^2 / (J (1 + a))),
+    U = (sum_j f_j, sum_j v_j f_j, sum_j v_j^2 f_j / 2) per node, v_j = j - (J - 1) / 2."""
+
+    def __init__(self, jb, je, J=8, nnode=5, a=3.0, c=0.12):
+        self.jb, self.je, self.J, self.a, self.c = jb, je, J, a, c
+        g = synth.splitmix64_uniform(11, J * nnode).reshape(J, nnode)
+        self.fk = torch.from_numpy(0.5 + g[jb:je]).to(torch.float64)
+        self.f = self.fk.clone()
+        self.v = torch.arange(jb, je, dtype=torch.float64) - (J - 1) / 2
+        self.nnode = nnode
+
+    def new_moments(self):
+        return torch.empty((self.nnode, 3), dtype=torch.float64)
+
+    def partial(self, U):
+        U[:, 0] = self.f.sum(0)
+        U[:, 1] = (self.v[:, None] * self.f).sum(0)
+        U[:, 2] = (0.5 * self.v[:, None] ** 2 * self.f).sum(0)
+
+    def sweep(self, U):
+        M = (U[:, 0][None, :] + self.c * self.v[:, None] * U[:, 1][None, :]) / self.J
+        self.f = (self.fk + self.a * M) / (1 + self.a)
+
+    def commit(self):
+        self.fk = self.f.clone()
+
+
+def _sharded_rank(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    (jb, je), = [r for k, r in enumerate(shard.ordinate_shards(8, 1, world)) if k == rank]
+    part = _ToyShard(jb, je)
+    its = [shard.picard_sharded([part], shard.sum_fixed_order, 1, 1e-12, 200) for _ in range(3)]
+    q.put((rank, its, part.f.numpy()))
+    dist.destroy_process_group()
+
+
+def test_sharded_picard_across_two_gloo_ranks_matches_one_process():
+    """picard_sharded with the ordinates split over two gloo ranks takes the same number of
+    iterations on both ranks as one process holding every ordinate, and each rank's
+    ordinates end where the single-process run puts them (up to summation order)."""
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _port()
+    ps = [ctx.Process(target=_sharded_rank, args=(r, world, port, q)) for r in range(world)]
+    for p in ps:
+        p.start()
+    for p in ps:
+        p.join(120)
+        assert p.exitcode == 0
+    res = {r: (its, f) for r, its, f in (q.get(timeout=5) for _ in range(world))}
+    whole = _ToyShard(0, 8)
+    its_ref = [shard.picard_sharded([whole], lambda U: U, 1, 1e-12, 200) for _ in range(3)]
+    assert res[0][0] == res[1][0] == its_ref
+    assert min(its_ref) > 10
+    for r, (a, b) in enumerate(shard.ordinate_shards(8, 1, world)):
+        np.testing.assert_allclose(res[r][1], whole.f.numpy()[a:b], rtol=1e-14, atol=0)
+
+
+def test_sharded_picard_in_one_process_with_two_parts():
+    parts = [_ToyShard(0, 4), _ToyShard(4, 8)]
+    whole = _ToyShard(0, 8)
+    assert (shard.picard_sharded(parts, lambda U: U, 1, 1e-12, 200)
+            == shard.picard_sharded([whole], lambda U: U, 1, 1e-12, 200))
+    np.testing.assert_allclose(torch.cat([p.f for p in parts]).numpy(), whole.f.numpy(), rtol=1e-14)
+    with pytest.raises(RuntimeError):
+        shard.picard_sharded([_ToyShard(0, 8)], lambda U: U, 1, 1e-30, 3)
