@@ -109,6 +109,10 @@ class SolverShard:
         self.s.moments_range_device(self.jb, self.je, U_out.data_ptr())
 
     def sweep(self, U_in):
+        # U_in may come from torch kernels (the sum of the partials) on torch's stream; the
+        # library works on its own stream, so wait for them first
+        import torch
+        torch.cuda.current_stream().synchronize()
         self.s.sweep_range(self.jb, self.je, U_in.data_ptr())
 
     def commit(self):
