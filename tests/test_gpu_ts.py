@@ -19,11 +19,12 @@ pytestmark = pytest.mark.gpu
 def _cases():
     return {"p2_tri": small_shock_tube(n=8, kx=2, n_v=16, integrator="DIRK3"),
             "p1_strip": synth.workload_strip(nx=48, ny=2, n_v=16, integrator="BDF2"),
-            "p1_tet": twisted_workload(3, 8)}
+            "p1_tet": twisted_workload(3, 8),
+            "q1_sod": synth.workload_sod_strip(nx=48, ny=6, n_v=16, knudsen=1.0, integrator="DIRK2")}
 
 
 @pytest.mark.parametrize("precision,cache", [("fp64", "on"), ("fp64", "off"), ("fp32", "off"), ("mixed", "auto")])
-@pytest.mark.parametrize("name", ["p2_tri", "p1_strip", "p1_tet"])
+@pytest.mark.parametrize("name", ["p2_tri", "p1_strip", "p1_tet", "q1_sod"])
 def test_ts_equals_tgs(name, precision, cache):
     w = _cases()[name]
     tau = 1e-6 if precision == "fp32" else 1e-8
