@@ -1,0 +1,39 @@
+"""The 2D Sod problem (Sec. 5.1.2) on the GPU: X = [0, 2]^2, a disc of radius 0.4 of the
+high state, 160 x 160 Q1 squares, 16 x 16 velocities, dt = 3.7e-4 to t = 0.15, backward
+Euler, mixed precision.  The paper compares with a cylindrical Euler reference (gamma = 2);
+here that reference is an own radial finite-volume solver (tests/euler_radial.py).  As nu
+grows the kinetic density approaches the fluid limit (the paper: nu = 1e3 and 1e4)."""
+import numpy as np
+import pytest
+
+from euler_radial import solve
+from paper_2608_19150_b300 import bgk, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def test_sod_2d_approaches_the_cylindrical_euler_solution():
+    steps = int(round(synth.SOD_2D_T / 3.7e-4))
+    t = steps * 3.7e-4
+    rc, W = solve(lambda r: np.where(r < 0.4, 1.0, 0.125), lambda r: 0.0 * r,
+                  lambda r: np.where(r < 0.4, 1.0, 0.1), 1.0, t, n=4000, alpha=1)
+    err = {}
+    for nu in (1e3, 1e4):
+        w = synth.workload_sod_2d(knudsen=1.0 / nu)
+        s = bgk.Solver.from_workload(w, precision="mixed", l_max=3000)
+        s.set_state_maxwellian(w.init)
+        s.set_inflow_maxwellian(w.inflow)
+        its = 0
+        for _ in range(steps):
+            its += s.step(1).iterations[0]
+        n = s.get_moments()[:, 0]
+        x = synth.node_coords(w.mesh, 1).reshape(-1, 2)
+        r = np.sqrt(((x - 1.0) ** 2).sum(1))
+        inside = r < 0.95                      # the reference's domain (waves stay within r < 0.7)
+        ref = np.interp(r[inside], rc, W[0])
+        err[nu] = np.mean(np.abs(n[inside] - ref)) / np.mean(ref)
+        print("2D Sod nu=%g: L1 density error %.4f, %d steps, %.1f FP64 Picard iterations per step"
+              % (nu, err[nu], steps, its / steps))
+        s.close()
+    assert err[1e4] < err[1e3]
+    assert err[1e4] < 0.05
