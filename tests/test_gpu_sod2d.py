@@ -14,8 +14,8 @@ pytestmark = pytest.mark.gpu
 
 def test_sod_2d_approaches_the_cylindrical_euler_solution():
     err = {}
-    for nu in (1e3, 1e4):
-        w = synth.workload_sod_2d(knudsen=1.0 / nu)
+    for nu, n_v in ((1e2, 16), (1e3, 16), (1e4, 32)):
+        w = synth.workload_sod_2d(knudsen=1.0 / nu, n_v=n_v)
         s = bgk.Solver.from_workload(w, precision="mixed", l_max=3000)
         steps = int(round(synth.SOD_2D_T / s.dt))
         t = steps * s.dt
@@ -24,16 +24,22 @@ def test_sod_2d_approaches_the_cylindrical_euler_solution():
         s.set_state_maxwellian(w.init)
         s.set_inflow_maxwellian(w.inflow)
         its = 0
-        for _ in range(steps):
-            its += s.step(1).iterations[0]
+        try:
+            for _ in range(steps):
+                its += s.step(1).iterations[0]
+        except bgk.BgkError as e:
+            print("2D Sod nu=%g n_v=%d: status %d after %d steps" % (nu, n_v, e.status, _))
+            err[nu] = np.inf
+            s.close()
+            continue
         n = s.get_moments()[:, 0]
         x = synth.node_coords(w.mesh, 1).reshape(-1, 2)
         r = np.sqrt(((x - 1.0) ** 2).sum(1))
         inside = r < 0.95                      # the reference's domain (waves stay within r < 0.7)
         ref = np.interp(r[inside], rc, W[0])
         err[nu] = np.mean(np.abs(n[inside] - ref)) / np.mean(ref)
-        print("2D Sod nu=%g: L1 density error %.4f, %d steps, %.1f FP64 Picard iterations per step"
-              % (nu, err[nu], steps, its / steps))
+        print("2D Sod nu=%g n_v=%d: L1 density error %.4f, %d steps of %.3e, %.1f FP64 Picard iterations per step"
+              % (nu, n_v, err[nu], steps, s.dt, its / steps))
         s.close()
-    assert err[1e4] < err[1e3]
+    assert err[1e4] < err[1e3] < err[1e2]
     assert err[1e4] < 0.05
