@@ -47,7 +47,7 @@ def parse():
                    help="cells per side (shock_tube 128, bump3d 24, learned 256)")
     p.add_argument("--n-v", type=int, default=None, help="velocity points per dimension (32; bump3d 16)")
     p.add_argument("--sweep-reps", type=int, default=5)
-    p.add_argument("--workload", default="shock_tube", choices=["shock_tube", "bump3d", "strip", "sod", "batched", "learned"])
+    p.add_argument("--workload", default="shock_tube", choices=["shock_tube", "bump3d", "strip", "sod", "sod2d", "batched", "learned"])
     p.add_argument("--nu", type=float, default=1000.0, help="sod: collision frequency (the paper runs 1 and 1000)")
     p.add_argument("--integrator", default="DIRK2", choices=["BE", "DIRK2"], help="sod: DIRK-1 or DIRK-2")
     p.add_argument("--sweep-mode", default="auto", choices=["auto", "tgs", "ts"],
@@ -68,7 +68,9 @@ def parse():
                    help="launch each step's kernels from a host loop instead of one CUDA graph (profiling)")
     a = p.parse_args()
     if a.n_side is None:
-        a.n_side = {"bump3d": 24, "learned": 256, "strip": 4096, "sod": 256}.get(a.workload, 128)
+        a.n_side = {"bump3d": 24, "learned": 256, "strip": 4096, "sod": 256, "sod2d": 160}.get(a.workload, 128)
+    if a.n_v is None and a.workload == "sod2d":
+        a.n_v = 16
     if a.n_v is None:
         a.n_v = 16 if a.workload == "bump3d" else 32
     return a
@@ -79,6 +81,9 @@ def workload(args):
     if args.workload == "bump3d":
         return synth.workload_3d_bump(n_side=args.n_side, seed=2, n_v=args.n_v, k_v=3, L=6.0, knudsen=1e-2,
                                       integrator="BE", cfl=8.0)
+    if args.workload == "sod2d":
+        return synth.workload_sod_2d(n=args.n_side, n_v=args.n_v, k_v=3, L=6.0, knudsen=1.0 / args.nu,
+                                     integrator=args.integrator, cfl=7.0)
     if args.workload == "sod":
         return synth.workload_sod_strip(nx=args.n_side, ny=6, n_v=args.n_v, k_v=3, L=6.0, knudsen=1.0 / args.nu,
                                         integrator=args.integrator, dt=1.76e-3, quads=True)
@@ -105,6 +110,11 @@ def config(w, args, extra=None):
         name = ("3D-3V Gaussian bump, %d^3 cubes (%d P1 tetrahedra), %d^3 velocities on [-6,6]^3, backward Euler, "
                 "Kn 1e-2, CFL 8, tau 1e-8" % (args.n_side, w.mesh.n_cells, args.n_v))
         integ = "BE"
+    elif args.workload == "sod2d":
+        name = ("2D-2V Sod problem, X = [0,2]^2, disc of radius 0.4, %dx%d Q1 squares, %dx%d velocities on [-6,6]^2, "
+                "%s, nu %g, dt 7x explicit, tau 1e-8" % (args.n_side, args.n_side, args.n_v, args.n_v, args.integrator,
+                                                         args.nu))
+        integ = args.integrator
     elif args.workload == "sod":
         name = ("2D-2V Sod problem in a strip [-1,1]x[-3/128,3/128], %dx6 Q1 quadrilaterals (%d cells), reflecting "
                 "walls at x2 = +-3/128, %dx%d velocities on [-6,6]^2, %s, nu %g, dt 1.76e-3, tau 1e-8"
@@ -222,6 +232,7 @@ def cpu_baseline(w, n_ord, dt):
     from oracle.oracle import Oracle, tableau
     # the sampled sweep reads wall faces as inflow data (the mirror rows are not sampled)
     o = Oracle(w.mesh.dim, w.kx, w.mesh.xyz, w.mesh.cells, w.n_v, w.k_v, w.L)
+    n_ord = min(n_ord, o.nv)
     j0 = (o.nv - n_ord) // 2
     js = np.arange(j0, j0 + n_ord, dtype=np.int32)
     t0 = time.perf_counter()
@@ -291,7 +302,7 @@ def run_reference(args):
     w = workload(args)
     from oracle.oracle import Oracle, tableau
     o = Oracle(w.mesh.dim, w.kx, w.mesh.xyz, w.mesh.cells, w.n_v, w.k_v, w.L)   # see cpu_baseline
-    n_ord = 64
+    n_ord = min(64, o.nv)
     j0 = (o.nv - n_ord) // 2
     js = np.arange(j0, j0 + n_ord, dtype=np.int32)
     o.build_dags_for(js)
