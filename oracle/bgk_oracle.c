@@ -1013,14 +1013,15 @@ void orc_maxwellian_rows(const orc_t *o, const double *nut, const int *js, int n
 
 /* One sweep for the listed ordinates only; all arrays hold just those rows
  * ([nj][nnode]); the graphs must have been built.  Inflow boundaries only (a wall needs
- * the mirror ordinates' rows): with walls set it does nothing. */
-void orc_sweep_rows(const orc_t *o, const int *js, int nj, const double *fold, const double *Mn, const double *q,
+ * the mirror ordinates' rows): with walls set it returns ORC_E_INVALID and sweeps nothing. */
+int orc_sweep_rows(const orc_t *o, const int *js, int nj, const double *fold, const double *Mn, const double *q,
                     const double *fbc, double nu, double nu_s, double *fnew) {
   size_t nn = (size_t)o->nnode;
-  if (o->wmirror) return;
+  if (o->wmirror) return ORC_E_INVALID;
   for (int r = 0; r < nj; ++r)
     sweep_ordinate(o, js[r], fold + (size_t)r * nn, Mn + (size_t)r * nn, q + (size_t)r * nn, fbc + (size_t)r * nn, nu,
                    nu_s, fnew + (size_t)r * nn, NULL);
+  return ORC_OK;
 }
 
 /* explicit time-step bound (Sec. 5): dt_e = (1/d) (1/(2 kx + 1)) h_min / max_j |v_j|,

@@ -68,6 +68,7 @@ def _load():
         lib.orc_sweep.argtypes = [P, dp, dp, dp, dp, C.c_double, C.c_double, dp]
         lib.orc_sweep_range.argtypes = [P, dp, dp, dp, dp, C.c_double, C.c_double, dp, C.c_int, C.c_int]
         lib.orc_maxwellian_rows.argtypes = [P, dp, ip, C.c_int, dp]
+        lib.orc_sweep_rows.restype = C.c_int
         lib.orc_sweep_rows.argtypes = [P, ip, C.c_int, dp, dp, dp, dp, C.c_double, C.c_double, dp]
         lib.orc_dt_explicit.restype = C.c_double
         lib.orc_dt_explicit.argtypes = [P]
@@ -170,7 +171,9 @@ class Oracle:
         js = np.ascontiguousarray(js, dtype=np.int32)
         c = lambda a: np.ascontiguousarray(a, dtype=np.float64).reshape(len(js), self.nnode)  # noqa: E731
         fnew = np.zeros((len(js), self.nnode))
-        self.lib.orc_sweep_rows(self.h, js, len(js), c(fold), c(Mn), c(q), c(fbc), float(nu), float(nu_s), fnew)
+        st = self.lib.orc_sweep_rows(self.h, js, len(js), c(fold), c(Mn), c(q), c(fbc), float(nu), float(nu_s), fnew)
+        if st != 0:
+            raise ValueError("sweep_rows needs the mirror rows of wall faces: not available with walls set")
         return fnew
 
     def moments(self, f):

@@ -214,3 +214,15 @@ def test_interpolation_is_not_conservative_and_projection_is():
     assert defect[(8, "maxwellian")] < 1e-12 and defect[(16, "maxwellian")] < 1e-12
     assert defect[(8, "interpolated")] > 1e-4
     assert defect[(16, "interpolated")] < 0.5 * defect[(8, "interpolated")]
+
+
+def test_row_sweep_refuses_walls():
+    """A sweep of selected ordinates has no mirror rows for wall faces: the oracle refuses
+    it instead of reading rows it was not given."""
+    m = synth.square_mesh(3, 0)
+    o = _oracle(m)
+    o.set_walls(ALL_REFLECT)
+    js = np.arange(4, dtype=np.int32)
+    f = np.ones((4, o.nnode))
+    with pytest.raises(ValueError):
+        o.sweep_rows(js, f, f, f, f, 1.0, 2.0)
