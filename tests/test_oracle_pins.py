@@ -512,6 +512,12 @@ def test_tableaus_match_printed_digits_and_order_conditions():
     np.testing.assert_allclose(A2, [[g, 0], [math.sqrt(2) / 2, g]], atol=1e-15)
     assert abs(b2.sum() - 1) < 1e-15 and abs(b2 @ c2 - 0.5) < 1e-15
     Ab, bb, cb = tableau("BSTABLE2")
+    # the values printed in closed form in Eq. (B-RK): gamma = (3 + sqrt 3)/6,
+    # A = [[gamma, 0], [1 - (3 + sqrt 3)/3, gamma]], c = (gamma, 1 - gamma), b = (1/2, 1/2)
+    gb = (3 + math.sqrt(3)) / 6
+    np.testing.assert_allclose(Ab, [[gb, 0], [1 - (3 + math.sqrt(3)) / 3, gb]], atol=1e-15)
+    np.testing.assert_allclose(cb, [gb, 1 - gb], atol=1e-15)
+    np.testing.assert_allclose(bb, [0.5, 0.5], atol=1e-15)
     B = np.diag(bb)
     Mb = B @ Ab + Ab.T @ B - np.outer(bb, bb)     # algebraic stability (App. A)
     assert np.linalg.eigvalsh(Mb).min() > -1e-14
