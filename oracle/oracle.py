@@ -7,7 +7,9 @@ code with the CUDA library.
 The C source follows the paper's statement step by step (its header lists the sections
 and the readings taken where the paper is silent).  This wrapper only marshals arrays.
 
-Parity status per function (pins live in ``tests/test_oracle_pins.py``):
+Parity status per function (pins live in ``tests/test_oracle_pins*.py``; the multi-stage
+time integration in ``tests/test_oracle_pins_time.py``: the stability function of each
+tableau on a transport-free relaxation, the BDF2 recurrence, the temporal order):
   velocity grid, element matrices, projection, moments, sweep graph / generations,
   one sweep, one time step (BE, DIRK2, DIRK3, B-stable DIRK2, BDF2), the simplified
   Maxwellian collision model, the interpolated Maxwellian, bounce-back and reflecting
@@ -24,66 +26,91 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "bgk_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "_build", "libbgk_oracle.so")
+# the same source with the loop over ordinates of a sweep on all host cores (OpenMP): the
+# timed CPU baseline only; parity checks use the sequential build above
+_LIB_OMP_PATH = os.path.join(_HERE, "_build", "libbgk_oracle_omp.so")
 
 INTEGRATORS = {"BE": 0, "DIRK2": 1, "DIRK3": 2, "BSTABLE2": 3, "BDF2": 4}
 
 _lib = None
+_lib_omp = None
+
+
+def _compile(path, extra):
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    if not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
+        tmp = path + ".tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+                               "-fno-fast-math"] + extra + ["-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, path)
+    return path
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain C11, no fused multiply-add)."""
-    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-                               "-fno-fast-math", "-o", _LIB_PATH, _SRC, "-lm"])
-    return _LIB_PATH
+    """Compile the oracle with gcc (plain C11, no fused multiply-add): the sequential
+    parity build and the OpenMP build of the CPU baseline."""
+    if force:
+        for p in (_LIB_PATH, _LIB_OMP_PATH):
+            if os.path.exists(p):
+                os.remove(p)
+    _compile(_LIB_OMP_PATH, ["-fopenmp"])
+    return _compile(_LIB_PATH, [])
 
 
-def _load():
-    global _lib
+def _load(omp: bool = False):
+    global _lib, _lib_omp
+    if omp:
+        if _lib_omp is None:
+            build()
+            _lib_omp = _declare(C.CDLL(_LIB_OMP_PATH))
+        return _lib_omp
     if _lib is None:
-        lib = C.CDLL(build())
-        P = C.c_void_p
-        dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
-        ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
-        up = np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")
-        lib.orc_create.restype = P
-        lib.orc_create.argtypes = [C.c_int, C.c_int, C.c_int, dp, C.c_int, ip, C.c_int, C.c_int, C.c_double]
-        lib.orc_create_quad.restype = P
-        lib.orc_create_quad.argtypes = [C.c_int, dp, C.c_int, ip, C.c_int, C.c_int, C.c_double]
-        lib.orc_destroy.argtypes = [P]
-        lib.orc_info.argtypes = [P, ip]
-        lib.orc_velocity.argtypes = [P, dp, dp, dp, dp]
-        lib.orc_cell.argtypes = [P, C.c_int, dp, dp, dp, dp, dp, dp, ip, ip]
-        lib.orc_project_1d.argtypes = [P, C.c_double, C.c_double, dp]
-        lib.orc_maxwellian.argtypes = [P, dp, dp]
-        lib.orc_moments.argtypes = [P, dp, dp]
-        lib.orc_build_dags.restype = C.c_long
-        lib.orc_build_dags.argtypes = [P]
-        lib.orc_build_dags_for.restype = C.c_long
-        lib.orc_build_dags_for.argtypes = [P, ip, C.c_int]
-        lib.orc_generations.restype = C.c_int
-        lib.orc_generations.argtypes = [P, C.c_int, ip, up]
-        lib.orc_face_signs.argtypes = [P, C.c_int, ip]
-        lib.orc_sweep.argtypes = [P, dp, dp, dp, dp, C.c_double, C.c_double, dp]
-        lib.orc_sweep_range.argtypes = [P, dp, dp, dp, dp, C.c_double, C.c_double, dp, C.c_int, C.c_int]
-        lib.orc_maxwellian_rows.argtypes = [P, dp, ip, C.c_int, dp]
-        lib.orc_sweep_rows.restype = C.c_int
-        lib.orc_sweep_rows.argtypes = [P, ip, C.c_int, dp, dp, dp, dp, C.c_double, C.c_double, dp]
-        lib.orc_dt_explicit.restype = C.c_double
-        lib.orc_dt_explicit.argtypes = [P]
-        lib.orc_tableau.restype = C.c_int
-        lib.orc_tableau.argtypes = [C.c_int, dp, dp, dp]
-        lib.orc_conv_measure.restype = C.c_double
-        lib.orc_conv_measure.argtypes = [P, dp, dp]
-        lib.orc_set_physics.argtypes = [P, C.c_double, C.c_double, C.c_int, C.c_double, C.c_int]
-        lib.orc_set_collision.argtypes = [P, C.c_int]
-        lib.orc_set_walls.restype = C.c_int
-        lib.orc_set_walls.argtypes = [P, ip]
-        lib.orc_step.restype = C.c_int
-        lib.orc_step.argtypes = [P, dp, C.c_void_p, dp, ip, dp]
-        _lib = lib
+        _lib = _declare(C.CDLL(build()))
     return _lib
+
+
+def _declare(lib):
+    """ctypes signatures of the oracle's entry points."""
+    P = C.c_void_p
+    dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+    ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+    up = np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")
+    lib.orc_create.restype = P
+    lib.orc_create.argtypes = [C.c_int, C.c_int, C.c_int, dp, C.c_int, ip, C.c_int, C.c_int, C.c_double]
+    lib.orc_create_quad.restype = P
+    lib.orc_create_quad.argtypes = [C.c_int, dp, C.c_int, ip, C.c_int, C.c_int, C.c_double]
+    lib.orc_destroy.argtypes = [P]
+    lib.orc_info.argtypes = [P, ip]
+    lib.orc_velocity.argtypes = [P, dp, dp, dp, dp]
+    lib.orc_cell.argtypes = [P, C.c_int, dp, dp, dp, dp, dp, dp, ip, ip]
+    lib.orc_project_1d.argtypes = [P, C.c_double, C.c_double, dp]
+    lib.orc_maxwellian.argtypes = [P, dp, dp]
+    lib.orc_moments.argtypes = [P, dp, dp]
+    lib.orc_build_dags.restype = C.c_long
+    lib.orc_build_dags.argtypes = [P]
+    lib.orc_build_dags_for.restype = C.c_long
+    lib.orc_build_dags_for.argtypes = [P, ip, C.c_int]
+    lib.orc_generations.restype = C.c_int
+    lib.orc_generations.argtypes = [P, C.c_int, ip, up]
+    lib.orc_face_signs.argtypes = [P, C.c_int, ip]
+    lib.orc_sweep.argtypes = [P, dp, dp, dp, dp, C.c_double, C.c_double, dp]
+    lib.orc_sweep_range.argtypes = [P, dp, dp, dp, dp, C.c_double, C.c_double, dp, C.c_int, C.c_int]
+    lib.orc_maxwellian_rows.argtypes = [P, dp, ip, C.c_int, dp]
+    lib.orc_sweep_rows.restype = C.c_int
+    lib.orc_sweep_rows.argtypes = [P, ip, C.c_int, dp, dp, dp, dp, C.c_double, C.c_double, dp]
+    lib.orc_dt_explicit.restype = C.c_double
+    lib.orc_dt_explicit.argtypes = [P]
+    lib.orc_tableau.restype = C.c_int
+    lib.orc_tableau.argtypes = [C.c_int, dp, dp, dp]
+    lib.orc_conv_measure.restype = C.c_double
+    lib.orc_conv_measure.argtypes = [P, dp, dp]
+    lib.orc_set_physics.argtypes = [P, C.c_double, C.c_double, C.c_int, C.c_double, C.c_int]
+    lib.orc_set_collision.argtypes = [P, C.c_int]
+    lib.orc_set_walls.restype = C.c_int
+    lib.orc_set_walls.argtypes = [P, ip]
+    lib.orc_step.restype = C.c_int
+    lib.orc_step.argtypes = [P, dp, C.c_void_p, dp, ip, dp]
+    return lib
 
 
 def tableau(integrator: str):
@@ -96,8 +123,9 @@ def tableau(integrator: str):
 class Oracle:
     """One problem: mesh + spatial degree + velocity grid (+ physics for time steps)."""
 
-    def __init__(self, dim, kx, xyz, cells, n1d, kv, L):
-        self.lib = _load()
+    def __init__(self, dim, kx, xyz, cells, n1d, kv, L, omp=False):
+        """omp: run sweeps on all host cores (the OpenMP build; CPU baseline only)."""
+        self.lib = _load(omp)
         self.dim, self.kx, self.n1d, self.kv, self.L = dim, kx, n1d, kv, L
         xyz = np.ascontiguousarray(xyz, dtype=np.float64)
         cells = np.ascontiguousarray(cells, dtype=np.int32)
@@ -113,8 +141,8 @@ class Oracle:
         self._dags = False
 
     @classmethod
-    def from_workload(cls, w):
-        o = cls(w.mesh.dim, w.kx, w.mesh.xyz, w.mesh.cells, w.n_v, w.k_v, w.L)
+    def from_workload(cls, w, omp=False):
+        o = cls(w.mesh.dim, w.kx, w.mesh.xyz, w.mesh.cells, w.n_v, w.k_v, w.L, omp=omp)
         if getattr(w, "walls", None):
             o.set_walls(w.walls)
         return o
