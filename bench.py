@@ -33,7 +33,6 @@ WALL_SETS = {"none": None,
              "channel": {"y-": "reflect", "y+": "reflect"},
              "closed_reflect": {sd: "reflect" for sd in ("x-", "x+", "y-", "y+", "z-", "z+")},
              "closed_bounce_back": {sd: "bounce_back" for sd in ("x-", "x+", "y-", "y+", "z-", "z+")}}
-FP64_PEAK_TFLOPS = 1.25   # nominal B300 FP64 rate (no tensor path); see the design notes
 
 
 def parse():
@@ -47,7 +46,8 @@ def parse():
                    help="cells per side (shock_tube 128, bump3d 24, learned 256)")
     p.add_argument("--n-v", type=int, default=None, help="velocity points per dimension (32; bump3d 16)")
     p.add_argument("--sweep-reps", type=int, default=5)
-    p.add_argument("--workload", default="shock_tube", choices=["shock_tube", "bump3d", "strip", "sod", "sod2d", "batched", "learned"])
+    p.add_argument("--workload", default="shock_tube", choices=["shock_tube", "p1_square", "bump3d", "strip", "sod", "sod2d", "batched",
+                                                         "learned"])
     p.add_argument("--nu", type=float, default=1000.0, help="sod: collision frequency (the paper runs 1 and 1000)")
     p.add_argument("--integrator", default="DIRK2", choices=["BE", "DIRK2"], help="sod: DIRK-1 or DIRK-2")
     p.add_argument("--sweep-mode", default="auto", choices=["auto", "tgs", "ts"],
@@ -68,8 +68,9 @@ def parse():
                    help="launch each step's kernels from a host loop instead of one CUDA graph (profiling)")
     a = p.parse_args()
     if a.n_side is None:
-        a.n_side = {"bump3d": 24, "learned": 256, "strip": 4096, "sod": 256, "sod2d": 160}.get(a.workload, 128)
-    if a.n_v is None and a.workload == "sod2d":
+        a.n_side = {"bump3d": 24, "learned": 256, "strip": 4096, "sod": 256, "sod2d": 160,
+                    "p1_square": 16}.get(a.workload, 128)
+    if a.n_v is None and a.workload in ("sod2d", "p1_square"):
         a.n_v = 16
     if a.n_v is None:
         a.n_v = 16 if a.workload == "bump3d" else 32
@@ -78,6 +79,9 @@ def parse():
 
 def workload(args):
     from paper_2608_19150_b300 import synth
+    if args.workload == "p1_square":
+        return synth.workload_p1_square(n_side=args.n_side, seed=0, n_v=args.n_v, k_v=3, L=6.0, knudsen=1e-2,
+                                        integrator="BE", cfl=10.0)
     if args.workload == "bump3d":
         return synth.workload_3d_bump(n_side=args.n_side, seed=2, n_v=args.n_v, k_v=3, L=6.0, knudsen=1e-2,
                                       integrator="BE", cfl=8.0)
@@ -103,12 +107,39 @@ def elem_of(w):
     return ("p2tri", 6, 2) if w.kx == 2 else ("p1tri", 3, 2)
 
 
+L2_BYTES = 126 * 2 ** 20           # B300 L2
+
+
+def l2_note(f_bytes):
+    if f_bytes > 2 * L2_BYTES:
+        return "inputs larger than L2 (f %.2f GB per array)" % (f_bytes / 1e9)
+    return "L2 flushed before every timed step (a 504 MiB buffer written outside the timed region; f %.1f MB)" % (
+        f_bytes / 1e6)
+
+
+def l2_flusher(f_bytes):
+    """A callable that evicts L2 by writing a buffer four times its size, or None when the
+    step's arrays are larger than L2 themselves."""
+    if f_bytes > 2 * L2_BYTES:
+        return None
+    import torch
+    buf = torch.empty(4 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def flush():
+        buf.fill_(1.0)
+    return flush
+
+
 def config(w, args, extra=None):
     _, nd, dv = elem_of(w)
     dof = int(w.mesh.n_cells * nd * args.n_v ** dv)
     if w.mesh.dim == 3:
         name = ("3D-3V Gaussian bump, %d^3 cubes (%d P1 tetrahedra), %d^3 velocities on [-6,6]^3, backward Euler, "
                 "Kn 1e-2, CFL 8, tau 1e-8" % (args.n_side, w.mesh.n_cells, args.n_v))
+        integ = "BE"
+    elif args.workload == "p1_square":
+        name = ("2D-2V smooth problem, %dx%d squares (%d P1 triangles), %dx%d velocities on [-6,6]^2, backward Euler, "
+                "Kn 1e-2, CFL 10, tau 1e-8" % (args.n_side, args.n_side, w.mesh.n_cells, args.n_v, args.n_v))
         integ = "BE"
     elif args.workload == "sod2d":
         name = ("2D-2V Sod problem, X = [0,2]^2, disc of radius 0.4, %dx%d Q1 squares, %dx%d velocities on [-6,6]^2, "
@@ -138,7 +169,7 @@ def config(w, args, extra=None):
          "precision": {"fp64": "FP64 sweeps", "fp32": "FP32 sweeps, FP64-accurate moments",
                        "mixed": "FP32 sweeps to the FP32 floor, then FP64 sweeps; FP64 moments"}[args.precision],
          "integrator": integ,
-         "l2": "inputs larger than L2 (f %.2f GB per array)" % (dof * (4 if args.precision == "fp32" else 8) / 1e9),
+         "l2": l2_note(dof * (4 if args.precision == "fp32" else 8)),
          "parallelism": "replicas", "launch": "eager host loop" if args.eager else
          "one CUDA graph per step, conditional while-node per stage", "sweep_mode": args.sweep_mode}
     if extra:
@@ -226,29 +257,64 @@ class Clocks:
 
 
 # --------------------------------------------------------------------- CPU oracle
-def cpu_baseline(w, n_ord, dt):
-    """The oracle as it stands (single thread): one sweep of n_ord ordinates of the full
-    mesh, on the sampled ordinates' own rows (graphs, Maxwellian, sweep)."""
+def host_cpu():
+    """(logical cores this process may use, CPU model name) of the host."""
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    model = "unknown"
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                if ln.startswith("model name"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return cores, model
+
+
+def _oracle_sweep_rate(w, js, dt, omp):
+    """DOF-updates/s of one oracle sweep over the ordinates js of the full mesh (the
+    first-stage coefficient, f^l = M = f of the initial state), and the seconds it took."""
     from oracle.oracle import Oracle, tableau
     # the sampled sweep reads wall faces as inflow data (the mirror rows are not sampled)
-    o = Oracle(w.mesh.dim, w.kx, w.mesh.xyz, w.mesh.cells, w.n_v, w.k_v, w.L)
-    n_ord = min(n_ord, o.nv)
-    j0 = (o.nv - n_ord) // 2
-    js = np.arange(j0, j0 + n_ord, dtype=np.int32)
-    t0 = time.perf_counter()
+    o = Oracle(w.mesh.dim, w.kx, w.mesh.xyz, w.mesh.cells, w.n_v, w.k_v, w.L, omp=omp)
     o.build_dags_for(js)
     f0 = o.maxwellian_rows(w.init, js)
     fbc = o.maxwellian_rows(w.inflow, js)
-    setup = time.perf_counter() - t0
     A, _, _ = tableau(w.integrator)
     nus = w.nu + 1.0 / (dt * A[0, 0])
     t0 = time.perf_counter()
     o.sweep_rows(js, f0, f0, f0 / (dt * A[0, 0]), fbc, w.nu, nus)
     el = time.perf_counter() - t0
-    dof = n_ord * o.nnode
-    return {"value": dof / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "one sweep over %d of %d ordinates of the full mesh (%d DOF) in %.1f s, single thread; "
-                      "set-up %.1f s untimed" % (n_ord, o.nv, dof, el, setup)}
+    return len(js) * o.nnode / el, el, o.nv, len(js) * o.nnode
+
+
+def _sample_ordinates(nv, n_ord):
+    n_ord = min(n_ord, nv)
+    j0 = (nv - n_ord) // 2
+    return np.arange(j0, j0 + n_ord, dtype=np.int32)
+
+
+def cpu_baseline(w, n_ord, dt):
+    """The oracle as it stands on the host: one sweep over n_ord ordinates of the full mesh
+    with the loop over ordinates on all cores (the OpenMP build of the same source), and a
+    quarter of that sample on one core (the sequential parity build)."""
+    cores, model = host_cpu()
+    os.environ["OMP_NUM_THREADS"] = str(cores)
+    nv = w.n_v ** w.mesh.dim
+    js = _sample_ordinates(nv, n_ord)
+    v_all, el_all, nv, dof_all = _oracle_sweep_rate(w, js, dt, omp=True)
+    js1 = _sample_ordinates(nv, max(1, len(js) // 4))
+    v_one, el_one, _, dof_one = _oracle_sweep_rate(w, js1, dt, omp=False)
+    return {"value": v_all, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": model,
+            "sample": "one sweep over %d of %d ordinates of the full mesh (%d DOF) in %.2f s, OpenMP loop over "
+                      "ordinates on %d threads" % (len(js), nv, dof_all, el_all, cores),
+            "single_thread": {"value": v_one, "unit": UNIT, "cores": 1,
+                              "sample": "one sweep over %d ordinates (%d DOF) in %.2f s, sequential build"
+                                        % (len(js1), dof_one, el_one)}}
 
 
 # --------------------------------------------------------------------- runs
@@ -294,17 +360,19 @@ def job_throughput(units, elapsed_max, world):
 
 
 def run_reference(args):
-    """The reference arm: the CPU oracle as it stands, each step one oracle sweep over a
-    bounded sample of the workload's ordinates (rank 0 only)."""
+    """The reference arm: the CPU oracle as it stands (the OpenMP build, all host cores),
+    each step one oracle sweep over a bounded sample of the workload's ordinates (rank 0
+    only)."""
     rank, world, _ = dist_init(args)
     if rank != 0:
         return
     w = workload(args)
+    cores, model = host_cpu()
+    os.environ["OMP_NUM_THREADS"] = str(cores)
     from oracle.oracle import Oracle, tableau
-    o = Oracle(w.mesh.dim, w.kx, w.mesh.xyz, w.mesh.cells, w.n_v, w.k_v, w.L)   # see cpu_baseline
-    n_ord = min(64, o.nv)
-    j0 = (o.nv - n_ord) // 2
-    js = np.arange(j0, j0 + n_ord, dtype=np.int32)
+    o = Oracle(w.mesh.dim, w.kx, w.mesh.xyz, w.mesh.cells, w.n_v, w.k_v, w.L, omp=True)   # see cpu_baseline
+    js = _sample_ordinates(o.nv, 16 * cores)
+    n_ord = len(js)
     o.build_dags_for(js)
     dt = w.dt if w.dt > 0 else w.cfl * o.dt_explicit()
     f0 = o.maxwellian_rows(w.init, js)
@@ -312,7 +380,7 @@ def run_reference(args):
     A, _, _ = tableau(w.integrator)
     nus = w.nu + 1.0 / (dt * A[0, 0])
     for _ in range(max(0, args.warmup)):
-        o.sweep_rows(js[:2], f0[:2], f0[:2], f0[:2] / (dt * A[0, 0]), fbc[:2], w.nu, nus)
+        o.sweep_rows(js[:cores], f0[:cores], f0[:cores], f0[:cores] / (dt * A[0, 0]), fbc[:cores], w.nu, nus)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         o.sweep_rows(js, f0, f0, f0 / (dt * A[0, 0]), fbc, w.nu, nus)
@@ -325,10 +393,11 @@ def run_reference(args):
             "data": "synthetic",
             "config": config(w, args, {"sample": "each step: one oracle sweep over %d of %d ordinates of the "
                                                  "full mesh" % (n_ord, o.nv), "precision": "FP64 CPU oracle"}),
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "%d ordinates x %d cells x %d nodes per step%s" % (
-                                 n_ord, o.ncell, o.nnode // o.ncell,
-                                 WALL_NOTE if (args.walls != "none" or w.walls) else "")},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": model,
+                             "sample": "%d ordinates x %d cells x %d nodes per step, OpenMP loop over ordinates "
+                                       "on %d threads%s" % (
+                                           n_ord, o.ncell, o.nnode // o.ncell, cores,
+                                           WALL_NOTE if (args.walls != "none" or w.walls) else "")},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -348,10 +417,12 @@ def launches_per_step(st, guess=False, main_fp32=False, walls=False):
     return n
 
 
-def timed_steps(s, steps, world, local, tstream, guess=False, main_fp32=False, walls=False):
+def timed_steps(s, steps, world, local, tstream, guess=False, main_fp32=False, walls=False, restore=None):
     """Run `steps` steps of solver s (already warmed up; created on torch stream tstream),
     each bracketed by CUDA events on that stream; the time is the sum of the steps'
-    device times (the statistics read between steps is not inside any bracket)."""
+    device times (the statistics read between steps is not inside any bracket).
+    restore: called before every step, outside the bracket (puts back the step's input
+    state, so every timed step advances the same f^k)."""
     import torch
     s.synchronize()
     sweeps0 = s.last_stats().total_sweeps
@@ -361,6 +432,8 @@ def timed_steps(s, steps, world, local, tstream, guess=False, main_fp32=False, w
     torch.cuda.synchronize()
     iters, launches, el = [], 0, 0.0
     for _ in range(steps):
+        if restore is not None:
+            restore()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(tstream)
         s.step_async(1)
@@ -389,7 +462,7 @@ PROFILED_TRAFFIC = {
 }
 
 
-def sweep_roofline(w, precision, reps, peaks, n_side=None, n_v=None, sweep_mode="auto"):
+def sweep_roofline(w, precision, reps, peaks, n_side=None, n_v=None, sweep_mode="auto", fp64_peak=None):
     """Event-timed sweep kernel of the given precision on its own handle (first-stage
     coefficient, local-inverse cache as in the step) and its roofline entry."""
     from paper_2608_19150_b300 import bgk
@@ -415,10 +488,11 @@ def sweep_roofline(w, precision, reps, peaks, n_side=None, n_v=None, sweep_mode=
     if precision == "fp64":
         fl = sweep_flops_per_item(cached, kind)
         tf = fl * s.nv * s.ncell / (sweep_ms * 1e-3) / 1e12
-        r = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-             "frac": tf / FP64_PEAK_TFLOPS, "traffic": None,
+        r = {"bound": "alu", "achieved": tf, "peak": fp64_peak, "unit": "TFLOP/s",
+             "frac": tf / fp64_peak, "traffic": None,
              "kernel": "%s<%s,double,%s>" % (kname, ename, "cached" if cached else "uncached"),
-             "flops_per_local_solve": fl, "peak_source": "nominal B300 FP64 rate (measured FMA probe 1.125)"}
+             "flops_per_local_solve": fl,
+             "peak_source": "measured in this run: FP64 FMA probe (bgk_probe_fma_tflops), of measured"}
     else:
         r = {"bound": "hbm", "achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_gbs / hbm_peak,
              "traffic": None,
@@ -446,6 +520,14 @@ def state_errors(f, U, f_ref, U_ref, d):
             "E_l2_rel": float(nrm(U[:, -1] - U_ref[:, -1]) / nrm(U_ref[:, -1]))}
 
 
+PRE_STEPS = 3
+
+
+def pre_steps(args):
+    """Steps from the initial state to the state every timed step starts from."""
+    return PRE_STEPS
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_init(args)
@@ -468,17 +550,38 @@ def run_ours(args):
     chosen = s.sweep_mode
     dof = s.nv * s.nnode
     fdt = np.float32 if args.precision == "fp32" else np.float64
-    f0 = s.get_f(fdt)
+    tdt = torch.float64 if fdt == np.float64 else torch.float32
+    # the input state of every step: PRE_STEPS steps from the initial state (untimed); every
+    # warm-up and timed step starts from it (restored outside the timed bracket), so any
+    # --steps runs the same step (the shock tube itself turns non-physical after about
+    # 3.7e-3 time units, the 13th step at CFL 10, as the oracle does on coarser grids)
+    pre = pre_steps(args)
+    for _ in range(pre):
+        s.step(1)
+    f_in = torch.empty(dof, dtype=tdt, device="cuda")
+    s.get_f_device(f_in.data_ptr(), fdt)
+    torch.cuda.synchronize()
+
+    flush = l2_flusher(dof * np.dtype(fdt).itemsize)
+
+    def restore_main():
+        s.set_f_device(f_in.data_ptr(), fdt)
+        if flush:
+            flush()
+            torch.cuda.synchronize()
+
     for _ in range(args.warmup):
+        restore_main()
         s.step(1)
     el_max, sweeps, iters, launches, clk = timed_steps(s, args.steps, world, local, tstream,
-                                                       main_fp32=args.precision == "fp32", walls=bool(walls))
+                                                       main_fp32=args.precision == "fp32", walls=bool(walls),
+                                                       restore=restore_main)
     value = job_throughput(dof * sweeps, el_max, world)
     f_end, U_end = s.get_f(np.float64), s.get_moments()
     # end to end through the C ABI with host buffers: f^k in from pinned host memory,
     # moments out to host, every step
-    f_host = torch.empty(dof, dtype=torch.float64 if fdt == np.float64 else torch.float32, pin_memory=True)
-    f_host.copy_(torch.from_numpy(s.get_f(fdt).ravel()))
+    f_host = torch.empty(dof, dtype=tdt, pin_memory=True)
+    f_host.copy_(f_in.cpu())
     U = np.empty((s.nnode, s.dim + 2))
     barrier(world)
     t0 = time.perf_counter()
@@ -499,20 +602,33 @@ def run_ours(args):
     if args.precision != "fp64":
         p = bgk.Solver.from_workload(w, precision="fp64", stream=tstream.cuda_stream, sweep_mode=args.sweep_mode,
                                      walls=walls, collision=args.collision)
-        p.set_f(f0.astype(np.float64))
+        f_in64 = f_in.to(torch.float64)
+        p.set_f_device(f_in64.data_ptr(), np.float64)
         p.set_inflow_maxwellian(w.inflow)
         if args.sweep_mode == "auto":
             p.autotune_sweep(2)
+
+        def restore_plain():
+            p.set_f_device(f_in64.data_ptr(), np.float64)
+            if flush:
+                flush()
+                torch.cuda.synchronize()
+
         for _ in range(args.warmup):
+            restore_plain()
             p.step(1)
-        pe, psw, pit, _, pclk = timed_steps(p, args.steps, world, local, tstream, walls=bool(walls))
+        pe, psw, pit, _, pclk = timed_steps(p, args.steps, world, local, tstream, walls=bool(walls),
+                                            restore=restore_plain)
         plain = {"ms_per_step": 1e3 * pe / args.steps, "value": job_throughput(dof * psw, pe, world), "picard_iterations": pit,
                  "clocks": pclk,
                  "error_vs_plain_fp64": state_errors(f_end, U_end, p.get_f(np.float64), p.get_moments(), p.dim)}
         p.close()
         del p
-    # the sweep kernels, event-timed on their own stream
-    rl = {"fp64": sweep_roofline(w, "fp64", args.sweep_reps, peaks, args.n_side, args.n_v, args.sweep_mode)}
+    # the sweep kernels, event-timed on their own stream; the FP64 sweep's arithmetic peak
+    # is the FMA rate measured here and now
+    fp64_peak = bgk.probe_fma_tflops(np.float64)
+    rl = {"fp64": sweep_roofline(w, "fp64", args.sweep_reps, peaks, args.n_side, args.n_v, args.sweep_mode,
+                                 fp64_peak)}
     if args.precision != "fp64":
         rl["fp32"] = sweep_roofline(w, "fp32", args.sweep_reps, peaks, args.n_side, args.n_v, args.sweep_mode)
     # dominant kernel of the timed step: the sweep precision that used the most time
@@ -534,7 +650,10 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp64": "f64", "fp32": "f32", "mixed": "f32 sweeps then f64 (mixed)"}[args.precision],
-            "data": "synthetic", "config": config(w, args), "roofline": roofline, "rooflines": rl,
+            "data": "synthetic",
+            "config": config(w, args, {"step_input": "the state after %d steps from the initial state, restored "
+                                                     "before every step outside the timed region" % pre}),
+            "roofline": roofline, "rooflines": rl,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "picard_iterations": iters, "sweeps_timed": sweeps, "dt": dt}
     if tune:

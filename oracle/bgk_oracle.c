@@ -800,9 +800,14 @@ static void sweep_ordinate(const orc_t *o, int j, const double *fold, const doub
   }
 }
 
+/* The ordinates of one sweep are independent (each reads only its own rows, and f^l for
+ * walls), so the loop over them may run on several threads: the timed CPU baseline is this
+ * source built with -fopenmp; the parity build ignores the pragma and runs in order.  Each
+ * ordinate's arithmetic is the same either way. */
 static void sweep_range(const orc_t *o, const double *fold, const double *Mn, const double *q, const double *fbc,
                         double nu, double nu_s, double *fnew, int j0, int j1) {
   size_t nn = (size_t)o->nnode;
+#pragma omp parallel for schedule(dynamic, 1)
   for (int j = j0; j < j1; ++j)
     sweep_ordinate(o, j, fold + (size_t)j * nn, Mn + (size_t)j * nn, q + (size_t)j * nn, fbc + (size_t)j * nn, nu,
                    nu_s, fnew + (size_t)j * nn, fold);
@@ -1011,13 +1016,15 @@ void orc_maxwellian_rows(const orc_t *o, const double *nut, const int *js, int n
   }
 }
 
-/* One sweep for the listed ordinates only; all arrays hold just those rows
+/* One sweep for the listed ordinates only (in parallel in the OpenMP build, see
+ * sweep_range); all arrays hold just those rows
  * ([nj][nnode]); the graphs must have been built.  Inflow boundaries only (a wall needs
  * the mirror ordinates' rows): with walls set it returns ORC_E_INVALID and sweeps nothing. */
 int orc_sweep_rows(const orc_t *o, const int *js, int nj, const double *fold, const double *Mn, const double *q,
                     const double *fbc, double nu, double nu_s, double *fnew) {
   size_t nn = (size_t)o->nnode;
   if (o->wmirror) return ORC_E_INVALID;
+#pragma omp parallel for schedule(dynamic, 1)
   for (int r = 0; r < nj; ++r)
     sweep_ordinate(o, js[r], fold + (size_t)r * nn, Mn + (size_t)r * nn, q + (size_t)r * nn, fbc + (size_t)r * nn, nu,
                    nu_s, fnew + (size_t)r * nn, NULL);

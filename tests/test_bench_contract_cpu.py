@@ -1,5 +1,5 @@
 """The benchmark's JSON contract on CPU: the reference arm (the oracle) prints one line with
-the keys the contract names, for the small Sod configurations; and the launch tally of a
+the keys the contract names, for small configurations of the workloads; and the launch tally of a
 step counts the wall refresh once per iteration."""
 import json
 import os
@@ -15,7 +15,9 @@ KEYS = {"impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_
 
 
 @pytest.mark.parametrize("args", [["--workload", "sod2d", "--n-side", "12", "--n-v", "8"],
-                                  ["--workload", "sod", "--n-side", "16", "--n-v", "8"]])
+                                  ["--workload", "sod", "--n-side", "16", "--n-v", "8"],
+                                  ["--workload", "p1_square"],
+                                  ["--workload", "shock_tube", "--n-side", "8", "--n-v", "8"]])
 def test_reference_arm_prints_one_contract_line(args):
     out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "1"] + args,
                          cwd=ROOT, capture_output=True, text=True, timeout=600)
@@ -26,7 +28,9 @@ def test_reference_arm_prints_one_contract_line(args):
     assert KEYS <= set(d)
     assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
-    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    # the oracle's OpenMP build on every core this process may use
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == len(os.sched_getaffinity(0))
+    assert "OpenMP" in d["cpu_baseline"]["sample"] and d["cpu_baseline"]["cpu_model"]
     assert ("wall faces" in d["cpu_baseline"]["sample"]) == (args[1] == "sod")   # the strip has walls
 
 
