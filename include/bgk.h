@@ -194,7 +194,10 @@ int bgk_get_lagged_edges(bgk_handle* h, int j, int32_t* h_edges, int cap, int* n
  * model, walls and storage precision; else BGK_E_IO) and replaces its state: the next
  * bgk_step is bit-identical to the one the saving handle would take, given the same inflow
  * data (these are not in the file: set them on the loading handle).
- * Returns BGK_E_IO when the file cannot be written/read or does not match. */
+ * Returns BGK_E_IO when the file cannot be written/read or does not match.  A file whose
+ * header does not match leaves the handle's state as it was; a file that matches but ends
+ * early (or fails to copy) leaves the handle without a state: bgk_step then returns
+ * BGK_E_INVALID until the next bgk_set_* call or successful bgk_load. */
 int bgk_save(bgk_handle* h, const char* path);
 int bgk_load(bgk_handle* h, const char* path);
 /* Steps taken since the state was last set or loaded (bgk_set_*, bgk_load restores the
@@ -231,7 +234,8 @@ int bgk_moments_range_device(bgk_handle* h, int j_begin, int j_end, double* d_U)
 
 /* Advance nsteps implicit steps (Sec. 3.5 stages, Sec. 4 Picard loop to tolerance).
  * Each step runs as one CUDA graph with one conditional while-loop per stage.  st may
- * be NULL.  Errors: BGK_E_NOCONV, BGK_E_NONPHYSICAL, BGK_E_CUDA. */
+ * be NULL.  Errors: BGK_E_INVALID (no state set), BGK_E_NOCONV, BGK_E_NONPHYSICAL,
+ * BGK_E_CUDA. */
 int bgk_step(bgk_handle* h, int nsteps, bgk_stats* st);
 /* Same, host-synchronous only at the end; returns immediately after enqueueing when
  * async != 0 (stats then come from bgk_last_stats after a stream sync). */
@@ -243,6 +247,14 @@ int bgk_synchronize(bgk_handle* h);
 /* Instrumentation: the sweep kernel's event-timed average duration (ms) and launch
  * count since the last reset, recorded on the handle's stream. */
 int bgk_timing(bgk_handle* h, int reset, double* sweep_ms_total, int64_t* sweep_launches);
+
+/* Measured FMA rate of the current device in TFLOP/s (2 flops per fused multiply-add),
+ * dtype BGK_DTYPE_F64 or BGK_DTYPE_F32: the best of three event-timed launches of
+ * independent FMA chains on every SM (after one warm-up launch), on a stream of its own.
+ * It is the denominator of the arithmetic roofline of the FP64 sweeps, whose local solves
+ * are bound by the FP64 pipe (no FP64 tensor path is used).  Allocates and frees a few KB
+ * of device memory.  Errors: BGK_E_INVALID, BGK_E_OOM, BGK_E_CUDA. */
+int bgk_probe_fma_tflops(int dtype, double* tflops);
 
 /* Choose the sweep algorithm by measurement (Sec. 4.1: TS wins when generations are narrow
  * and the ordinates many, TGS otherwise): times `reps` sweeps of each on the current state
@@ -337,7 +349,9 @@ int bgk_batch_set_guess(bgk_batch* b, bgk_mlp* m);
  * Computes, from d_f ([n_ordinates][n_nodes] of dtype on the current device), the
  * moments d_U_new ([n_nodes][dim+2], FP64) and writes to d_measure (one device double)
  * max(|dU_0|/|U_0|, |dU_1|/max(|U_1|, |U_0|), |dU_2|/|U_2|) against d_U_old -- the same
- * reduction and measure as the handle's Picard loop.  Work is enqueued on `stream`
+ * reduction and measure as the handle's Picard loop (FP32 data are summed in FP64 here and
+ * as compensated float pairs by the handle: the two agree to 1e-12 relative, like FP64
+ * data).  Work is enqueued on `stream`
  * (a cudaStream_t; NULL = the legacy default stream); results are ready when the
  * stream reaches that point.  Scratch lives in one file-scope device array of
  * 16384 x 6 doubles (768 KiB) that every GPU loading the library holds until exit:

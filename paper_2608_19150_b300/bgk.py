@@ -105,6 +105,7 @@ def load(path: str = LIB_PATH):
         "bgk_synchronize": [P],
         "bgk_timing": [P, I, C.POINTER(D), C.POINTER(C.c_int64)],
         "bgk_autotune_sweep": [P, I, V],
+        "bgk_probe_fma_tflops": [I, C.POINTER(D)],
         "bgk_moments_measure_noalloc": [C.POINTER(VGrid), I, C.c_int64, V, I, V, V, V, V],
         "bgk_batch_create": [I, C.POINTER(Mesh), C.POINTER(VGrid), C.POINTER(Physics), C.POINTER(Config),
                              C.POINTER(P)],
@@ -164,6 +165,13 @@ def moments_measure_noalloc(L, n_points, k_v, dim, n_nodes, f_ptr, dtype, U_old_
                                             DTYPES[np.dtype(dtype)], C.c_void_p(U_old_ptr), C.c_void_p(U_new_ptr),
                                             C.c_void_p(measure_ptr), C.c_void_p(stream) if stream else None),
         "bgk_moments_measure_noalloc")
+
+
+def probe_fma_tflops(dtype=np.float64):
+    """bgk_probe_fma_tflops: measured FMA rate of the current device (TFLOP/s)."""
+    t = C.c_double()
+    _ck(load().bgk_probe_fma_tflops(DTYPES[np.dtype(dtype)], C.byref(t)), "bgk_probe_fma_tflops")
+    return t.value
 
 
 def _wall_kinds(walls):

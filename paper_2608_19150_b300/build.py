@@ -13,7 +13,7 @@ LIB = os.path.join(HERE, "libbgk_b300.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-SOURCES = ["bgk_lib.cu", "bgk_batch.cuh", "bgk_mlp.cuh", "bgk_guess.cuh", "bgk_static.cu", "bgk_host.cpp", "bgk_kernels.cuh", "bgk_internal.h", "bgk_tables.h"]
+SOURCES = ["bgk_lib.cu", "bgk_batch.cuh", "bgk_mlp.cuh", "bgk_guess.cuh", "bgk_static.cu", "bgk_probe.cu", "bgk_host.cpp", "bgk_kernels.cuh", "bgk_internal.h", "bgk_tables.h"]
 
 
 def _stale() -> bool:
@@ -34,7 +34,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
                            "-I", INC, "-c", os.path.join(CSRC, "bgk_host.cpp"), "-o", host_o])
     cmd = [NVCC] + ARCH + ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
                            "-shared", "-I", INC, os.path.join(CSRC, "bgk_lib.cu"),
-                           os.path.join(CSRC, "bgk_static.cu"), host_o, "-o", LIB + ".tmp"]
+                           os.path.join(CSRC, "bgk_static.cu"), os.path.join(CSRC, "bgk_probe.cu"), host_o, "-o", LIB + ".tmp"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     subprocess.check_call(cmd)

@@ -1288,8 +1288,12 @@ int bgk_load(bgk_handle* h, const char* path) {
             c.ncell == want.ncell && c.ndof == want.ndof && c.nv == want.nv && c.npoints == want.npoints &&
             c.kv == want.kv && c.integrator == want.integrator && c.nnode == want.nnode && c.nfv == want.nfv &&
             c.L == want.L && c.nu == want.nu && c.dt == want.dt && c.mesh_hash == want.mesh_hash;
+  if (!ok) {  // nothing of the handle's state has been touched
+    std::fclose(fp);
+    return BGK_E_IO;
+  }
   const size_t fb = h->nfv * h->tsize;
-  ok = ok && ckpt_stream(fp, h->f, fb, false, h->stream);
+  ok = ckpt_stream(fp, h->f, fb, false, h->stream);
   if (ok && c.have_prev) ok = ckpt_stream(fp, h->fprev, fb, false, h->stream);
   if (ok && c.have_hist) {
     // the guess history is restored when this handle has a network attached
@@ -1302,7 +1306,13 @@ int bgk_load(bgk_handle* h, const char* path) {
     ok = cudaMemset(h->have_hist, 0, sizeof(int)) == cudaSuccess;
   }
   std::fclose(fp);
-  if (!ok) return BGK_E_IO;
+  if (!ok) {
+    // f (and perhaps the history) is partly overwritten: the handle has no valid state
+    // until the next bgk_set_* or a successful bgk_load
+    h->state_set = false;
+    h->have_prev = false;
+    return BGK_E_IO;
+  }
   if (cudaMemcpyAsync(h->fk, h->f, fb, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess ||
       cudaStreamSynchronize(h->stream) != cudaSuccess)
     return BGK_E_CUDA;
@@ -1379,7 +1389,7 @@ int bgk_moments_range_device(bgk_handle* h, int j_begin, int j_end, double* d_U)
 }
 
 int bgk_step_async(bgk_handle* h, int nsteps) {
-  if (!h || nsteps < 0) return BGK_E_INVALID;
+  if (!h || nsteps < 0 || !h->state_set) return BGK_E_INVALID;
   for (int k = 0; k < nsteps; ++k) {
     const bool start = h->phys.integrator == BGK_BDF2 && !h->have_prev;
     if (h->cfg.eager) {

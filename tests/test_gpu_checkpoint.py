@@ -75,6 +75,51 @@ def test_mismatched_or_broken_files_are_refused(tmp_path):
     assert e.value.status == bgk.BGK_E_IO
 
 
+def test_failed_load_never_leaves_mixed_state(tmp_path):
+    """A file refused at its header leaves the state as it was (the next step equals the
+    step of an untouched handle); a file that matches but ends early leaves no state, so a
+    step is refused (BGK_E_INVALID) until a state is set again."""
+    w = synth.workload_p1_square(n_side=6, n_v=12, k_v=2, knudsen=0.05)
+    a = bgk.Solver.from_workload(w)
+    a.set_state_maxwellian(w.init)
+    a.set_inflow_maxwellian(w.inflow)
+    a.step(1)
+    path = str(tmp_path / "state.bgk")
+    a.save(path)
+    other = synth.workload_p1_square(n_side=6, n_v=12, k_v=2, knudsen=0.07)
+    bad_header = str(tmp_path / "other.bgk")
+    o = bgk.Solver.from_workload(other)
+    o.set_state_maxwellian(other.init)
+    o.save(bad_header)
+    truncated = str(tmp_path / "short.bgk")
+    with open(path, "rb") as src, open(truncated, "wb") as dst:
+        dst.write(src.read()[: os.path.getsize(path) * 2 // 3])
+    ref = bgk.Solver.from_workload(w)
+    ref.set_state_maxwellian(w.init)
+    ref.set_inflow_maxwellian(w.inflow)
+    ref.step(1)
+    b = bgk.Solver.from_workload(w)
+    b.set_state_maxwellian(w.init)
+    b.set_inflow_maxwellian(w.inflow)
+    b.step(1)
+    with pytest.raises(bgk.BgkError) as e:
+        b.load(bad_header)
+    assert e.value.status == bgk.BGK_E_IO
+    st_b, st_r = b.step(1), ref.step(1)
+    np.testing.assert_array_equal(b.get_f(), ref.get_f())
+    assert list(st_b.iterations) == list(st_r.iterations)
+    with pytest.raises(bgk.BgkError) as e:
+        b.load(truncated)
+    assert e.value.status == bgk.BGK_E_IO
+    with pytest.raises(bgk.BgkError) as e:
+        b.step(1)
+    assert e.value.status == bgk.BGK_E_INVALID
+    b.load(path)                                  # a good file restores a usable state
+    st_b, st_a = b.step(1), a.step(1)
+    np.testing.assert_array_equal(b.get_f(), a.get_f())
+    assert list(st_b.iterations) == list(st_a.iterations)
+
+
 def test_lagged_edges_match_the_oracle():
     w = twisted_workload(3, 8)
     s, o = make_pair(w)

@@ -88,3 +88,44 @@ def test_autotune_needs_a_state():
     with pytest.raises(bgk.BgkError) as e:
         s.autotune_sweep()
     assert e.value.status == bgk.BGK_E_INVALID
+
+
+def _oracle_sweep(o, f, f0, fbc, nu, nus, dt):
+    """One oracle sweep from iterate f with the Maxwellian of f's moments, q = f0 / dt."""
+    U = o.moments(f)
+    nut = U.copy()
+    d = o.dim
+    nut[:, 1:1 + d] = U[:, 1:1 + d] / U[:, :1]
+    nut[:, 1 + d] = (2 * U[:, 1 + d] / U[:, 0] - (nut[:, 1:1 + d] ** 2).sum(1)) / d
+    return o.sweep(f, o.maxwellian(nut), f0 / dt, fbc, nu, nus)
+
+
+def _oracle_cases():
+    return {"p1_tri": synth.workload_p1_square(n_side=8, n_v=16),
+            "p2_tri": small_shock_tube(n=8, kx=2, n_v=16, integrator="BE"),
+            "p1_tet_cycles": twisted_workload(3, 8),
+            "q1_sod_walls": synth.workload_sod_strip(nx=32, ny=6, n_v=16, knudsen=1e-3, integrator="BE")}
+
+
+@pytest.mark.parametrize("precision,cache", [("fp64", "on"), ("fp64", "off"), ("fp32", "off")])
+@pytest.mark.parametrize("name", ["p1_tri", "p2_tri", "p1_tet_cycles", "q1_sod_walls"])
+def test_ts_matches_oracle(name, precision, cache):
+    """TS (Sec. 4.1) against the oracle's sweep, element by element: two sweeps from the
+    initial state (the second reads the first's lagged and wall values), FP64 at 1e-12
+    and FP32 at 2e-5 (the generation sweep's tolerances)."""
+    from gpu_common import make_pair
+    w = _oracle_cases()[name]
+    s, o = make_pair(w, precision=precision, cache_inverse=cache, sweep_mode="ts")
+    assert s.sweep_mode == "ts"
+    s.set_state_maxwellian(w.init)
+    s.set_inflow_maxwellian(w.inflow)
+    f0 = o.maxwellian(w.init)
+    fbc = o.maxwellian(w.inflow)
+    dt = s.dt
+    f = f0
+    tol = 2e-5 if precision == "fp32" else 1e-12
+    for it in range(2):
+        s.sweep(0.0, 0.0)
+        f = _oracle_sweep(o, f, f0, fbc, w.nu, w.nu + 1.0 / dt, dt)
+        err = rel_err(s.get_f(), f)
+        assert err < tol, (it, err)
