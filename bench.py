@@ -459,7 +459,7 @@ def timed_steps(s, steps, world, local, tstream, guess=False, main_fp32=False, w
 PROFILED_TRAFFIC = {
     "fp64": (3.750e9, "profiles/sweep_fp64_cached_shock_tube_64_p2_v32.md"),
     "fp32": (0.631e9, "profiles/sweep_fp32_fused_shock_tube_64_p2_v32.md"),
-}
+}   # the shared-memory front sweep (k_sweep_front) has no capture yet: its traffic is null
 
 
 def sweep_roofline(w, precision, reps, peaks, n_side=None, n_v=None, sweep_mode="auto", fp64_peak=None):
@@ -485,6 +485,7 @@ def sweep_roofline(w, precision, reps, peaks, n_side=None, n_v=None, sweep_mode=
     kind = elem_of(w)[0]
     ename = {"p2tri": "ElemP2Tri", "p1tri": "ElemP1Tri", "p1tet": "ElemP1Tet", "q1quad": "ElemQ1Quad"}[kind]
     kname = "k_sweep_ts" if s.sweep_mode == "ts" else "k_sweep"
+    front = precision != "fp64" and kname == "k_sweep" and s.front_slots > 0
     if precision == "fp64":
         fl = sweep_flops_per_item(cached, kind)
         tf = fl * s.nv * s.ncell / (sweep_ms * 1e-3) / 1e12
@@ -496,9 +497,10 @@ def sweep_roofline(w, precision, reps, peaks, n_side=None, n_v=None, sweep_mode=
     else:
         r = {"bound": "hbm", "achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_gbs / hbm_peak,
              "traffic": None,
-             "kernel": "%s<%s,float,%s>" % (kname, ename, "cached" if cached else "uncached,fused source"),
-             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
-    profiled = PROFILED_TRAFFIC.get(precision)
+             "kernel": ("k_sweep_front<%s>" % ename) if front else
+                       "%s<%s,float,%s>" % (kname, ename, "cached" if cached else "uncached,fused source"),
+             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)", "front_slots": s.front_slots}
+    profiled = PROFILED_TRAFFIC.get("fp32_front" if front else precision)
     if profiled and kind == "p2tri" and kname == "k_sweep" and n_side and n_v == 32 and (precision == "fp32" or cached):
         r["traffic"] = profiled[0] * (n_side / 64.0) ** 2
         r["traffic_source"] = profiled[1] + " (scaled from 64x64 by the cell count)"

@@ -54,7 +54,7 @@ class Config(C.Structure):
     _fields_ = [("tau", C.c_double), ("l_max", C.c_int), ("precision", C.c_int), ("block_threads", C.c_int),
                 ("stream", C.c_void_p), ("eager", C.c_int),
                 ("cache_inverse", C.c_int), ("fp32_floor", C.c_double), ("prefetch", C.c_int),
-                ("sweep_mode", C.c_int)]
+                ("sweep_mode", C.c_int), ("sweep_front", C.c_int)]
 
 SWEEP_MODES = {"auto": 0, "tgs": 1, "ts": 2}
 
@@ -81,6 +81,7 @@ def load(path: str = LIB_PATH):
         "bgk_destroy": [P],
         "bgk_sizes": [P, C.POINTER(C.c_int64)],
         "bgk_get_dt": [P, C.POINTER(D)],
+        "bgk_front_slots": [P, C.POINTER(I)],
         "bgk_set_state_maxwellian": [P, V],
         "bgk_set_inflow_maxwellian": [P, V],
         "bgk_set_inflow": [P, V],
@@ -187,7 +188,7 @@ class Solver:
 
     def __init__(self, dim, kx, xyz, cells, n_v, k_v, L, nu, integrator="BE", dt=0.0, cfl=10.0, tau=1e-8,
                  l_max=1000, precision="fp64", block_threads=0, stream=None, eager=False, cache_inverse="auto", fp32_floor=0.0, prefetch=False,
-                 sweep_mode="auto", collision="maxwellian", walls=None):
+                 sweep_mode="auto", collision="maxwellian", walls=None, sweep_front=True):
         self.lib = load()
         self._xyz = np.ascontiguousarray(xyz, dtype=np.float64)
         self._cells = np.ascontiguousarray(cells, dtype=np.int32)
@@ -199,7 +200,7 @@ class Solver:
         cf = Config(float(tau), int(l_max), PRECISIONS[precision], int(block_threads),
                     C.c_void_p(stream) if stream else None, int(bool(eager)),
                     {"auto": 0, "on": 1, "off": 2}[cache_inverse], float(fp32_floor), 1 if prefetch else 0,
-                    SWEEP_MODES[sweep_mode])
+                    SWEEP_MODES[sweep_mode], 0 if sweep_front else 2)
         h = C.c_void_p()
         _ck(self.lib.bgk_create(C.byref(m), C.byref(vg), C.byref(ph), C.byref(cf), C.byref(h)), "bgk_create")
         self.h = h
@@ -247,6 +248,13 @@ class Solver:
 
     def __del__(self):
         self.close()
+
+    @property
+    def front_slots(self):
+        """Shared-memory front slots of the FP32 generation sweep (0: global reads)."""
+        n = C.c_int()
+        _ck(self.lib.bgk_front_slots(self.h, C.byref(n)), "bgk_front_slots")
+        return n.value
 
     @property
     def dt(self):

@@ -382,6 +382,7 @@ int bgk_batch_create(int n, const bgk_mesh* meshes, const bgk_vgrid* vgrids, con
   }
   c.stream = b->stream;
   c.eager = 1;  // instances never capture their own graphs; the batch captures one
+  c.sweep_front = 2;  // the batched sweep reads upwind traces from global memory
   const int cache_policy = c.cache_inverse;
   c.cache_inverse = 2;  // caches are added below, once every instance's arrays exist
   for (int i = 0; i < n; ++i) {

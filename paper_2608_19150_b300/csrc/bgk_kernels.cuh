@@ -1258,6 +1258,287 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs sa, VGrid g, T nus, Src
                                                       (int)threadIdx.x, (int)blockDim.x, CtaBarrier(), pf_smem);
 }
 
+// ---------------------------------------------------------------------------------
+// Shared-memory front of the FP32 generation sweep.  The trace of a cell on one of its
+// outflow faces is read by the neighbour across that face, in a later generation of the
+// same ordinate when the edge is not lagged (Sec. 4.1), so it only has to live from the
+// cell's generation to the neighbour's.  Per ordinate, every such (cell, outflow face)
+// gets a 16-byte slot of a shared-memory buffer by greedy interval colouring in generation
+// order (a slot is free again one generation after its reader), and every schedule
+// position records per face either the slot it writes (outflow) or the slot it reads
+// (non-lagged inflow) plus whether the two cells list the face's vertices in opposite
+// order.  The sweep then reads those upwind traces with one shared-memory load per face;
+// lagged upwind cells (their global values are still f^l) and boundary faces read global
+// memory as before.  Packed per position: 12 bits per face (kFrontNone: none), then one
+// reversal bit per face from bit 48.
+constexpr unsigned kFrontNone = 0xFFFu;
+constexpr int kFrontMaxSlots = 4000;
+constexpr int kFrontSmemMax = 96 * 1024;  // dynamic shared memory of one front-sweep CTA
+
+// genc[j][c] = generation of cell c for ordinate j (one CTA per ordinate)
+__global__ void k_front_gen(const uint32_t* __restrict__ glist, const int32_t* __restrict__ lvl,
+                            const int32_t* __restrict__ ngen, int ncell, int32_t* __restrict__ genc) {
+  const int j = blockIdx.x;
+  const uint32_t* gl = glist + (size_t)j * ncell;
+  const int32_t* lv = lvl + (size_t)j * (ncell + 1);
+  int32_t* gc = genc + (size_t)j * ncell;
+  const int G = ngen[j];
+  for (int gg = 0; gg < G; ++gg)
+    for (int k = lv[gg] + threadIdx.x; k < lv[gg + 1]; k += blockDim.x) gc[gl[k] & kCellMask] = gg;
+}
+
+// Greedy slot allocation of one ordinate per thread, in generation order.  A face that is
+// outflow for cell c is inflow for its neighbour, which reads c's trace in this sweep
+// exactly when its generation is higher (a lagged edge points the other way).
+// fslot[j][c][f] receives the slot of (c, f) or -1; work holds 2 * kFrontMaxSlots int16
+// per ordinate (release lists, free stack); head (ncell + 1) ints per ordinate;
+// *nslots the largest slot count, *overflow set when an ordinate needs too many.
+template <int NF>
+__global__ void k_front_alloc(const uint32_t* __restrict__ glist, const int32_t* __restrict__ lvl,
+                              const int32_t* __restrict__ ngen, const int32_t* __restrict__ nbr, int ncell, int nv,
+                              const int32_t* __restrict__ genc, int16_t* __restrict__ fslot,
+                              int32_t* __restrict__ head, int16_t* __restrict__ work, int* nslots, int* overflow) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nv) return;
+  const uint32_t* gl = glist + (size_t)j * ncell;
+  const int32_t* lv = lvl + (size_t)j * (ncell + 1);
+  const int32_t* gc = genc + (size_t)j * ncell;
+  int16_t* fs = fslot + (size_t)j * ncell * 4;
+  int32_t* hd = head + (size_t)j * (ncell + 1);  // hd[g]: slots released at the start of generation g
+  int16_t* nxt = work + (size_t)j * 2 * kFrontMaxSlots;
+  int16_t* stk = nxt + kFrontMaxSlots;
+  const int G = ngen[j];
+  for (int gg = 0; gg <= G; ++gg) hd[gg] = -1;
+  int nfree = 0, top = 0, over = 0;
+  for (int gg = 0; gg < G; ++gg) {
+    for (int sl = hd[gg]; sl >= 0; sl = nxt[sl]) stk[nfree++] = (int16_t)sl;
+    for (int k = lv[gg]; k < lv[gg + 1]; ++k) {
+      const uint32_t e = gl[k];
+      const int c = (int)(e & kCellMask);
+      const uint32_t code = e >> kCellBits;
+      for (int i = 0; i < 4; ++i) {
+        int sl = -1;
+        if (i < NF && ((code >> (2 * i)) & 3u) == 1u) {
+          const int nb = nbr[(size_t)c * 4 + i];
+          const int gr = nb >= 0 ? gc[nb] : -1;
+          if (gr > gg) {
+            if (nfree > 0)
+              sl = stk[--nfree];
+            else if (top < kFrontMaxSlots)
+              sl = top++;
+            else
+              over = 1;
+            if (sl >= 0) {
+              nxt[sl] = (int16_t)hd[gr + 1];
+              hd[gr + 1] = sl;
+            }
+          }
+        }
+        fs[(size_t)c * 4 + i] = (int16_t)sl;
+      }
+    }
+  }
+  atomicMax(nslots, top);
+  if (over) atomicOr(overflow, 1);
+}
+
+// Packed front slots of every schedule position (see above).
+template <class E>
+__global__ void k_front_pack(const uint32_t* __restrict__ glist, const int32_t* __restrict__ nbr,
+                             const int32_t* __restrict__ nbr_face, const uint64_t* __restrict__ perm, int ncell,
+                             const int32_t* __restrict__ genc, const int16_t* __restrict__ fslot,
+                             uint64_t* __restrict__ fslots) {
+  constexpr int NF = E::NF;
+  const int j = blockIdx.x;
+  const uint32_t* gl = glist + (size_t)j * ncell;
+  const int32_t* gc = genc + (size_t)j * ncell;
+  const int16_t* fs = fslot + (size_t)j * ncell * 4;
+  for (int k = threadIdx.x; k < ncell; k += blockDim.x) {
+    const uint32_t e = gl[k];
+    const int c = (int)(e & kCellMask);
+    const uint32_t code = e >> kCellBits;
+    uint64_t w = 0;
+#pragma unroll
+    for (int i = 0; i < NF; ++i) {
+      uint64_t sl = kFrontNone, rev = 0;
+      const uint32_t fl = (code >> (2 * i)) & 3u;
+      if (fl == 1u) {
+        const int s0 = fs[(size_t)c * 4 + i];
+        if (s0 >= 0) sl = (uint64_t)s0;
+      } else if (fl == 2u) {
+        const int nb = nbr[(size_t)c * 4 + i];
+        if (nb >= 0 && gc[nb] < gc[c]) {
+          const int f2 = nbr_face[(size_t)c * 4 + i];
+          const int s0 = fs[(size_t)nb * 4 + f2];
+          if (s0 >= 0) {
+            sl = (uint64_t)s0;
+            // the neighbour wrote its face-node values in its own face order
+            const int p0 = (int)((perm[c] >> (16 * i)) & 15u);
+            rev = p0 == E::fn(f2, 0) ? 0u : 1u;
+          }
+        }
+      }
+      w |= sl << (12 * i);
+      w |= rev << (48 + i);
+    }
+    fslots[(size_t)j * ncell + k] = w;
+  }
+}
+
+// Store the N values of T at p with the widest vector stores the alignment allows.
+template <typename T, int N, int ALIGN>
+__device__ __forceinline__ void store_vec(T* __restrict__ p, const T (&v)[N]) {
+  constexpr int BYTES = N * (int)sizeof(T);
+  if constexpr (sizeof(T) == 4 && ALIGN % 16 == 0 && BYTES % 16 == 0) {
+#pragma unroll
+    for (int q = 0; q < N / 4; ++q)
+      reinterpret_cast<float4*>(p)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+  } else if constexpr (sizeof(T) == 4 && ALIGN % 8 == 0 && BYTES % 8 == 0) {
+#pragma unroll
+    for (int q = 0; q < N / 2; ++q) reinterpret_cast<float2*>(p)[q] = make_float2(v[2 * q], v[2 * q + 1]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < N; ++q) p[q] = v[q];
+  }
+}
+
+// FP32 generation sweep with the shared-memory front (one CTA per ordinate, the same
+// operations per cell as sweep_ordinate with the fused source): Sec. 4, Eq. bgk-ss-picard,
+//   (nu_s Mh + sum_i r_i (Dd_i + [s_i>0] Eh_i)) f_K = Mh src_K + sum_{s_i<0} (-r_i) Eh_i y_i,
+// src = prod_a cf[a][j_a] + qscale q.  The generation offsets sit in shared memory; each
+// thread takes positions lv[g] + tid + m nt of generation g and carries the next item's
+// neighbours, permutation, geometry, q, factors and front slots in registers (loaded
+// while the current item is solved; the schedule entry one item earlier still).
+// Dynamic shared memory: the front (S float4), then the generation offsets (lvcap ints,
+// G + 1 of the largest G rounded up to 4).  2D elements (P1/P2 triangles, Q1).
+template <class E>
+__global__ void __launch_bounds__(128, 4) k_sweep_front(SweepArgs sa, VGrid g, float nus, SrcArgs<float> sr,
+                                                       const float* __restrict__ fbc, float* f, const DevState* ds,
+                                                       int jofs, const uint64_t* __restrict__ fslots, int S,
+                                                       int lvcap) {
+  using T = float;
+  constexpr int ND = E::NDOF, NF = E::NF, FD = E::FD;
+  static_assert(E::D == 2 && FD <= 4, "2D elements");
+  extern __shared__ __align__(16) float fsm[];
+  if (ds && (ds->status != BGK_OK || ds->done)) return;
+  const int j = jofs + (int)blockIdx.x, tid = (int)threadIdx.x, nt = (int)blockDim.x;
+  const int G = sa.ngen[j];
+  float4* front = reinterpret_cast<float4*>(fsm);
+  int* lv = reinterpret_cast<int*>(fsm + 4 * S);
+  {
+    const int32_t* lvg = sa.lvl + (size_t)j * (sa.ncell + 1);
+    for (int i = tid; i <= G; i += nt) lv[i] = lvg[i];
+  }
+  double vd[3];
+  ordinate(g, j, vd);
+  const T v0 = (T)vd[0], v1 = (T)vd[1];
+  const uint32_t* gl = sa.glist + (size_t)j * sa.ncell;
+  const uint64_t* slj = fslots + (size_t)j * sa.ncell;
+  T* fj = f + (size_t)j * sa.nnode;
+  const SrcRows<T> rw = src_rows<T, true>(sr, g, j, sa.nnode);
+  const T* bj = fbc + (size_t)j * sa.nbface * FD;
+  __syncthreads();
+  auto seek = [&](int g2, int& kq, int& gq) {
+    for (; g2 < G; ++g2) {
+      const int k2 = lv[g2] + tid;
+      if (k2 < lv[g2 + 1]) {
+        kq = k2;
+        gq = g2;
+        return;
+      }
+    }
+    kq = -1;
+    gq = G;
+  };
+  auto advance = [&](int kq, int gq, int& kr, int& gr) {
+    if (kq < 0) {
+      kr = -1;
+      gr = G;
+    } else if (kq + nt < lv[gq + 1]) {
+      kr = kq + nt;
+      gr = gq;
+    } else {
+      seek(gq + 1, kr, gr);
+    }
+  };
+  SweepItem<E, T, true, true> cur, nxt;
+  uint64_t scur = 0, snxt = 0;
+  // current item k, next kn (its data is loaded while k is solved) and the one after,
+  // kn2 (its schedule entry is loaded while k is solved)
+  int k, gk, kn, gn, kn2, gn2;
+  seek(0, k, gk);
+  advance(k, gk, kn, gn);
+  advance(kn, gn, kn2, gn2);
+  if (k >= 0) {
+    fetch_item<E, T, true, true>(sa, gl, rw, k, cur);
+    scur = slj[k];
+    resolve_src(cur, sr.qscale);
+  }
+  uint32_t en = kn >= 0 ? gl[kn] : 0u;
+  for (int gg = 0; gg < G; ++gg) {
+    while (k >= 0 && gk == gg) {
+      if (kn >= 0) {
+        fetch_item_e<E, T, true, true>(sa, en, rw, nxt);
+        snxt = slj[kn];
+      }
+      const uint32_t en2 = kn2 >= 0 ? gl[kn2] : 0u;
+      const int c = (int)(cur.e & kCellMask);
+      const uint32_t code = cur.e >> kCellBits;
+      T r[NF];
+      unsigned outm = 0;
+      face_rates_t<E, T>(cur.geo, code, v0, v1, T(0), r, outm);
+      T b[ND];
+      E::mass(cur.src, b);
+      const int nbs[4] = {cur.nb.x, cur.nb.y, cur.nb.z, cur.nb.w};
+#pragma unroll
+      for (int i = 0; i < NF; ++i) {
+        if (((code >> (2 * i)) & 3u) != 2u) continue;
+        const unsigned su = (unsigned)(scur >> (12 * i)) & kFrontNone;
+        T y[FD];
+        if (su != kFrontNone) {
+          // non-lagged interior inflow: the upwind cell's face trace from the front
+          const float4 t = front[su];
+          const bool rv = (scur >> (48 + i)) & 1u;
+          y[0] = rv ? t.y : t.x;
+          y[1] = rv ? t.x : t.y;
+          if constexpr (FD > 2) y[2] = t.z;
+        } else if (nbs[i] < 0) {
+#pragma unroll
+          for (int kk = 0; kk < FD; ++kk) y[kk] = bj[(-nbs[i] - 1) * FD + kk];
+        } else {
+          // lagged upwind cell: its global values are still f^l
+#pragma unroll
+          for (int kk = 0; kk < FD; ++kk) y[kk] = fj[nbs[i] * ND + (int)((cur.pm >> (16 * i + 4 * kk)) & 15u)];
+        }
+        E::inflow(i, -r[i], y, b);
+      }
+      T A[ND][ND];
+      E::assemble(nus, r, outm, A);
+      lu_solve<ND, T>(A, b);
+      store_vec<T, ND, cell_align<E, T>()>(fj + c * ND, b);
+      // this cell's traces on its outflow faces, in its own face order, for the readers
+#pragma unroll
+      for (int i = 0; i < NF; ++i) {
+        const unsigned so = (unsigned)(scur >> (12 * i)) & kFrontNone;
+        if (((code >> (2 * i)) & 3u) == 1u && so != kFrontNone)
+          front[so] = make_float4(b[E::fn(i, 0)], b[E::fn(i, 1)], FD > 2 ? b[E::fn(i, 2 % FD)] : T(0), T(0));
+      }
+      if (kn >= 0) {
+        cur = nxt;
+        scur = snxt;
+        resolve_src(cur, sr.qscale);
+      }
+      k = kn;
+      gk = gn;
+      kn = kn2;
+      gn = gn2;
+      en = en2;
+      advance(kn, gn, kn2, gn2);
+    }
+    __syncthreads();
+  }
+}
+
 // out = a_k * fk + a_f * f + sum_r cF[r] * F[r]   (stage bookkeeping of Sec. 3.5)
 template <typename T>
 __global__ void k_combine(size_t n, T* __restrict__ out, double a_k, const T* __restrict__ fk, double a_f,

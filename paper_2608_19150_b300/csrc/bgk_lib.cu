@@ -72,6 +72,10 @@ struct bgk_handle {
   bool fuse_src = false;
   const void* fused_q = nullptr;
   double fused_qscale = 0.0;
+  // shared-memory front of the FP32 generation sweep (k_sweep_front): packed slots per
+  // schedule position, the slot count and the dynamic shared memory of one CTA
+  uint64_t* fslots = nullptr;
+  int front_slots = 0;
   int mom_blocks = 0;
   DevState* ds = nullptr;
   bool have_prev = false;    // BDF2 history present
@@ -216,6 +220,10 @@ size_t prefetch_smem(const bgk_handle* h) {
   return 2 * (size_t)h->sweep_threads * (h->hm.geo_stride * sizeof(double) + ainv_stride<E, T>() * sizeof(T));
 }
 
+// generation offsets of the front sweep: G + 1 ints of the largest G, rounded up to 4
+int front_lvcap(const bgk_handle* h) { return (h->Gmax + 1 + 3) & ~3; }
+size_t front_smem_bytes(const bgk_handle* h, int S, int threads);
+
 template <class E, typename T>
 void launch_sweep_t(bgk_handle* h, double nus, int jb, int je) {
   const bool cached = h->Ainv && nus == h->nus_cached;
@@ -242,6 +250,14 @@ void launch_sweep_t(bgk_handle* h, double nus, int jb, int je) {
   if constexpr (sizeof(T) == 4) {
     if (h->fuse_src) {
       const SrcArgs<T> fr{nullptr, (const T*)h->cf, (const T*)h->fused_q, (T)h->fused_qscale};
+      if constexpr (E::D == 2) {
+        if (h->fslots && front_smem_bytes(h, h->front_slots, h->sweep_threads) <= (size_t)kFrontSmemMax) {
+          k_sweep_front<E><<<je - jb, h->sweep_threads, front_smem_bytes(h, h->front_slots, h->sweep_threads),
+                             h->stream>>>(sweep_args(h), h->g, (T)nus, fr, (const T*)h->fbc, (T*)h->f, h->ds, jb,
+                                          h->fslots, h->front_slots, front_lvcap(h));
+          return;
+        }
+      }
       k_sweep<E, T, false, false, true><<<je - jb, h->sweep_threads, 0, h->stream>>>(
           sweep_args(h), h->g, (T)nus, fr, (const T*)h->fbc, nullptr, (T*)h->f, h->ds, jb);
       return;
@@ -707,6 +723,69 @@ int build_dags(bgk_handle* h) {
   return BGK_OK;
 }
 
+// Shared-memory front of the FP32 generation sweep (k_sweep_front): per ordinate, the
+// generation of every cell, greedy slots of the (cell, outflow face) traces that a later
+// generation reads, then the packed slots of every schedule position.  Skipped (global
+// reads, same results) when a CTA's shared memory would exceed kFrontSmemMax, an
+// ordinate needs more than kFrontMaxSlots slots, or the scratch cannot be allocated.
+// 2D meshes only (3D fronts are surfaces, too wide to fit).
+size_t front_smem_bytes(const bgk_handle* h, int S, int threads) {
+  (void)threads;
+  return sizeof(float) * (4 * (size_t)S + front_lvcap(h));
+}
+
+int build_front(bgk_handle* h) {
+  if (!h->fuse_src || h->hm.dim != 2 || h->cfg.sweep_front == 2) return BGK_OK;
+  const int n = h->hm.ncell, nv = h->g.nv;
+  const size_t cells = (size_t)nv * n;
+  int32_t *genc = nullptr, *head = nullptr;
+  int16_t *fslot = nullptr, *work = nullptr;
+  int* cnt = nullptr;
+  int rc = BGK_OK;
+  if (dalloc(genc, sizeof(int32_t) * cells) != BGK_OK || dalloc(fslot, sizeof(int16_t) * 4 * cells) != BGK_OK ||
+      dalloc(head, sizeof(int32_t) * (size_t)nv * (n + 1)) != BGK_OK ||
+      dalloc(work, sizeof(int16_t) * 2 * kFrontMaxSlots * (size_t)nv) != BGK_OK ||
+      dalloc(cnt, sizeof(int) * 2) != BGK_OK)
+    rc = BGK_E_OOM;
+  int hc[2] = {0, 1};
+  if (rc == BGK_OK) {
+    cudaStream_t s = h->stream;
+    k_front_gen<<<nv, 256, 0, s>>>(h->glist, h->lvl, h->ngen, n, genc);
+    cudaMemsetAsync(cnt, 0, sizeof(int) * 2, s);
+    if (h->hm.quad)
+      k_front_alloc<4><<<(nv + 63) / 64, 64, 0, s>>>(h->glist, h->lvl, h->ngen, h->nbr, n, nv, genc, fslot, head,
+                                                     work, cnt, cnt + 1);
+    else
+      k_front_alloc<3><<<(nv + 63) / 64, 64, 0, s>>>(h->glist, h->lvl, h->ngen, h->nbr, n, nv, genc, fslot, head,
+                                                     work, cnt, cnt + 1);
+    if (cudaGetLastError() != cudaSuccess || cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, s) !=
+                                                   cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+      rc = BGK_E_CUDA;
+  }
+  const int S = std::max(1, hc[0]);
+  if (rc == BGK_OK && hc[1] == 0 && front_smem_bytes(h, S, h->sweep_threads) <= (size_t)kFrontSmemMax) {
+    if (dalloc(h->fslots, sizeof(uint64_t) * cells) == BGK_OK) {
+      if (h->hm.quad)
+        k_front_pack<ElemQ1Quad><<<nv, 256, 0, h->stream>>>(h->glist, h->nbr, h->nbr_face, h->perm, n, genc, fslot,
+                                                            h->fslots);
+      else if (h->hm.kx == 2)
+        k_front_pack<ElemP2Tri><<<nv, 256, 0, h->stream>>>(h->glist, h->nbr, h->nbr_face, h->perm, n, genc, fslot,
+                                                           h->fslots);
+      else
+        k_front_pack<ElemP1Tri><<<nv, 256, 0, h->stream>>>(h->glist, h->nbr, h->nbr_face, h->perm, n, genc, fslot,
+                                                           h->fslots);
+      if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(h->stream) != cudaSuccess) rc = BGK_E_CUDA;
+      h->front_slots = S;
+    } else {
+      h->fslots = nullptr;
+    }
+  }
+  if (rc == BGK_E_OOM) rc = BGK_OK;  // no room for the scratch: sweep from global memory
+  for (void* p : {(void*)genc, (void*)fslot, (void*)head, (void*)work, (void*)cnt})
+    if (p) cudaFree(p);
+  return rc;
+}
+
 void release(bgk_handle* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
@@ -715,7 +794,8 @@ void release(bgk_handle* h) {
   if (h->exec_main) cudaGraphExecDestroy(h->exec_main);
   if (h->exec_start) cudaGraphExecDestroy(h->exec_start);
   void* ptrs[] = {h->gX, h->gY, h->Uhist, h->have_hist, h->geof, h->wall,
-                  h->geo, h->nbr, h->nbr_face, h->perm, h->bnode, h->glist, h->lvl, h->ngen, h->nproc, h->Ainv, h->f, h->fk,
+                  h->geo, h->nbr, h->nbr_face, h->perm, h->bnode, h->glist, h->lvl, h->ngen, h->nproc, h->Ainv,
+                  h->fslots, h->f, h->fk,
                   h->fprev, h->src, h->fbc, h->q, h->F[0], h->F[1], h->F[2], h->U[0], h->U[1], h->partial, h->cf,
                   h->ds};
   for (void* p : ptrs)
@@ -912,6 +992,9 @@ int bgk_create(const bgk_mesh* mesh, const bgk_vgrid* vg, const bgk_physics* phy
                           96 * 1024));
   CK(cudaFuncSetAttribute(k_sweep<ElemQ1Quad, float, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           96 * 1024));
+  CK(cudaFuncSetAttribute(k_sweep_front<ElemP1Tri>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFrontSmemMax));
+  CK(cudaFuncSetAttribute(k_sweep_front<ElemP2Tri>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFrontSmemMax));
+  CK(cudaFuncSetAttribute(k_sweep_front<ElemQ1Quad>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFrontSmemMax));
   rc = build_dags(h);
   if (rc == BGK_OK) {
     // the stage coefficient nu_s = nu + 1/(dt A_ss) of the step's main stages
@@ -923,6 +1006,7 @@ int bgk_create(const bgk_mesh* mesh, const bgk_vgrid* vg, const bgk_physics* phy
     rc = build_inverse_cache(h, h->nus_main);
     h->fuse_src = h->precision == BGK_FP32_SWEEP && !h->Ainv && h->cfg.prefetch != 1;
   }
+  if (rc == BGK_OK) rc = build_front(h);
   if (rc == BGK_OK && h->cfg.precision == BGK_MIXED) {
     // the FP32 shadow: same mesh, grid, physics and stream; no graphs of its own
     bgk_config c32 = h->cfg;
@@ -967,6 +1051,13 @@ int bgk_sizes(const bgk_handle* h, int64_t* out) {
   out[7] = h->Ainv ? (int64_t)h->ainv_bytes : 0;
   out[8] = h->sweep_threads;
   out[9] = h->sweep_ts ? 2 : 1;
+  return BGK_OK;
+}
+
+int bgk_front_slots(const bgk_handle* h, int* slots) {
+  if (!h || !slots) return BGK_E_INVALID;
+  const bgk_handle* s32 = h->shadow ? h->shadow : h;
+  *slots = s32->fslots ? s32->front_slots : 0;
   return BGK_OK;
 }
 
