@@ -240,6 +240,36 @@ int bgk_sweep(bgk_handle* h, double nu_s, double q_scale);
 int bgk_sweep_range(bgk_handle* h, int j_begin, int j_end, const double* d_U, double nu_s, double q_scale);
 int bgk_moments_range_device(bgk_handle* h, int j_begin, int j_end, double* d_U);
 
+/* The rest of a sharded step, so that the caller only orders calls and moves partial
+ * moments between devices (Sec. 3.5 stages, Sec. 4 Picard loop):
+ *   bgk_shard_step_begin(h, &S, &tol): f^k <- f (BDF2 after its start-up step: the stage
+ *     source (4 f^n - f^{n-1}) / (2 dt) and the history); S = stages of this step, tol =
+ *     tau / max(1, nu dt), the Picard tolerance of Eq. (convergence-criteria).
+ *   for s < S: bgk_shard_stage_begin(h, s) -- stage s's source q^(s) (Eq. q-stages) and
+ *     coefficient nu + 1/(dt A_ss); until the measure is below tol: partial moments
+ *     (bgk_moments_range_device) summed over all parts in a fixed order
+ *     (bgk_sum_partials_device after gathering), bgk_sweep_range with nu_s = q_scale = 0
+ *     (the open stage's values), the new summed moments, bgk_conv_measure_device; then
+ *     bgk_shard_stage_end(h, s) -- the stage derivative F_s (Eq. dirk-recursive-def).
+ *   bgk_shard_step_end(h): f^{k+1} = f^k + dt sum_s b_s F_s (Eq. dirk-n) unless the method
+ *     is stiffly accurate; the BDF2 history after the start-up step; the step count.
+ * Every part holds the whole problem on its device and only its ordinates' values are
+ * meaningful; given the same summed moments every part computes the same measure, so all
+ * stop at the same iteration.  FP64 or FP32 handles without walls (BGK_MIXED and wall
+ * coupling are not sharded): BGK_E_INVALID otherwise, or when called out of order.
+ *   bgk_sum_partials_device: d_U = sum of n_parts arrays [node][d+2] stored one after
+ *     another at d_parts, added in part order 0, 1, ... (the same bits on every device).
+ *   bgk_conv_measure_device: *measure (host) = max(|dU_0|/|U_0|, |dU_1..d|/max(|U_1..d|,
+ *     |U_0|), |dU_d+1|/|U_d+1|) of device moments d_U_new against d_U_old, l2 over nodes,
+ *     summed in a fixed order (Eq. convergence-criteria with the design's reading for a
+ *     zero momentum).  Allocates a small scratch; synchronizes the handle's stream. */
+int bgk_shard_step_begin(bgk_handle* h, int* n_stages, double* tol);
+int bgk_shard_stage_begin(bgk_handle* h, int stage);
+int bgk_shard_stage_end(bgk_handle* h, int stage);
+int bgk_shard_step_end(bgk_handle* h);
+int bgk_sum_partials_device(const bgk_handle* h, const double* d_parts, int n_parts, double* d_U);
+int bgk_conv_measure_device(bgk_handle* h, const double* d_U_new, const double* d_U_old, double* measure);
+
 /* Advance nsteps implicit steps (Sec. 3.5 stages, Sec. 4 Picard loop to tolerance).
  * Each step runs as one CUDA graph with one conditional while-loop per stage.  st may
  * be NULL.  Errors: BGK_E_INVALID (no state set), BGK_E_NOCONV, BGK_E_NONPHYSICAL,

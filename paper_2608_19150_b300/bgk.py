@@ -100,6 +100,12 @@ def load(path: str = LIB_PATH):
         "bgk_sweep": [P, D, D],
         "bgk_sweep_range": [P, I, I, V, D, D],
         "bgk_moments_range_device": [P, I, I, V],
+        "bgk_shard_step_begin": [P, C.POINTER(I), C.POINTER(D)],
+        "bgk_shard_stage_begin": [P, I],
+        "bgk_shard_stage_end": [P, I],
+        "bgk_shard_step_end": [P],
+        "bgk_sum_partials_device": [P, V, I, V],
+        "bgk_conv_measure_device": [P, V, V, C.POINTER(D)],
         "bgk_step": [P, I, C.POINTER(Stats)],
         "bgk_step_async": [P, I],
         "bgk_last_stats": [P, C.POINTER(Stats)],
@@ -204,6 +210,7 @@ class Solver:
         h = C.c_void_p()
         _ck(self.lib.bgk_create(C.byref(m), C.byref(vg), C.byref(ph), C.byref(cf), C.byref(h)), "bgk_create")
         self.h = h
+        self.stream = stream
         sz = (C.c_int64 * 10)()
         _ck(self.lib.bgk_sizes(self.h, sz), "bgk_sizes")
         (self.nv, self.nnode, self.ndof, self.ncell, self.dim, self.gmax, self.lagged, self.cache_bytes,
@@ -343,6 +350,32 @@ class Solver:
         """Partial moments of ordinates [j_begin, j_end) into the device buffer at U_ptr."""
         _ck(self.lib.bgk_moments_range_device(self.h, int(j_begin), int(j_end), C.c_void_p(U_ptr)),
             "bgk_moments_range_device")
+
+    # ---- a step driven stage by stage (ordinate shards; bgk_shard_*)
+    def shard_step_begin(self):
+        """(stages of the step, Picard tolerance)"""
+        n, tol = C.c_int(), C.c_double()
+        _ck(self.lib.bgk_shard_step_begin(self.h, C.byref(n), C.byref(tol)), "bgk_shard_step_begin")
+        return n.value, tol.value
+
+    def shard_stage_begin(self, stage):
+        _ck(self.lib.bgk_shard_stage_begin(self.h, int(stage)), "bgk_shard_stage_begin")
+
+    def shard_stage_end(self, stage):
+        _ck(self.lib.bgk_shard_stage_end(self.h, int(stage)), "bgk_shard_stage_end")
+
+    def shard_step_end(self):
+        _ck(self.lib.bgk_shard_step_end(self.h), "bgk_shard_step_end")
+
+    def sum_partials_device(self, parts_ptr, n_parts, U_ptr):
+        _ck(self.lib.bgk_sum_partials_device(self.h, C.c_void_p(parts_ptr), int(n_parts), C.c_void_p(U_ptr)),
+            "bgk_sum_partials_device")
+
+    def conv_measure_device(self, U_new_ptr, U_old_ptr):
+        m = C.c_double()
+        _ck(self.lib.bgk_conv_measure_device(self.h, C.c_void_p(U_new_ptr), C.c_void_p(U_old_ptr), C.byref(m)),
+            "bgk_conv_measure_device")
+        return m.value
 
     def step(self, nsteps=1):
         st = Stats()

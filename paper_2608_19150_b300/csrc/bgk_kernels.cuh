@@ -608,6 +608,50 @@ __global__ void k_finalize(DevState* ds, const double* __restrict__ partial, int
   if (use_cond) cudaGraphSetConditional(cond, cont);
 }
 
+// U = sum_p parts[p] in part order p = 0, 1, ... (elementwise; the same bits for the same
+// inputs on every device), n values per part.
+__global__ void k_sum_parts(const double* __restrict__ parts, int nparts, size_t n, double* __restrict__ U) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    double s = parts[i];
+    for (int p = 1; p < nparts; ++p) s += parts[(size_t)p * n + i];
+    U[i] = s;
+  }
+}
+
+// Per-block sums of the convergence measure's squares (Eq. convergence-criteria): for
+// U_new, U_old [node][d+2]: |dU_0|^2, |U_0|^2, |dU_1..d|^2, |U_1..d|^2, |dU_d+1|^2, |U_d+1|^2
+// into partial[block][6]; one fixed block size and grid, so the sums are deterministic.
+__global__ void __launch_bounds__(256) k_measure_parts(const double* __restrict__ Un, const double* __restrict__ Uo,
+                                                       int nnode, int dim, double* __restrict__ partial) {
+  __shared__ double red[6][256];
+  const int nm = dim + 2;
+  double s[6] = {0, 0, 0, 0, 0, 0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nnode; i += gridDim.x * blockDim.x) {
+    const double* a = Un + (size_t)i * nm;
+    const double* b = Uo + (size_t)i * nm;
+    double d = a[0] - b[0];
+    s[0] += d * d;
+    s[1] += b[0] * b[0];
+    for (int al = 1; al <= dim; ++al) {
+      d = a[al] - b[al];
+      s[2] += d * d;
+      s[3] += b[al] * b[al];
+    }
+    d = a[dim + 1] - b[dim + 1];
+    s[4] += d * d;
+    s[5] += b[dim + 1] * b[dim + 1];
+  }
+  for (int k = 0; k < 6; ++k) red[k][threadIdx.x] = s[k];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+      for (int k = 0; k < 6; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 6; ++k) partial[(size_t)blockIdx.x * 6 + k] = red[k][0];
+}
+
 __global__ void k_stage_begin(DevState* ds, int stage) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     ds->stage_it = 0;

@@ -81,6 +81,11 @@ struct bgk_handle {
   bool have_prev = false;    // BDF2 history present
   bool state_set = false;    // a distribution has been set (bgk_set_state_maxwellian / bgk_set_f)
   int64_t steps = 0;         // steps taken since the state was set or loaded
+  // a step driven stage by stage from outside (bgk_shard_*): its stage count, kind (0 DIRK /
+  // backward Euler, 1 BDF2 proper, 2 BDF2 start-up) and the current stage's source
+  int sh_stages = 0, sh_kind = 0;
+  const void* sh_qsrc = nullptr;
+  double sh_qscale = 0.0, sh_nus = 0.0;
   // graphs
   cudaGraphExec_t exec_main = nullptr;   // the integrator's step
   cudaGraphExec_t exec_start = nullptr;  // BDF2 start-up step (backward Euler)
@@ -1444,8 +1449,10 @@ int bgk_sweep(bgk_handle* h, double nu_s, double q_scale) {
 
 int bgk_sweep_range(bgk_handle* h, int j_begin, int j_end, const double* d_U, double nu_s, double q_scale) {
   if (!h || !d_U || j_begin < 0 || j_end > h->g.nv || j_begin >= j_end || h->has_walls) return BGK_E_INVALID;
-  if (nu_s <= 0.0) nu_s = h->nus_main;
-  if (q_scale <= 0.0) q_scale = h->qscale_main;
+  // inside a stage opened by bgk_shard_stage_begin: that stage's source and coefficient
+  const void* qsrc = h->sh_qsrc ? h->sh_qsrc : h->fk;
+  if (nu_s <= 0.0) nu_s = h->sh_qsrc ? h->sh_nus : h->nus_main;
+  if (q_scale <= 0.0) q_scale = h->sh_qsrc ? h->sh_qscale : h->qscale_main;
   k_reset_state<<<1, 1, 0, h->stream>>>(h->ds);
   DevState st;
   CK(cudaMemcpyAsync(&st, h->ds, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
@@ -1453,13 +1460,149 @@ int bgk_sweep_range(bgk_handle* h, int j_begin, int j_end, const double* d_U, do
   // the given moments become the current iterate's (U[it & 1]) for the source
   CK(cudaMemcpyAsync(h->U[st.it & 1], d_U, sizeof(double) * h->nnode * h->nm, cudaMemcpyDeviceToDevice,
                      h->stream));
-  int rc = build_src(h, h->fk, q_scale);
+  int rc = build_src(h, qsrc, q_scale);
   if (rc != BGK_OK) return rc;
   launch_sweep_any(h, nu_s, j_begin, j_end);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(&st, h->ds, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return st.err ? BGK_E_NONPHYSICAL : BGK_OK;
+}
+
+int bgk_sum_partials_device(const bgk_handle* h, const double* d_parts, int n_parts, double* d_U) {
+  if (!h || !d_parts || !d_U || n_parts < 1) return BGK_E_INVALID;
+  const size_t n = (size_t)h->nnode * h->nm;
+  k_sum_parts<<<148 * 4, 256, 0, h->stream>>>(d_parts, n_parts, n, d_U);
+  CK(cudaGetLastError());
+  return BGK_OK;
+}
+
+int bgk_conv_measure_device(bgk_handle* h, const double* d_U_new, const double* d_U_old, double* measure) {
+  if (!h || !d_U_new || !d_U_old || !measure) return BGK_E_INVALID;
+  const int nblk = 148;
+  double* part = nullptr;
+  if (dalloc(part, sizeof(double) * 6 * nblk) != BGK_OK) return BGK_E_OOM;
+  k_measure_parts<<<nblk, 256, 0, h->stream>>>(d_U_new, d_U_old, h->nnode, h->hm.dim, part);
+  std::vector<double> hp(6 * nblk);
+  int rc = BGK_OK;
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(hp.data(), part, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, h->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    rc = BGK_E_CUDA;
+  cudaFree(part);
+  if (rc != BGK_OK) return rc;
+  double t[6] = {0, 0, 0, 0, 0, 0};
+  for (int b = 0; b < nblk; ++b)
+    for (int k = 0; k < 6; ++k) t[k] += hp[(size_t)b * 6 + k];
+  // R5: the momentum change relative to max(|n u|, |n|)
+  const double r0 = std::sqrt(t[0]) / std::sqrt(t[1]);
+  const double r1 = std::sqrt(t[2]) / std::max(std::sqrt(t[3]), std::sqrt(t[1]));
+  const double r2 = std::sqrt(t[4]) / std::sqrt(t[5]);
+  *measure = std::max(r0, std::max(r1, r2));
+  return BGK_OK;
+}
+
+int bgk_shard_step_begin(bgk_handle* h, int* n_stages, double* tol) {
+  if (!h || !n_stages || !h->state_set || h->shadow || h->has_walls) return BGK_E_INVALID;
+  const size_t bytes = h->nfv * h->tsize;
+  cudaStream_t s = h->stream;
+  double A[3][3], b[3], c[3];
+  const double dt = h->dt;
+  h->sh_qsrc = nullptr;
+  if (h->phys.integrator == BGK_BDF2 && h->have_prev) {
+    // q = (4 f^n - f^{n-1}) / (2 dt); history: fprev <- f^n   (BDF2 as read from Sec. 3.5)
+    double cF[1] = {-1.0 / (2.0 * dt)};
+    void* Fp[1] = {h->fprev};
+    combine(h, h->q, 0.0, nullptr, 4.0 / (2.0 * dt), h->f, 1, cF, Fp);
+    CK(cudaMemcpyAsync(h->fprev, h->f, bytes, cudaMemcpyDeviceToDevice, s));
+    h->sh_stages = 1;
+    h->sh_kind = 1;
+  } else {
+    CK(cudaMemcpyAsync(h->fk, h->f, bytes, cudaMemcpyDeviceToDevice, s));
+    h->sh_stages = tableau(h->phys.integrator == BGK_BDF2 ? BGK_BE : h->phys.integrator, A, b, c);
+    h->sh_kind = h->phys.integrator == BGK_BDF2 ? 2 : 0;
+  }
+  CK(cudaGetLastError());
+  *n_stages = h->sh_stages;
+  if (tol) *tol = h->cfg.tau / std::max(1.0, h->phys.nu * dt);
+  return BGK_OK;
+}
+
+int bgk_shard_stage_begin(bgk_handle* h, int stage) {
+  if (!h || stage < 0 || stage >= h->sh_stages) return BGK_E_INVALID;
+  const double dt = h->dt, nu = h->phys.nu;
+  if (h->sh_kind == 1) {
+    h->sh_nus = nu + 3.0 / (2.0 * dt);
+    h->sh_qsrc = h->q;
+    h->sh_qscale = 1.0;
+    return BGK_OK;
+  }
+  double A[3][3], b[3], c[3];
+  tableau(h->sh_kind == 2 ? BGK_BE : h->phys.integrator, A, b, c);
+  const double ass = A[stage][stage];
+  h->sh_nus = nu + 1.0 / (dt * ass);
+  if (stage == 0) {
+    h->sh_qsrc = h->fk;  // q = f^k / (dt A_11)
+    h->sh_qscale = 1.0 / (dt * ass);
+  } else {
+    // q = (f^k + dt sum_{r<s} A_sr F_r) / (dt A_ss)   (Eq. q-stages)
+    double cF[3];
+    for (int r = 0; r < stage; ++r) cF[r] = dt * A[stage][r] / (dt * ass);
+    combine(h, h->q, 1.0 / (dt * ass), h->fk, 0.0, nullptr, stage, cF, h->F);
+    h->sh_qsrc = h->q;
+    h->sh_qscale = 1.0;
+  }
+  CK(cudaGetLastError());
+  return BGK_OK;
+}
+
+int bgk_shard_stage_end(bgk_handle* h, int stage) {
+  if (!h || stage < 0 || stage >= h->sh_stages) return BGK_E_INVALID;
+  if (h->sh_kind == 0) {
+    double A[3][3], b[3], c[3];
+    const int S = tableau(h->phys.integrator, A, b, c);
+    const double dt = h->dt, ass = A[stage][stage];
+    // stage derivative F_s = f^(s) / (dt A_ss) - q^(s)   (Eq. dirk-recursive-def)
+    if (stage < S - 1 || !stiffly_accurate(S, A, b)) {
+      if (stage == 0) {
+        combine(h, h->F[0], -1.0 / (dt * ass), h->fk, 1.0 / (dt * ass), h->f, 0, nullptr, nullptr);
+      } else {
+        double cF[1] = {-1.0};
+        void* Fq[1] = {h->q};
+        combine(h, h->F[stage], 0.0, nullptr, 1.0 / (dt * ass), h->f, 1, cF, Fq);
+      }
+    }
+  }
+  h->sh_qsrc = nullptr;
+  CK(cudaGetLastError());
+  return BGK_OK;
+}
+
+int bgk_shard_step_end(bgk_handle* h) {
+  if (!h || h->sh_stages == 0) return BGK_E_INVALID;
+  const double dt = h->dt;
+  if (h->sh_kind == 0) {
+    double A[3][3], b[3], c[3];
+    const int S = tableau(h->phys.integrator, A, b, c);
+    if (!stiffly_accurate(S, A, b)) {
+      // f^{k+1} = f^k + dt sum_s b_s F_s   (Eq. dirk-n)
+      double cF[3];
+      for (int r = 0; r < S; ++r) cF[r] = dt * b[r];
+      combine(h, h->f, 1.0, h->fk, 0.0, nullptr, S, cF, h->F);
+    }
+  } else if (h->sh_kind == 2) {
+    // the start-up step was backward Euler; its f^k becomes the BDF2 history
+    CK(cudaMemcpyAsync(h->fprev, h->fk, h->nfv * h->tsize, cudaMemcpyDeviceToDevice, h->stream));
+    h->have_prev = true;
+  }
+  // the stepped state is the base of the next stage source
+  CK(cudaMemcpyAsync(h->fk, h->f, h->nfv * h->tsize, cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  h->sh_stages = 0;
+  h->sh_qsrc = nullptr;
+  h->steps += 1;
+  return BGK_OK;
 }
 
 int bgk_moments_range_device(bgk_handle* h, int j_begin, int j_end, double* d_U) {

@@ -1,14 +1,20 @@
-"""Ordinate sharding of the sweep (Sec. 4: the ordinates' sweeps are independent given the
-Maxwellian of the current moments; the sum over ordinates in Eq. moments is the one
-coupling per Picard iteration).
+"""Ordinate sharding of implicit steps (Sec. 4: the ordinates' sweeps are independent given
+the Maxwellian of the current moments; the sum over ordinates in Eq. moments is the one
+coupling per Picard iteration; Sec. 3.5: the stages of a step run one after another).
 
 - ``ordinate_shards``: contiguous ranges of whole values of the outermost velocity index,
   one per part, sizes differing by at most one index value.
-- ``sum_fixed_order``: the parts' partial moments summed in part order, the same on every
-  part (an allreduce whose result does not depend on the collective's internal order).
+- ``gather_sum``: every process's partial moments, gathered (``all_gather``: NCCL for CUDA
+  tensors, gloo for host tensors) and added in rank order by the part's own fixed-order
+  sum, so that every process holds the same bits.
+- ``sharded_steps``: implicit steps of a problem whose ordinates are split over parts
+  (several per process, or one per device): per stage, the Picard loop sweeps every part
+  with the summed moments and stops on the measure of Eq. (convergence-criteria).
 
-Host logic only; the partial moments and the range sweeps are ``Solver.moments_range_device``
-and ``Solver.sweep_range``.
+This module orders calls and collectives only: the stage bookkeeping, the sweeps, the
+partial moments, the fixed-order sum and the measure are the parts' own operations (for
+``SolverShard`` the library's bgk_shard_* / bgk_sweep_range / bgk_moments_range_device /
+bgk_sum_partials_device / bgk_conv_measure_device calls).
 """
 from __future__ import annotations
 
@@ -27,13 +33,32 @@ def ordinate_shards(n_points: int, dim: int, parts: int):
     return out
 
 
-def sum_fixed_order(partial, group=None):
-    """Sum of every rank's tensor `partial` added in rank order 0, 1, ... on every rank
-    (all_gather, then a local ordered sum): bitwise the same result on all ranks and for
-    any collective algorithm.  Without a process group (one part) it returns `partial`."""
+def _dist_active(group):
+    import torch.distributed as dist
+    return group is not None or (dist.is_available() and dist.is_initialized())
+
+
+def gather_sum(local, part, group=None):
+    """The sum over all processes of `local` ([node][d+2]), added in rank order 0, 1, ... by
+    `part.sum_partials` on the gathered stack: the same bits on every process, for any
+    collective algorithm.  `local` is a CUDA tensor with an NCCL group or a host tensor
+    with a gloo group.  Without a process group it returns `local`."""
     import torch
     import torch.distributed as dist
-    if group is None and not (dist.is_available() and dist.is_initialized()):
+    if not _dist_active(group):
+        return local
+    world = dist.get_world_size(group)
+    bufs = [torch.empty_like(local) for _ in range(world)]
+    dist.all_gather(bufs, local.contiguous(), group=group)
+    return part.sum_partials(torch.stack(bufs))
+
+
+def sum_fixed_order(partial, group=None):
+    """The rank-ordered sum of every process's `partial` with a plain elementwise sum (host
+    tensors, tests and tools); the solver path uses gather_sum with the library's sum."""
+    import torch
+    import torch.distributed as dist
+    if not _dist_active(group):
         return partial.clone()
     world = dist.get_world_size(group)
     bufs = [torch.empty_like(partial) for _ in range(world)]
@@ -44,91 +69,107 @@ def sum_fixed_order(partial, group=None):
     return total
 
 
-def moment_change(U_new, U_old, dim):
-    """The Picard convergence measure of Eq. (convergence-criteria) on summed moments
-    [node][d+2]: the largest of the relative l2 changes of n, n u (relative to
-    max(|n u|, |n|)) and E."""
+def _summed(parts, group):
+    """Partial moments of this process's parts, summed in part order, then over processes."""
     import torch
-    n = torch.linalg.vector_norm
-    dU = U_new - U_old
-    m0 = n(dU[:, 0]) / n(U_old[:, 0])
-    m1 = n(dU[:, 1:1 + dim]) / torch.maximum(n(U_old[:, 1:1 + dim]), n(U_old[:, 0]))
-    m2 = n(dU[:, -1]) / n(U_old[:, -1])
-    return float(torch.max(torch.stack([m0, m1, m2])))
+    local = []
+    for p in parts:
+        U = p.new_moments()
+        p.partial(U)
+        local.append(U)
+    U = local[0] if len(local) == 1 else parts[0].sum_partials(torch.stack(local))
+    return gather_sum(U, parts[0], group)
 
 
-def picard_sharded(parts, allreduce, dim, tol, l_max):
-    """One backward-Euler stage's Picard loop (Sec. 4) over ordinate shards.
+def sharded_steps(parts, steps, group=None, l_max=1000):
+    """`steps` implicit steps of a problem split over ordinate parts.
 
-    parts: the shards this process holds, each an object with
-      partial(U_out)  -- its partial moments (sum over its ordinates) into U_out,
-      sweep(U_in)     -- one sweep of its ordinates with the summed moments U_in,
-      commit()        -- make the converged state the base of the next step.
-    allreduce(U): the sum over all processes of U, the same bits on every process (e.g.
-    sum_fixed_order; identity when this process holds every shard).
-    Every process computes the same measure from the same summed moments, so all of them
-    stop at the same iteration.  Returns the iteration count; raises RuntimeError if the
-    loop does not converge within l_max."""
-    def summed():
-        local = None
-        for p in parts:
-            U = p.new_moments()
-            p.partial(U)
-            local = U if local is None else local + U
-        return allreduce(local)
-    U_old = summed()
-    for it in range(1, l_max + 1):
-        for p in parts:
-            p.sweep(U_old)
-        U_new = summed()
-        meas = moment_change(U_new, U_old, dim)
-        U_old = U_new
-        if meas < tol:
+    parts: the parts this process holds (objects with step_begin() -> (stages, tol),
+    stage_begin(s), stage_end(s), step_end(), new_moments(), partial(U), sweep(U),
+    sum_partials(stack) -> U, measure(U_new, U_old) -> float).  group: the process group
+    over which the partial moments are summed (None: this process holds every part).
+    Every process computes the same measure from the same summed moments, so all stop at
+    the same iteration.  Returns the Picard iterations of every stage of every step;
+    raises RuntimeError when a stage does not converge within l_max."""
+    out = []
+    for _ in range(steps):
+        shape = [p.step_begin() for p in parts]
+        n_stages, tol = shape[0]
+        if any(x != shape[0] for x in shape):
+            raise RuntimeError("parts disagree on the step's stages")
+        its = []
+        for st in range(n_stages):
             for p in parts:
-                p.commit()
-            return it
-    raise RuntimeError("sharded Picard loop did not converge within l_max")
+                p.stage_begin(st)
+            U_old = _summed(parts, group)
+            for it in range(1, l_max + 1):
+                for p in parts:
+                    p.sweep(U_old)
+                U_new = _summed(parts, group)
+                meas = parts[0].measure(U_new, U_old)
+                U_old = U_new
+                if meas < tol:
+                    break
+            else:
+                raise RuntimeError("sharded Picard loop did not converge within l_max")
+            for p in parts:
+                p.stage_end(st)
+            its.append(it)
+        for p in parts:
+            p.step_end()
+        out.append(its)
+    return out
 
 
 class SolverShard:
-    """A shard of ordinates [j_begin, j_end) of one problem held by a Solver (the whole
-    problem is set up on every device; only the shard's ordinates are swept and summed)."""
+    """Ordinates [j_begin, j_end) of one problem held by a Solver (the whole problem is set
+    up on every device; only the part's ordinates are swept and summed).  The Solver should
+    run on torch's current stream (Solver(..., stream=torch.cuda.current_stream().cuda_stream))
+    so that the gathered moments and the library's work are ordered without host waits."""
 
     def __init__(self, solver, j_begin, j_end):
         import torch
         self.s, self.jb, self.je = solver, int(j_begin), int(j_end)
         self.shape = (solver.nnode, solver.dim + 2)
         self.device = torch.device("cuda", torch.cuda.current_device())
-        self._f = None
+        self.same_stream = getattr(solver, "stream", None) == torch.cuda.current_stream().cuda_stream
+
+    def _order(self):
+        # moments made by torch or a collective on torch's stream, read by the library
+        if not self.same_stream:
+            import torch
+            torch.cuda.current_stream().synchronize()
 
     def new_moments(self):
         import torch
         return torch.empty(self.shape, dtype=torch.float64, device=self.device)
 
+    def step_begin(self):
+        return self.s.shard_step_begin()
+
+    def stage_begin(self, stage):
+        self.s.shard_stage_begin(stage)
+
+    def stage_end(self, stage):
+        self.s.shard_stage_end(stage)
+
+    def step_end(self):
+        self.s.shard_step_end()
+
     def partial(self, U_out):
         self.s.moments_range_device(self.jb, self.je, U_out.data_ptr())
 
     def sweep(self, U_in):
-        # U_in may come from torch kernels (the sum of the partials) on torch's stream; the
-        # library works on its own stream, so wait for them first
-        import torch
-        torch.cuda.current_stream().synchronize()
+        self._order()
         self.s.sweep_range(self.jb, self.je, U_in.data_ptr())
 
-    def commit(self):
-        # f^{k+1} becomes the stage base f^k of the next step (bgk_set_f_device copies f
-        # into both the state and the base)
-        import torch
-        import numpy as np
-        if self._f is None:
-            dt = torch.float64 if self.s.fdtype == np.float64 else torch.float32
-            self._f = torch.empty((self.s.nv, self.s.nnode), dtype=dt, device=self.device)
-        self.s.get_f_device(self._f.data_ptr(), self.s.fdtype)
-        self.s.set_f_device(self._f.data_ptr(), self.s.fdtype)
+    def sum_partials(self, stack):
+        self._order()
+        stack = stack.contiguous()
+        out = self.new_moments()
+        self.s.sum_partials_device(stack.data_ptr(), stack.shape[0], out.data_ptr())
+        return out
 
-
-def sharded_be_steps(parts, allreduce, dim, nu, dt, tau, steps, l_max=1000):
-    """`steps` backward-Euler steps of a sharded problem; returns the iteration counts.
-    The tolerance is the single-device one, tau / max(1, nu dt)."""
-    tol = tau / max(1.0, nu * dt)
-    return [picard_sharded(parts, allreduce, dim, tol, l_max) for _ in range(steps)]
+    def measure(self, U_new, U_old):
+        self._order()
+        return self.s.conv_measure_device(U_new.data_ptr(), U_old.data_ptr())

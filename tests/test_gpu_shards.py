@@ -107,25 +107,78 @@ def test_sharded_picard_step_matches_the_step(name):
     assert rel_err(s.get_f(), ref.get_f()) < 1e-12
 
 
+@pytest.mark.parametrize("integ", ["BE", "DIRK2", "DIRK3", "BSTABLE2", "BDF2"])
 @pytest.mark.parametrize("name", ["p2_tri", "p1_tet"])
-def test_sharded_be_steps_with_one_handle_per_shard(name):
-    """shard.sharded_be_steps over four Solver handles (one per shard, as four devices would
-    hold them; the summed moments added in shard order) reproduces three backward-Euler
-    steps of one handle: the same Picard counts, and every shard's ordinates within 1e-12."""
+def test_sharded_steps_with_one_handle_per_shard(name, integ):
+    """shard.sharded_steps over four Solver handles (one per part, as four devices would hold
+    them; the library sums the partial moments in part order and computes the measure)
+    reproduces three steps of one handle for every integrator: the same Picard counts in
+    every stage, and every part's ordinates within 1e-12."""
+    import torch
     w = _cases()[name]
+    w = synth.Workload(w.name, w.mesh, w.kx, w.n_v, w.k_v, w.L, w.knudsen, integ, w.cfl, w.init, w.inflow)
     ref = bgk.Solver.from_workload(w)
     ref.set_state_maxwellian(w.init)
     ref.set_inflow_maxwellian(w.inflow)
-    its_ref = [ref.step(1).iterations[0] for _ in range(3)]
+    its_ref = []
+    for _ in range(3):
+        st = ref.step(1)
+        its_ref.append(list(st.iterations)[:st.n_stages])
     ranges = shard.ordinate_shards(w.n_v, ref.dim, 4)
+    stream = torch.cuda.current_stream().cuda_stream
     parts = []
-    for a, b in ranges:
-        s = bgk.Solver.from_workload(w)
+    for k, (a, b) in enumerate(ranges):
+        # two parts on torch's stream, two on streams of their own (host-ordered)
+        s = bgk.Solver.from_workload(w, stream=stream if k % 2 == 0 else None)
         s.set_state_maxwellian(w.init)
         s.set_inflow_maxwellian(w.inflow)
         parts.append(shard.SolverShard(s, a, b))
-    its = shard.sharded_be_steps(parts, lambda U: U, ref.dim, w.nu, ref.dt, 1e-8, 3)
-    assert its == its_ref
+    assert [p.same_stream for p in parts] == [True, False, True, False]
+    its = shard.sharded_steps(parts, 3)
+    assert its == its_ref, (its, its_ref)
     fr = ref.get_f()
     for p, (a, b) in zip(parts, ranges):
         assert rel_err(p.s.get_f()[a:b], fr[a:b]) < 1e-12
+    assert parts[0].s.time() == ref.time()
+
+
+def test_shard_calls_refuse_mixed_precision_and_out_of_order_use():
+    w = _cases()["p2_tri"]
+    m = bgk.Solver.from_workload(w, precision="mixed")
+    m.set_state_maxwellian(w.init)
+    with pytest.raises(bgk.BgkError):
+        m.shard_step_begin()
+    s = bgk.Solver.from_workload(w)
+    s.set_state_maxwellian(w.init)
+    with pytest.raises(bgk.BgkError):
+        s.shard_stage_begin(0)            # no step open
+    n, tol = s.shard_step_begin()
+    assert n == 1 and tol == pytest.approx(1e-8 / max(1.0, w.nu * s.dt))
+    with pytest.raises(bgk.BgkError):
+        s.shard_stage_begin(1)            # backward Euler has one stage
+
+
+def test_fixed_order_sum_and_measure_on_device():
+    """bgk_sum_partials_device adds the parts in order; bgk_conv_measure_device gives the
+    measure of Eq. (convergence-criteria) of two moment arrays (numpy reference)."""
+    import torch
+    w = _cases()["p2_tri"]
+    s = bgk.Solver.from_workload(w)
+    g = torch.Generator().manual_seed(3)
+    parts = (torch.rand((3, s.nnode, s.dim + 2), generator=g, dtype=torch.float64) - 0.5) * torch.tensor(
+        [1.0, 1e3, 1e-3, 10.0], dtype=torch.float64)
+    d = parts.cuda()
+    out = torch.empty((s.nnode, s.dim + 2), dtype=torch.float64, device="cuda")
+    s.sum_partials_device(d.data_ptr(), 3, out.data_ptr())
+    s.synchronize()
+    expect = parts[0] + parts[1] + parts[2]
+    assert torch.equal(out.cpu(), expect)
+    Uo = (expect + 2.0).cuda()
+    Un = Uo * (1.0 + 1e-4 * torch.rand(Uo.shape, generator=g, dtype=torch.float64).cuda())
+    m = s.conv_measure_device(Un.data_ptr(), Uo.data_ptr())
+    a, b = Un.cpu().numpy(), Uo.cpu().numpy()
+    nrm = np.linalg.norm
+    ref = max(nrm(a[:, 0] - b[:, 0]) / nrm(b[:, 0]),
+              nrm(a[:, 1:3] - b[:, 1:3]) / max(nrm(b[:, 1:3]), nrm(b[:, 0])),
+              nrm(a[:, 3] - b[:, 3]) / nrm(b[:, 3]))
+    assert m == pytest.approx(ref, rel=1e-12)
