@@ -20,7 +20,8 @@ struct DevState {
   int total_sweeps;
   int cont;          // the stage loop continues (read by the host in eager mode)
   int done;          // the stage loop of this problem has ended (batched runs skip it)
-  int pad;
+  int cf_fresh;      // the Maxwellian factors were rebuilt from the current moments by the
+                     // moment kernel itself (the factor pass then has nothing to do)
 };
 
 __device__ __forceinline__ void ordinate(const VGrid& g, int j, double (&v)[3]) {
@@ -81,15 +82,24 @@ struct GridVals<float> {
 
 // KV: the velocity degree k_v as a compile-time constant, so the per-cell arrays below
 // stay in registers (proj_factors_t dispatches on g.kv).
+// Velocity cells [cl0, cl1) only: the boundary values at cell cl0's left edge are
+// evaluated directly (the same expressions the loop carries from cell to cell), so
+// disjoint ranges computed separately give the whole projection's values bit for bit.
 template <typename R, typename TO, int KV>
-__device__ __forceinline__ void proj_factors_kv(const VGrid& g, R u, R theta, TO* out, size_t stride, R scale) {
+__device__ __forceinline__ void proj_factors_cells(const VGrid& g, R u, R theta, TO* out, size_t stride, R scale,
+                                                   int cl0, int cl1) {
   constexpr int NP = KV + 1;
   const R rs2 = (R)0.70710678118654752440, rs2pi = (R)0.39894228040143267794;
   const R sig = sqrt(theta), isig = R(1) / sig;
   const GridVals<R> gv{g};
   const R hh = gv.hh();
   R tprev = -(R)INFINITY, phiprev = 0, Eprev = 0;
-  for (int cl = 0; cl < g.ncl; ++cl) {
+  if (cl0 > 0) {
+    tprev = (gv.bnd(cl0) - u) * isig;
+    phiprev = rs2pi * exp(R(-0.5) * tprev * tprev);
+    Eprev = R(0.5) * erfc(fabs(tprev) * rs2);
+  }
+  for (int cl = cl0; cl < cl1; ++cl) {
     R tb, phib, Eb;
     if (cl == g.ncl - 1) {
       tb = (R)INFINITY;
@@ -158,13 +168,19 @@ __device__ __forceinline__ void proj_factors_kv(const VGrid& g, R u, R theta, TO
 }
 
 template <typename R, typename TO>
-__device__ __forceinline__ void proj_factors_t(const VGrid& g, R u, R theta, TO* out, size_t stride, R scale) {
+__device__ __forceinline__ void proj_factors_range(const VGrid& g, R u, R theta, TO* out, size_t stride, R scale,
+                                                   int cl0, int cl1) {
   switch (g.kv) {
-    case 1: proj_factors_kv<R, TO, 1>(g, u, theta, out, stride, scale); break;
-    case 2: proj_factors_kv<R, TO, 2>(g, u, theta, out, stride, scale); break;
-    case 3: proj_factors_kv<R, TO, 3>(g, u, theta, out, stride, scale); break;
-    default: proj_factors_kv<R, TO, 4>(g, u, theta, out, stride, scale); break;
+    case 1: proj_factors_cells<R, TO, 1>(g, u, theta, out, stride, scale, cl0, cl1); break;
+    case 2: proj_factors_cells<R, TO, 2>(g, u, theta, out, stride, scale, cl0, cl1); break;
+    case 3: proj_factors_cells<R, TO, 3>(g, u, theta, out, stride, scale, cl0, cl1); break;
+    default: proj_factors_cells<R, TO, 4>(g, u, theta, out, stride, scale, cl0, cl1); break;
   }
+}
+
+template <typename R, typename TO>
+__device__ __forceinline__ void proj_factors_t(const VGrid& g, R u, R theta, TO* out, size_t stride, R scale) {
+  proj_factors_range<R, TO>(g, u, theta, out, stride, scale, 0, g.ncl);
 }
 
 __device__ __forceinline__ void proj_factors(const VGrid& g, double u, double theta, double* c, int stride) {
@@ -233,6 +249,69 @@ __global__ void k_maxwell(VGrid g, int npos, int nm, const double* __restrict__ 
       }
     }
   }
+}
+
+// Primitive variables of one node from its moments (n, n u, E) (Eq. moments) and the
+// scale coef * n of the collision term's first factor.  ok = false for n <= 0, theta <= 0
+// or a non-finite value (the simplified Maxwellian needs only n); the factors are then
+// written as those of (0, 0, 1) and the caller raises the non-physical flag.
+struct NodePrim {
+  double n, u[3], th, scale;
+  bool ok;
+};
+__device__ __forceinline__ NodePrim node_prim(const double* U, int dim, double coef, int kind) {
+  NodePrim P;
+  P.n = U[0];
+  P.u[0] = P.u[1] = P.u[2] = 0.0;
+  if (kind == BGK_COLL_LINEAR) {
+    P.ok = P.n > 0.0 && isfinite(P.n);
+    P.th = 1.0;
+    P.scale = P.ok ? coef * P.n : 0.0;
+    return P;
+  }
+  double u2 = 0.0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    if (a < dim) {
+      P.u[a] = U[1 + a] / P.n;
+      u2 += P.u[a] * P.u[a];
+    }
+  P.th = (2.0 * U[1 + dim] / P.n - u2) / dim;
+  P.scale = coef * P.n;
+  P.ok = P.n > 0.0 && P.th > 0.0 && isfinite(P.n) && isfinite(P.th);
+  if (!P.ok) {
+    P.scale = 0.0;
+    P.th = 1.0;
+    P.u[0] = P.u[1] = P.u[2] = 0.0;
+  }
+  return P;
+}
+
+// Factors of one node along velocity dimension a, for the velocity cells [cl0, cl1):
+// out[m * stride], m the 1D points of those cells.  Projected Maxwellian (App. B): c_a[m]
+// in the storage type T, with the scale in a = 0; simplified Maxwellian (Eq.
+// linear-Maxwellian): scale / (2L)^d in a = 0 and 1 elsewhere; interpolated Maxwellian
+// (Sec. 5.1.1): the 1D Gaussian's values at the points.
+template <typename T>
+__device__ __forceinline__ void node_factors(const VGrid& g, int kind, const NodePrim& P, int a, T* out,
+                                             size_t stride, int cl0, int cl1) {
+  const int np = g.kv + 1;
+  if (kind == BGK_COLL_LINEAR) {
+    double vol = 1.0;
+    for (int b = 0; b < g.dim; ++b) vol *= 2.0 * g.L;
+    const double val = a == 0 ? P.scale / vol : 1.0;
+    for (int m = cl0 * np; m < cl1 * np; ++m) out[(size_t)m * stride] = (T)val;
+    return;
+  }
+  if (kind == BGK_COLL_INTERP) {
+    const double rs = rsqrt(2.0 * 3.14159265358979323846 * P.th), h = 0.5 / P.th;
+    for (int m = cl0 * np; m < cl1 * np; ++m) {
+      const double dv = g.x[m] - P.u[a];
+      out[(size_t)m * stride] = (T)((a == 0 ? P.scale : 1.0) * rs * exp(-h * dv * dv));
+    }
+    return;
+  }
+  proj_factors_range<T, T>(g, (T)P.u[a], (T)P.th, out, stride, (T)(a == 0 ? P.scale : 1.0), cl0, cl1);
 }
 
 // ---------------------------------------------------------------------------------
@@ -335,11 +414,19 @@ struct MomentParts {
   static constexpr int value = sizeof(T) == 8 ? 4 : 1;
 };
 
+//
+// Fused with the Maxwellian rebuild (cf != nullptr, mode 1): the block then also writes the
+// collision-term factors cf[a][m][i] of its nodes from the new moments (node_factors; the
+// work of every (node, dimension, half of the velocity cells) spread over the block's
+// threads) and marks them current (ds->cf_fresh), so the next iteration needs no factor
+// pass; non-physical moments raise ds->err.  Mode 0 marks the factors stale.
 template <typename T>
 __global__ void __launch_bounds__(128) k_moments(VGrid g, const T* __restrict__ f, int nnode, double* U0,
-                                                 double* U1, const DevState* ds, int mode,
-                                                 double* __restrict__ partial) {
+                                                 double* U1, DevState* ds, int mode,
+                                                 double* __restrict__ partial, T* __restrict__ cf, double coef,
+                                                 int kind) {
   if (ds->status != BGK_OK || ds->done) return;
+  if (mode == 0 && blockIdx.x == 0 && threadIdx.x == 0) ds->cf_fresh = 0;
   constexpr int PARTS = MomentParts<T>::value, NPB = 128 / PARTS;
   const int nl = threadIdx.x % NPB, part = threadIdx.x / NPB;
   const int i = blockIdx.x * NPB + nl;
@@ -435,6 +522,27 @@ __global__ void __launch_bounds__(128) k_moments(VGrid g, const T* __restrict__ 
   if (threadIdx.x < 6)
     partial[(size_t)blockIdx.x * 6 + threadIdx.x] =
         ((red[threadIdx.x][0] + red[threadIdx.x][1]) + red[threadIdx.x][2]) + red[threadIdx.x][3];
+  if (!cf) return;
+  // the Maxwellian of the new moments (Sec. 3.3, App. B) for the next iteration
+  __shared__ NodePrim prim[NPB];
+  if (part == 0) {
+    double Uc[5];
+#pragma unroll
+    for (int m = 0; m < 5; ++m) Uc[m] = acc[m];
+    prim[nl] = node_prim(Uc, g.dim, coef, kind);
+    if (i < nnode && !prim[nl].ok) atomicOr(&ds->err, 1);
+  }
+  __syncthreads();
+  const int H = (128 / NPB) / g.dim > 1 ? 2 : 1;
+  const int tasks = NPB * g.dim * H;
+  for (int t = threadIdx.x; t < tasks; t += 128) {
+    const int q = t % NPB, r = t / NPB, a = r % g.dim, hh = r / g.dim;
+    const int iq = blockIdx.x * NPB + q;
+    if (iq < nnode)
+      node_factors<T>(g, kind, prim[q], a, cf + (size_t)a * g.N * nnode + iq, (size_t)nnode, hh * g.ncl / H,
+                      (hh + 1) * g.ncl / H);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) ds->cf_fresh = 1;
 }
 
 // Partial moments over the ordinates whose outermost velocity index lies in [ja, jb) (one
@@ -479,65 +587,22 @@ __global__ void k_moments_range(VGrid g, const T* __restrict__ f, int nnode, int
     if (m < nm) out[(size_t)i * nm + m] = acc[m];
 }
 
-// Projected-Maxwellian factors of every node from the current moments U[it & 1]:
-// cf[a][m][i] = c_a[m](u_i, theta_i) (App. B), with coef * n_i folded into a = 0.  The
-// moments and primitive variables are FP64; the projection runs in the storage type T
-// (FP64 for FP64 states, FP32 for FP32 sweeps, whose source is FP32 anyway).
-// Non-physical moments set the error flag (the stage loop then stops).
-// linear != 0: the simplified Maxwellian N_h = n / |V| at every ordinate (Eq.
-// linear-Maxwellian): cf[0][m] = coef n / (2L)^d, cf[a > 0][m] = 1.
+// Collision-term factors of every node from the current moments U[it & 1]: cf[a][m][i]
+// (node_factors), coef * n_i folded into a = 0.  The moments and primitive variables are
+// FP64; the projection runs in the storage type T (FP64 for FP64 states, FP32 for FP32
+// sweeps, whose source is FP32 anyway).  Non-physical moments set the error flag (the
+// stage loop then stops).  Nothing to do when the moment kernel has already rebuilt the
+// factors from these moments (ds->cf_fresh).
 template <typename T>
 __global__ void k_factors(VGrid g, int nnode, const double* __restrict__ U0, const double* __restrict__ U1,
                           DevState* ds, double coef, T* __restrict__ cf, int kind) {
-  if (ds->status != BGK_OK || ds->done) return;
+  if (ds->status != BGK_OK || ds->done || ds->cf_fresh) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nnode) return;
   const int nm = g.dim + 2;
-  const double* Un = (((ds->it & 1) == 0) ? U0 : U1) + (size_t)i * nm;
-  const double n = Un[0];
-  if (kind == BGK_COLL_LINEAR) {
-    double vol = 1.0;
-    for (int a = 0; a < g.dim; ++a) vol *= 2.0 * g.L;
-    double val = coef * n / vol;
-    if (!(n > 0.0) || !isfinite(n)) {
-      atomicOr(&ds->err, 1);
-      val = 0.0;
-    }
-    for (int a = 0; a < g.dim; ++a)
-      for (int m = 0; m < g.N; ++m) cf[((size_t)a * g.N + m) * nnode + i] = (T)(a == 0 ? val : 1.0);
-    return;
-  }
-  double u[3] = {0, 0, 0}, u2 = 0.0;
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-    if (a < g.dim) {
-      u[a] = Un[1 + a] / n;
-      u2 += u[a] * u[a];
-    }
-  double th = (2.0 * Un[1 + g.dim] / n - u2) / g.dim;
-  double scale = coef * n;
-  if (!(n > 0.0) || !(th > 0.0) || !isfinite(n) || !isfinite(th)) {
-    atomicOr(&ds->err, 1);
-    scale = 0.0;
-    th = 1.0;
-    u[0] = u[1] = u[2] = 0.0;
-  }
-  if (kind == BGK_COLL_INTERP) {
-    // the Maxwellian's values at the grid points (Sec. 5.1.1, the non-conservative
-    // alternative): one 1D Gaussian per dimension, n and coef in the first
-    const double rs = rsqrt(2.0 * 3.14159265358979323846 * th), h = 0.5 / th;
-    for (int a = 0; a < g.dim; ++a)
-      for (int m = 0; m < g.N; ++m) {
-        const double dv = g.x[m] - u[a];
-        cf[((size_t)a * g.N + m) * nnode + i] = (T)((a == 0 ? scale : 1.0) * rs * exp(-h * dv * dv));
-      }
-    return;
-  }
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-    if (a < g.dim)
-      proj_factors_t<T, T>(g, (T)u[a], (T)th, cf + (size_t)a * g.N * nnode + i, (size_t)nnode,
-                           (T)(a == 0 ? scale : 1.0));
+  const NodePrim P = node_prim((((ds->it & 1) == 0) ? U0 : U1) + (size_t)i * nm, g.dim, coef, kind);
+  if (!P.ok) atomicOr(&ds->err, 1);
+  for (int a = 0; a < g.dim; ++a) node_factors<T>(g, kind, P, a, cf + (size_t)a * g.N * nnode + i, (size_t)nnode, 0, g.ncl);
 }
 
 // src[j][i] = prod_a cf[a][j_a][i] + qscale * q[j][i]  (nu M^l + q of Eq. bgk-ss-picard)
@@ -667,6 +732,7 @@ __global__ void k_reset_state(DevState* ds) {
     ds->status = BGK_OK;
     ds->err = 0;
     ds->done = 0;
+    ds->cf_fresh = 0;
     for (int s = 0; s < 4; ++s) {
       ds->iters[s] = 0;
       ds->meas[s] = 0.0;
@@ -1611,9 +1677,10 @@ __global__ void k_convert_gated(size_t n, const TI* __restrict__ in, TO* __restr
 
 // Copy the current moments of one state to another (parities from each state's counter).
 __global__ void k_copy_moments(size_t n, const double* __restrict__ A0, const double* __restrict__ A1,
-                               const DevState* __restrict__ da, double* B0, double* B1, const DevState* db) {
+                               const DevState* __restrict__ da, double* B0, double* B1, DevState* db) {
   const double* A = (da->it & 1) == 0 ? A0 : A1;
   double* B = (db->it & 1) == 0 ? B0 : B1;
+  if (blockIdx.x == 0 && threadIdx.x == 0) db->cf_fresh = 0;  // B's factors are not built yet
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     B[i] = A[i];
 }
