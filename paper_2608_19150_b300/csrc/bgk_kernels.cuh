@@ -813,6 +813,47 @@ __global__ void k_peel(const double* __restrict__ geo, int gs, const int32_t* __
   }
 }
 
+// Order of the cells inside each generation (Sec. 4.1: the cells of one generation are
+// independent, so any order gives the same sweep): counting sort by the packed face code,
+// so that the threads of a warp, which take consecutive positions, mostly share one
+// inflow/outflow pattern and the face-dependent code of the local solve does not diverge.
+// One CTA per ordinate; generations longer than cap entries keep their order.
+__global__ void k_sort_gen(uint32_t* __restrict__ glist, const int32_t* __restrict__ lvl,
+                           const int32_t* __restrict__ ngen, int ncell, int cap) {
+  extern __shared__ uint32_t sbuf[];  // cap entries
+  __shared__ int hist[256];
+  const int j = blockIdx.x;
+  uint32_t* gl = glist + (size_t)j * ncell;
+  const int32_t* lv = lvl + (size_t)j * (ncell + 1);
+  const int G = ngen[j];
+  for (int gg = 0; gg < G; ++gg) {
+    const int a = lv[gg], n = lv[gg + 1] - a;
+    if (n <= 1 || n > cap) continue;  // (uniform over the block)
+    for (int t = threadIdx.x; t < 256; t += blockDim.x) hist[t] = 0;
+    __syncthreads();
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      const uint32_t e = gl[a + k];
+      sbuf[k] = e;
+      atomicAdd(&hist[e >> kCellBits], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int acc = 0;
+      for (int t = 0; t < 256; ++t) {
+        const int c = hist[t];
+        hist[t] = acc;
+        acc += c;
+      }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      const uint32_t e = sbuf[k];
+      gl[a + atomicAdd(&hist[e >> kCellBits], 1)] = e;
+    }
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------------------------
 // LU without pivoting: the local matrix has a positive definite symmetric part
 // (nu_s M + upwind transport), so elimination in natural order is stable.

@@ -716,6 +716,14 @@ int build_dags(bgk_handle* h) {
     for (int j = 0; j < h->g.nv; ++j)
       if (nproc[j] != n) return BGK_E_INVALID;
   }
+  // FP64 sweeps: cells of a generation ordered by face code (the same sweep; the warps'
+  // face-dependent FP64 code diverges less: shock tube 128x128, 8.93 -> 8.38 ms).  FP32
+  // sweeps keep the peel's order, which is faster for them (2.23 vs 2.32 ms sorted).
+  if (h->precision == BGK_FP64) {
+    const int cap = 8192;
+    k_sort_gen<<<h->g.nv, 256, cap * sizeof(uint32_t), h->stream>>>(h->glist, h->lvl, h->ngen, n, cap);
+    CK(cudaGetLastError());
+  }
   CK(cudaMemcpy(ngen.data(), h->ngen, sizeof(int32_t) * h->g.nv, cudaMemcpyDeviceToHost));
   h->Gmax = *std::max_element(ngen.begin(), ngen.end());
   // CTA size of the sweep: about the mean width of a generation, rounded to warps
