@@ -1438,32 +1438,46 @@ __global__ void k_front_gen(const uint32_t* __restrict__ glist, const int32_t* _
     for (int k = lv[gg] + threadIdx.x; k < lv[gg + 1]; k += blockDim.x) gc[gl[k] & kCellMask] = gg;
 }
 
-// Greedy slot allocation of one ordinate per thread, in generation order.  A face that is
+// Greedy slot allocation, one CTA per ordinate, in generation order.  A face that is
 // outflow for cell c is inflow for its neighbour, which reads c's trace in this sweep
-// exactly when its generation is higher (a lagged edge points the other way).
-// fslot[j][c][f] receives the slot of (c, f) or -1; work holds 2 * kFrontMaxSlots int16
-// per ordinate (release lists, free stack); head (ncell + 1) ints per ordinate;
-// *nslots the largest slot count, *overflow set when an ordinate needs too many.
+// exactly when its generation is higher (a lagged edge points the other way).  At the
+// start of generation g the slots whose reader ran in generation g-1 go back to the free
+// stack (one thread walks that release list); then the generation's cells take slots
+// concurrently (free stack first, else a new slot) and each slot joins the release list of
+// its reader's generation + 1.  The slot count equals the largest number of traces alive
+// at a generation boundary, whatever the order inside a generation.  fslot[j][c][f]
+// receives the slot of (c, f) or -1; head holds (ncell + 1) ints per ordinate; *nslots the
+// largest slot count, *overflow set when an ordinate needs more than kFrontMaxSlots.
 template <int NF>
-__global__ void k_front_alloc(const uint32_t* __restrict__ glist, const int32_t* __restrict__ lvl,
-                              const int32_t* __restrict__ ngen, const int32_t* __restrict__ nbr, int ncell, int nv,
-                              const int32_t* __restrict__ genc, int16_t* __restrict__ fslot,
-                              int32_t* __restrict__ head, int16_t* __restrict__ work, int* nslots, int* overflow) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= nv) return;
+__global__ void __launch_bounds__(256) k_front_alloc(const uint32_t* __restrict__ glist, const int32_t* __restrict__ lvl,
+                                                     const int32_t* __restrict__ ngen, const int32_t* __restrict__ nbr,
+                                                     int ncell, const int32_t* __restrict__ genc,
+                                                     int16_t* __restrict__ fslot, int32_t* __restrict__ head,
+                                                     int* nslots, int* overflow) {
+  __shared__ int16_t stk[kFrontMaxSlots], nxt[kFrontMaxSlots];
+  __shared__ int nfree, top, over;
+  const int j = blockIdx.x;
   const uint32_t* gl = glist + (size_t)j * ncell;
   const int32_t* lv = lvl + (size_t)j * (ncell + 1);
   const int32_t* gc = genc + (size_t)j * ncell;
   int16_t* fs = fslot + (size_t)j * ncell * 4;
   int32_t* hd = head + (size_t)j * (ncell + 1);  // hd[g]: slots released at the start of generation g
-  int16_t* nxt = work + (size_t)j * 2 * kFrontMaxSlots;
-  int16_t* stk = nxt + kFrontMaxSlots;
   const int G = ngen[j];
-  for (int gg = 0; gg <= G; ++gg) hd[gg] = -1;
-  int nfree = 0, top = 0, over = 0;
+  for (int gg = threadIdx.x; gg <= G; gg += blockDim.x) hd[gg] = -1;
+  if (threadIdx.x == 0) {
+    nfree = 0;
+    top = 0;
+    over = 0;
+  }
+  __syncthreads();
   for (int gg = 0; gg < G; ++gg) {
-    for (int sl = hd[gg]; sl >= 0; sl = nxt[sl]) stk[nfree++] = (int16_t)sl;
-    for (int k = lv[gg]; k < lv[gg + 1]; ++k) {
+    if (threadIdx.x == 0) {
+      int nf = max(nfree, 0);
+      for (int sl = hd[gg]; sl >= 0; sl = nxt[sl]) stk[nf++] = (int16_t)sl;
+      nfree = nf;
+    }
+    __syncthreads();
+    for (int k = lv[gg] + threadIdx.x; k < lv[gg + 1]; k += blockDim.x) {
       const uint32_t e = gl[k];
       const int c = (int)(e & kCellMask);
       const uint32_t code = e >> kCellBits;
@@ -1473,24 +1487,28 @@ __global__ void k_front_alloc(const uint32_t* __restrict__ glist, const int32_t*
           const int nb = nbr[(size_t)c * 4 + i];
           const int gr = nb >= 0 ? gc[nb] : -1;
           if (gr > gg) {
-            if (nfree > 0)
-              sl = stk[--nfree];
-            else if (top < kFrontMaxSlots)
-              sl = top++;
-            else
-              over = 1;
-            if (sl >= 0) {
-              nxt[sl] = (int16_t)hd[gr + 1];
-              hd[gr + 1] = sl;
+            const int p = atomicSub(&nfree, 1) - 1;
+            if (p >= 0) {
+              sl = stk[p];
+            } else {
+              const int t = atomicAdd(&top, 1);
+              if (t < kFrontMaxSlots)
+                sl = t;
+              else
+                over = 1;
             }
+            if (sl >= 0) nxt[sl] = (int16_t)atomicExch(&hd[gr + 1], sl);
           }
         }
         fs[(size_t)c * 4 + i] = (int16_t)sl;
       }
     }
+    __syncthreads();
   }
-  atomicMax(nslots, top);
-  if (over) atomicOr(overflow, 1);
+  if (threadIdx.x == 0) {
+    atomicMax(nslots, min(top, kFrontMaxSlots));
+    if (over) atomicOr(overflow, 1);
+  }
 }
 
 // Packed front slots of every schedule position (see above).

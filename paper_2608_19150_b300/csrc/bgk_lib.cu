@@ -759,13 +759,11 @@ int build_front(bgk_handle* h) {
   const int n = h->hm.ncell, nv = h->g.nv;
   const size_t cells = (size_t)nv * n;
   int32_t *genc = nullptr, *head = nullptr;
-  int16_t *fslot = nullptr, *work = nullptr;
+  int16_t* fslot = nullptr;
   int* cnt = nullptr;
   int rc = BGK_OK;
   if (dalloc(genc, sizeof(int32_t) * cells) != BGK_OK || dalloc(fslot, sizeof(int16_t) * 4 * cells) != BGK_OK ||
-      dalloc(head, sizeof(int32_t) * (size_t)nv * (n + 1)) != BGK_OK ||
-      dalloc(work, sizeof(int16_t) * 2 * kFrontMaxSlots * (size_t)nv) != BGK_OK ||
-      dalloc(cnt, sizeof(int) * 2) != BGK_OK)
+      dalloc(head, sizeof(int32_t) * (size_t)nv * (n + 1)) != BGK_OK || dalloc(cnt, sizeof(int) * 2) != BGK_OK)
     rc = BGK_E_OOM;
   int hc[2] = {0, 1};
   if (rc == BGK_OK) {
@@ -773,11 +771,9 @@ int build_front(bgk_handle* h) {
     k_front_gen<<<nv, 256, 0, s>>>(h->glist, h->lvl, h->ngen, n, genc);
     cudaMemsetAsync(cnt, 0, sizeof(int) * 2, s);
     if (h->hm.quad)
-      k_front_alloc<4><<<(nv + 63) / 64, 64, 0, s>>>(h->glist, h->lvl, h->ngen, h->nbr, n, nv, genc, fslot, head,
-                                                     work, cnt, cnt + 1);
+      k_front_alloc<4><<<nv, 256, 0, s>>>(h->glist, h->lvl, h->ngen, h->nbr, n, genc, fslot, head, cnt, cnt + 1);
     else
-      k_front_alloc<3><<<(nv + 63) / 64, 64, 0, s>>>(h->glist, h->lvl, h->ngen, h->nbr, n, nv, genc, fslot, head,
-                                                     work, cnt, cnt + 1);
+      k_front_alloc<3><<<nv, 256, 0, s>>>(h->glist, h->lvl, h->ngen, h->nbr, n, genc, fslot, head, cnt, cnt + 1);
     if (cudaGetLastError() != cudaSuccess || cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, s) !=
                                                    cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
       rc = BGK_E_CUDA;
@@ -801,7 +797,7 @@ int build_front(bgk_handle* h) {
     }
   }
   if (rc == BGK_E_OOM) rc = BGK_OK;  // no room for the scratch: sweep from global memory
-  for (void* p : {(void*)genc, (void*)fslot, (void*)head, (void*)work, (void*)cnt})
+  for (void* p : {(void*)genc, (void*)fslot, (void*)head, (void*)cnt})
     if (p) cudaFree(p);
   return rc;
 }
