@@ -459,7 +459,8 @@ def timed_steps(s, steps, world, local, tstream, guess=False, main_fp32=False, w
 PROFILED_TRAFFIC = {
     "fp64": (3.750e9, "profiles/sweep_fp64_cached_shock_tube_64_p2_v32.md"),
     "fp32": (0.631e9, "profiles/sweep_fp32_fused_shock_tube_64_p2_v32.md"),
-}   # the shared-memory front sweep (k_sweep_front) has no capture yet: its traffic is null
+    "fp32_front": (0.535e9, "profiles/sweep_front_fp32_shock_tube_64_p2_v32.md"),
+}
 
 
 def sweep_roofline(w, precision, reps, peaks, n_side=None, n_v=None, sweep_mode="auto", fp64_peak=None):
