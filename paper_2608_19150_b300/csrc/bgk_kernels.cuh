@@ -606,23 +606,38 @@ __global__ void k_factors(VGrid g, int nnode, const double* __restrict__ U0, con
 }
 
 // src[j][i] = prod_a cf[a][j_a][i] + qscale * q[j][i]  (nu M^l + q of Eq. bgk-ss-picard)
+// Launch: 2D grid, blockIdx.y (and its strides) over ordinates, x over nodes (k_source_grid),
+// so no thread divides a flat index.
 template <typename T, typename TQ = T>
 __global__ void k_source(VGrid g, int nnode, const T* __restrict__ cf, const TQ* __restrict__ q, T qscale,
                          T* __restrict__ src, const DevState* ds) {
   if (ds->status != BGK_OK || ds->done) return;
-  const size_t total = (size_t)g.nv * nnode;
-  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    const int j = (int)(t / nnode);
-    const int i = (int)(t - (size_t)j * nnode);
-    T m;
+  for (int j = blockIdx.y; j < g.nv; j += gridDim.y) {
+    const T* c1;
+    const T* c2;
+    const T* c3 = nullptr;
     if (g.dim == 2) {
-      m = cf[(size_t)(j / g.N) * nnode + i] * cf[(size_t)(g.N + j % g.N) * nnode + i];
+      c1 = cf + (size_t)(j / g.N) * nnode;
+      c2 = cf + (size_t)(g.N + j % g.N) * nnode;
     } else {
-      m = cf[(size_t)(j / (g.N * g.N)) * nnode + i] * cf[(size_t)(g.N + (j / g.N) % g.N) * nnode + i] *
-          cf[(size_t)(2 * g.N + j % g.N) * nnode + i];
+      c1 = cf + (size_t)(j / (g.N * g.N)) * nnode;
+      c2 = cf + (size_t)(g.N + (j / g.N) % g.N) * nnode;
+      c3 = cf + (size_t)(2 * g.N + j % g.N) * nnode;
     }
-    src[t] = fma(qscale, (T)q[t], m);
+    const TQ* qj = q + (size_t)j * nnode;
+    T* sj = src + (size_t)j * nnode;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nnode; i += gridDim.x * blockDim.x) {
+      T m = c1[i] * c2[i];
+      if (c3) m = m * c3[i];
+      sj[i] = fma(qscale, (T)qj[i], m);
+    }
   }
+}
+
+// grid of k_source: about four nodes per thread of 256, at most 65535 ordinate rows
+inline dim3 k_source_grid(int nnode, int nv) {
+  const int bx = (nnode + 1023) / 1024;
+  return dim3((unsigned)(bx > 0 ? bx : 1), (unsigned)(nv < 65535 ? nv : 65535));
 }
 
 // Reduce the partials in a fixed order, evaluate Eq. (convergence-criteria) (m = 1

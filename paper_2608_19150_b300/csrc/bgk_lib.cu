@@ -389,7 +389,8 @@ int build_src_t(bgk_handle* h, const void* qsrc, double qscale) {
     h->fused_q = qsrc;
     h->fused_qscale = qscale;
   } else {
-    k_source<T><<<148 * 16, 256, 0, h->stream>>>(h->g, h->nnode, (const T*)h->cf, (const T*)qsrc, (T)qscale,
+    k_source<T><<<k_source_grid(h->nnode, h->g.nv), 256, 0, h->stream>>>(h->g, h->nnode, (const T*)h->cf,
+                                                                        (const T*)qsrc, (T)qscale,
                                                  (T*)h->src, h->ds);
   }
   return cudaGetLastError() == cudaSuccess ? BGK_OK : BGK_E_CUDA;
@@ -912,7 +913,10 @@ int bgk_create(const bgk_mesh* mesh, const bgk_vgrid* vg, const bgk_physics* phy
   const size_t fb = h->nfv * h->tsize;
   const size_t fbcb = nv * (size_t)hm.nbface * hm.fd * h->tsize;
   // k_moments: 128 / MomentParts nodes per block of 128 threads
-  h->mom_blocks = h->precision == BGK_FP64 ? (h->nnode + 31) / 32 : (h->nnode + 127) / 128;
+  {
+    const int npb = 128 / (h->precision == BGK_FP64 ? MomentParts<double>::value : MomentParts<float>::value);
+    h->mom_blocks = (h->nnode + npb - 1) / npb;  // nodes per block of k_moments
+  }
   rc = BGK_OK;
   auto A = [&](int r) {
     if (rc == BGK_OK) rc = r;
