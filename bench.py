@@ -458,16 +458,21 @@ def timed_steps(s, steps, world, local, tstream, guess=False, main_fp32=False, w
 # of the n x n workload moves (n / 64)^2 times as much (traffic grows with the cells).
 PROFILED_TRAFFIC = {
     "fp64": (3.750e9, "profiles/sweep_fp64_cached_shock_tube_64_p2_v32.md"),
+    "fp64_pairs": (3.751e9, "profiles/sweep_pair_fp64_shock_tube_64_p2_v32.md"),
     "fp32": (0.631e9, "profiles/sweep_fp32_fused_shock_tube_64_p2_v32.md"),
     "fp32_front": (0.535e9, "profiles/sweep_front_fp32_shock_tube_64_p2_v32.md"),
 }
 
 
-def sweep_roofline(w, precision, reps, peaks, n_side=None, n_v=None, sweep_mode="auto", fp64_peak=None):
+def sweep_roofline(w, precision, reps, peaks, n_side=None, n_v=None, sweep_mode="auto", fp64_peak=None,
+                   pairs=False):
     """Event-timed sweep kernel of the given precision on its own handle (first-stage
-    coefficient, local-inverse cache as in the step) and its roofline entry."""
+    coefficient, local-inverse cache as in the step) and its roofline entry.  pairs: the
+    FP64-data sweep in float pairs (the FP64 phase of the mixed precision), reported
+    against HBM like the FP32 sweep, with its FP64-equivalent rate beside it."""
     from paper_2608_19150_b300 import bgk
-    s = bgk.Solver.from_workload(w, precision=precision, sweep_mode=sweep_mode)
+    s = bgk.Solver.from_workload(w, precision=precision, sweep_mode=sweep_mode,
+                                 hp_sweep="pairs" if pairs else "fp64")
     s.set_state_maxwellian(w.init)
     s.set_inflow_maxwellian(w.inflow)
     if sweep_mode == "auto":
@@ -487,7 +492,17 @@ def sweep_roofline(w, precision, reps, peaks, n_side=None, n_v=None, sweep_mode=
     ename = {"p2tri": "ElemP2Tri", "p1tri": "ElemP1Tri", "p1tet": "ElemP1Tet", "q1quad": "ElemQ1Quad"}[kind]
     kname = "k_sweep_ts" if s.sweep_mode == "ts" else "k_sweep"
     front = precision != "fp64" and kname == "k_sweep" and s.front_slots > 0
-    if precision == "fp64":
+    if precision == "fp64" and pairs and cached:
+        fl = sweep_flops_per_item(cached, kind)
+        tf = fl * s.nv * s.ncell / (sweep_ms * 1e-3) / 1e12
+        r = {"bound": "hbm", "achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_gbs / hbm_peak,
+             "traffic": None,
+             "kernel": ("k_sweep_ts<%s,double,cached,pairs>" % ename) if kname == "k_sweep_ts" else
+                       "k_sweep_pair<%s>" % ename,
+             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+             "fp64_equivalent_tflops": tf, "fp64_peak_tflops": fp64_peak, "fp64_equivalent_frac": tf / fp64_peak,
+             "flops_per_local_solve": fl}
+    elif precision == "fp64":
         fl = sweep_flops_per_item(cached, kind)
         tf = fl * s.nv * s.ncell / (sweep_ms * 1e-3) / 1e12
         r = {"bound": "alu", "achieved": tf, "peak": fp64_peak, "unit": "TFLOP/s",
@@ -501,7 +516,8 @@ def sweep_roofline(w, precision, reps, peaks, n_side=None, n_v=None, sweep_mode=
              "kernel": ("k_sweep_front<%s>" % ename) if front else
                        "%s<%s,float,%s>" % (kname, ename, "cached" if cached else "uncached,fused source"),
              "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)", "front_slots": s.front_slots}
-    profiled = PROFILED_TRAFFIC.get("fp32_front" if front else precision)
+    profiled = PROFILED_TRAFFIC.get("fp32_front" if front else "fp64_pairs" if (pairs and precision == "fp64")
+                                    else precision)
     if profiled and kind == "p2tri" and kname == "k_sweep" and n_side and n_v == 32 and (precision == "fp32" or cached):
         r["traffic"] = profiled[0] * (n_side / 64.0) ** 2
         r["traffic_source"] = profiled[1] + " (scaled from 64x64 by the cell count)"
@@ -632,13 +648,18 @@ def run_ours(args):
     fp64_peak = bgk.probe_fma_tflops(np.float64)
     rl = {"fp64": sweep_roofline(w, "fp64", args.sweep_reps, peaks, args.n_side, args.n_v, args.sweep_mode,
                                  fp64_peak)}
+    if args.precision == "mixed":
+        # the kernel of the mixed step's FP64 phase (float pairs; the plain path keeps FP64)
+        rl["fp64_pairs"] = sweep_roofline(w, "fp64", args.sweep_reps, peaks, args.n_side, args.n_v,
+                                          args.sweep_mode, fp64_peak, pairs=True)
     if args.precision != "fp64":
         rl["fp32"] = sweep_roofline(w, "fp32", args.sweep_reps, peaks, args.n_side, args.n_v, args.sweep_mode)
-    # dominant kernel of the timed step: the sweep precision that used the most time
+    # dominant kernel of the timed step: the sweep that used the most time
     n64 = sum(sum(i["fp64"]) for i in iters)
     n32 = sum(sum(i["fp32"]) for i in iters)
-    dom = "fp64"
-    if "fp32" in rl and n32 * rl["fp32"]["sweep_ms"] > n64 * rl["fp64"]["sweep_ms"]:
+    k64 = "fp64_pairs" if "fp64_pairs" in rl and rl["fp64_pairs"]["local_inverse_cache_gb"] > 0 else "fp64"
+    dom = k64
+    if "fp32" in rl and n32 * rl["fp32"]["sweep_ms"] > n64 * rl[k64]["sweep_ms"]:
         dom = "fp32"
     roofline = dict(rl[dom])
     cpu = None

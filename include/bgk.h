@@ -127,6 +127,14 @@ typedef struct {
                          the sweep itself produced from a shared-memory buffer when every
                          ordinate's live front fits (slots assigned once at creation), else
                          from global memory; 2 = always from global memory.  Same results */
+  int hp_sweep;       /* arithmetic of the FP64-data sweeps that use cached local inverses:
+                         0 = automatic: float pairs in the FP64 phase of BGK_MIXED, FP64 otherwise;
+                         1 = FP64; 2 = float pairs: the mass-weighted source, the inflow terms
+                         and the product with the inverse (stored as float pairs) in
+                         compensated FP32 arithmetic (error-free transformations), about
+                         2^-44 relative per operation (FP64: 2^-53), eight orders below the
+                         Picard tolerance, at a fraction of B300's FP64 instruction cost.
+                         The data in memory stay FP64 */
 } bgk_config;
 
 typedef struct {

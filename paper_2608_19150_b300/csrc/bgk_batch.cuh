@@ -296,7 +296,7 @@ int capture_batch_step(bgk_batch* b) {
   }
   if (rc == BGK_OK)
     rc = batch_loop(b, s, b->d_ds, [&](cudaStream_t bs) {
-      int r = fork_instances(b, bs, b->side_body, [&](bgk_handle* h) { return build_src(h, h->fk, h->qscale_main); });
+      int r = fork_instances(b, bs, b->side_body, [&](bgk_handle* h) { return build_src(h, h->fk, h->qscale_main, h->nus_main); });
       if (r == BGK_OK) launch_batched_sweep(b, bs);
       if (r == BGK_OK)
         r = fork_instances(b, bs, b->side_body, [&](bgk_handle* h) {
@@ -383,6 +383,7 @@ int bgk_batch_create(int n, const bgk_mesh* meshes, const bgk_vgrid* vgrids, con
   c.stream = b->stream;
   c.eager = 1;  // instances never capture their own graphs; the batch captures one
   c.sweep_front = 2;  // the batched sweep reads upwind traces from global memory
+  c.hp_sweep = 1;  // the batched sweep runs FP64 data in FP64 arithmetic
   const int cache_policy = c.cache_inverse;
   c.cache_inverse = 2;  // caches are added below, once every instance's arrays exist
   for (int i = 0; i < n; ++i) {
@@ -622,7 +623,7 @@ int bgk_batch_sweep(bgk_batch* b) {
     h->stream = b->stream;
     k_reset_state<<<1, 1, 0, b->stream>>>(h->ds);
     moments(h, 0);
-    int rc = build_src(h, h->fk, h->qscale_main);
+    int rc = build_src(h, h->fk, h->qscale_main, h->nus_main);
     h->stream = keep;
     if (rc != BGK_OK) return rc;
   }

@@ -960,7 +960,10 @@ __device__ __forceinline__ void face_rates_t(const T (&Gc)[E::NF * E::D + 1], ui
 // by Gauss-Jordan elimination in natural order and stored as T in schedule order:
 // Ainv[(j * ncell + k) * S + a * ND + b], S = ainv_stride.  Valid for one nu_s; a sweep with that
 // nu_s then needs only the right-hand side and one matrix-vector product per cell.
-template <class E, typename T>
+// PAIR (T = double): each FP64 entry is stored as a float pair hi + lo (split_double,
+// |X - hi - lo| <= 2^-47 |X|) in the same S * 8 bytes: the S hi floats, then the S lo
+// floats, for the float-pair product of the sweep (sweep_ordinate, PAIR).
+template <class E, typename T, bool PAIR = false>
 __global__ void k_local_inverse(SweepArgs sa, VGrid g, double nus, T* __restrict__ Ainv) {
   constexpr int ND = E::NDOF, NF = E::NF;
   const size_t total = (size_t)g.nv * sa.ncell;
@@ -1000,10 +1003,20 @@ __global__ void k_local_inverse(SweepArgs sa, VGrid g, double nus, T* __restrict
       }
     }
     T* out = Ainv + it * ainv_stride<E, T>();
+    if constexpr (PAIR) {
+      static_assert(sizeof(T) == 8, "float pairs replace FP64 entries");
+      constexpr int AS = ainv_stride<E, T>();
+      float* o = reinterpret_cast<float*>(out);
 #pragma unroll
-    for (int a = 0; a < ND; ++a)
+      for (int a = 0; a < ND; ++a)
 #pragma unroll
-      for (int bb = 0; bb < ND; ++bb) out[a * ND + bb] = (T)X[a][bb];
+        for (int bb = 0; bb < ND; ++bb) split_double(X[a][bb], o[a * ND + bb], o[AS + a * ND + bb]);
+    } else {
+#pragma unroll
+      for (int a = 0; a < ND; ++a)
+#pragma unroll
+        for (int bb = 0; bb < ND; ++bb) out[a * ND + bb] = (T)X[a][bb];
+    }
   }
 }
 
@@ -1213,6 +1226,136 @@ struct NamedBarrier {
   }
 };
 
+// ---------------------------------------------------------------------------------
+// Float-pair arithmetic for the FP64-data sweeps of the mixed precision's FP64 phase (PAIR):
+// B300 runs FP64 at about 1/62 of its FP32 rate, so the FP64-data sweep forms its
+// right-hand side and its product with the cached inverse in pairs of floats hi + lo
+// (error-free transformations: TwoProduct by fma, TwoSum, Dekker's renormalisation),
+// about 2^-44..2^-47 relative per operation instead of FP64's 2^-53: eight orders below
+// the Picard tolerance, at FP32 instruction rates.  The data in memory stay FP64 (split
+// with integer operations on load, rebuilt exactly from the pair on store).
+struct fpair {
+  float h, l;
+  __host__ __device__ constexpr fpair() : h(0.f), l(0.f) {}
+  __host__ __device__ constexpr fpair(float hi, float lo) : h(hi), l(lo) {}
+  // compile-time constants of the element tables (folded by the compiler; runtime FP64
+  // values go through fp_split)
+  __host__ __device__ constexpr explicit fpair(double d) : h((float)d), l((float)(d - (double)(float)d)) {}
+};
+__device__ __forceinline__ fpair fp_split(double d) {
+  fpair r;
+  split_double(d, r.h, r.l);
+  return r;
+}
+__device__ __forceinline__ fpair operator*(fpair a, fpair b) {
+  const float p = a.h * b.h;
+  const float e = fmaf(a.h, b.l, fmaf(a.l, b.h, fmaf(a.h, b.h, -p)));
+  const float s = p + e;
+  return fpair(s, e - (s - p));
+}
+__device__ __forceinline__ fpair operator+(fpair a, fpair b) {
+  const float s = a.h + b.h;  // TwoSum(a.h, b.h), then the low parts, renormalised
+  const float v = s - a.h;
+  const float e = ((a.h - (s - v)) + (b.h - v)) + (a.l + b.l);
+  const float t = s + e;
+  return fpair(t, e - (t - s));
+}
+__device__ __forceinline__ fpair& operator+=(fpair& a, fpair b) {
+  a = a + b;
+  return a;
+}
+
+// The double of a float by integer operations (no FP64 conversion instruction): exact for
+// normal floats, zero for zeros and subnormals (at most 2^-126 absolute), infinities and
+// NaNs kept non-finite.
+__device__ __forceinline__ double float_to_double(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned s = u & 0x80000000u;
+  if (e == 0u) return __hiloint2double((int)s, 0);
+  const unsigned ed = e == 0xffu ? 0x7ffu : e + 896u;  // 1023 - 127
+  return __hiloint2double((int)(s | (ed << 20) | ((u & 0x7fffffu) >> 3)), (int)(u << 29));
+}
+// a pair stored in the 8 bytes of one double (hi at the lower address) and back
+__device__ __forceinline__ fpair fp_from_bits(double d) {
+  return fpair(__int_as_float(__double2loint(d)), __int_as_float(__double2hiint(d)));
+}
+__device__ __forceinline__ double fp_to_bits(fpair a) {
+  return __hiloint2double(__float_as_int(a.l), __float_as_int(a.h));
+}
+
+// x = Ainv b of one cell in pairs: Ainv as the float pairs of k_local_inverse<E, double,
+// true> (hi at Ap[0 .. S), lo at Ap[S .. 2S)); each x_a = sum_b (Ah + Al)(bh + bl) is the
+// compensated dot product of Ogita, Rump and Oishi (TwoProduct by fma, TwoSum) with the
+// cross terms Ah bl + Al bh in the error term and Al bl (2^-48 of the product) left out:
+// about 2^-47 of the sum of |terms|.  x is returned as FP64 (hi + lo, one FP64 add).
+template <int ND, int S>
+__device__ __forceinline__ void inverse_product_pair(const float* __restrict__ Ap, const fpair (&b)[ND],
+                                                     double (&x)[ND]) {
+  float Ah[S], Al[S];
+  load_vec<float, S, 16>(Ap, Ah);
+  load_vec<float, S, (S % 4 == 0 ? 16 : 8)>(Ap + S, Al);
+#pragma unroll
+  for (int a = 0; a < ND; ++a) {
+    const float* ah = Ah + a * ND;
+    const float* al = Al + a * ND;
+    float hi = ah[0] * b[0].h;
+    float lo = fmaf(ah[0], b[0].h, -hi) + fmaf(ah[0], b[0].l, al[0] * b[0].h);
+#pragma unroll
+    for (int q = 1; q < ND; ++q) {
+      const float p = ah[q] * b[q].h;
+      const float ep = fmaf(ah[q], b[q].h, -p) + fmaf(ah[q], b[q].l, al[q] * b[q].h);
+      const float t = hi + p;  // TwoSum(hi, p)
+      const float z = t - hi;
+      const float es = (hi - (t - z)) + (p - z);
+      hi = t;
+      lo += es + ep;
+    }
+    x[a] = float_to_double(hi) + float_to_double(lo);
+  }
+}
+
+// PAIR source pass: b0[j][cell] = Mh (prod_a cf[a][j_a] + qscale q[j]) over the cell's
+// nodes, in pairs, stored as pairs in the 8 bytes of each node's double (fp_to_bits), so
+// the PAIR sweep starts from the mass-weighted source (the FP64 sweep applies Mh itself).
+// Launch: 2D grid, blockIdx.y (and its strides) over ordinates, x over cells.
+template <class E>
+__global__ void k_source_pair(VGrid g, int ncell, const double* __restrict__ cf, const double* __restrict__ q,
+                              double qscale, double* __restrict__ b0, const DevState* ds) {
+  if (ds->status != BGK_OK || ds->done) return;
+  constexpr int ND = E::NDOF;
+  const size_t nnode = (size_t)ncell * ND;
+  const fpair qs = fp_split(qscale);
+  for (int j = blockIdx.y; j < g.nv; j += gridDim.y) {
+    const double* c1;
+    const double* c2;
+    const double* c3 = nullptr;
+    if (g.dim == 2) {
+      c1 = cf + (size_t)(j / g.N) * nnode;
+      c2 = cf + (size_t)(g.N + j % g.N) * nnode;
+    } else {
+      c1 = cf + (size_t)(j / (g.N * g.N)) * nnode;
+      c2 = cf + (size_t)(g.N + (j / g.N) % g.N) * nnode;
+      c3 = cf + (size_t)(2 * g.N + j % g.N) * nnode;
+    }
+    const double* qj = q + (size_t)j * nnode;
+    double* bj = b0 + (size_t)j * nnode;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
+      const size_t o = (size_t)c * ND;
+      fpair sv[ND], bv[ND];
+#pragma unroll
+      for (int a = 0; a < ND; ++a) {
+        fpair m = fp_split(c1[o + a]) * fp_split(c2[o + a]);
+        if (c3) m = m * fp_split(c3[o + a]);
+        sv[a] = m + qs * fp_split(qj[o + a]);
+      }
+      E::mass(sv, bv);
+#pragma unroll
+      for (int a = 0; a < ND; ++a) bj[o + a] = fp_to_bits(bv[a]);
+    }
+  }
+}
+
 // One ordinate's transport sweep (Sec. 4, Eq. bgk-ss-picard) by a group of `nt` threads
 // (thread `tid` of the group) walking the ordinate's generations; the cells of one
 // generation are independent and share the group's threads.  For cell K and ordinate j
@@ -1222,10 +1365,12 @@ struct NamedBarrier {
 // updated in place.  An upwind cell reached by a lagged (cycle) edge has a higher
 // generation, so it still holds f^l when read; boundary faces read fbc.
 // CACHED: the local inverse comes from k_local_inverse (schedule order, coalesced);
-// otherwise the matrix is assembled and factorised in place.  The schedule entry, the
+// otherwise the matrix is assembled and factorised in place.  PAIR (FP64 data, cached
+// float-pair inverse): src holds the pairs of Mh src (k_source_pair) and the inflow terms
+// and the product with the inverse run in float pairs (fpair).  The schedule entry, the
 // neighbour ids, the node permutation and src of the thread's next item are loaded
 // before the current item is solved (they are not written during the sweep).
-template <class E, typename T, bool CACHED, class Bar, bool PF = false, bool FUSED = false>
+template <class E, typename T, bool CACHED, class Bar, bool PF = false, bool FUSED = false, bool PAIR = false>
 __device__ __forceinline__ void sweep_ordinate(const SweepArgs& sa, const VGrid& g, int j, T nus,
                                                const SrcArgs<T>& sr, const T* __restrict__ fbc,
                                                const T* __restrict__ Ainv, T* f, int tid, int nt, const Bar& bar,
@@ -1313,7 +1458,13 @@ __device__ __forceinline__ void sweep_ordinate(const SweepArgs& sa, const VGrid&
           face_rates<E, T>(sa.geo + (size_t)c * sa.gs, code, v0, v1, v2, r, outm);
       }
       T b[ND];
-      E::mass(cur.src, b);
+      fpair bp[PAIR ? ND : 1];  // PAIR: the right-hand side in pairs, from Mh src
+      if constexpr (PAIR) {
+#pragma unroll
+        for (int a = 0; a < ND; ++a) bp[a] = fp_from_bits(cur.src[a]);
+      } else {
+        E::mass(cur.src, b);
+      }
       const int nbs[4] = {cur.nb.x, cur.nb.y, cur.nb.z, cur.nb.w};
       // upwind traces of all faces in one round of loads (no branch between them): an
       // inflow face reads its neighbour's values (or the boundary data), any other face
@@ -1350,10 +1501,21 @@ __device__ __forceinline__ void sweep_ordinate(const SweepArgs& sa, const VGrid&
         } else {
           ci = -r[i];
         }
-        E::inflow(i, ci, y[i], b);
+        if constexpr (PAIR) {
+          fpair yp[FD];
+#pragma unroll
+          for (int kk = 0; kk < FD; ++kk) yp[kk] = fp_split(y[i][kk]);
+          E::inflow(i, fp_split(ci), yp, bp);
+        } else {
+          E::inflow(i, ci, y[i], b);
+        }
       }
       T x[ND];
-      if (CACHED) {
+      if constexpr (CACHED && PAIR) {
+        static_assert(sizeof(T) == 8 && !PF && !REG, "pair sweep: FP64 data, inverse read in place");
+        inverse_product_pair<ND, ainv_stride<E, T>()>(
+            reinterpret_cast<const float*>(Aj + (size_t)k * ainv_stride<E, T>()), bp, x);
+      } else if (CACHED) {
         // the inverse is 16-byte aligned and padded: read it with 128-bit loads
         constexpr int AS = ainv_stride<E, T>(), NV = AS * (int)sizeof(T) / 16;
         static_assert(AS * (int)sizeof(T) == NV * 16, "padded inverse");
@@ -1396,6 +1558,19 @@ __device__ __forceinline__ void sweep_ordinate(const SweepArgs& sa, const VGrid&
   if (PF) cp_async_wait<0>();
 }
 
+// The FP64-data sweep in float pairs (PAIR): at most 128 registers, so that every CTA of
+// the launch is resident at once.
+template <class E>
+__global__ void __launch_bounds__(128, 4) k_sweep_pair(SweepArgs sa, VGrid g, double nus, SrcArgs<double> sr,
+                                                     const double* __restrict__ fbc,
+                                                     const double* __restrict__ Ainv, double* f,
+                                                     const DevState* ds, int jofs) {
+  if (ds && (ds->status != BGK_OK || ds->done)) return;
+  sweep_ordinate<E, double, true, CtaBarrier, false, false, true>(sa, g, jofs + (int)blockIdx.x, nus, sr, fbc,
+                                                                  Ainv, f, (int)threadIdx.x, (int)blockDim.x,
+                                                                  CtaBarrier());
+}
+
 // One sweep of every ordinate of one problem: one CTA per ordinate.  PF: the cached
 // local inverse and the geometry of each thread's next cell are copied to shared memory
 // asynchronously while the current cell is solved (dynamic shared memory).
@@ -1403,14 +1578,14 @@ __device__ __forceinline__ void sweep_ordinate(const SweepArgs& sa, const VGrid&
 // schedule alone, cell after cell in generation order, with no barrier; the concurrent
 // work is the number of ordinates (the generation sweep's is ordinates x generation
 // width).  Same operations per cell as the generation sweep.
-template <class E, typename T, bool CACHED, bool FUSED = false>
+template <class E, typename T, bool CACHED, bool FUSED = false, bool PAIR = false>
 __global__ void __launch_bounds__(64) k_sweep_ts(SweepArgs sa, VGrid g, T nus, SrcArgs<T> sr,
                                                  const T* __restrict__ fbc, const T* __restrict__ Ainv, T* f,
                                                  const DevState* ds, int jb, int je) {
   if (ds && (ds->status != BGK_OK || ds->done)) return;
   const int j = jb + (int)(blockIdx.x * blockDim.x + threadIdx.x);
   if (j >= je) return;
-  sweep_ordinate<E, T, CACHED, NoBarrier, false, FUSED>(sa, g, j, nus, sr, fbc, Ainv, f, 0, 1, NoBarrier());
+  sweep_ordinate<E, T, CACHED, NoBarrier, false, FUSED, PAIR>(sa, g, j, nus, sr, fbc, Ainv, f, 0, 1, NoBarrier());
 }
 
 // (ordinates jofs + blockIdx.x: all of them, or one shard's range)

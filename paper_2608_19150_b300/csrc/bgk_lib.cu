@@ -53,6 +53,7 @@ struct bgk_handle {
   int32_t* ngen = nullptr;
   int32_t* nproc = nullptr;
   void* Ainv = nullptr;      // cached local inverses (schedule order), valid for nus_cached
+  bool ainv_pairs = false;   // the FP64 cache holds float pairs (float-pair sweeps, k_sweep_pair)
   double nus_cached = -1.0;
   double nus_main = 0.0, qscale_main = 0.0;  // stage coefficient and 1/(dt A_ss) of the step
   size_t ainv_bytes = 0;
@@ -234,11 +235,16 @@ size_t prefetch_smem(const bgk_handle* h) {
 
 // generation offsets of the front sweep: G + 1 ints of the largest G, rounded up to 4
 int front_lvcap(const bgk_handle* h) { return (h->Gmax + 1 + 3) & ~3; }
+
+// A sweep with coefficient nus runs in float pairs (k_sweep_pair; its source from
+// k_source_pair) when the handle's cache holds float pairs for that coefficient.
+bool pair_sweep(const bgk_handle* h, double nus) { return h->ainv_pairs && h->Ainv && nus == h->nus_cached; }
 size_t front_smem_bytes(const bgk_handle* h, int S, int threads);
 
 template <class E, typename T>
 void launch_sweep_t(bgk_handle* h, double nus, int jb, int je) {
   const bool cached = h->Ainv && nus == h->nus_cached;
+  const bool pairs = sizeof(T) == 8 && pair_sweep(h, nus);
   const size_t pf = prefetch_smem<E, T>(h);
   const SrcArgs<T> sr{(const T*)h->src, nullptr, nullptr, T(0)};
   if (h->sweep_ts) {
@@ -248,6 +254,13 @@ void launch_sweep_t(bgk_handle* h, double nus, int jb, int je) {
         const SrcArgs<T> fr{nullptr, (const T*)h->cf, (const T*)h->fused_q, (T)h->fused_qscale};
         k_sweep_ts<E, T, false, true><<<blk, thr, 0, h->stream>>>(sweep_args(h), h->g, (T)nus, fr, (const T*)h->fbc,
                                                                   nullptr, (T*)h->f, h->ds, jb, je);
+        return;
+      }
+    }
+    if constexpr (sizeof(T) == 8) {
+      if (pairs) {
+        k_sweep_ts<E, T, true, false, true><<<blk, thr, 0, h->stream>>>(
+            sweep_args(h), h->g, (T)nus, sr, (const T*)h->fbc, (const T*)h->Ainv, (T*)h->f, h->ds, jb, je);
         return;
       }
     }
@@ -275,6 +288,13 @@ void launch_sweep_t(bgk_handle* h, double nus, int jb, int je) {
       return;
     }
   }
+  if constexpr (sizeof(T) == 8) {
+    if (pairs) {
+      k_sweep_pair<E><<<je - jb, h->sweep_threads, 0, h->stream>>>(
+          sweep_args(h), h->g, (T)nus, sr, (const T*)h->fbc, (const T*)h->Ainv, (T*)h->f, h->ds, jb);
+      return;
+    }
+  }
   if (cached && h->cfg.prefetch == 1 && pf <= 96 * 1024)
     k_sweep<E, T, true, true><<<je - jb, h->sweep_threads, pf, h->stream>>>(
         sweep_args(h), h->g, (T)nus, sr, (const T*)h->fbc, (const T*)h->Ainv, (T*)h->f, h->ds, jb);
@@ -288,6 +308,12 @@ void launch_sweep_t(bgk_handle* h, double nus, int jb, int je) {
 
 template <class E, typename T>
 void launch_inverse_t(bgk_handle* h, double nus) {
+  if constexpr (sizeof(T) == 8) {
+    if (h->ainv_pairs) {
+      k_local_inverse<E, T, true><<<148 * 16, 128, 0, h->stream>>>(sweep_args(h), h->g, nus, (T*)h->Ainv);
+      return;
+    }
+  }
   k_local_inverse<E, T><<<148 * 16, 128, 0, h->stream>>>(sweep_args(h), h->g, nus, (T*)h->Ainv);
 }
 
@@ -314,6 +340,7 @@ int build_inverse_cache(bgk_handle* h, double nus) {
     return h->cfg.cache_inverse == 1 ? BGK_E_OOM : BGK_OK;
   }
   const bool f64 = h->precision == BGK_FP64;
+  h->ainv_pairs = f64 && (h->cfg.hp_sweep == 2 || (h->cfg.hp_sweep == 0 && h->cfg.precision == BGK_MIXED));
   if (h->hm.dim == 3)
     f64 ? launch_inverse_t<ElemP1Tet, double>(h, nus) : launch_inverse_t<ElemP1Tet, float>(h, nus);
   else if (h->hm.quad)
@@ -375,8 +402,17 @@ void moments(bgk_handle* h, int mode) {
 
 // src = nu * M(U[it&1]) + qscale * qsrc: per-node factors, then a streaming product
 // (fused sweeps: the factors only; the sweep forms src from them, qsrc and qscale)
+template <class E>
+void launch_source_pair(bgk_handle* h, const void* qsrc, double qscale) {
+  const int bx = (h->hm.ncell + 255) / 256;
+  const dim3 grid((unsigned)(bx > 0 ? bx : 1), (unsigned)(h->g.nv < 65535 ? h->g.nv : 65535));
+  k_source_pair<E><<<grid, 256, 0, h->stream>>>(h->g, h->hm.ncell, (const double*)h->cf, (const double*)qsrc, qscale,
+                                                (double*)h->src, h->ds);
+}
+
+// (nus: the coefficient of the sweep that follows, which decides the source's form)
 template <typename T>
-int build_src_t(bgk_handle* h, const void* qsrc, double qscale) {
+int build_src_t(bgk_handle* h, const void* qsrc, double qscale, double nus) {
   if (h->has_walls) {
     const int npos = h->hm.nbface * h->hm.fd;
     const int blocks = std::min<size_t>(148 * 8, ((size_t)h->g.nv * npos + 255) / 256);
@@ -388,6 +424,15 @@ int build_src_t(bgk_handle* h, const void* qsrc, double qscale) {
   if (h->fuse_src) {
     h->fused_q = qsrc;
     h->fused_qscale = qscale;
+  } else if (sizeof(T) == 8 && pair_sweep(h, nus)) {
+    if (h->hm.dim == 3)
+      launch_source_pair<ElemP1Tet>(h, qsrc, qscale);
+    else if (h->hm.quad)
+      launch_source_pair<ElemQ1Quad>(h, qsrc, qscale);
+    else if (h->hm.kx == 2)
+      launch_source_pair<ElemP2Tri>(h, qsrc, qscale);
+    else
+      launch_source_pair<ElemP1Tri>(h, qsrc, qscale);
   } else {
     k_source<T><<<k_source_grid(h->nnode, h->g.nv), 256, 0, h->stream>>>(h->g, h->nnode, (const T*)h->cf,
                                                                         (const T*)qsrc, (T)qscale,
@@ -396,14 +441,15 @@ int build_src_t(bgk_handle* h, const void* qsrc, double qscale) {
   return cudaGetLastError() == cudaSuccess ? BGK_OK : BGK_E_CUDA;
 }
 
-int build_src(bgk_handle* h, const void* qsrc, double qscale) {
-  return h->precision == BGK_FP64 ? build_src_t<double>(h, qsrc, qscale) : build_src_t<float>(h, qsrc, qscale);
+int build_src(bgk_handle* h, const void* qsrc, double qscale, double nus) {
+  return h->precision == BGK_FP64 ? build_src_t<double>(h, qsrc, qscale, nus)
+                                  : build_src_t<float>(h, qsrc, qscale, nus);
 }
 
 // FP32 source of the shadow problem; q32 is the main problem's stage source q converted
 // to FP32 once per stage (held in the shadow's fk array, which the shadow does not use).
 int build_src_shadow(bgk_handle* sh, const float* q32, double qscale) {
-  return build_src_t<float>(sh, q32, qscale);
+  return build_src_t<float>(sh, q32, qscale, 0.0);
 }
 
 // Conditional while-node appended to the capture of stream s; returns the body graph.
@@ -563,7 +609,7 @@ int enqueue_step(bgk_handle* h, int mode_bdf2, cudaGraphExec_t* exec_out) {
       CK(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
       CK(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
       h->stream = bs;
-      int rc = build_src(h, qsrc, qscale);
+      int rc = build_src(h, qsrc, qscale, nus);
       launch_sweep_any(h, nus);
       moments(h, 1);
       k_finalize<<<1, 256, 0, bs>>>(h->ds, h->partial, h->mom_blocks, tol, h->cfg.l_max, st, cond, 1);
@@ -578,7 +624,7 @@ int enqueue_step(bgk_handle* h, int mode_bdf2, cudaGraphExec_t* exec_out) {
       }
     } else {
       for (;;) {
-        int rc = build_src(h, qsrc, qscale);
+        int rc = build_src(h, qsrc, qscale, nus);
         if (rc != BGK_OK) return rc;
         launch_sweep_any(h, nus);
         moments(h, 1);
@@ -638,7 +684,7 @@ int recapture_steps(bgk_handle* h) {
 int time_sweeps(bgk_handle* h, const void* qsrc, int reps, float* ms) {
   k_reset_state<<<1, 1, 0, h->stream>>>(h->ds);
   moments(h, 0);
-  int rc = build_src(h, qsrc, h->qscale_main);
+  int rc = build_src(h, qsrc, h->qscale_main, h->nus_main);
   if (rc != BGK_OK) return rc;
   launch_sweep_any(h, h->nus_main);  // warm-up
   CK(cudaEventRecord(h->ev0, h->stream));
@@ -1446,7 +1492,7 @@ int bgk_sweep(bgk_handle* h, double nu_s, double q_scale) {
   if (q_scale <= 0.0) q_scale = h->qscale_main;
   k_reset_state<<<1, 1, 0, h->stream>>>(h->ds);
   moments(h, 0);
-  int rc = build_src(h, h->fk, q_scale);
+  int rc = build_src(h, h->fk, q_scale, nu_s);
   if (rc != BGK_OK) return rc;
   CK(cudaEventRecord(h->ev0, h->stream));
   launch_sweep_any(h, nu_s);
@@ -1475,7 +1521,7 @@ int bgk_sweep_range(bgk_handle* h, int j_begin, int j_end, const double* d_U, do
   // the given moments become the current iterate's (U[it & 1]) for the source
   CK(cudaMemcpyAsync(h->U[st.it & 1], d_U, sizeof(double) * h->nnode * h->nm, cudaMemcpyDeviceToDevice,
                      h->stream));
-  int rc = build_src(h, qsrc, q_scale);
+  int rc = build_src(h, qsrc, q_scale, nu_s);
   if (rc != BGK_OK) return rc;
   launch_sweep_any(h, nu_s, j_begin, j_end);
   CK(cudaGetLastError());
