@@ -123,10 +123,11 @@ typedef struct {
                          give the same results up to rounding.  TS wins only on narrow
                          domains with many ordinates (the Sod strip from 96x96 velocities);
                          bgk_autotune_sweep chooses by measurement */
-  int sweep_front;    /* FP32 generation sweeps of 2D meshes: 0 = read the upwind traces that
-                         the sweep itself produced from a shared-memory buffer when every
-                         ordinate's live front fits (slots assigned once at creation), else
-                         from global memory; 2 = always from global memory.  Same results */
+  int sweep_front;    /* FP32 and float-pair generation sweeps of 2D meshes: 0 = read the
+                         upwind traces that the sweep itself produced from a shared-memory
+                         buffer when every ordinate's live front fits (slots assigned once at
+                         creation; float-pair sweeps of at most 64 threads per CTA), else from
+                         global memory; 2 = always from global memory.  Same results */
   int hp_sweep;       /* arithmetic of the FP64-data sweeps that use cached local inverses:
                          0 = automatic: float pairs in the FP64 phase of BGK_MIXED, FP64 otherwise;
                          1 = FP64; 2 = float pairs: the mass-weighted source, the inflow terms
@@ -161,9 +162,10 @@ int bgk_destroy(bgk_handle* h);
  * [7]=bytes of the local-inverse cache (0 if none), [8]=threads per sweep CTA,
  * [9]=sweep algorithm in use (1 TGS, 2 TS).  out holds 10 values. */
 int bgk_sizes(const bgk_handle* h, int64_t* out);
-/* Slots of the shared-memory front that the handle's FP32 generation sweeps use (the FP32
- * shadow's with BGK_MIXED; bgk_config.sweep_front), or 0 when they read every upwind trace
- * from global memory. */
+/* Slots of the shared-memory front that the handle's generation sweeps use: its FP32
+ * sweeps' (the FP32 shadow's with BGK_MIXED) or, for an FP64 handle, its float-pair sweeps'
+ * (bgk_config.sweep_front, hp_sweep); 0 when they read every upwind trace from global
+ * memory. */
 int bgk_front_slots(const bgk_handle* h, int* slots);
 /* Time step actually used (after the CFL rule). */
 int bgk_get_dt(const bgk_handle* h, double* dt);

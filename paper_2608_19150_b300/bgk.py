@@ -262,7 +262,8 @@ class Solver:
 
     @property
     def front_slots(self):
-        """Shared-memory front slots of the FP32 generation sweep (0: global reads)."""
+        """Shared-memory front slots of the FP32 generation sweep (an FP64 handle: of its
+        float-pair sweep; 0: global reads)."""
         n = C.c_int()
         _ck(self.lib.bgk_front_slots(self.h, C.byref(n)), "bgk_front_slots")
         return n.value

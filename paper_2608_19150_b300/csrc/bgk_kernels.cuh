@@ -358,6 +358,65 @@ __device__ __forceinline__ void split_double(double f, float& hi, float& lo) {
   lo = __int_as_float(__float_as_int(r * sc) | (int)sign);
 }
 
+// ---------------------------------------------------------------------------------
+// Float-pair arithmetic for the FP64-data sweeps of the mixed precision's FP64 phase (PAIR):
+// B300 runs FP64 at about 1/62 of its FP32 rate, so the FP64-data sweep forms its
+// right-hand side and its product with the cached inverse in pairs of floats hi + lo
+// (error-free transformations: TwoProduct by fma, TwoSum, Dekker's renormalisation),
+// about 2^-44..2^-47 relative per operation instead of FP64's 2^-53: eight orders below
+// the Picard tolerance, at FP32 instruction rates.  The data in memory stay FP64 (split
+// with integer operations on load, rebuilt exactly from the pair on store).
+struct fpair {
+  float h, l;
+  __host__ __device__ constexpr fpair() : h(0.f), l(0.f) {}
+  __host__ __device__ constexpr fpair(float hi, float lo) : h(hi), l(lo) {}
+  // compile-time constants of the element tables (folded by the compiler; runtime FP64
+  // values go through fp_split)
+  __host__ __device__ constexpr explicit fpair(double d) : h((float)d), l((float)(d - (double)(float)d)) {}
+};
+__device__ __forceinline__ fpair fp_split(double d) {
+  fpair r;
+  split_double(d, r.h, r.l);
+  return r;
+}
+__device__ __forceinline__ fpair operator*(fpair a, fpair b) {
+  const float p = a.h * b.h;
+  const float e = fmaf(a.h, b.l, fmaf(a.l, b.h, fmaf(a.h, b.h, -p)));
+  const float s = p + e;
+  return fpair(s, e - (s - p));
+}
+__device__ __forceinline__ fpair operator+(fpair a, fpair b) {
+  const float s = a.h + b.h;  // TwoSum(a.h, b.h), then the low parts, renormalised
+  const float v = s - a.h;
+  const float e = ((a.h - (s - v)) + (b.h - v)) + (a.l + b.l);
+  const float t = s + e;
+  return fpair(t, e - (t - s));
+}
+__device__ __forceinline__ fpair& operator+=(fpair& a, fpair b) {
+  a = a + b;
+  return a;
+}
+
+// The double of a float by integer operations (no FP64 conversion instruction): exact for
+// normal floats, zero for zeros and subnormals (at most 2^-126 absolute), infinities and
+// NaNs kept non-finite.
+__device__ __forceinline__ double float_to_double(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned s = u & 0x80000000u;
+  if (e == 0u) return __hiloint2double((int)s, 0);
+  const unsigned ed = e == 0xffu ? 0x7ffu : e + 896u;  // 1023 - 127
+  return __hiloint2double((int)(s | (ed << 20) | ((u & 0x7fffffu) >> 3)), (int)(u << 29));
+}
+// a pair stored in the 8 bytes of one double (hi at the lower address) and back
+__device__ __forceinline__ fpair fp_from_bits(double d) {
+  return fpair(__int_as_float(__double2loint(d)), __int_as_float(__double2hiint(d)));
+}
+__device__ __forceinline__ double fp_to_bits(fpair a) {
+  return __hiloint2double(__float_as_int(a.l), __float_as_int(a.h));
+}
+
+
 template <>
 struct InnerSums<float> {
   float hi[3] = {0.f, 0.f, 0.f}, lo[3] = {0.f, 0.f, 0.f};
@@ -593,18 +652,26 @@ __global__ void k_moments_range(VGrid g, const T* __restrict__ f, int nnode, int
 // sweeps, whose source is FP32 anyway).  Non-physical moments set the error flag (the
 // stage loop then stops).  Nothing to do when the moment kernel has already rebuilt the
 // factors from these moments (ds->cf_fresh).
+// pairs (T = double, float-pair sweeps): each factor is stored as its float pair in the
+// 8 bytes of its double (fp_to_bits), split once here for the pair source pass.
 template <typename T>
 __global__ void k_factors(VGrid g, int nnode, const double* __restrict__ U0, const double* __restrict__ U1,
-                          DevState* ds, double coef, T* __restrict__ cf, int kind) {
+                          DevState* ds, double coef, T* __restrict__ cf, int kind, int pairs) {
   if (ds->status != BGK_OK || ds->done || ds->cf_fresh) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nnode) return;
   const int nm = g.dim + 2;
   const NodePrim P = node_prim((((ds->it & 1) == 0) ? U0 : U1) + (size_t)i * nm, g.dim, coef, kind);
   if (!P.ok) atomicOr(&ds->err, 1);
-  for (int a = 0; a < g.dim; ++a) node_factors<T>(g, kind, P, a, cf + (size_t)a * g.N * nnode + i, (size_t)nnode, 0, g.ncl);
+  for (int a = 0; a < g.dim; ++a) {
+    T* out = cf + (size_t)a * g.N * nnode + i;
+    node_factors<T>(g, kind, P, a, out, (size_t)nnode, 0, g.ncl);
+    if constexpr (sizeof(T) == 8) {
+      if (pairs)
+        for (int m = 0; m < g.N; ++m) out[(size_t)m * nnode] = fp_to_bits(fp_split(out[(size_t)m * nnode]));
+    }
+  }
 }
-
 // src[j][i] = prod_a cf[a][j_a][i] + qscale * q[j][i]  (nu M^l + q of Eq. bgk-ss-picard)
 // Launch: 2D grid, blockIdx.y (and its strides) over ordinates, x over nodes (k_source_grid),
 // so no thread divides a flat index.
@@ -1226,62 +1293,15 @@ struct NamedBarrier {
   }
 };
 
-// ---------------------------------------------------------------------------------
-// Float-pair arithmetic for the FP64-data sweeps of the mixed precision's FP64 phase (PAIR):
-// B300 runs FP64 at about 1/62 of its FP32 rate, so the FP64-data sweep forms its
-// right-hand side and its product with the cached inverse in pairs of floats hi + lo
-// (error-free transformations: TwoProduct by fma, TwoSum, Dekker's renormalisation),
-// about 2^-44..2^-47 relative per operation instead of FP64's 2^-53: eight orders below
-// the Picard tolerance, at FP32 instruction rates.  The data in memory stay FP64 (split
-// with integer operations on load, rebuilt exactly from the pair on store).
-struct fpair {
-  float h, l;
-  __host__ __device__ constexpr fpair() : h(0.f), l(0.f) {}
-  __host__ __device__ constexpr fpair(float hi, float lo) : h(hi), l(lo) {}
-  // compile-time constants of the element tables (folded by the compiler; runtime FP64
-  // values go through fp_split)
-  __host__ __device__ constexpr explicit fpair(double d) : h((float)d), l((float)(d - (double)(float)d)) {}
-};
-__device__ __forceinline__ fpair fp_split(double d) {
-  fpair r;
-  split_double(d, r.h, r.l);
-  return r;
-}
-__device__ __forceinline__ fpair operator*(fpair a, fpair b) {
-  const float p = a.h * b.h;
-  const float e = fmaf(a.h, b.l, fmaf(a.l, b.h, fmaf(a.h, b.h, -p)));
-  const float s = p + e;
-  return fpair(s, e - (s - p));
-}
-__device__ __forceinline__ fpair operator+(fpair a, fpair b) {
-  const float s = a.h + b.h;  // TwoSum(a.h, b.h), then the low parts, renormalised
-  const float v = s - a.h;
-  const float e = ((a.h - (s - v)) + (b.h - v)) + (a.l + b.l);
-  const float t = s + e;
-  return fpair(t, e - (t - s));
-}
-__device__ __forceinline__ fpair& operator+=(fpair& a, fpair b) {
-  a = a + b;
-  return a;
-}
-
-// The double of a float by integer operations (no FP64 conversion instruction): exact for
-// normal floats, zero for zeros and subnormals (at most 2^-126 absolute), infinities and
-// NaNs kept non-finite.
-__device__ __forceinline__ double float_to_double(float x) {
-  const unsigned u = __float_as_uint(x);
-  const unsigned e = (u >> 23) & 0xffu;
-  const unsigned s = u & 0x80000000u;
-  if (e == 0u) return __hiloint2double((int)s, 0);
-  const unsigned ed = e == 0xffu ? 0x7ffu : e + 896u;  // 1023 - 127
-  return __hiloint2double((int)(s | (ed << 20) | ((u & 0x7fffffu) >> 3)), (int)(u << 29));
-}
-// a pair stored in the 8 bytes of one double (hi at the lower address) and back
-__device__ __forceinline__ fpair fp_from_bits(double d) {
-  return fpair(__int_as_float(__double2loint(d)), __int_as_float(__double2hiint(d)));
-}
-__device__ __forceinline__ double fp_to_bits(fpair a) {
-  return __hiloint2double(__float_as_int(a.l), __float_as_int(a.h));
+// |v . N_i| / |K| of face i in FP64 for the pair sweeps, with explicit roundings so that
+// every pair kernel forms the same value
+template <class E>
+__device__ __forceinline__ double inflow_rate64(const double* __restrict__ Gc, int i, double v0, double v1,
+                                                double v2) {
+  double sf = __dmul_rn(v0, Gc[i * E::D]);
+  sf = __fma_rn(v1, Gc[i * E::D + 1], sf);
+  if constexpr (E::D == 3) sf = __fma_rn(v2, Gc[i * E::D + 2], sf);
+  return __dmul_rn(fabs(sf), Gc[E::NF * E::D]);
 }
 
 // x = Ainv b of one cell in pairs: Ainv as the float pairs of k_local_inverse<E, double,
@@ -1290,11 +1310,8 @@ __device__ __forceinline__ double fp_to_bits(fpair a) {
 // cross terms Ah bl + Al bh in the error term and Al bl (2^-48 of the product) left out:
 // about 2^-47 of the sum of |terms|.  x is returned as FP64 (hi + lo, one FP64 add).
 template <int ND, int S>
-__device__ __forceinline__ void inverse_product_pair(const float* __restrict__ Ap, const fpair (&b)[ND],
-                                                     double (&x)[ND]) {
-  float Ah[S], Al[S];
-  load_vec<float, S, 16>(Ap, Ah);
-  load_vec<float, S, (S % 4 == 0 ? 16 : 8)>(Ap + S, Al);
+__device__ __forceinline__ void inverse_product_pair_r(const float (&Ah)[S], const float (&Al)[S],
+                                                       const fpair (&b)[ND], double (&x)[ND]) {
 #pragma unroll
   for (int a = 0; a < ND; ++a) {
     const float* ah = Ah + a * ND;
@@ -1314,8 +1331,21 @@ __device__ __forceinline__ void inverse_product_pair(const float* __restrict__ A
     x[a] = float_to_double(hi) + float_to_double(lo);
   }
 }
+template <int S>
+__device__ __forceinline__ void load_inverse_pair(const float* __restrict__ Ap, float (&Ah)[S], float (&Al)[S]) {
+  load_vec<float, S, 16>(Ap, Ah);
+  load_vec<float, S, (S % 4 == 0 ? 16 : 8)>(Ap + S, Al);
+}
+template <int ND, int S>
+__device__ __forceinline__ void inverse_product_pair(const float* __restrict__ Ap, const fpair (&b)[ND],
+                                                     double (&x)[ND]) {
+  float Ah[S], Al[S];
+  load_inverse_pair<S>(Ap, Ah, Al);
+  inverse_product_pair_r<ND, S>(Ah, Al, b, x);
+}
 
-// PAIR source pass: b0[j][cell] = Mh (prod_a cf[a][j_a] + qscale q[j]) over the cell's
+// PAIR source pass (cf as float pairs from k_factors<double> with pairs set):
+// b0[j][cell] = Mh (prod_a cf[a][j_a] + qscale q[j]) over the cell's
 // nodes, in pairs, stored as pairs in the 8 bytes of each node's double (fp_to_bits), so
 // the PAIR sweep starts from the mass-weighted source (the FP64 sweep applies Mh itself).
 // Launch: 2D grid, blockIdx.y (and its strides) over ordinates, x over cells.
@@ -1345,8 +1375,8 @@ __global__ void k_source_pair(VGrid g, int ncell, const double* __restrict__ cf,
       fpair sv[ND], bv[ND];
 #pragma unroll
       for (int a = 0; a < ND; ++a) {
-        fpair m = fp_split(c1[o + a]) * fp_split(c2[o + a]);
-        if (c3) m = m * fp_split(c3[o + a]);
+        fpair m = fp_from_bits(c1[o + a]) * fp_from_bits(c2[o + a]);
+        if (c3) m = m * fp_from_bits(c3[o + a]);
         sv[a] = m + qs * fp_split(qj[o + a]);
       }
       E::mass(sv, bv);
@@ -1492,6 +1522,8 @@ __device__ __forceinline__ void sweep_ordinate(const SweepArgs& sa, const VGrid&
             T sf = v0 * cur.geo[i * E::D] + v1 * cur.geo[i * E::D + 1];
             if (E::D == 3) sf += v2 * cur.geo[i * E::D + 2];
             ci = fabs(sf) * cur.geo[NF * E::D];
+          } else if constexpr (PAIR) {
+            ci = inflow_rate64<E>(sa.geo + (size_t)c * sa.gs, i, v0, v1, v2);
           } else {
             const double* Gc = PF ? pfs.geo(slot) : sa.geo + (size_t)c * sa.gs;
             T sf = v0 * (T)Gc[i * E::D] + v1 * (T)Gc[i * E::D + 1];
@@ -1886,6 +1918,151 @@ __global__ void __launch_bounds__(128, 4) k_sweep_front(SweepArgs sa, VGrid g, f
         cur = nxt;
         scur = snxt;
         resolve_src(cur, sr.qscale);
+      }
+      k = kn;
+      gk = gn;
+      kn = kn2;
+      gn = gn2;
+      en = en2;
+      advance(kn, gn, kn2, gn2);
+    }
+    __syncthreads();
+  }
+}
+
+// The float-pair FP64-data sweep (PAIR, see sweep_ordinate) with the shared-memory front
+// of k_sweep_front: one CTA per ordinate, the generation offsets in shared memory, the
+// next item's schedule entry, neighbours, permutation and mass-weighted source (pairs in
+// FP64 words, k_source_pair) in registers, the next cached inverse prefetched into L2.
+// A non-lagged interior upwind trace comes from the front as the float pairs of the
+// upwind cell's FP64 values (split once by the writer, the same pairs the reader would
+// split from global memory, so the results equal k_sweep_pair's bit for bit).  Front slot
+// s holds FD pairs in FW float4: (h0 l0 h1 l1)(h2 l2 - -).  Dynamic shared memory: the
+// front (S * FW float4), then the generation offsets (lvcap ints).  2D elements.
+template <class E>
+__global__ void __launch_bounds__(128, 4) k_sweep_front_pair(SweepArgs sa, VGrid g, SrcArgs<double> sr,
+                                                            const double* __restrict__ fbc,
+                                                            const double* __restrict__ Ainv, double* f,
+                                                            const DevState* ds, int jofs,
+                                                            const uint64_t* __restrict__ fslots, int S, int lvcap) {
+  using T = double;
+  constexpr int ND = E::NDOF, NF = E::NF, FD = E::FD, FW = FD > 2 ? 2 : 1, AS = ainv_stride<E, T>();
+  static_assert(E::D == 2 && FD <= 4, "2D elements");
+  extern __shared__ __align__(16) float fsm[];
+  if (ds && (ds->status != BGK_OK || ds->done)) return;
+  const int j = jofs + (int)blockIdx.x, tid = (int)threadIdx.x, nt = (int)blockDim.x;
+  const int G = sa.ngen[j];
+  float4* front = reinterpret_cast<float4*>(fsm);
+  int* lv = reinterpret_cast<int*>(fsm + 4 * FW * S);
+  {
+    const int32_t* lvg = sa.lvl + (size_t)j * (sa.ncell + 1);
+    for (int i = tid; i <= G; i += nt) lv[i] = lvg[i];
+  }
+  double vd[3];
+  ordinate(g, j, vd);
+  const T v0 = vd[0], v1 = vd[1];
+  const uint32_t* gl = sa.glist + (size_t)j * sa.ncell;
+  const uint64_t* slj = fslots + (size_t)j * sa.ncell;
+  const T* Aj = Ainv + (size_t)j * sa.ncell * AS;
+  T* fj = f + (size_t)j * sa.nnode;
+  const SrcRows<T> rw = src_rows<T, false>(sr, g, j, sa.nnode);
+  const T* bj = fbc + (size_t)j * sa.nbface * FD;
+  __syncthreads();
+  auto seek = [&](int g2, int& kq, int& gq) {
+    for (; g2 < G; ++g2) {
+      const int k2 = lv[g2] + tid;
+      if (k2 < lv[g2 + 1]) {
+        kq = k2;
+        gq = g2;
+        return;
+      }
+    }
+    kq = -1;
+    gq = G;
+  };
+  auto advance = [&](int kq, int gq, int& kr, int& gr) {
+    if (kq < 0) {
+      kr = -1;
+      gr = G;
+    } else if (kq + nt < lv[gq + 1]) {
+      kr = kq + nt;
+      gr = gq;
+    } else {
+      seek(gq + 1, kr, gr);
+    }
+  };
+  SweepItem<E, T, false, false> cur, nxt;
+  uint64_t scur = 0, snxt = 0;
+  int k, gk, kn, gn, kn2, gn2;
+  seek(0, k, gk);
+  advance(k, gk, kn, gn);
+  advance(kn, gn, kn2, gn2);
+  if (k >= 0) {
+    fetch_item<E, T, false, false>(sa, gl, rw, k, cur);
+    scur = slj[k];
+  }
+  uint32_t en = kn >= 0 ? gl[kn] : 0u;
+  for (int gg = 0; gg < G; ++gg) {
+    while (k >= 0 && gk == gg) {
+      if (kn >= 0) {
+        prefetch_l2_bulk(Aj + (size_t)kn * AS, AS * (uint32_t)sizeof(T));
+        fetch_item_e<E, T, false, false>(sa, en, rw, nxt);
+        snxt = slj[kn];
+      }
+      const uint32_t en2 = kn2 >= 0 ? gl[kn2] : 0u;
+      const int c = (int)(cur.e & kCellMask);
+      const uint32_t code = cur.e >> kCellBits;
+      fpair bp[ND];
+#pragma unroll
+      for (int a = 0; a < ND; ++a) bp[a] = fp_from_bits(cur.src[a]);
+      const int nbs[4] = {cur.nb.x, cur.nb.y, cur.nb.z, cur.nb.w};
+      const double* Gc = sa.geo + (size_t)c * sa.gs;
+#pragma unroll
+      for (int i = 0; i < NF; ++i) {
+        if (((code >> (2 * i)) & 3u) != 2u) continue;
+        const T ci = inflow_rate64<E>(Gc, i, v0, v1, 0.0);
+        const unsigned su = (unsigned)(scur >> (12 * i)) & kFrontNone;
+        fpair yp[FD];
+        if (su != kFrontNone) {
+          // non-lagged interior inflow: the upwind cell's face trace from the front
+          const float4 t0 = front[(size_t)FW * su];
+          const bool rv = (scur >> (48 + i)) & 1u;
+          yp[0] = rv ? fpair(t0.z, t0.w) : fpair(t0.x, t0.y);
+          yp[1] = rv ? fpair(t0.x, t0.y) : fpair(t0.z, t0.w);
+          if constexpr (FD > 2) {
+            const float4 t1 = front[(size_t)FW * su + 1];
+            yp[2] = fpair(t1.x, t1.y);
+          }
+        } else if (nbs[i] < 0) {
+#pragma unroll
+          for (int kk = 0; kk < FD; ++kk) yp[kk] = fp_split(bj[(-nbs[i] - 1) * FD + kk]);
+        } else {
+          // lagged upwind cell: its global values are still f^l
+#pragma unroll
+          for (int kk = 0; kk < FD; ++kk)
+            yp[kk] = fp_split(fj[nbs[i] * ND + (int)((cur.pm >> (16 * i + 4 * kk)) & 15u)]);
+        }
+        E::inflow(i, fp_split(ci), yp, bp);
+      }
+      T x[ND];
+      inverse_product_pair<ND, AS>(reinterpret_cast<const float*>(Aj + (size_t)k * AS), bp, x);
+      store_vec<T, ND, cell_align<E, T>()>(fj + c * ND, x);
+      // this cell's traces on its outflow faces, in its own face order, for the readers
+#pragma unroll
+      for (int i = 0; i < NF; ++i) {
+        const unsigned so = (unsigned)(scur >> (12 * i)) & kFrontNone;
+        if (((code >> (2 * i)) & 3u) == 1u && so != kFrontNone) {
+          const fpair p0 = fp_split(x[E::fn(i, 0)]), p1 = fp_split(x[E::fn(i, 1)]);
+          front[(size_t)FW * so] = make_float4(p0.h, p0.l, p1.h, p1.l);
+          if constexpr (FD > 2) {
+            const fpair p2 = fp_split(x[E::fn(i, 2 % FD)]);
+            front[(size_t)FW * so + 1] = make_float4(p2.h, p2.l, 0.f, 0.f);
+          }
+        }
+      }
+      if (kn >= 0) {
+        cur = nxt;
+        scur = snxt;
       }
       k = kn;
       gk = gn;

@@ -54,6 +54,7 @@ struct bgk_handle {
   int32_t* nproc = nullptr;
   void* Ainv = nullptr;      // cached local inverses (schedule order), valid for nus_cached
   bool ainv_pairs = false;   // the FP64 cache holds float pairs (float-pair sweeps, k_sweep_pair)
+  bool front_pairs = false;  // the front (fslots) serves the float-pair sweep (k_sweep_front_pair)
   double nus_cached = -1.0;
   double nus_main = 0.0, qscale_main = 0.0;  // stage coefficient and 1/(dt A_ss) of the step
   size_t ainv_bytes = 0;
@@ -290,6 +291,15 @@ void launch_sweep_t(bgk_handle* h, double nus, int jb, int je) {
   }
   if constexpr (sizeof(T) == 8) {
     if (pairs) {
+      if constexpr (E::D == 2) {
+        if (h->fslots && h->front_pairs && h->sweep_threads <= 64 &&
+            front_smem_bytes(h, h->front_slots, h->sweep_threads) <= (size_t)kFrontSmemMax) {
+          k_sweep_front_pair<E><<<je - jb, h->sweep_threads, front_smem_bytes(h, h->front_slots, h->sweep_threads),
+                                  h->stream>>>(sweep_args(h), h->g, sr, (const T*)h->fbc, (const T*)h->Ainv,
+                                               (T*)h->f, h->ds, jb, h->fslots, h->front_slots, front_lvcap(h));
+          return;
+        }
+      }
       k_sweep_pair<E><<<je - jb, h->sweep_threads, 0, h->stream>>>(
           sweep_args(h), h->g, (T)nus, sr, (const T*)h->fbc, (const T*)h->Ainv, (T*)h->f, h->ds, jb);
       return;
@@ -420,7 +430,8 @@ int build_src_t(bgk_handle* h, const void* qsrc, double qscale, double nus) {
                                                 (T*)h->fbc);
   }
   k_factors<T><<<(h->nnode + 127) / 128, 128, 0, h->stream>>>(h->g, h->nnode, h->U[0], h->U[1], h->ds, h->phys.nu,
-                                                              (T*)h->cf, h->phys.collision);
+                                                              (T*)h->cf, h->phys.collision,
+                                                              (sizeof(T) == 8 && pair_sweep(h, nus)) ? 1 : 0);
   if (h->fuse_src) {
     h->fused_q = qsrc;
     h->fused_qscale = qscale;
@@ -798,11 +809,15 @@ int build_dags(bgk_handle* h) {
 // 2D meshes only (3D fronts are surfaces, too wide to fit).
 size_t front_smem_bytes(const bgk_handle* h, int S, int threads) {
   (void)threads;
-  return sizeof(float) * (4 * (size_t)S + front_lvcap(h));
+  // a slot: FD floats in a float4 (FP32 front), FD float pairs in one or two (pair front)
+  const size_t slot = h->front_pairs ? (h->hm.fd > 2 ? 8 : 4) : 4;
+  return sizeof(float) * (slot * (size_t)S + front_lvcap(h));
 }
 
 int build_front(bgk_handle* h) {
-  if (!h->fuse_src || h->hm.dim != 2 || h->cfg.sweep_front == 2) return BGK_OK;
+  const bool pairs = h->ainv_pairs && h->Ainv;
+  if (!(h->fuse_src || pairs) || h->hm.dim != 2 || h->cfg.sweep_front == 2) return BGK_OK;
+  h->front_pairs = pairs;
   const int n = h->hm.ncell, nv = h->g.nv;
   const size_t cells = (size_t)nv * n;
   int32_t *genc = nullptr, *head = nullptr;
@@ -1061,6 +1076,10 @@ int bgk_create(const bgk_mesh* mesh, const bgk_vgrid* vg, const bgk_physics* phy
   CK(cudaFuncSetAttribute(k_sweep_front<ElemP1Tri>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFrontSmemMax));
   CK(cudaFuncSetAttribute(k_sweep_front<ElemP2Tri>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFrontSmemMax));
   CK(cudaFuncSetAttribute(k_sweep_front<ElemQ1Quad>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFrontSmemMax));
+  CK(cudaFuncSetAttribute(k_sweep_front_pair<ElemP1Tri>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFrontSmemMax));
+  CK(cudaFuncSetAttribute(k_sweep_front_pair<ElemP2Tri>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFrontSmemMax));
+  CK(cudaFuncSetAttribute(k_sweep_front_pair<ElemQ1Quad>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          kFrontSmemMax));
   rc = build_dags(h);
   if (rc == BGK_OK) {
     // the stage coefficient nu_s = nu + 1/(dt A_ss) of the step's main stages

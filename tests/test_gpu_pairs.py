@@ -126,3 +126,21 @@ def test_pair_range_sweeps_reproduce_the_full_sweep(name):
     for a, b in shard.ordinate_shards(w.n_v, s2.dim, 3):
         s2.sweep_range(a, b, U.data_ptr())
     np.testing.assert_array_equal(s2.get_f(), f_full)
+
+
+@pytest.mark.parametrize("name", ["p1_tri", "p2_tri", "q1"])
+def test_pair_front_equals_global_reads(name):
+    """The float-pair sweep with the shared-memory front (k_sweep_front_pair) gives the
+    global-memory pair sweep's results bit for bit: the front holds the pairs the reader
+    would split from the upwind cell's FP64 values."""
+    w = _cases()[name]
+    out = []
+    for front in (True, False):
+        s = bgk.Solver.from_workload(w, hp_sweep="pairs", cache_inverse="on", sweep_front=front)
+        assert (s.front_slots > 0) == front
+        s.set_state_maxwellian(w.init)
+        s.set_inflow_maxwellian(w.inflow)
+        s.sweep(0.0, 0.0)
+        s.sweep(0.0, 0.0)
+        out.append(s.get_f())
+    np.testing.assert_array_equal(out[0], out[1])
