@@ -279,7 +279,7 @@ int capture_batch_step(bgk_batch* b) {
             sh->stream = keep;
             const double tol = h->cfg.tau / std::max(1.0, h->phys.nu * h->dt);
             k_finalize<<<1, 256, 0, h->stream>>>(sh->ds, sh->partial, sh->mom_blocks, std::max(tol, h->fp32_floor),
-                                                 sh->cfg.l_max, 0, 0, 0, 1);
+                                                 sh->cfg.l_max, 0, 0, 0, 1, tol);
             return BGK_OK;
           });
         return r;

@@ -712,8 +712,14 @@ inline dim3 k_source_grid(int nnode, int nv) {
 // condition of the stage loop.
 // stall_stop (FP32 phase of the mixed mode): also stop once the measure is below 1e-5
 // and has decreased by less than 10% over the last iteration (FP32 rounding floor).
+// stall_stop (the FP32 phase of the mixed precision): also stop once the measure is below
+// 1e-5 and fell by less than 10% (stagnation), or once two more iterations at the observed
+// contraction rate rho = meas / prev would bring it below half the next phase's tolerance
+// tol_next (rho^2 meas < tol_next / 2): the FP64 phase then needs its two iterations
+// whatever further FP32 iterations do.
 __global__ void k_finalize(DevState* ds, const double* __restrict__ partial, int nblk, double tol, int lmax, int stage,
-                           cudaGraphConditionalHandle cond, int use_cond, int stall_stop = 0) {
+                           cudaGraphConditionalHandle cond, int use_cond, int stall_stop = 0,
+                           double tol_next = 0.0) {
   __shared__ double red[6][256];
   double s[6] = {0, 0, 0, 0, 0, 0};
   const bool skip = ds->status != BGK_OK || ds->done;
@@ -741,9 +747,11 @@ __global__ void k_finalize(DevState* ds, const double* __restrict__ partial, int
     ds->iters[stage] = ds->stage_it;
     ds->meas[stage] = meas;
     const bool stalled = stall_stop && ds->stage_it > 2 && meas < 1e-5 && meas > 0.9 * prev;
+    const double rho = prev > 0.0 ? meas / prev : 1.0;
+    const bool enough = stall_stop && ds->stage_it > 1 && rho < 1.0 && rho * rho * meas < 0.5 * tol_next;
     if (ds->err) {
       ds->status = BGK_E_NONPHYSICAL;
-    } else if (!(meas < tol) && !stalled) {
+    } else if (!(meas < tol) && !stalled && !enough) {
       if (ds->stage_it >= lmax)
         ds->status = BGK_E_NOCONV;
       else

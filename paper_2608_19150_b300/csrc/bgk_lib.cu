@@ -509,7 +509,7 @@ int shadow_phase(bgk_handle* h, int st, const void* qsrc, double qscale, double 
     rc = build_src_shadow(sh, (const float*)sh->fk, qscale);
     launch_sweep_any(sh, nus);
     moments(sh, 1);
-    k_finalize<<<1, 256, 0, bs>>>(sh->ds, sh->partial, sh->mom_blocks, tol32, sh->cfg.l_max, st, cond, 1, 1);
+    k_finalize<<<1, 256, 0, bs>>>(sh->ds, sh->partial, sh->mom_blocks, tol32, sh->cfg.l_max, st, cond, 1, 1, tol);
     sh->stream = keep;
     cudaGraph_t body_out;
     cudaError_t e2 = cudaStreamEndCapture(bs, &body_out);
@@ -525,7 +525,7 @@ int shadow_phase(bgk_handle* h, int st, const void* qsrc, double qscale, double 
       }
       launch_sweep_any(sh, nus);
       moments(sh, 1);
-      k_finalize<<<1, 256, 0, s>>>(sh->ds, sh->partial, sh->mom_blocks, tol32, sh->cfg.l_max, st, 0, 0, 1);
+      k_finalize<<<1, 256, 0, s>>>(sh->ds, sh->partial, sh->mom_blocks, tol32, sh->cfg.l_max, st, 0, 0, 1, tol);
       DevState d;
       CK(cudaMemcpyAsync(&d, sh->ds, sizeof(DevState), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
