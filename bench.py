@@ -459,6 +459,7 @@ def timed_steps(s, steps, world, local, tstream, guess=False, main_fp32=False, w
 PROFILED_TRAFFIC = {
     "fp64": (3.750e9, "profiles/sweep_fp64_cached_shock_tube_64_p2_v32.md"),
     "fp64_pairs": (3.751e9, "profiles/sweep_pair_fp64_shock_tube_64_p2_v32.md"),
+    "fp64_pairs_front": (3.410e9, "profiles/sweep_front_pair_fp64_shock_tube_64_p2_v32.md"),
     "fp32": (0.631e9, "profiles/sweep_fp32_fused_shock_tube_64_p2_v32.md"),
     "fp32_front": (0.535e9, "profiles/sweep_front_fp32_shock_tube_64_p2_v32.md"),
 }
@@ -498,7 +499,9 @@ def sweep_roofline(w, precision, reps, peaks, n_side=None, n_v=None, sweep_mode=
         r = {"bound": "hbm", "achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_gbs / hbm_peak,
              "traffic": None,
              "kernel": ("k_sweep_ts<%s,double,cached,pairs>" % ename) if kname == "k_sweep_ts" else
-                       "k_sweep_pair<%s>" % ename,
+                       ("k_sweep_front_pair<%s>" % ename) if (s.front_slots > 0 and s.sweep_threads <= 64)
+                       else "k_sweep_pair<%s>" % ename,
+             "front_slots": s.front_slots,
              "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
              "fp64_equivalent_tflops": tf, "fp64_peak_tflops": fp64_peak, "fp64_equivalent_frac": tf / fp64_peak,
              "flops_per_local_solve": fl}
@@ -516,8 +519,11 @@ def sweep_roofline(w, precision, reps, peaks, n_side=None, n_v=None, sweep_mode=
              "kernel": ("k_sweep_front<%s>" % ename) if front else
                        "%s<%s,float,%s>" % (kname, ename, "cached" if cached else "uncached,fused source"),
              "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)", "front_slots": s.front_slots}
-    profiled = PROFILED_TRAFFIC.get("fp32_front" if front else "fp64_pairs" if (pairs and precision == "fp64")
-                                    else precision)
+    if pairs and precision == "fp64":
+        profiled = PROFILED_TRAFFIC.get("fp64_pairs_front" if (s.front_slots > 0 and s.sweep_threads <= 64 and
+                                                               kname == "k_sweep") else "fp64_pairs")
+    else:
+        profiled = PROFILED_TRAFFIC.get("fp32_front" if front else precision)
     if profiled and kind == "p2tri" and kname == "k_sweep" and n_side and n_v == 32 and (precision == "fp32" or cached):
         r["traffic"] = profiled[0] * (n_side / 64.0) ** 2
         r["traffic_source"] = profiled[1] + " (scaled from 64x64 by the cell count)"
