@@ -479,12 +479,22 @@ struct MomentParts {
 // work of every (node, dimension, half of the velocity cells) spread over the block's
 // threads) and marks them current (ds->cf_fresh), so the next iteration needs no factor
 // pass; non-physical moments raise ds->err.  Mode 0 marks the factors stale.
+//
+// conv (FP32 data): each value read is also written there as its double, at the same index
+// (the FP32 phase's result handed to the FP64 state in the same pass that takes its FP64
+// moments).  gate: the kernel runs only when gate's loop succeeded (gate_when 1) or only
+// when it failed (gate_when 2; failed = non-physical, as k_convert_gated skips).
 template <typename T>
 __global__ void __launch_bounds__(128) k_moments(VGrid g, const T* __restrict__ f, int nnode, double* U0,
                                                  double* U1, DevState* ds, int mode,
                                                  double* __restrict__ partial, T* __restrict__ cf, double coef,
-                                                 int kind) {
+                                                 int kind, double* __restrict__ conv = nullptr,
+                                                 const DevState* __restrict__ gate = nullptr, int gate_when = 0) {
   if (ds->status != BGK_OK || ds->done) return;
+  if (gate) {
+    const bool failed = gate->err || gate->status == BGK_E_NONPHYSICAL;
+    if ((gate_when == 1 && failed) || (gate_when == 2 && !failed)) return;
+  }
   if (mode == 0 && blockIdx.x == 0 && threadIdx.x == 0) ds->cf_fresh = 0;
   constexpr int PARTS = MomentParts<T>::value, NPB = 128 / PARTS;
   const int nl = threadIdx.x % NPB, part = threadIdx.x / NPB;
@@ -497,8 +507,18 @@ __global__ void __launch_bounds__(128) k_moments(VGrid g, const T* __restrict__ 
       for (int j0 = ja; j0 < jb; ++j0) {
         InnerSums<T> S;
         const T* fr = f + (size_t)j0 * g.N * nnode + i;
+        if (conv) {
+          double* cr = conv + (size_t)j0 * g.N * nnode + i;
 #pragma unroll 8
-        for (int j1 = 0; j1 < g.N; ++j1) S.add(g, j1, fr[(size_t)j1 * nnode]);
+          for (int j1 = 0; j1 < g.N; ++j1) {
+            const T v = fr[(size_t)j1 * nnode];
+            cr[(size_t)j1 * nnode] = (double)v;
+            S.add(g, j1, v);
+          }
+        } else {
+#pragma unroll 8
+          for (int j1 = 0; j1 < g.N; ++j1) S.add(g, j1, fr[(size_t)j1 * nnode]);
+        }
         const double s0 = S.get(0), s1 = S.get(1), s2 = S.get(2);
         const double w0 = g.w[j0], x0 = g.x[j0];
         acc[0] += w0 * s0;
@@ -512,8 +532,18 @@ __global__ void __launch_bounds__(128) k_moments(VGrid g, const T* __restrict__ 
         for (int j1 = 0; j1 < g.N; ++j1) {
           InnerSums<T> S;
           const T* fr = f + ((size_t)j0 * g.N + j1) * g.N * nnode + i;
+          if (conv) {
+            double* cr = conv + ((size_t)j0 * g.N + j1) * g.N * nnode + i;
 #pragma unroll 8
-          for (int j2 = 0; j2 < g.N; ++j2) S.add(g, j2, fr[(size_t)j2 * nnode]);
+            for (int j2 = 0; j2 < g.N; ++j2) {
+              const T v = fr[(size_t)j2 * nnode];
+              cr[(size_t)j2 * nnode] = (double)v;
+              S.add(g, j2, v);
+            }
+          } else {
+#pragma unroll 8
+            for (int j2 = 0; j2 < g.N; ++j2) S.add(g, j2, fr[(size_t)j2 * nnode]);
+          }
           const double s0 = S.get(0), s1 = S.get(1), s2 = S.get(2);
           const double w1 = g.w[j1], x1 = g.x[j1];
           t0 += w1 * s0;

@@ -534,8 +534,15 @@ int shadow_phase(bgk_handle* h, int st, const void* qsrc, double qscale, double 
     sh->stream = keep;
   }
   k_record_fp32<<<1, 1, 0, s>>>(sh->ds, h->ds, st);
-  k_convert_gated<float, double><<<blk, thr, 0, s>>>(h->nfv, (const float*)sh->f, (double*)h->f, sh->ds);
-  moments(h, 0);
+  // the FP32 result becomes the FP64 state and its FP64 moments are taken in one pass over
+  // the FP32 data (the moments of the exact doubles of the FP32 values); when the FP32
+  // phase failed, the FP64 state keeps its values and its moments come from them
+  k_moments<float><<<sh->mom_blocks, 128, 0, s>>>(h->g, (const float*)sh->f, h->nnode, h->U[0], h->U[1], h->ds, 0,
+                                                  h->partial, nullptr, h->phys.nu, h->phys.collision,
+                                                  (double*)h->f, sh->ds, 1);
+  k_moments<double><<<h->mom_blocks, 128, 0, s>>>(h->g, (const double*)h->f, h->nnode, h->U[0], h->U[1], h->ds, 0,
+                                                  h->partial, nullptr, h->phys.nu, h->phys.collision, nullptr,
+                                                  sh->ds, 2);
   return cudaGetLastError() == cudaSuccess ? BGK_OK : BGK_E_CUDA;
 }
 
