@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "bgk_internal.h"
 #include "bgk_tables.h"
 
@@ -480,16 +482,18 @@ struct MomentParts {
 // threads) and marks them current (ds->cf_fresh), so the next iteration needs no factor
 // pass; non-physical moments raise ds->err.  Mode 0 marks the factors stale.
 //
-// conv (FP32 data): each value read is also written there as its double, at the same index
-// (the FP32 phase's result handed to the FP64 state in the same pass that takes its FP64
-// moments).  gate: the kernel runs only when gate's loop succeeded (gate_when 1) or only
-// when it failed (gate_when 2; failed = non-physical, as k_convert_gated skips).
+// conv: each value read is also written there in the other storage type (FP32 data: its
+// double; FP64 data: the float nearest to it), at the same index -- the states handed
+// between the FP32 and the FP64 phases of the mixed precision in the same pass that takes
+// the moments.  gate: the kernel runs only when gate's loop succeeded (gate_when 1) or
+// only when it failed (gate_when 2; failed = non-physical, as k_convert_gated skips).
 template <typename T>
 __global__ void __launch_bounds__(128) k_moments(VGrid g, const T* __restrict__ f, int nnode, double* U0,
                                                  double* U1, DevState* ds, int mode,
                                                  double* __restrict__ partial, T* __restrict__ cf, double coef,
-                                                 int kind, double* __restrict__ conv = nullptr,
+                                                 int kind, void* __restrict__ conv = nullptr,
                                                  const DevState* __restrict__ gate = nullptr, int gate_when = 0) {
+  using TC = typename std::conditional<sizeof(T) == 4, double, float>::type;
   if (ds->status != BGK_OK || ds->done) return;
   if (gate) {
     const bool failed = gate->err || gate->status == BGK_E_NONPHYSICAL;
@@ -508,11 +512,11 @@ __global__ void __launch_bounds__(128) k_moments(VGrid g, const T* __restrict__ 
         InnerSums<T> S;
         const T* fr = f + (size_t)j0 * g.N * nnode + i;
         if (conv) {
-          double* cr = conv + (size_t)j0 * g.N * nnode + i;
+          TC* cr = static_cast<TC*>(conv) + (size_t)j0 * g.N * nnode + i;
 #pragma unroll 8
           for (int j1 = 0; j1 < g.N; ++j1) {
             const T v = fr[(size_t)j1 * nnode];
-            cr[(size_t)j1 * nnode] = (double)v;
+            cr[(size_t)j1 * nnode] = (TC)v;
             S.add(g, j1, v);
           }
         } else {
@@ -533,11 +537,11 @@ __global__ void __launch_bounds__(128) k_moments(VGrid g, const T* __restrict__ 
           InnerSums<T> S;
           const T* fr = f + ((size_t)j0 * g.N + j1) * g.N * nnode + i;
           if (conv) {
-            double* cr = conv + ((size_t)j0 * g.N + j1) * g.N * nnode + i;
+            TC* cr = static_cast<TC*>(conv) + ((size_t)j0 * g.N + j1) * g.N * nnode + i;
 #pragma unroll 8
             for (int j2 = 0; j2 < g.N; ++j2) {
               const T v = fr[(size_t)j2 * nnode];
-              cr[(size_t)j2 * nnode] = (double)v;
+              cr[(size_t)j2 * nnode] = (TC)v;
               S.add(g, j2, v);
             }
           } else {

@@ -486,14 +486,22 @@ int add_while(cudaStream_t s, cudaGraphConditionalHandle* cond, cudaGraph_t* bod
 // Mixed precision, at a stage start (main moments already in U): FP32 sweeps on the
 // shadow until the FP32 floor (or the main tolerance), then the FP64 state takes the
 // FP32 result (unless that phase failed) and its moments are recomputed.
-int shadow_phase(bgk_handle* h, int st, const void* qsrc, double qscale, double nus, double tol, bool capture) {
+// f_ready: the stage's moment pass already wrote the FP32 copy of f into the shadow.
+int shadow_phase(bgk_handle* h, int st, const void* qsrc, double qscale, double nus, double tol, bool capture,
+                 bool f_ready) {
   bgk_handle* sh = h->shadow;
   cudaStream_t s = h->stream;
   const int thr = 256, blk = 148 * 8;
   k_reset_state<<<1, 1, 0, s>>>(sh->ds);
   k_stage_begin<<<1, 1, 0, s>>>(sh->ds, st);
-  k_convert_gated<double, float><<<blk, thr, 0, s>>>(h->nfv, (const double*)h->f, (float*)sh->f, nullptr);
-  k_convert_gated<double, float><<<blk, thr, 0, s>>>(h->nfv, (const double*)qsrc, (float*)sh->fk, nullptr);
+  if (!f_ready)
+    k_convert_gated<double, float><<<blk, thr, 0, s>>>(h->nfv, (const double*)h->f, (float*)sh->f, nullptr);
+  if (f_ready && qsrc == h->fk && st == 0) {
+    // the first stage's q is f^k, equal to this stage's f: its FP32 copy too
+    CK(cudaMemcpyAsync(sh->fk, sh->f, h->nfv * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  } else {
+    k_convert_gated<double, float><<<blk, thr, 0, s>>>(h->nfv, (const double*)qsrc, (float*)sh->fk, nullptr);
+  }
   k_copy_moments<<<148, 256, 0, s>>>((size_t)h->nnode * h->nm, h->U[0], h->U[1], h->ds, sh->U[0], sh->U[1], sh->ds);
   const double tol32 = std::max(tol, h->fp32_floor);
   cudaStream_t keep = sh->stream;
@@ -596,13 +604,21 @@ int enqueue_step(bgk_handle* h, int mode_bdf2, cudaGraphExec_t* exec_out) {
       qscale = 1.0;
     }
     k_stage_begin<<<1, 1, 0, s>>>(h->ds, st);
-    moments(h, 0);
+    // with an FP32 phase to follow (and no guess to change f first), the moment pass also
+    // writes the FP32 copy of f that the phase starts from
+    const bool f_ready = h->shadow && !h->guess;
+    if (f_ready)
+      k_moments<double><<<h->mom_blocks, 128, 0, s>>>(h->g, (const double*)h->f, h->nnode, h->U[0], h->U[1], h->ds, 0,
+                                                      h->partial, nullptr, h->phys.nu, h->phys.collision,
+                                                      h->shadow->f, nullptr, 0);
+    else
+      moments(h, 0);
     if (h->guess) {
       int rg = guess_hook(h);
       if (rg != BGK_OK) return rg;
     }
     if (h->shadow) {
-      int rs = shadow_phase(h, st, qsrc, qscale, nus, tol, capture);
+      int rs = shadow_phase(h, st, qsrc, qscale, nus, tol, capture, f_ready);
       if (rs != BGK_OK) return rs;
     }
     if (capture) {
