@@ -2117,11 +2117,13 @@ __global__ void __launch_bounds__(128, 4) k_sweep_front_pair(SweepArgs sa, VGrid
   }
 }
 
-// out = a_k * fk + a_f * f + sum_r cF[r] * F[r]   (stage bookkeeping of Sec. 3.5)
+// out = a_k * fk + a_f * f + sum_r cF[r] * F[r]   (stage bookkeeping of Sec. 3.5); out32
+// (if given) also receives the float of each value written (the FP32 phase's copy of q)
 template <typename T>
 __global__ void k_combine(size_t n, T* __restrict__ out, double a_k, const T* __restrict__ fk, double a_f,
                           const T* __restrict__ f, int nF, double c0, const T* __restrict__ F0, double c1,
-                          const T* __restrict__ F1, double c2, const T* __restrict__ F2, const DevState* ds) {
+                          const T* __restrict__ F1, double c2, const T* __restrict__ F2, const DevState* ds,
+                          float* __restrict__ out32 = nullptr) {
   if (ds && ds->status != BGK_OK) return;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     double s = 0.0;
@@ -2131,6 +2133,7 @@ __global__ void k_combine(size_t n, T* __restrict__ out, double a_k, const T* __
     if (nF > 1) s += c1 * (double)F1[i];
     if (nF > 2) s += c2 * (double)F2[i];
     out[i] = (T)s;
+    if (out32) out32[i] = (float)(T)s;
   }
 }
 

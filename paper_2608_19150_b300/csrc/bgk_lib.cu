@@ -387,20 +387,22 @@ void launch_sweep_any(bgk_handle* h, double nus, int jb = 0, int je = -1) {
 
 template <typename T>
 void launch_combine(bgk_handle* h, void* out, double ak, const void* fk, double af, const void* f, int nF,
-                    const double* cF, void* const* F) {
+                    const double* cF, void* const* F, float* out32) {
   int threads = 256, blocks = 148 * 8;
   k_combine<T><<<blocks, threads, 0, h->stream>>>(h->nfv, (T*)out, ak, (const T*)fk, af, (const T*)f, nF,
                                                  nF > 0 ? cF[0] : 0.0, nF > 0 ? (const T*)F[0] : nullptr,
                                                  nF > 1 ? cF[1] : 0.0, nF > 1 ? (const T*)F[1] : nullptr,
-                                                 nF > 2 ? cF[2] : 0.0, nF > 2 ? (const T*)F[2] : nullptr, h->ds);
+                                                 nF > 2 ? cF[2] : 0.0, nF > 2 ? (const T*)F[2] : nullptr, h->ds,
+                                                 out32);
 }
 
+// out32: also write the float of every value (FP64 handles only)
 void combine(bgk_handle* h, void* out, double ak, const void* fk, double af, const void* f, int nF, const double* cF,
-             void* const* F) {
+             void* const* F, float* out32 = nullptr) {
   if (h->precision == BGK_FP64)
-    launch_combine<double>(h, out, ak, fk, af, f, nF, cF, F);
+    launch_combine<double>(h, out, ak, fk, af, f, nF, cF, F, out32);
   else
-    launch_combine<float>(h, out, ak, fk, af, f, nF, cF, F);
+    launch_combine<float>(h, out, ak, fk, af, f, nF, cF, F, nullptr);
 }
 
 void moments(bgk_handle* h, int mode) {
@@ -486,9 +488,10 @@ int add_while(cudaStream_t s, cudaGraphConditionalHandle* cond, cudaGraph_t* bod
 // Mixed precision, at a stage start (main moments already in U): FP32 sweeps on the
 // shadow until the FP32 floor (or the main tolerance), then the FP64 state takes the
 // FP32 result (unless that phase failed) and its moments are recomputed.
-// f_ready: the stage's moment pass already wrote the FP32 copy of f into the shadow.
+// f_ready: the stage's moment pass already wrote the FP32 copy of f into the shadow;
+// q_ready: the stage source's producer already wrote its FP32 copy (sh->fk).
 int shadow_phase(bgk_handle* h, int st, const void* qsrc, double qscale, double nus, double tol, bool capture,
-                 bool f_ready) {
+                 bool f_ready, bool q_ready) {
   bgk_handle* sh = h->shadow;
   cudaStream_t s = h->stream;
   const int thr = 256, blk = 148 * 8;
@@ -496,7 +499,8 @@ int shadow_phase(bgk_handle* h, int st, const void* qsrc, double qscale, double 
   k_stage_begin<<<1, 1, 0, s>>>(sh->ds, st);
   if (!f_ready)
     k_convert_gated<double, float><<<blk, thr, 0, s>>>(h->nfv, (const double*)h->f, (float*)sh->f, nullptr);
-  if (f_ready && qsrc == h->fk && st == 0) {
+  if (q_ready) {
+  } else if (f_ready && qsrc == h->fk && st == 0) {
     // the first stage's q is f^k, equal to this stage's f: its FP32 copy too
     CK(cudaMemcpyAsync(sh->fk, sh->f, h->nfv * sizeof(float), cudaMemcpyDeviceToDevice, s));
   } else {
@@ -578,7 +582,7 @@ int enqueue_step(bgk_handle* h, int mode_bdf2, cudaGraphExec_t* exec_out) {
     // q = (4 f^n - f^{n-1}) / (2 dt); history: fprev <- f^n after the step
     double cF[1] = {-1.0 / (2.0 * dt)};
     void* Fp[1] = {h->fprev};
-    combine(h, h->q, 0.0, nullptr, 4.0 / (2.0 * dt), h->f, 1, cF, Fp);
+    combine(h, h->q, 0.0, nullptr, 4.0 / (2.0 * dt), h->f, 1, cF, Fp, h->shadow ? (float*)h->shadow->fk : nullptr);
     CK(cudaMemcpyAsync(h->fprev, h->f, bytes, cudaMemcpyDeviceToDevice, s));
     S = 1;
   } else {
@@ -599,7 +603,8 @@ int enqueue_step(bgk_handle* h, int mode_bdf2, cudaGraphExec_t* exec_out) {
       // q = (f^k + dt sum_{r<s} A_sr F_r) / (dt A_ss)   (Eq. q-stages)
       double cF[3];
       for (int r = 0; r < st; ++r) cF[r] = dt * A[st][r] / (dt * ass);
-      combine(h, h->q, 1.0 / (dt * ass), h->fk, 0.0, nullptr, st, cF, h->F);
+      combine(h, h->q, 1.0 / (dt * ass), h->fk, 0.0, nullptr, st, cF, h->F,
+              h->shadow ? (float*)h->shadow->fk : nullptr);
       qsrc = h->q;
       qscale = 1.0;
     }
@@ -618,7 +623,7 @@ int enqueue_step(bgk_handle* h, int mode_bdf2, cudaGraphExec_t* exec_out) {
       if (rg != BGK_OK) return rg;
     }
     if (h->shadow) {
-      int rs = shadow_phase(h, st, qsrc, qscale, nus, tol, capture, f_ready);
+      int rs = shadow_phase(h, st, qsrc, qscale, nus, tol, capture, f_ready, qsrc == h->q);
       if (rs != BGK_OK) return rs;
     }
     if (capture) {
