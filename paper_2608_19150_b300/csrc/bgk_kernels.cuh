@@ -398,6 +398,8 @@ __device__ __forceinline__ fpair& operator+=(fpair& a, fpair b) {
   a = a + b;
   return a;
 }
+// scaling by a signed power of two k (the integer face-mass entries of inflow_int): exact
+__device__ __forceinline__ fpair operator*(fpair a, float k) { return fpair(a.h * k, a.l * k); }
 
 // The double of a float by integer operations (no FP64 conversion instruction): exact for
 // normal floats, zero for zeros and subnormals (at most 2^-126 absolute), infinities and
@@ -1579,7 +1581,7 @@ __device__ __forceinline__ void sweep_ordinate(const SweepArgs& sa, const VGrid&
           fpair yp[FD];
 #pragma unroll
           for (int kk = 0; kk < FD; ++kk) yp[kk] = fp_split(y[i][kk]);
-          E::inflow(i, fp_split(ci), yp, bp);
+          E::inflow_int(i, fp_split(ci) * fpair(1.0 / E::inflow_den), yp, bp);
         } else {
           E::inflow(i, ci, y[i], b);
         }
@@ -2084,7 +2086,7 @@ __global__ void __launch_bounds__(128, 4) k_sweep_front_pair(SweepArgs sa, VGrid
           for (int kk = 0; kk < FD; ++kk)
             yp[kk] = fp_split(fj[nbs[i] * ND + (int)((cur.pm >> (16 * i + 4 * kk)) & 15u)]);
         }
-        E::inflow(i, fp_split(ci), yp, bp);
+        E::inflow_int(i, fp_split(ci) * fpair(1.0 / E::inflow_den), yp, bp);
       }
       T x[ND];
       inverse_product_pair<ND, AS>(reinterpret_cast<const float*>(Aj + (size_t)k * AS), bp, x);

@@ -211,9 +211,46 @@ def emit(name, kind):
     o.append("      default: break;")
     o.append("    }")
     o.append("  }")
+    # the same with the face mass written as (1/den) x integers that are all signed powers
+    # of two: b += (c/den) * sum_k n_k y_k, the products by n_k exact scalings (float pairs)
+    den = 1
+    for i in range(nf):
+        for a in range(nd):
+            for k in range(fd):
+                x = Eh[i][a][fn[i][k]]
+                den = den * x.denominator // _gcd(den, x.denominator)
+    ints = all(_pow2(abs(Eh[i][a][fn[i][k]] * den)) for i in range(nf) for a in range(nd) for k in range(fd)
+               if Eh[i][a][fn[i][k]] != 0)
+    if ints:
+        o.append("  static constexpr double inflow_den = %d.0;" % den)
+        o.append("  template <typename T> __device__ static __forceinline__ void inflow_int("
+                 "int i, T c_den, const T (&y)[%d], T (&b)[%d]) {" % (fd, nd))
+        o.append("    switch (i) {")
+        for i in range(nf):
+            o.append("      case %d:" % i)
+            for a in range(nd):
+                terms = ["y[%d] * %.1ff" % (k, float(Eh[i][a][fn[i][k]] * den)) for k in range(fd)
+                         if Eh[i][a][fn[i][k]] != 0]
+                if terms:
+                    o.append("        b[%d] += c_den * (%s);" % (a, " + ".join(terms)))
+            o.append("        break;")
+        o.append("      default: break;")
+        o.append("    }")
+        o.append("  }")
     o.append("#endif")
     o.append("};")
     return "\n".join(o)
+
+
+def _gcd(a, b):
+    while b:
+        a, b = b, a % b
+    return a
+
+
+def _pow2(x):
+    """x a positive integer power of two (Fraction or int)."""
+    return x > 0 and x.denominator == 1 and (int(x) & (int(x) - 1)) == 0
 
 
 if __name__ == "__main__":
