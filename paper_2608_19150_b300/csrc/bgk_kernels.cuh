@@ -489,12 +489,15 @@ struct MomentParts {
 // between the FP32 and the FP64 phases of the mixed precision in the same pass that takes
 // the moments.  gate: the kernel runs only when gate's loop succeeded (gate_when 1) or
 // only when it failed (gate_when 2; failed = non-physical, as k_convert_gated skips).
+// fupd, addin (2D; f then unused): the pass first updates fupd += addin in place (the change
+// of a Picard iterate, FP32) and sums the updated values.
 template <typename T>
 __global__ void __launch_bounds__(128) k_moments(VGrid g, const T* __restrict__ f, int nnode, double* U0,
                                                  double* U1, DevState* ds, int mode,
                                                  double* __restrict__ partial, T* __restrict__ cf, double coef,
                                                  int kind, void* __restrict__ conv = nullptr,
-                                                 const DevState* __restrict__ gate = nullptr, int gate_when = 0) {
+                                                 const DevState* __restrict__ gate = nullptr, int gate_when = 0,
+                                                 T* fupd = nullptr, const float* __restrict__ addin = nullptr) {
   using TC = typename std::conditional<sizeof(T) == 4, double, float>::type;
   if (ds->status != BGK_OK || ds->done) return;
   if (gate) {
@@ -512,9 +515,19 @@ __global__ void __launch_bounds__(128) k_moments(VGrid g, const T* __restrict__ 
     if (g.dim == 2) {
       for (int j0 = ja; j0 < jb; ++j0) {
         InnerSums<T> S;
-        const T* fr = f + (size_t)j0 * g.N * nnode + i;
-        if (conv) {
-          TC* cr = static_cast<TC*>(conv) + (size_t)j0 * g.N * nnode + i;
+        const size_t o0 = (size_t)j0 * g.N * nnode + i;
+        const T* fr = addin ? nullptr : f + o0;
+        if (addin) {
+          T* fw = fupd + o0;
+          const float* dr = addin + o0;
+#pragma unroll 8
+          for (int j1 = 0; j1 < g.N; ++j1) {
+            const T v = fw[(size_t)j1 * nnode] + (T)float_to_double(dr[(size_t)j1 * nnode]);
+            fw[(size_t)j1 * nnode] = v;
+            S.add(g, j1, v);
+          }
+        } else if (conv) {
+          TC* cr = static_cast<TC*>(conv) + o0;
 #pragma unroll 8
           for (int j1 = 0; j1 < g.N; ++j1) {
             const T v = fr[(size_t)j1 * nnode];
@@ -733,6 +746,42 @@ __global__ void k_source(VGrid g, int nnode, const T* __restrict__ cf, const TQ*
       T m = c1[i] * c2[i];
       if (c3) m = m * c3[i];
       sj[i] = fma(qscale, (T)qj[i], m);
+    }
+  }
+}
+
+// Picard refinement of the mixed precision (2D): the change of the collision-term factors
+// between two FP64-phase iterates.  C32 = the new factors as floats, D32 = new - old as
+// floats of the difference taken in the stored precision (FP64 values, or float pairs:
+// (hi - hi') + (lo - lo'), exact to about 2^-48 of the factors).  n = rows x nodes.
+__global__ void k_delta_factors(size_t n, const double* __restrict__ cf, const double* __restrict__ cf_prev,
+                                int pairs, float* __restrict__ C32, float* __restrict__ D32, const DevState* ds) {
+  if (ds->status != BGK_OK || ds->done) return;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    if (pairs) {
+      const fpair a = fp_from_bits(cf[t]), b = fp_from_bits(cf_prev[t]);
+      C32[t] = a.h;
+      D32[t] = (a.h - b.h) + (a.l - b.l);
+    } else {
+      C32[t] = (float)cf[t];
+      D32[t] = (float)(cf[t] - cf_prev[t]);
+    }
+  }
+}
+
+// The change of the source nu M between two iterates (2D: M = c_1[j_1] c_2[j_2]), from the
+// factors' change: c1' c2' - c1 c2 = c1' (c2' - c2) + (c1' - c1) c2, in FP32 (it is the
+// source of a correction sweep whose result is a small change of f).  dM[j][i].
+// Launch: 2D grid, blockIdx.y (and its strides) over ordinates, x over nodes.
+__global__ void k_delta_source(VGrid g, int nnode, const float* __restrict__ C32, const float* __restrict__ D32,
+                               float* __restrict__ dM, const DevState* ds) {
+  if (ds->status != BGK_OK || ds->done) return;
+  for (int j = blockIdx.y; j < g.nv; j += gridDim.y) {
+    const size_t r1 = (size_t)(j / g.N) * nnode, r2 = (size_t)(g.N + j % g.N) * nnode;
+    float* out = dM + (size_t)j * nnode;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nnode; i += gridDim.x * blockDim.x) {
+      const float c2old = C32[r2 + i] - D32[r2 + i];
+      out[i] = fmaf(C32[r1 + i], D32[r2 + i], D32[r1 + i] * c2old);
     }
   }
 }

@@ -55,6 +55,15 @@ struct bgk_handle {
   void* Ainv = nullptr;      // cached local inverses (schedule order), valid for nus_cached
   bool ainv_pairs = false;   // the FP64 cache holds float pairs (float-pair sweeps, k_sweep_pair)
   bool front_pairs = false;  // the front (fslots) serves the float-pair sweep (k_sweep_front_pair)
+  // Picard refinement of the mixed precision (bgk_config.refine): factors of the previous
+  // iterate, the new factors and their change as floats, zero factors and boundary data
+  // for the correction sweeps
+  bool refine = false;
+  void* cf_prev = nullptr;
+  float* c32 = nullptr;
+  float* d32 = nullptr;
+  float* cf_zero32 = nullptr;
+  float* fbc_zero32 = nullptr;
   double nus_cached = -1.0;
   double nus_main = 0.0, qscale_main = 0.0;  // stage coefficient and 1/(dt A_ss) of the step
   size_t ainv_bytes = 0;
@@ -485,6 +494,79 @@ int add_while(cudaStream_t s, cudaGraphConditionalHandle* cond, cudaGraph_t* bod
   return BGK_OK;
 }
 
+// Picard refinement (2D, no walls or lagged edges): once the FP64 phase has swept a stage
+// once, the next iterate differs from the current one by the sweep of the change of the
+// source alone: f <- f + d, d = L^-1 (Mh nu (M' - M)) with the boundary data and q fixed,
+// so d comes from an FP32 sweep (the shadow's) of the FP32 change of nu M with zero
+// boundary data; its rounding is relative to the small d.  One iteration: the new factors
+// (the old ones kept), their change, the change of the source, the correction sweep, and
+// the update of f fused with the moment pass.
+template <class E>
+void launch_corr_sweep_t(bgk_handle* h, double nus) {
+  bgk_handle* sh = h->shadow;
+  const SrcArgs<float> fr{nullptr, h->cf_zero32, (const float*)sh->fk, 1.0f};
+  if constexpr (E::D == 2) {
+    if (sh->fslots && front_smem_bytes(sh, sh->front_slots, sh->sweep_threads) <= (size_t)kFrontSmemMax) {
+      k_sweep_front<E><<<sh->g.nv, sh->sweep_threads, front_smem_bytes(sh, sh->front_slots, sh->sweep_threads),
+                         h->stream>>>(sweep_args(sh), sh->g, (float)nus, fr, h->fbc_zero32, (float*)sh->f, h->ds, 0,
+                                      sh->fslots, sh->front_slots, front_lvcap(sh));
+      return;
+    }
+  }
+  k_sweep<E, float, false, false, true><<<sh->g.nv, sh->sweep_threads, 0, h->stream>>>(
+      sweep_args(sh), sh->g, (float)nus, fr, h->fbc_zero32, nullptr, (float*)sh->f, h->ds, 0);
+}
+
+int refine_iteration(bgk_handle* h, double nus, double tol, int st, cudaGraphConditionalHandle cond, int use_cond) {
+  bgk_handle* sh = h->shadow;
+  cudaStream_t s = h->stream;
+  const size_t ncf = (size_t)h->g.dim * h->g.N * h->nnode;
+  CK(cudaMemcpyAsync(h->cf_prev, h->cf, ncf * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  const int pairs = pair_sweep(h, nus) ? 1 : 0;
+  k_factors<double><<<(h->nnode + 127) / 128, 128, 0, s>>>(h->g, h->nnode, h->U[0], h->U[1], h->ds, h->phys.nu,
+                                                         (double*)h->cf, h->phys.collision, pairs);
+  k_delta_factors<<<148 * 8, 256, 0, s>>>(ncf, (const double*)h->cf, (const double*)h->cf_prev, pairs, h->c32,
+                                          h->d32, h->ds);
+  k_delta_source<<<k_source_grid(h->nnode, h->g.nv), 256, 0, s>>>(h->g, h->nnode, h->c32, h->d32, (float*)sh->fk,
+                                                                  h->ds);
+  if (h->hm.quad)
+    launch_corr_sweep_t<ElemQ1Quad>(h, nus);
+  else if (h->hm.kx == 2)
+    launch_corr_sweep_t<ElemP2Tri>(h, nus);
+  else
+    launch_corr_sweep_t<ElemP1Tri>(h, nus);
+  k_moments<double><<<h->mom_blocks, 128, 0, s>>>(h->g, nullptr, h->nnode, h->U[0], h->U[1], h->ds, 1, h->partial,
+                                                  nullptr, h->phys.nu, h->phys.collision, nullptr, nullptr, 0,
+                                                  (double*)h->f, (const float*)sh->f);
+  k_finalize<<<1, 256, 0, s>>>(h->ds, h->partial, h->mom_blocks, tol, h->cfg.l_max, st, cond, use_cond);
+  return cudaGetLastError() == cudaSuccess ? BGK_OK : BGK_E_CUDA;
+}
+
+// Buffers of the Picard refinement; off (full sweeps) when the problem does not qualify.
+int build_refine(bgk_handle* h) {
+  h->refine = false;
+  bgk_handle* sh = h->shadow;
+  if (!sh || h->cfg.refine == 1 || h->hm.dim != 2 || h->has_walls || h->lagged != 0 || !sh->fuse_src)
+    return BGK_OK;
+  const size_t ncf = (size_t)h->g.dim * h->g.N * h->nnode;
+  const size_t nfb = (size_t)h->g.nv * h->hm.nbface * h->hm.fd;
+  int rc = BGK_OK;
+  auto A = [&](int r) {
+    if (rc == BGK_OK) rc = r;
+  };
+  A(dalloc(h->cf_prev, ncf * sizeof(double)));
+  A(dalloc(h->c32, ncf * sizeof(float)));
+  A(dalloc(h->d32, ncf * sizeof(float)));
+  A(dalloc(h->cf_zero32, ncf * sizeof(float)));
+  A(dalloc(h->fbc_zero32, std::max<size_t>(1, nfb) * sizeof(float)));
+  if (rc != BGK_OK) return rc;
+  CK(cudaMemsetAsync(h->cf_zero32, 0, ncf * sizeof(float), h->stream));
+  CK(cudaMemsetAsync(h->fbc_zero32, 0, std::max<size_t>(1, nfb) * sizeof(float), h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  h->refine = true;
+  return BGK_OK;
+}
+
 // Mixed precision, at a stage start (main moments already in U): FP32 sweeps on the
 // shadow until the FP32 floor (or the main tolerance), then the FP64 state takes the
 // FP32 result (unless that phase failed) and its moments are recomputed.
@@ -626,7 +708,46 @@ int enqueue_step(bgk_handle* h, int mode_bdf2, cudaGraphExec_t* exec_out) {
       int rs = shadow_phase(h, st, qsrc, qscale, nus, tol, capture, f_ready, qsrc == h->q);
       if (rs != BGK_OK) return rs;
     }
-    if (capture) {
+    if (capture && h->refine) {
+      // one full sweep; then while (cond) { refinement iteration }, the first finalize
+      // setting cond
+      cudaGraph_t cg;
+      cudaStreamCaptureStatus cst;
+      CK(cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, nullptr, nullptr, nullptr));
+      cudaGraphConditionalHandle cond;
+      CK(cudaGraphConditionalHandleCreate(&cond, cg, 1, cudaGraphCondAssignDefault));
+      int rc = build_src(h, qsrc, qscale, nus);
+      if (rc != BGK_OK) return rc;
+      launch_sweep_any(h, nus);
+      moments(h, 1);
+      k_finalize<<<1, 256, 0, s>>>(h->ds, h->partial, h->mom_blocks, tol, h->cfg.l_max, st, cond, 1);
+      const cudaGraphNode_t* deps = nullptr;
+      size_t ndeps = 0;
+      CK(cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, &deps, nullptr, &ndeps));
+      cudaGraphNodeParams cp = {};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = cond;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      cudaGraphNode_t node;
+      CK(cudaGraphAddNode(&node, cg, deps, nullptr, ndeps, &cp));
+      CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+      cudaGraph_t body = cp.conditional.phGraph_out[0];
+      cudaStream_t bs;
+      CK(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
+      CK(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+      h->stream = bs;
+      rc = refine_iteration(h, nus, tol, st, cond, 1);
+      h->stream = s;
+      cudaGraph_t body_out;
+      cudaError_t e2 = cudaStreamEndCapture(bs, &body_out);
+      cudaStreamDestroy(bs);
+      if (rc != BGK_OK || e2 != cudaSuccess) {
+        cudaStreamEndCapture(s, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        return BGK_E_CUDA;
+      }
+    } else if (capture) {
       // while (cond) { src; sweep; moments; finalize }
       cudaGraph_t cg;
       cudaStreamCaptureStatus cst;
@@ -662,12 +783,17 @@ int enqueue_step(bgk_handle* h, int mode_bdf2, cudaGraphExec_t* exec_out) {
         return BGK_E_CUDA;
       }
     } else {
-      for (;;) {
-        int rc = build_src(h, qsrc, qscale, nus);
-        if (rc != BGK_OK) return rc;
-        launch_sweep_any(h, nus);
-        moments(h, 1);
-        k_finalize<<<1, 256, 0, s>>>(h->ds, h->partial, h->mom_blocks, tol, h->cfg.l_max, st, 0, 0);
+      for (int it = 0;; ++it) {
+        if (h->refine && it > 0) {
+          int rc = refine_iteration(h, nus, tol, st, 0, 0);
+          if (rc != BGK_OK) return rc;
+        } else {
+          int rc = build_src(h, qsrc, qscale, nus);
+          if (rc != BGK_OK) return rc;
+          launch_sweep_any(h, nus);
+          moments(h, 1);
+          k_finalize<<<1, 256, 0, s>>>(h->ds, h->partial, h->mom_blocks, tol, h->cfg.l_max, st, 0, 0);
+        }
         CK(cudaGetLastError());
         DevState d;
         CK(cudaMemcpyAsync(&d, h->ds, sizeof(DevState), cudaMemcpyDeviceToHost, s));
@@ -899,7 +1025,8 @@ void release(bgk_handle* h) {
   h->shadow = nullptr;
   if (h->exec_main) cudaGraphExecDestroy(h->exec_main);
   if (h->exec_start) cudaGraphExecDestroy(h->exec_start);
-  void* ptrs[] = {h->gX, h->gY, h->Uhist, h->have_hist, h->geof, h->wall,
+  void* ptrs[] = {h->gX, h->gY, h->Uhist, h->have_hist, h->geof, h->wall, h->cf_prev, h->c32, h->d32,
+                  h->cf_zero32, h->fbc_zero32,
                   h->geo, h->nbr, h->nbr_face, h->perm, h->bnode, h->glist, h->lvl, h->ngen, h->nproc, h->Ainv,
                   h->fslots, h->f, h->fk,
                   h->fprev, h->src, h->fbc, h->q, h->F[0], h->F[1], h->F[2], h->U[0], h->U[1], h->partial, h->cf,
@@ -1130,6 +1257,7 @@ int bgk_create(const bgk_mesh* mesh, const bgk_vgrid* vg, const bgk_physics* phy
     p32.dt = h->dt;
     rc = bgk_create(mesh, vg, &p32, &c32, &h->shadow);
     if (h->cfg.fp32_floor > 0.0) h->fp32_floor = h->cfg.fp32_floor;
+    if (rc == BGK_OK) rc = build_refine(h);
   }
   if (rc == BGK_OK && !h->cfg.eager) rc = enqueue_step(h, 0, &h->exec_main);
   if (rc == BGK_OK && !h->cfg.eager && phys->integrator == BGK_BDF2) {
