@@ -402,22 +402,31 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def launches_per_step(st, guess=False, main_fp32=False, walls=False):
+def launches_per_step(st, guess=False, main_fp32=False, walls=False, refine=False, bdf2=False):
     """Kernels one step launches (graph nodes of kernel type), from its statistics.  FP32
     sweeps form their source themselves (factors, sweep, moments, test per iteration);
-    FP64 iterations add the source pass; walls add their refresh to every iteration."""
+    FP64 iterations add the source pass; walls add their refresh to every iteration.  The
+    mixed precision's FP32 phase: state reset, stage begin, moment copy, record, the
+    hand-over moment pass and its fallback, plus the conversions of f and q that the
+    stage-start moment pass and the stage combine do not already write (with a guess
+    changing f first).  refine: the FP64 iterations after the first of a stage are
+    corrections (factors, factor change, source change, FP32 sweep, update with moments,
+    test)."""
     n = 1
     per_main = (4 if main_fp32 else 5) + bool(walls)
     for k in range(st.n_stages):
         n += 2 + (k > 0) + (k < st.n_stages - 1)          # stage set-up, moments, stage combines
         n += 9 if guess else 0
         if st.iterations_fp32[k]:
-            n += 7 + (4 + bool(walls)) * st.iterations_fp32[k]   # FP32 phase
-        n += per_main * st.iterations[k]
+            conv = (1 + (0 if (bdf2 or k > 0) else 1)) if guess else 0
+            n += 6 + conv + (4 + bool(walls)) * st.iterations_fp32[k]   # FP32 phase
+        its = st.iterations[k]
+        n += (per_main + 6 * (its - 1)) if (refine and its > 0) else per_main * its
     return n
 
 
-def timed_steps(s, steps, world, local, tstream, guess=False, main_fp32=False, walls=False, restore=None):
+def timed_steps(s, steps, world, local, tstream, guess=False, main_fp32=False, walls=False, restore=None,
+                refine=False):
     """Run `steps` steps of solver s (already warmed up; created on torch stream tstream),
     each bracketed by CUDA events on that stream; the time is the sum of the steps'
     device times (the statistics read between steps is not inside any bracket).
@@ -444,7 +453,7 @@ def timed_steps(s, steps, world, local, tstream, guess=False, main_fp32=False, w
         e1.synchronize()
         el += e0.elapsed_time(e1) * 1e-3
         iters.append({"fp64": list(st.iterations)[:st.n_stages], "fp32": list(st.iterations_fp32)[:st.n_stages]})
-        launches += launches_per_step(st, guess, main_fp32, walls)
+        launches += launches_per_step(st, guess, main_fp32, walls, refine)
     s.synchronize()
     torch.cuda.synchronize()
     barrier(world)
@@ -598,9 +607,10 @@ def run_ours(args):
     for _ in range(args.warmup):
         restore_main()
         s.step(1)
+    refine = s.refine_active
     el_max, sweeps, iters, launches, clk = timed_steps(s, args.steps, world, local, tstream,
                                                        main_fp32=args.precision == "fp32", walls=bool(walls),
-                                                       restore=restore_main)
+                                                       restore=restore_main, refine=refine)
     value = job_throughput(dof * sweeps, el_max, world)
     f_end, U_end = s.get_f(np.float64), s.get_moments()
     # end to end through the C ABI with host buffers: f^k in from pinned host memory,
@@ -663,6 +673,11 @@ def run_ours(args):
     # dominant kernel of the timed step: the sweep that used the most time
     n64 = sum(sum(i["fp64"]) for i in iters)
     n32 = sum(sum(i["fp32"]) for i in iters)
+    if refine:
+        # the FP64 iterations after the first of a stage are FP32 correction sweeps
+        full = sum(sum(1 for x in i["fp64"] if x > 0) for i in iters)
+        n32 += n64 - full
+        n64 = full
     k64 = "fp64_pairs" if "fp64_pairs" in rl and rl["fp64_pairs"]["local_inverse_cache_gb"] > 0 else "fp64"
     dom = k64
     if "fp32" in rl and n32 * rl["fp32"]["sweep_ms"] > n64 * rl[k64]["sweep_ms"]:
@@ -685,7 +700,9 @@ def run_ours(args):
                                                      "before every step outside the timed region" % pre}),
             "roofline": roofline, "rooflines": rl,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-            "picard_iterations": iters, "sweeps_timed": sweeps, "dt": dt}
+            "picard_iterations": iters, "sweeps_timed": sweeps, "dt": dt,
+            "fp64_phase": ("per stage one full float-pair sweep, then FP32 correction sweeps of the change of "
+                           "the source (Picard refinement)") if refine else "full sweeps"}
     if tune:
         line["sweep_autotune_ms"] = tune
         line["sweep_chosen"] = chosen

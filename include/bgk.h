@@ -174,6 +174,9 @@ int bgk_sizes(const bgk_handle* h, int64_t* out);
  * (bgk_config.sweep_front, hp_sweep); 0 when they read every upwind trace from global
  * memory. */
 int bgk_front_slots(const bgk_handle* h, int* slots);
+/* Whether the mixed precision's FP64 phase uses the Picard refinement (bgk_config.refine):
+ * *on = 1 when its iterations after the first of a stage are FP32 correction sweeps, else 0. */
+int bgk_refine_active(const bgk_handle* h, int* on);
 /* Time step actually used (after the CFL rule). */
 int bgk_get_dt(const bgk_handle* h, double* dt);
 

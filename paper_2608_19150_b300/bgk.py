@@ -86,6 +86,7 @@ def load(path: str = LIB_PATH):
         "bgk_sizes": [P, C.POINTER(C.c_int64)],
         "bgk_get_dt": [P, C.POINTER(D)],
         "bgk_front_slots": [P, C.POINTER(I)],
+        "bgk_refine_active": [P, C.POINTER(I)],
         "bgk_set_state_maxwellian": [P, V],
         "bgk_set_inflow_maxwellian": [P, V],
         "bgk_set_inflow": [P, V],
@@ -261,6 +262,14 @@ class Solver:
 
     def __del__(self):
         self.close()
+
+    @property
+    def refine_active(self):
+        """True when the FP64 phase's iterations after the first of a stage are FP32
+        correction sweeps (the Picard refinement of the mixed precision)."""
+        n = C.c_int()
+        _ck(self.lib.bgk_refine_active(self.h, C.byref(n)), "bgk_refine_active")
+        return bool(n.value)
 
     @property
     def front_slots(self):

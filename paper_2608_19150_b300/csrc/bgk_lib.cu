@@ -1302,6 +1302,12 @@ int bgk_front_slots(const bgk_handle* h, int* slots) {
   return BGK_OK;
 }
 
+int bgk_refine_active(const bgk_handle* h, int* on) {
+  if (!h || !on) return BGK_E_INVALID;
+  *on = h->refine ? 1 : 0;
+  return BGK_OK;
+}
+
 int bgk_get_dt(const bgk_handle* h, double* dt) {
   if (!h || !dt) return BGK_E_INVALID;
   *dt = h->dt;

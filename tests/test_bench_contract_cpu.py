@@ -42,3 +42,13 @@ def test_launch_tally_counts_the_wall_refresh():
     walls = bench.launches_per_step(st, walls=True)
     # one refresh per FP64 iteration (7) and per FP32 iteration (5)
     assert walls - plain == 7 + 5
+
+
+def test_launch_tally_counts_the_refinement_iterations():
+    sys.path.insert(0, ROOT)
+    import bench
+    st = SimpleNamespace(n_stages=1, iterations=[3, 0, 0], iterations_fp32=[5, 0, 0])
+    full = bench.launches_per_step(st)
+    refined = bench.launches_per_step(st, refine=True)
+    # the first FP64 iteration as before (5), each later one 6 kernels instead of 5
+    assert refined - full == 2 * (6 - 5)
