@@ -613,22 +613,28 @@ def run_ours(args):
                                                        restore=restore_main, refine=refine)
     value = job_throughput(dof * sweeps, el_max, world)
     f_end, U_end = s.get_f(np.float64), s.get_moments()
-    # end to end through the C ABI with host buffers: f^k in from pinned host memory,
-    # moments out to host, every step
+    # end to end through the C ABI with host buffers: every step's f^k comes in from pinned
+    # host memory (the next step's copy overlapping this step's sweeps on the handle's copy
+    # stream) and its moments go out to the host
     f_host = torch.empty(dof, dtype=tdt, pin_memory=True)
     f_host.copy_(f_in.cpu())
     U = np.empty((s.nnode, s.dim + 2))
     barrier(world)
     t0 = time.perf_counter()
     e2e_sweeps = 0
-    for _ in range(args.steps):
-        s.lib.bgk_set_f(s.h, bgk.C.c_void_p(f_host.data_ptr()), 0 if fdt == np.float64 else 1)
+    s.upload_f_async(f_host.data_ptr(), fdt)
+    for k in range(args.steps):
+        s.set_f_uploaded()
+        if k + 1 < args.steps:
+            s.upload_f_async(f_host.data_ptr(), fdt)
         st = s.step(1)
         e2e_sweeps += sum(list(st.iterations)[:st.n_stages]) + sum(list(st.iterations_fp32)[:st.n_stages])
         s.lib.bgk_get_moments(s.h, U.ctypes.data_as(bgk.C.c_void_p))
     el_e2e = max_over_ranks(time.perf_counter() - t0, world)
     e2e = {"value": job_throughput(dof * e2e_sweeps, el_e2e, world), "unit": UNIT,
-           "h2d_bytes_per_step": int(f_host.numel() * f_host.element_size()), "d2h_bytes_per_step": int(U.nbytes)}
+           "h2d_bytes_per_step": int(f_host.numel() * f_host.element_size()), "d2h_bytes_per_step": int(U.nbytes),
+           "copies": "bgk_upload_f_async / bgk_set_f_uploaded: each step's input copied from pinned host memory "
+                     "on the handle's copy stream while the previous step runs; moments read back every step"}
     dt = s.dt
     s.close()
     del s

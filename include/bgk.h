@@ -196,6 +196,18 @@ int bgk_get_f(bgk_handle* h, void* h_f, int dtype);
 /* Device-pointer variants (same layout), ordered on the handle's stream. */
 int bgk_set_f_device(bgk_handle* h, const void* d_f, int dtype);
 int bgk_get_f_device(bgk_handle* h, void* d_f, int dtype);
+/* Overlapped input of the next state: bgk_upload_f_async starts copying host h_f ([n_ordinates]
+ * [n_nodes] in the handle's storage type: BGK_DTYPE_F64 unless the precision is
+ * BGK_FP32_SWEEP) into a staging buffer of the handle on a copy stream of its own and
+ * returns at once; the copy may overlap the steps already queued.  h_f should be pinned
+ * (page-locked) for the copy to run asynchronously and must stay valid and unchanged until
+ * the next bgk_set_f_uploaded returns.  bgk_set_f_uploaded makes the state the staged one,
+ * as bgk_set_f does, ordered after the copy on the handle's stream, without waiting on the
+ * host.  A second upload before the staged state is taken waits (on the device) for that
+ * hand-over.  BGK_E_INVALID: null arguments, the other dtype, or no upload pending;
+ * BGK_E_OOM: no room for the staging buffer. */
+int bgk_upload_f_async(bgk_handle* h, const void* h_f, int dtype);
+int bgk_set_f_uploaded(bgk_handle* h);
 
 /* Velocity moments of the current f, host [n_nodes][d+2] (Eq. moments). */
 int bgk_get_moments(bgk_handle* h, double* h_U);

@@ -93,6 +93,8 @@ def load(path: str = LIB_PATH):
         "bgk_set_f": [P, V, I],
         "bgk_get_f": [P, V, I],
         "bgk_set_f_device": [P, V, I],
+        "bgk_upload_f_async": [P, V, I],
+        "bgk_set_f_uploaded": [P],
         "bgk_get_f_device": [P, V, I],
         "bgk_get_moments": [P, V],
         "bgk_get_moments_device": [P, V],
@@ -312,6 +314,16 @@ class Solver:
 
     def get_f_device(self, ptr, dtype=np.float64):
         _ck(self.lib.bgk_get_f_device(self.h, C.c_void_p(ptr), DTYPES[np.dtype(dtype)]), "bgk_get_f_device")
+
+    def upload_f_async(self, host_ptr, dtype=np.float64):
+        """Start copying the next state from (pinned) host memory to the handle's staging
+        buffer on its copy stream; keep the host buffer unchanged until set_f_uploaded."""
+        _ck(self.lib.bgk_upload_f_async(self.h, C.c_void_p(host_ptr), DTYPES[np.dtype(dtype)]),
+            "bgk_upload_f_async")
+
+    def set_f_uploaded(self):
+        """The staged state becomes the state (ordered after its copy, no host wait)."""
+        _ck(self.lib.bgk_set_f_uploaded(self.h), "bgk_set_f_uploaded")
 
     def get_moments(self):
         U = np.empty((self.nnode, self.dim + 2))

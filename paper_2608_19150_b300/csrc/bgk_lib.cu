@@ -58,6 +58,11 @@ struct bgk_handle {
   // Picard refinement of the mixed precision (bgk_config.refine): factors of the previous
   // iterate, the new factors and their change as floats, zero factors and boundary data
   // for the correction sweeps
+  // overlapped input (bgk_upload_f_async / bgk_set_f_uploaded)
+  void* f_stage = nullptr;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_uploaded = nullptr, ev_stage_free = nullptr;
+  bool upload_pending = false;
   bool refine = false;
   void* cf_prev = nullptr;
   float* c32 = nullptr;
@@ -1033,6 +1038,10 @@ void release(bgk_handle* h) {
                   h->ds};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  if (h->f_stage) cudaFree(h->f_stage);
+  if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+  if (h->ev_uploaded) cudaEventDestroy(h->ev_uploaded);
+  if (h->ev_stage_free) cudaEventDestroy(h->ev_stage_free);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -1436,6 +1445,41 @@ int bgk_set_f_device(bgk_handle* h, const void* d_f, int dtype) {
 }
 int bgk_get_f_device(bgk_handle* h, void* d_f, int dtype) {
   return transfer_f(h, d_f, dtype, false, cudaMemcpyDeviceToDevice);
+}
+
+int bgk_upload_f_async(bgk_handle* h, const void* h_f, int dtype) {
+  if (!h || !h_f || (dtype != BGK_DTYPE_F64 && dtype != BGK_DTYPE_F32)) return BGK_E_INVALID;
+  if ((dtype == BGK_DTYPE_F64 ? 8u : 4u) != h->tsize) return BGK_E_INVALID;
+  if (!h->f_stage) {
+    if (dalloc(h->f_stage, h->nfv * h->tsize) != BGK_OK) {
+      h->f_stage = nullptr;
+      return BGK_E_OOM;
+    }
+    if (cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_uploaded, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_stage_free, cudaEventDisableTiming) != cudaSuccess)
+      return BGK_E_CUDA;
+    CK(cudaEventRecord(h->ev_stage_free, h->stream));
+  }
+  // the staging buffer is free once the last hand-over from it has run
+  CK(cudaStreamWaitEvent(h->copy_stream, h->ev_stage_free, 0));
+  CK(cudaMemcpyAsync(h->f_stage, h_f, h->nfv * h->tsize, cudaMemcpyHostToDevice, h->copy_stream));
+  CK(cudaEventRecord(h->ev_uploaded, h->copy_stream));
+  h->upload_pending = true;
+  return BGK_OK;
+}
+
+int bgk_set_f_uploaded(bgk_handle* h) {
+  if (!h || !h->upload_pending) return BGK_E_INVALID;
+  CK(cudaStreamWaitEvent(h->stream, h->ev_uploaded, 0));
+  CK(cudaMemcpyAsync(h->f, h->f_stage, h->nfv * h->tsize, cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaEventRecord(h->ev_stage_free, h->stream));
+  CK(cudaMemcpyAsync(h->fk, h->f, h->nfv * h->tsize, cudaMemcpyDeviceToDevice, h->stream));
+  h->upload_pending = false;
+  h->have_prev = false;
+  h->state_set = true;
+  h->steps = 0;
+  return BGK_OK;
 }
 
 static int moments_to(bgk_handle* h, double* out, cudaMemcpyKind kind) {
