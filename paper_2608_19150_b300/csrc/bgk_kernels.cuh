@@ -468,13 +468,13 @@ struct InnerSums<double> {
 // Velocity moments U_i = sum_j w_j (1, v_j, |v_j|^2/2) f_{j,i} (Eq. moments), FP64
 // accuracy for either storage type.  A block of 128 threads covers 128 / PARTS nodes;
 // PARTS thread groups split the outermost velocity index into ranges (more loads in
-// flight per node for the costlier FP64 data) and their partial sums are added in a
+// flight per node: 4 for FP64 data, 2 for FP32) and their partial sums are added in a
 // fixed order.  mode 0: write U[it&1].  mode 1: write U[(it+1)&1] and per-block partial
 // sums of |dU_m|^2 and |U_old,m|^2, m = 0, 1, 2, for the criterion of Eq.
 // (convergence-criteria).  Launch: 128 threads, ceil(nnode * PARTS / 128) blocks.
 template <typename T>
 struct MomentParts {
-  static constexpr int value = sizeof(T) == 8 ? 4 : 1;
+  static constexpr int value = sizeof(T) == 8 ? 4 : 2;
 };
 
 //
@@ -534,11 +534,21 @@ __global__ void __launch_bounds__(128) k_moments(VGrid g, const T* __restrict__ 
             cr[(size_t)j1 * nnode] = (TC)v;
             S.add(g, j1, v);
           }
-        } else {
-#pragma unroll 8
-          for (int j1 = 0; j1 < g.N; ++j1) S.add(g, j1, fr[(size_t)j1 * nnode]);
         }
-        const double s0 = S.get(0), s1 = S.get(1), s2 = S.get(2);
+        // the plain pass: two independent compensated sums (even and odd points) for more
+        // loads and arithmetic in flight, added at the end
+        InnerSums<T> S2;
+        if (!addin && !conv) {
+          int j1 = 0;
+#pragma unroll 4
+          for (; j1 + 1 < g.N; j1 += 2) {
+            const T a0 = fr[(size_t)j1 * nnode], a1 = fr[(size_t)(j1 + 1) * nnode];
+            S.add(g, j1, a0);
+            S2.add(g, j1 + 1, a1);
+          }
+          if (j1 < g.N) S.add(g, j1, fr[(size_t)j1 * nnode]);
+        }
+        const double s0 = S.get(0) + S2.get(0), s1 = S.get(1) + S2.get(1), s2 = S.get(2) + S2.get(2);
         const double w0 = g.w[j0], x0 = g.x[j0];
         acc[0] += w0 * s0;
         acc[1] += w0 * x0 * s0;
