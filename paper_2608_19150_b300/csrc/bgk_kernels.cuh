@@ -1899,13 +1899,14 @@ __device__ __forceinline__ void store_vec(T* __restrict__ p, const T (&v)[N]) {
 // FP32 generation sweep with the shared-memory front (one CTA per ordinate, the same
 // operations per cell as sweep_ordinate with the fused source): Sec. 4, Eq. bgk-ss-picard,
 //   (nu_s Mh + sum_i r_i (Dd_i + [s_i>0] Eh_i)) f_K = Mh src_K + sum_{s_i<0} (-r_i) Eh_i y_i,
-// src = prod_a cf[a][j_a] + qscale q.  The generation offsets sit in shared memory; each
+// src = prod_a cf[a][j_a] + qscale q (FUSED; otherwise src is read as given: the
+// corrections of the Picard refinement).  The generation offsets sit in shared memory; each
 // thread takes positions lv[g] + tid + m nt of generation g and carries the next item's
-// neighbours, permutation, geometry, q, factors and front slots in registers (loaded
+// neighbours, permutation, geometry, q (src), factors and front slots in registers (loaded
 // while the current item is solved; the schedule entry one item earlier still).
 // Dynamic shared memory: the front (S float4), then the generation offsets (lvcap ints,
 // G + 1 of the largest G rounded up to 4).  2D elements (P1/P2 triangles, Q1).
-template <class E>
+template <class E, bool FUSED = true>
 __global__ void __launch_bounds__(128, 4) k_sweep_front(SweepArgs sa, VGrid g, float nus, SrcArgs<float> sr,
                                                        const float* __restrict__ fbc, float* f, const DevState* ds,
                                                        int jofs, const uint64_t* __restrict__ fslots, int S,
@@ -1929,7 +1930,7 @@ __global__ void __launch_bounds__(128, 4) k_sweep_front(SweepArgs sa, VGrid g, f
   const uint32_t* gl = sa.glist + (size_t)j * sa.ncell;
   const uint64_t* slj = fslots + (size_t)j * sa.ncell;
   T* fj = f + (size_t)j * sa.nnode;
-  const SrcRows<T> rw = src_rows<T, true>(sr, g, j, sa.nnode);
+  const SrcRows<T> rw = src_rows<T, FUSED>(sr, g, j, sa.nnode);
   const T* bj = fbc + (size_t)j * sa.nbface * FD;
   __syncthreads();
   auto seek = [&](int g2, int& kq, int& gq) {
@@ -1955,7 +1956,7 @@ __global__ void __launch_bounds__(128, 4) k_sweep_front(SweepArgs sa, VGrid g, f
       seek(gq + 1, kr, gr);
     }
   };
-  SweepItem<E, T, true, true> cur, nxt;
+  SweepItem<E, T, true, FUSED> cur, nxt;
   uint64_t scur = 0, snxt = 0;
   // current item k, next kn (its data is loaded while k is solved) and the one after,
   // kn2 (its schedule entry is loaded while k is solved)
@@ -1964,7 +1965,7 @@ __global__ void __launch_bounds__(128, 4) k_sweep_front(SweepArgs sa, VGrid g, f
   advance(k, gk, kn, gn);
   advance(kn, gn, kn2, gn2);
   if (k >= 0) {
-    fetch_item<E, T, true, true>(sa, gl, rw, k, cur);
+    fetch_item<E, T, true, FUSED>(sa, gl, rw, k, cur);
     scur = slj[k];
     resolve_src(cur, sr.qscale);
   }
@@ -1972,7 +1973,7 @@ __global__ void __launch_bounds__(128, 4) k_sweep_front(SweepArgs sa, VGrid g, f
   for (int gg = 0; gg < G; ++gg) {
     while (k >= 0 && gk == gg) {
       if (kn >= 0) {
-        fetch_item_e<E, T, true, true>(sa, en, rw, nxt);
+        fetch_item_e<E, T, true, FUSED>(sa, en, rw, nxt);
         snxt = slj[kn];
       }
       const uint32_t en2 = kn2 >= 0 ? gl[kn2] : 0u;

@@ -512,9 +512,12 @@ void launch_corr_sweep_t(bgk_handle* h, double nus) {
   const SrcArgs<float> fr{nullptr, h->cf_zero32, (const float*)sh->fk, 1.0f};
   if constexpr (E::D == 2) {
     if (sh->fslots && front_smem_bytes(sh, sh->front_slots, sh->sweep_threads) <= (size_t)kFrontSmemMax) {
-      k_sweep_front<E><<<sh->g.nv, sh->sweep_threads, front_smem_bytes(sh, sh->front_slots, sh->sweep_threads),
-                         h->stream>>>(sweep_args(sh), sh->g, (float)nus, fr, h->fbc_zero32, (float*)sh->f, h->ds, 0,
-                                      sh->fslots, sh->front_slots, front_lvcap(sh));
+      // the change of the source is given: the front sweep reads it as src
+      const SrcArgs<float> fs{(const float*)sh->fk, nullptr, nullptr, 0.0f};
+      k_sweep_front<E, false><<<sh->g.nv, sh->sweep_threads,
+                                front_smem_bytes(sh, sh->front_slots, sh->sweep_threads), h->stream>>>(
+          sweep_args(sh), sh->g, (float)nus, fs, h->fbc_zero32, (float*)sh->f, h->ds, 0, sh->fslots, sh->front_slots,
+          front_lvcap(sh));
       return;
     }
   }
@@ -1240,6 +1243,12 @@ int bgk_create(const bgk_mesh* mesh, const bgk_vgrid* vg, const bgk_physics* phy
   CK(cudaFuncSetAttribute(k_sweep_front<ElemP1Tri>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFrontSmemMax));
   CK(cudaFuncSetAttribute(k_sweep_front<ElemP2Tri>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFrontSmemMax));
   CK(cudaFuncSetAttribute(k_sweep_front<ElemQ1Quad>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFrontSmemMax));
+  CK(cudaFuncSetAttribute(k_sweep_front<ElemP1Tri, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          kFrontSmemMax));
+  CK(cudaFuncSetAttribute(k_sweep_front<ElemP2Tri, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          kFrontSmemMax));
+  CK(cudaFuncSetAttribute(k_sweep_front<ElemQ1Quad, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          kFrontSmemMax));
   CK(cudaFuncSetAttribute(k_sweep_front_pair<ElemP1Tri>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFrontSmemMax));
   CK(cudaFuncSetAttribute(k_sweep_front_pair<ElemP2Tri>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFrontSmemMax));
   CK(cudaFuncSetAttribute(k_sweep_front_pair<ElemQ1Quad>, cudaFuncAttributeMaxDynamicSharedMemorySize,
