@@ -136,13 +136,13 @@ typedef struct {
                          2^-44 relative per operation (FP64: 2^-53), eight orders below the
                          Picard tolerance, at a fraction of B300's FP64 instruction cost.
                          The data in memory stay FP64 */
-  int refine;         /* BGK_MIXED on 2D meshes without walls or lagged edges: 0 = after the first
-                         FP64-phase sweep of a stage, every further Picard iteration f <- f + d
-                         solves for the change d with an FP32 sweep whose source is the change
-                         of nu M (exact in exact arithmetic: the iterate just swept satisfies
-                         the sweep's equations, so the sweep of the next iterate differs from
-                         it only through the source); 1 = every FP64-phase iteration a full
-                         sweep */
+  int refine;         /* BGK_MIXED: 0 = after the first FP64-phase sweep of a stage, every
+                         further Picard iteration f <- f + d solves for the change d with an
+                         FP32 sweep whose source is the change of nu M, whose wall data and
+                         lagged inflow are those of the previous change and whose inflow data
+                         are zero (exact in exact arithmetic: the iterate just swept satisfies
+                         the sweep's equations, so the next sweep differs from it only through
+                         these changes); 1 = every FP64-phase iteration a full sweep */
 } bgk_config;
 
 typedef struct {

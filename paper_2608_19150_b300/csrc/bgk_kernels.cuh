@@ -489,8 +489,8 @@ struct MomentParts {
 // between the FP32 and the FP64 phases of the mixed precision in the same pass that takes
 // the moments.  gate: the kernel runs only when gate's loop succeeded (gate_when 1) or
 // only when it failed (gate_when 2; failed = non-physical, as k_convert_gated skips).
-// fupd, addin (2D; f then unused): the pass first updates fupd += addin in place (the change
-// of a Picard iterate, FP32) and sums the updated values.
+// fupd, addin (f then unused): the pass first updates fupd += addin in place (the change of
+// a Picard iterate, FP32) and sums the updated values.
 template <typename T>
 __global__ void __launch_bounds__(128) k_moments(VGrid g, const T* __restrict__ f, int nnode, double* U0,
                                                  double* U1, DevState* ds, int mode,
@@ -560,9 +560,19 @@ __global__ void __launch_bounds__(128) k_moments(VGrid g, const T* __restrict__ 
         double t0 = 0, t1 = 0, t2 = 0, t3 = 0;
         for (int j1 = 0; j1 < g.N; ++j1) {
           InnerSums<T> S;
-          const T* fr = f + ((size_t)j0 * g.N + j1) * g.N * nnode + i;
-          if (conv) {
-            TC* cr = static_cast<TC*>(conv) + ((size_t)j0 * g.N + j1) * g.N * nnode + i;
+          const size_t o1 = ((size_t)j0 * g.N + j1) * g.N * nnode + i;
+          const T* fr = addin ? nullptr : f + o1;
+          if (addin) {
+            T* fw = fupd + o1;
+            const float* dr = addin + o1;
+#pragma unroll 8
+            for (int j2 = 0; j2 < g.N; ++j2) {
+              const T v = fw[(size_t)j2 * nnode] + (T)float_to_double(dr[(size_t)j2 * nnode]);
+              fw[(size_t)j2 * nnode] = v;
+              S.add(g, j2, v);
+            }
+          } else if (conv) {
+            TC* cr = static_cast<TC*>(conv) + o1;
 #pragma unroll 8
             for (int j2 = 0; j2 < g.N; ++j2) {
               const T v = fr[(size_t)j2 * nnode];
@@ -787,13 +797,47 @@ __global__ void k_delta_source(VGrid g, int nnode, const float* __restrict__ C32
                                float* __restrict__ dM, const DevState* ds) {
   if (ds->status != BGK_OK || ds->done) return;
   for (int j = blockIdx.y; j < g.nv; j += gridDim.y) {
-    const size_t r1 = (size_t)(j / g.N) * nnode, r2 = (size_t)(g.N + j % g.N) * nnode;
     float* out = dM + (size_t)j * nnode;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nnode; i += gridDim.x * blockDim.x) {
-      const float c2old = C32[r2 + i] - D32[r2 + i];
-      out[i] = fmaf(C32[r1 + i], D32[r2 + i], D32[r1 + i] * c2old);
+    if (g.dim == 2) {
+      const size_t r1 = (size_t)(j / g.N) * nnode, r2 = (size_t)(g.N + j % g.N) * nnode;
+      for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nnode; i += gridDim.x * blockDim.x) {
+        const float c2old = C32[r2 + i] - D32[r2 + i];
+        out[i] = fmaf(C32[r1 + i], D32[r2 + i], D32[r1 + i] * c2old);
+      }
+    } else {
+      // c1'c2'c3' - c1c2c3 = (c1'-c1) c2'c3' + c1 (c2'-c2) c3' + c1 c2 (c3'-c3)
+      const size_t r1 = (size_t)(j / (g.N * g.N)) * nnode, r2 = (size_t)(g.N + (j / g.N) % g.N) * nnode,
+                   r3 = (size_t)(2 * g.N + j % g.N) * nnode;
+      for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nnode; i += gridDim.x * blockDim.x) {
+        const float a1 = C32[r1 + i], a2 = C32[r2 + i], a3 = C32[r3 + i];
+        const float d1 = D32[r1 + i], d2 = D32[r2 + i], d3 = D32[r3 + i];
+        const float o1 = a1 - d1, o2 = a2 - d2;
+        out[i] = fmaf(d1, a2 * a3, fmaf(o1, d2 * a3, o1 * o2 * d3));
+      }
     }
   }
+}
+
+// The change of f made by the FP64 phase's full sweep of a stage, as the FP32 start of the
+// refinement's corrections (their wall data and lagged inflow read the previous change):
+// d = f - f_prev with f_prev the state the sweep started from -- the FP32 phase's result
+// (exactly the double of d's own buffer), or, when that phase failed and left the FP64
+// state as it was, the copy taken before the sweep.
+__global__ void k_delta0(size_t n, const double* __restrict__ f, float* d, const double* __restrict__ fsave,
+                         const DevState* __restrict__ gate, const DevState* ds) {
+  if (ds->status != BGK_OK || ds->done) return;
+  const bool failed = gate->err || gate->status == BGK_E_NONPHYSICAL;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    d[t] = (float)(f[t] - (failed ? fsave[t] : (double)d[t]));
+}
+
+// out <- in when gate reports that its loop failed (the state the FP64 phase starts from
+// is then not the FP32 phase's result)
+__global__ void k_copy_if_failed(size_t n, const double* __restrict__ in, double* __restrict__ out,
+                                 const DevState* __restrict__ gate) {
+  if (!(gate->err || gate->status == BGK_E_NONPHYSICAL)) return;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    out[t] = in[t];
 }
 
 // grid of k_source: about four nodes per thread of 256, at most 65535 ordinate rows

@@ -64,6 +64,8 @@ struct bgk_handle {
   cudaEvent_t ev_uploaded = nullptr, ev_stage_free = nullptr;
   bool upload_pending = false;
   bool refine = false;
+  bool refine_delta = false;  // the corrections read the previous change (walls, lagged edges)
+  void* f_save = nullptr;     // the FP64 state before the full sweep when the FP32 phase failed
   void* cf_prev = nullptr;
   float* c32 = nullptr;
   float* d32 = nullptr;
@@ -509,7 +511,6 @@ int add_while(cudaStream_t s, cudaGraphConditionalHandle* cond, cudaGraph_t* bod
 template <class E>
 void launch_corr_sweep_t(bgk_handle* h, double nus) {
   bgk_handle* sh = h->shadow;
-  const SrcArgs<float> fr{nullptr, h->cf_zero32, (const float*)sh->fk, 1.0f};
   if constexpr (E::D == 2) {
     if (sh->fslots && front_smem_bytes(sh, sh->front_slots, sh->sweep_threads) <= (size_t)kFrontSmemMax) {
       // the change of the source is given: the front sweep reads it as src
@@ -521,8 +522,9 @@ void launch_corr_sweep_t(bgk_handle* h, double nus) {
       return;
     }
   }
-  k_sweep<E, float, false, false, true><<<sh->g.nv, sh->sweep_threads, 0, h->stream>>>(
-      sweep_args(sh), sh->g, (float)nus, fr, h->fbc_zero32, nullptr, (float*)sh->f, h->ds, 0);
+  const SrcArgs<float> fs{(const float*)sh->fk, nullptr, nullptr, 0.0f};
+  k_sweep<E, float, false, false, false><<<sh->g.nv, sh->sweep_threads, 0, h->stream>>>(
+      sweep_args(sh), sh->g, (float)nus, fs, h->fbc_zero32, nullptr, (float*)sh->f, h->ds, 0);
 }
 
 int refine_iteration(bgk_handle* h, double nus, double tol, int st, cudaGraphConditionalHandle cond, int use_cond) {
@@ -537,7 +539,17 @@ int refine_iteration(bgk_handle* h, double nus, double tol, int st, cudaGraphCon
                                           h->d32, h->ds);
   k_delta_source<<<k_source_grid(h->nnode, h->g.nv), 256, 0, s>>>(h->g, h->nnode, h->c32, h->d32, (float*)sh->fk,
                                                                   h->ds);
-  if (h->hm.quad)
+  if (h->has_walls) {
+    // wall data of the correction: the mirror traces of the previous change (its inflow
+    // faces keep zero data)
+    const int npos = h->hm.nbface * h->hm.fd;
+    const int blocks = std::min<size_t>(148 * 8, ((size_t)h->g.nv * npos + 255) / 256);
+    k_wall_bc<float><<<blocks, 256, 0, s>>>(sh->g, npos, h->hm.fd, h->nnode, (const float*)sh->f, sh->bnode, sh->wall,
+                                            h->fbc_zero32);
+  }
+  if (h->hm.dim == 3)
+    launch_corr_sweep_t<ElemP1Tet>(h, nus);
+  else if (h->hm.quad)
     launch_corr_sweep_t<ElemQ1Quad>(h, nus);
   else if (h->hm.kx == 2)
     launch_corr_sweep_t<ElemP2Tri>(h, nus);
@@ -550,12 +562,27 @@ int refine_iteration(bgk_handle* h, double nus, double tol, int st, cudaGraphCon
   return cudaGetLastError() == cudaSuccess ? BGK_OK : BGK_E_CUDA;
 }
 
-// Buffers of the Picard refinement; off (full sweeps) when the problem does not qualify.
+// Around the FP64 phase's full sweep of a stage (refinement with walls or lagged edges):
+// keep the starting state when the FP32 phase failed, then turn the shadow's f (the FP32
+// phase's result, the starting state otherwise) into the sweep's change of f.
+void refine_save(bgk_handle* h) {
+  if (!h->refine_delta) return;
+  k_copy_if_failed<<<148 * 8, 256, 0, h->stream>>>(h->nfv, (const double*)h->f, (double*)h->f_save,
+                                                    h->shadow->ds);
+}
+void refine_delta0(bgk_handle* h) {
+  if (!h->refine_delta) return;
+  k_delta0<<<148 * 8, 256, 0, h->stream>>>(h->nfv, (const double*)h->f, (float*)h->shadow->f,
+                                            (const double*)h->f_save, h->shadow->ds, h->ds);
+}
+
+// Buffers of the Picard refinement; off (full sweeps) when asked.  With walls or lagged
+// edges the corrections also read the previous change of f (sh->f holds it between them).
 int build_refine(bgk_handle* h) {
   h->refine = false;
   bgk_handle* sh = h->shadow;
-  if (!sh || h->cfg.refine == 1 || h->hm.dim != 2 || h->has_walls || h->lagged != 0 || !sh->fuse_src)
-    return BGK_OK;
+  if (!sh || h->cfg.refine == 1) return BGK_OK;
+  h->refine_delta = h->has_walls || h->lagged != 0;
   const size_t ncf = (size_t)h->g.dim * h->g.N * h->nnode;
   const size_t nfb = (size_t)h->g.nv * h->hm.nbface * h->hm.fd;
   int rc = BGK_OK;
@@ -567,6 +594,7 @@ int build_refine(bgk_handle* h) {
   A(dalloc(h->d32, ncf * sizeof(float)));
   A(dalloc(h->cf_zero32, ncf * sizeof(float)));
   A(dalloc(h->fbc_zero32, std::max<size_t>(1, nfb) * sizeof(float)));
+  if (h->refine_delta) A(dalloc(h->f_save, h->nfv * sizeof(double)));
   if (rc != BGK_OK) return rc;
   CK(cudaMemsetAsync(h->cf_zero32, 0, ncf * sizeof(float), h->stream));
   CK(cudaMemsetAsync(h->fbc_zero32, 0, std::max<size_t>(1, nfb) * sizeof(float), h->stream));
@@ -724,11 +752,13 @@ int enqueue_step(bgk_handle* h, int mode_bdf2, cudaGraphExec_t* exec_out) {
       CK(cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, nullptr, nullptr, nullptr));
       cudaGraphConditionalHandle cond;
       CK(cudaGraphConditionalHandleCreate(&cond, cg, 1, cudaGraphCondAssignDefault));
+      refine_save(h);
       int rc = build_src(h, qsrc, qscale, nus);
       if (rc != BGK_OK) return rc;
       launch_sweep_any(h, nus);
       moments(h, 1);
       k_finalize<<<1, 256, 0, s>>>(h->ds, h->partial, h->mom_blocks, tol, h->cfg.l_max, st, cond, 1);
+      refine_delta0(h);
       const cudaGraphNode_t* deps = nullptr;
       size_t ndeps = 0;
       CK(cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, &deps, nullptr, &ndeps));
@@ -796,11 +826,13 @@ int enqueue_step(bgk_handle* h, int mode_bdf2, cudaGraphExec_t* exec_out) {
           int rc = refine_iteration(h, nus, tol, st, 0, 0);
           if (rc != BGK_OK) return rc;
         } else {
+          if (h->refine) refine_save(h);
           int rc = build_src(h, qsrc, qscale, nus);
           if (rc != BGK_OK) return rc;
           launch_sweep_any(h, nus);
           moments(h, 1);
           k_finalize<<<1, 256, 0, s>>>(h->ds, h->partial, h->mom_blocks, tol, h->cfg.l_max, st, 0, 0);
+          if (h->refine) refine_delta0(h);
         }
         CK(cudaGetLastError());
         DevState d;
@@ -1034,7 +1066,7 @@ void release(bgk_handle* h) {
   if (h->exec_main) cudaGraphExecDestroy(h->exec_main);
   if (h->exec_start) cudaGraphExecDestroy(h->exec_start);
   void* ptrs[] = {h->gX, h->gY, h->Uhist, h->have_hist, h->geof, h->wall, h->cf_prev, h->c32, h->d32,
-                  h->cf_zero32, h->fbc_zero32,
+                  h->cf_zero32, h->fbc_zero32, h->f_save,
                   h->geo, h->nbr, h->nbr_face, h->perm, h->bnode, h->glist, h->lvl, h->ngen, h->nproc, h->Ainv,
                   h->fslots, h->f, h->fk,
                   h->fprev, h->src, h->fbc, h->q, h->F[0], h->F[1], h->F[2], h->U[0], h->U[1], h->partial, h->cf,
