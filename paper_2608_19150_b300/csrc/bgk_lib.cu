@@ -728,14 +728,21 @@ int enqueue_step(bgk_handle* h, int mode_bdf2, cudaGraphExec_t* exec_out) {
     }
     k_stage_begin<<<1, 1, 0, s>>>(h->ds, st);
     // with an FP32 phase to follow (and no guess to change f first), the moment pass also
-    // writes the FP32 copy of f that the phase starts from
+    // writes the FP32 copy of f that the phase starts from; after the first stage the
+    // moments of f are already in U[it & 1] (the previous stage's last moment pass), so
+    // only the copy is made
     const bool f_ready = h->shadow && !h->guess;
-    if (f_ready)
+    if (st > 0 && !h->guess) {
+      if (f_ready)
+        k_convert_gated<double, float><<<148 * 8, 256, 0, s>>>(h->nfv, (const double*)h->f, (float*)h->shadow->f,
+                                                               nullptr);
+    } else if (f_ready) {
       k_moments<double><<<h->mom_blocks, 128, 0, s>>>(h->g, (const double*)h->f, h->nnode, h->U[0], h->U[1], h->ds, 0,
                                                       h->partial, nullptr, h->phys.nu, h->phys.collision,
                                                       h->shadow->f, nullptr, 0);
-    else
+    } else {
       moments(h, 0);
+    }
     if (h->guess) {
       int rg = guess_hook(h);
       if (rg != BGK_OK) return rg;
