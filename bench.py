@@ -402,7 +402,7 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def launches_per_step(st, guess=False, main_fp32=False, walls=False, refine=False, bdf2=False):
+def launches_per_step(st, guess=False, main_fp32=False, walls=False, refine=False, bdf2=False, mixed=False):
     """Kernels one step launches (graph nodes of kernel type), from its statistics.  FP32
     sweeps form their source themselves (factors, sweep, moments, test per iteration);
     FP64 iterations add the source pass; walls add their refresh to every iteration.  The
@@ -411,11 +411,16 @@ def launches_per_step(st, guess=False, main_fp32=False, walls=False, refine=Fals
     stage-start moment pass and the stage combine do not already write (with a guess
     changing f first).  refine: the FP64 iterations after the first of a stage are
     corrections (factors, factor change, source change, FP32 sweep, update with moments,
-    test)."""
+    test).  A stage after the first reuses the moments the previous one left (no moment
+    pass; the mixed precision converts f for its FP32 phase only when walls read it)."""
     n = 1
     per_main = (4 if main_fp32 else 5) + bool(walls)
     for k in range(st.n_stages):
-        n += 2 + (k > 0) + (k < st.n_stages - 1)          # stage set-up, moments, stage combines
+        if k == 0 or guess:
+            n += 2                                         # stage set-up, moments
+        else:
+            n += 1 + (1 if (mixed and walls) else 0)       # stage set-up, the FP32 copy of f
+        n += (k > 0) + (k < st.n_stages - 1)               # stage combines
         n += 9 if guess else 0
         if st.iterations_fp32[k]:
             conv = (1 + (0 if (bdf2 or k > 0) else 1)) if guess else 0
@@ -426,7 +431,7 @@ def launches_per_step(st, guess=False, main_fp32=False, walls=False, refine=Fals
 
 
 def timed_steps(s, steps, world, local, tstream, guess=False, main_fp32=False, walls=False, restore=None,
-                refine=False):
+                refine=False, mixed=False):
     """Run `steps` steps of solver s (already warmed up; created on torch stream tstream),
     each bracketed by CUDA events on that stream; the time is the sum of the steps'
     device times (the statistics read between steps is not inside any bracket).
@@ -453,7 +458,7 @@ def timed_steps(s, steps, world, local, tstream, guess=False, main_fp32=False, w
         e1.synchronize()
         el += e0.elapsed_time(e1) * 1e-3
         iters.append({"fp64": list(st.iterations)[:st.n_stages], "fp32": list(st.iterations_fp32)[:st.n_stages]})
-        launches += launches_per_step(st, guess, main_fp32, walls, refine)
+        launches += launches_per_step(st, guess, main_fp32, walls, refine, mixed=mixed)
     s.synchronize()
     torch.cuda.synchronize()
     barrier(world)
@@ -610,7 +615,8 @@ def run_ours(args):
     refine = s.refine_active
     el_max, sweeps, iters, launches, clk = timed_steps(s, args.steps, world, local, tstream,
                                                        main_fp32=args.precision == "fp32", walls=bool(walls),
-                                                       restore=restore_main, refine=refine)
+                                                       restore=restore_main, refine=refine,
+                                                       mixed=args.precision == "mixed")
     value = job_throughput(dof * sweeps, el_max, world)
     f_end, U_end = s.get_f(np.float64), s.get_moments()
     # end to end through the C ABI with host buffers: every step's f^k comes in from pinned

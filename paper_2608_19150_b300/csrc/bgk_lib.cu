@@ -606,19 +606,23 @@ int build_refine(bgk_handle* h) {
 // Mixed precision, at a stage start (main moments already in U): FP32 sweeps on the
 // shadow until the FP32 floor (or the main tolerance), then the FP64 state takes the
 // FP32 result (unless that phase failed) and its moments are recomputed.
-// f_ready: the stage's moment pass already wrote the FP32 copy of f into the shadow;
-// q_ready: the stage source's producer already wrote its FP32 copy (sh->fk).
+// f_ready: the shadow's f holds what the FP32 phase needs (the FP32 copy of f, written by
+// the stage's moment pass, or nothing when its sweeps do not read the iterate they
+// overwrite: no walls, no lagged edges); q_ready: the shadow's fk holds the FP32 copy of
+// the stage source; f_copy: the shadow's f is the FP32 copy of f.
 int shadow_phase(bgk_handle* h, int st, const void* qsrc, double qscale, double nus, double tol, bool capture,
-                 bool f_ready, bool q_ready) {
+                 bool f_ready, bool q_ready, bool f_copy) {
   bgk_handle* sh = h->shadow;
   cudaStream_t s = h->stream;
   const int thr = 256, blk = 148 * 8;
   k_reset_state<<<1, 1, 0, s>>>(sh->ds);
   k_stage_begin<<<1, 1, 0, s>>>(sh->ds, st);
-  if (!f_ready)
+  if (!f_ready) {
     k_convert_gated<double, float><<<blk, thr, 0, s>>>(h->nfv, (const double*)h->f, (float*)sh->f, nullptr);
+    f_copy = true;
+  }
   if (q_ready) {
-  } else if (f_ready && qsrc == h->fk && st == 0) {
+  } else if (f_copy && qsrc == h->fk && st == 0 && !h->guess) {
     // the first stage's q is f^k, equal to this stage's f: its FP32 copy too
     CK(cudaMemcpyAsync(sh->fk, sh->f, h->nfv * sizeof(float), cudaMemcpyDeviceToDevice, s));
   } else {
@@ -735,15 +739,27 @@ int enqueue_step(bgk_handle* h, int mode_bdf2, cudaGraphExec_t* exec_out) {
     // writes the FP32 copy of f that the phase starts from; after the first stage the
     // moments of f are already in U[it & 1] (the previous stage's last moment pass), so
     // only the copy is made
-    const bool f_ready = h->shadow && !h->guess;
+    // Sweeps read the iterate they overwrite only through walls and lagged edges; without
+    // those the FP32 phase needs no copy of f, and the first stage's moment pass writes the
+    // FP32 copy of q = f^k directly.
+    const bool mixed = h->shadow && !h->guess;
+    const bool f_read = h->has_walls || h->lagged != 0;
+    bool f_ready = false, f_copy = false, q_ready = qsrc == h->q;
     if (st > 0 && !h->guess) {
-      if (f_ready)
+      if (mixed && f_read)
         k_convert_gated<double, float><<<148 * 8, 256, 0, s>>>(h->nfv, (const double*)h->f, (float*)h->shadow->f,
                                                                nullptr);
-    } else if (f_ready) {
+      f_ready = mixed;
+      f_copy = mixed && f_read;
+    } else if (mixed) {
+      const bool q_direct = !f_read && qsrc == h->fk;
+      void* conv = f_read ? h->shadow->f : q_direct ? h->shadow->fk : nullptr;
       k_moments<double><<<h->mom_blocks, 128, 0, s>>>(h->g, (const double*)h->f, h->nnode, h->U[0], h->U[1], h->ds, 0,
-                                                      h->partial, nullptr, h->phys.nu, h->phys.collision,
-                                                      h->shadow->f, nullptr, 0);
+                                                      h->partial, nullptr, h->phys.nu, h->phys.collision, conv,
+                                                      nullptr, 0);
+      f_ready = true;
+      f_copy = f_read;
+      q_ready = q_ready || q_direct;
     } else {
       moments(h, 0);
     }
@@ -752,7 +768,7 @@ int enqueue_step(bgk_handle* h, int mode_bdf2, cudaGraphExec_t* exec_out) {
       if (rg != BGK_OK) return rg;
     }
     if (h->shadow) {
-      int rs = shadow_phase(h, st, qsrc, qscale, nus, tol, capture, f_ready, qsrc == h->q);
+      int rs = shadow_phase(h, st, qsrc, qscale, nus, tol, capture, f_ready, q_ready, f_copy);
       if (rs != BGK_OK) return rs;
     }
     if (capture && h->refine) {
