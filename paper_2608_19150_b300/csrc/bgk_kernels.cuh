@@ -1300,6 +1300,13 @@ struct SweepItem {
   T c1[FUSED ? E::NDOF : 1], c2[FUSED ? E::NDOF : 1], c3[(FUSED && E::D == 3) ? E::NDOF : 1];
 };
 
+// Values per cell of the geometry rows (face normals N_i, 1/|K|, padding): the layout of
+// the host set-up, checked when a handle is created.
+template <class E>
+__host__ __device__ constexpr int geo_stride() {
+  return E::D == 3 ? 16 : (E::NF == 4 ? 10 : 8);
+}
+
 // Source of one sweep launch: src = nu M^l + qscale q precomputed (src), or its factors
 // (FUSED: cf[a][m][node] of k_factors, q and qscale).
 template <typename T>
@@ -1374,6 +1381,31 @@ __device__ __forceinline__ void load_vec(const T* __restrict__ p, T (&v)[N]) {
   }
 }
 
+// Read-only global data (not written while the kernel runs) in 256-bit loads when p is
+// 32-byte aligned and the size a multiple of 32 bytes (sm_100 and later); otherwise as
+// load_vec.  A warp's scattered loads cost one L1 wavefront per distinct line and
+// instruction: a cell's data in half as many instructions.
+template <typename T, int N, int ALIGN>
+__device__ __forceinline__ void load_ro(const T* __restrict__ p, T (&v)[N]) {
+  constexpr int BYTES = N * (int)sizeof(T);
+  if constexpr (ALIGN % 32 == 0 && BYTES % 32 == 0 && sizeof(T) == 4) {
+#pragma unroll
+    for (int q = 0; q < N / 8; ++q)
+      asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+          : "=f"(v[8 * q]), "=f"(v[8 * q + 1]), "=f"(v[8 * q + 2]), "=f"(v[8 * q + 3]), "=f"(v[8 * q + 4]),
+            "=f"(v[8 * q + 5]), "=f"(v[8 * q + 6]), "=f"(v[8 * q + 7])
+          : "l"(p + 8 * q));
+  } else if constexpr (ALIGN % 32 == 0 && BYTES % 32 == 0 && sizeof(T) == 8) {
+#pragma unroll
+    for (int q = 0; q < N / 4; ++q)
+      asm("ld.global.nc.v4.f64 {%0,%1,%2,%3}, [%4];"
+          : "=d"(v[4 * q]), "=d"(v[4 * q + 1]), "=d"(v[4 * q + 2]), "=d"(v[4 * q + 3])
+          : "l"(p + 4 * q));
+  } else {
+    load_vec<T, N, ALIGN>(p, v);
+  }
+}
+
 // alignment in bytes of a cell's node values (cell * NDOF * sizeof(T) from a 256-byte
 // aligned array whose ordinate rows are NDOF * n_cells values long)
 template <class E, typename T>
@@ -1398,9 +1430,13 @@ __device__ __forceinline__ void fetch_item_e(const SweepArgs& sa, uint32_t e, co
     if constexpr (E::D == 3) load_vec<T, E::NDOF, AL>(rw.c3 + o, it.c3);
   }
   if constexpr (REG) {
-    const float* Gc = sa.geof + (size_t)c * sa.gs;
+    // the cell's whole geometry row (padding included) in the widest aligned vector loads:
+    // a warp's scattered loads cost one L1 wavefront per distinct line and instruction
+    constexpr int GS = geo_stride<E>(), GA = (GS * 4) % 32 == 0 ? 32 : (GS * 4) % 16 == 0 ? 16 : 8;
+    float gr[GS];
+    load_ro<float, GS, GA>(sa.geof + (size_t)c * GS, gr);
 #pragma unroll
-    for (int q = 0; q <= E::NF * E::D; ++q) it.geo[q] = Gc[q];
+    for (int q = 0; q <= E::NF * E::D; ++q) it.geo[q] = gr[q];
   }
 }
 
@@ -1480,8 +1516,31 @@ __device__ __forceinline__ void inverse_product_pair_r(const float (&Ah)[S], con
 }
 template <int S>
 __device__ __forceinline__ void load_inverse_pair(const float* __restrict__ Ap, float (&Ah)[S], float (&Al)[S]) {
-  load_vec<float, S, 16>(Ap, Ah);
-  load_vec<float, S, (S % 4 == 0 ? 16 : 8)>(Ap + S, Al);
+  if constexpr (S % 8 == 4) {
+    // 32-byte aligned inverses of 2 S floats (S = 8 m + 4): hi = m 32-byte loads and a
+    // 16-byte tail; lo = a 16-byte head, then m 32-byte loads from a 32-byte boundary
+    float h1[S - 4], t1[4], t2[4], l2[S - 4];
+    load_ro<float, S - 4, 32>(Ap, h1);
+    load_vec<float, 4, 16>(Ap + S - 4, t1);
+    load_vec<float, 4, 16>(Ap + S, t2);
+    load_ro<float, S - 4, 32>(Ap + S + 4, l2);
+#pragma unroll
+    for (int q = 0; q < S - 4; ++q) {
+      Ah[q] = h1[q];
+      Al[4 + q] = l2[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      Ah[S - 4 + q] = t1[q];
+      Al[q] = t2[q];
+    }
+  } else if constexpr (S % 8 == 0) {
+    load_ro<float, S, 32>(Ap, Ah);
+    load_ro<float, S, 32>(Ap + S, Al);
+  } else {
+    load_vec<float, S, 16>(Ap, Ah);
+    load_vec<float, S, (S % 4 == 0 ? 16 : 8)>(Ap + S, Al);
+  }
 }
 template <int ND, int S>
 __device__ __forceinline__ void inverse_product_pair(const float* __restrict__ Ap, const fpair (&b)[ND],
@@ -1940,6 +1999,29 @@ __device__ __forceinline__ void store_vec(T* __restrict__ p, const T (&v)[N]) {
   }
 }
 
+// One cell's N floats of an FP32 node row at p (N = 3: 4-byte aligned; N = 6: 8-byte
+// aligned; otherwise 16-byte aligned) in at most two vector stores: the split between a
+// 16-byte and an 8-byte part (N = 6) or an 8-byte and a 4-byte part (N = 3) follows the
+// address.  A warp's scattered stores cost one L1 wavefront per distinct line and
+// instruction.  (The same split for the loads measured slower: its selects cost more than
+// the wavefronts they save.)
+template <int N>
+__device__ __forceinline__ void store_cell_f32(float* __restrict__ p, const float (&v)[N]) {
+  if constexpr (N == 6) {
+    const bool odd = (reinterpret_cast<uintptr_t>(p) & 15u) != 0;
+    *reinterpret_cast<float4*>(p + (odd ? 2 : 0)) =
+        odd ? make_float4(v[2], v[3], v[4], v[5]) : make_float4(v[0], v[1], v[2], v[3]);
+    *reinterpret_cast<float2*>(p + (odd ? 0 : 4)) = odd ? make_float2(v[0], v[1]) : make_float2(v[4], v[5]);
+  } else if constexpr (N == 3) {
+    const bool odd = (reinterpret_cast<uintptr_t>(p) & 7u) != 0;
+    *reinterpret_cast<float2*>(p + (odd ? 1 : 0)) = odd ? make_float2(v[1], v[2]) : make_float2(v[0], v[1]);
+    p[odd ? 0 : 2] = odd ? v[0] : v[2];
+  } else {
+    static_assert((N * 4) % 16 == 0, "16-byte cells");
+    store_vec<float, N, 16>(p, v);
+  }
+}
+
 // FP32 generation sweep with the shared-memory front (one CTA per ordinate, the same
 // operations per cell as sweep_ordinate with the fused source): Sec. 4, Eq. bgk-ss-picard,
 //   (nu_s Mh + sum_i r_i (Dd_i + [s_i>0] Eh_i)) f_K = Mh src_K + sum_{s_i<0} (-r_i) Eh_i y_i,
@@ -2054,7 +2136,7 @@ __global__ void __launch_bounds__(128, 4) k_sweep_front(SweepArgs sa, VGrid g, f
       T A[ND][ND];
       E::assemble(nus, r, outm, A);
       lu_solve<ND, T>(A, b);
-      store_vec<T, ND, cell_align<E, T>()>(fj + c * ND, b);
+      store_cell_f32<ND>(fj + c * ND, b);
       // this cell's traces on its outflow faces, in its own face order, for the readers
 #pragma unroll
       for (int i = 0; i < NF; ++i) {

@@ -1186,6 +1186,16 @@ int bgk_create(const bgk_mesh* mesh, const bgk_vgrid* vg, const bgk_physics* phy
   h->nnode = h->hm.ncell * h->hm.ndof;
   h->nm = h->hm.dim + 2;
   h->nfv = (size_t)h->g.nv * h->nnode;
+  {
+    // the sweeps read the geometry rows with the element's compile-time stride
+    const int gs = h->hm.dim == 3 ? geo_stride<ElemP1Tet>()
+                   : h->hm.quad   ? geo_stride<ElemQ1Quad>()
+                                  : geo_stride<ElemP1Tri>();
+    if (h->hm.geo_stride != gs) {
+      delete h;
+      return BGK_E_INVALID;
+    }
+  }
   if (h->cfg.stream) {
     h->stream = (cudaStream_t)h->cfg.stream;
   } else {
