@@ -318,10 +318,10 @@ __device__ __forceinline__ void node_factors(const VGrid& g, int kind, const Nod
 
 // ---------------------------------------------------------------------------------
 // Inner moment sums over the last velocity dimension: S_k = sum_m W_k[m] f_m with
-// W = (w, w x, w x^2).  FP64 data: FP64 fused multiply-adds.  FP32 data: the
-// compensated dot product of Ogita, Rump and Oishi (2005) in FP32 (error-free
-// TwoProduct by fma and TwoSum), with each FP64 weight split into two floats, so the
-// sums carry about 48 significant bits -- FP64 accuracy at FP32 instruction rate.
+// W = (w, w x, w x^2), by the compensated dot product of Ogita, Rump and Oishi (2005) in
+// FP32 (error-free TwoProduct by fma and TwoSum), with each FP64 weight split into two
+// floats (and FP64 data into float pairs), so the sums carry about 48 significant bits --
+// FP64 accuracy at FP32 instruction rate.
 template <typename T>
 struct InnerSums;
 
@@ -452,6 +452,7 @@ struct InnerSums<float> {
     }
   }
   __device__ __forceinline__ double get(int k) const { return (double)hi[k] + (double)lo[k]; }
+  __device__ __forceinline__ fpair pair(int k) const { return fpair(hi[k], lo[k]); }
 };
 
 template <>
@@ -463,6 +464,26 @@ struct InnerSums<double> {
     S.add2(g, m, fh, fl);
   }
   __device__ __forceinline__ double get(int k) const { return S.get(k); }
+  __device__ __forceinline__ fpair pair(int k) const { return S.pair(k); }
+};
+
+// The outer levels of the moment sums in the same compensated FP32 arithmetic: acc +=
+// (wh + wl) s for a weight pair (the grid's float pairs of w, w x, w x^2, optionally
+// halved, which is exact) and a partial sum s carried as an unevaluated pair -- TwoProduct
+// and TwoSum with every error term gathered in lo, as in the inner sums, so no FP64
+// instruction runs per velocity point (B300 issues FP64 at a small fraction of FP32).
+struct MomAcc {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float wh, float wl, fpair v) {
+    const float p = wh * v.h;
+    const float ep = fmaf(wh, v.h, -p) + fmaf(wh, v.l, wl * v.h);
+    const float t = hi + p;
+    const float z = t - hi;
+    lo += ((hi - (t - z)) + (p - z)) + ep;
+    hi = t;
+  }
+  __device__ __forceinline__ fpair pair() const { return fpair(hi, lo); }
+  __device__ __forceinline__ double get() const { return (double)hi + (double)lo; }
 };
 
 // Velocity moments U_i = sum_j w_j (1, v_j, |v_j|^2/2) f_{j,i} (Eq. moments), FP64
@@ -511,6 +532,7 @@ __global__ void __launch_bounds__(128) k_moments(VGrid g, const T* __restrict__ 
   const int nm = g.dim + 2;
   const int ja = part * g.N / PARTS, jb = (part + 1) * g.N / PARTS;
   double acc[5] = {0, 0, 0, 0, 0};
+  MomAcc A[5];
   if (i < nnode) {
     if (g.dim == 2) {
       for (int j0 = ja; j0 < jb; ++j0) {
@@ -548,16 +570,17 @@ __global__ void __launch_bounds__(128) k_moments(VGrid g, const T* __restrict__ 
           }
           if (j1 < g.N) S.add(g, j1, fr[(size_t)j1 * nnode]);
         }
-        const double s0 = S.get(0) + S2.get(0), s1 = S.get(1) + S2.get(1), s2 = S.get(2) + S2.get(2);
-        const double w0 = g.w[j0], x0 = g.x[j0];
-        acc[0] += w0 * s0;
-        acc[1] += w0 * x0 * s0;
-        acc[2] += w0 * s1;
-        acc[3] += 0.5 * w0 * (x0 * x0 * s0 + s2);
+        const fpair s0 = S.pair(0) + S2.pair(0), s1 = S.pair(1) + S2.pair(1), s2 = S.pair(2) + S2.pair(2);
+        // acc += w0 (s0, x0 s0, s1, (x0^2 s0 + s2) / 2)
+        A[0].add(g.wh[0][j0], g.wl[0][j0], s0);
+        A[1].add(g.wh[1][j0], g.wl[1][j0], s0);
+        A[2].add(g.wh[0][j0], g.wl[0][j0], s1);
+        A[3].add(0.5f * g.wh[2][j0], 0.5f * g.wl[2][j0], s0);
+        A[3].add(0.5f * g.wh[0][j0], 0.5f * g.wl[0][j0], s2);
       }
     } else {
       for (int j0 = ja; j0 < jb; ++j0) {
-        double t0 = 0, t1 = 0, t2 = 0, t3 = 0;
+        MomAcc t[4];
         for (int j1 = 0; j1 < g.N; ++j1) {
           InnerSums<T> S;
           const size_t o1 = ((size_t)j0 * g.N + j1) * g.N * nnode + i;
@@ -583,21 +606,26 @@ __global__ void __launch_bounds__(128) k_moments(VGrid g, const T* __restrict__ 
 #pragma unroll 8
             for (int j2 = 0; j2 < g.N; ++j2) S.add(g, j2, fr[(size_t)j2 * nnode]);
           }
-          const double s0 = S.get(0), s1 = S.get(1), s2 = S.get(2);
-          const double w1 = g.w[j1], x1 = g.x[j1];
-          t0 += w1 * s0;
-          t1 += w1 * x1 * s0;
-          t2 += w1 * s1;
-          t3 += w1 * (x1 * x1 * s0 + s2);
+          const fpair s0 = S.pair(0), s1 = S.pair(1), s2 = S.pair(2);
+          // t += w1 (s0, x1 s0, s1, x1^2 s0 + s2)
+          t[0].add(g.wh[0][j1], g.wl[0][j1], s0);
+          t[1].add(g.wh[1][j1], g.wl[1][j1], s0);
+          t[2].add(g.wh[0][j1], g.wl[0][j1], s1);
+          t[3].add(g.wh[2][j1], g.wl[2][j1], s0);
+          t[3].add(g.wh[0][j1], g.wl[0][j1], s2);
         }
-        const double w0 = g.w[j0], x0 = g.x[j0];
-        acc[0] += w0 * t0;
-        acc[1] += w0 * x0 * t0;
-        acc[2] += w0 * t1;
-        acc[3] += w0 * t2;
-        acc[4] += 0.5 * w0 * (x0 * x0 * t0 + t3);
+        // acc += w0 (t0, x0 t0, t1, t2, (x0^2 t0 + t3) / 2)
+        const fpair t0 = t[0].pair(), t1 = t[1].pair(), t2 = t[2].pair(), t3 = t[3].pair();
+        A[0].add(g.wh[0][j0], g.wl[0][j0], t0);
+        A[1].add(g.wh[1][j0], g.wl[1][j0], t0);
+        A[2].add(g.wh[0][j0], g.wl[0][j0], t1);
+        A[3].add(g.wh[0][j0], g.wl[0][j0], t2);
+        A[4].add(0.5f * g.wh[2][j0], 0.5f * g.wl[2][j0], t0);
+        A[4].add(0.5f * g.wh[0][j0], 0.5f * g.wl[0][j0], t3);
       }
     }
+#pragma unroll
+    for (int m = 0; m < 5; ++m) acc[m] = A[m].get();
   }
   if constexpr (PARTS > 1) {
     __shared__ double accp[PARTS][5][NPB];
