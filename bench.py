@@ -472,10 +472,8 @@ def timed_steps(s, steps, world, local, tstream, guess=False, main_fp32=False, w
 # of the n x n workload moves (n / 64)^2 times as much (traffic grows with the cells).
 PROFILED_TRAFFIC = {
     "fp64": (3.750e9, "profiles/sweep_fp64_cached_shock_tube_64_p2_v32.md"),
-    "fp64_pairs": (3.751e9, "profiles/sweep_pair_fp64_shock_tube_64_p2_v32.md"),
-    "fp64_pairs_front": (3.410e9, "profiles/sweep_front_pair_fp64_shock_tube_64_p2_v32.md"),
-    "fp32": (0.631e9, "profiles/sweep_fp32_fused_shock_tube_64_p2_v32.md"),
-    "fp32_front": (0.535e9, "profiles/sweep_front_fp32_shock_tube_64_p2_v32.md"),
+    "fp64_pairs_front": (3.409e9, "profiles/sweep_front_pair_fp64_shock_tube_64_p2_v32.md"),
+    "fp32_front": (0.528e9, "profiles/sweep_front_fp32_shock_tube_64_p2_v32.md"),
 }
 
 
