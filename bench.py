@@ -64,6 +64,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cache", default="auto", choices=["auto", "on", "off"],
                    help="local-inverse cache of the sweep")
+    p.add_argument("--stage-predictor", action="store_true",
+                   help="start each DIRK stage after the first from moments extrapolated across the stage "
+                        "abscissae (both arms; off: the previous stage's moments, the paper's iteration)")
     p.add_argument("--eager", action="store_true",
                    help="launch each step's kernels from a host loop instead of one CUDA graph (profiling)")
     a = p.parse_args()
@@ -580,7 +583,7 @@ def run_ours(args):
     walls = WALL_SETS[args.walls] or w.walls
     s = bgk.Solver.from_workload(w, precision=args.precision, eager=args.eager, cache_inverse=args.cache,
                                  stream=tstream.cuda_stream, sweep_mode=args.sweep_mode, walls=walls,
-                                 collision=args.collision)
+                                 collision=args.collision, stage_predictor=args.stage_predictor)
     s.set_state_maxwellian(w.init)
     s.set_inflow_maxwellian(w.inflow)
     tune = s.autotune_sweep(2) if args.sweep_mode == "auto" else None   # untimed set-up
@@ -646,7 +649,7 @@ def run_ours(args):
     plain = None
     if args.precision != "fp64":
         p = bgk.Solver.from_workload(w, precision="fp64", stream=tstream.cuda_stream, sweep_mode=args.sweep_mode,
-                                     walls=walls, collision=args.collision)
+                                     walls=walls, collision=args.collision, stage_predictor=args.stage_predictor)
         f_in64 = f_in.to(torch.float64)
         p.set_f_device(f_in64.data_ptr(), np.float64)
         p.set_inflow_maxwellian(w.inflow)
@@ -706,8 +709,11 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp64": "f64", "fp32": "f32", "mixed": "f32 sweeps then f64 (mixed)"}[args.precision],
             "data": "synthetic",
-            "config": config(w, args, {"step_input": "the state after %d steps from the initial state, restored "
-                                                     "before every step outside the timed region" % pre}),
+            "config": config(w, args, dict({"step_input": "the state after %d steps from the initial state, "
+                                                          "restored before every step outside the timed region" % pre},
+                                           **({"stage_predictor": "stages after the first start from moments "
+                                                                  "extrapolated across the stage abscissae (both arms)"}
+                                              if args.stage_predictor else {}))),
             "roofline": roofline, "rooflines": rl,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "picard_iterations": iters, "sweeps_timed": sweeps, "dt": dt,

@@ -143,6 +143,15 @@ typedef struct {
                          are zero (exact in exact arithmetic: the iterate just swept satisfies
                          the sweep's equations, so the next sweep differs from it only through
                          these changes); 1 = every FP64-phase iteration a full sweep */
+  int stage_predictor; /* multi-stage DIRK steps: 1 = each stage after the first starts its
+                         Picard iteration from moments extrapolated across the stage
+                         abscissae (U_k + dt sum_r A_sr G_r + dt A_ss G_{s-1}, G_r the moment
+                         rate the earlier stages imply; the collision term conserves the
+                         moments, so they move by transport only) instead of the previous
+                         stage's moments; a node whose extrapolated density or temperature is
+                         not positive keeps the previous stage's moments.  Changes where the
+                         iteration starts, not its fixed point; 0 = off (the previous stage's
+                         moments, as the paper's iteration) */
 } bgk_config;
 
 typedef struct {

@@ -55,7 +55,7 @@ class Config(C.Structure):
                 ("stream", C.c_void_p), ("eager", C.c_int),
                 ("cache_inverse", C.c_int), ("fp32_floor", C.c_double), ("prefetch", C.c_int),
                 ("sweep_mode", C.c_int), ("sweep_front", C.c_int), ("hp_sweep", C.c_int),
-                ("refine", C.c_int)]
+                ("refine", C.c_int), ("stage_predictor", C.c_int)]
 
 SWEEP_MODES = {"auto": 0, "tgs": 1, "ts": 2}
 # arithmetic of FP64-data sweeps with cached local inverses (bgk_config.hp_sweep): automatic
@@ -202,7 +202,7 @@ class Solver:
     def __init__(self, dim, kx, xyz, cells, n_v, k_v, L, nu, integrator="BE", dt=0.0, cfl=10.0, tau=1e-8,
                  l_max=1000, precision="fp64", block_threads=0, stream=None, eager=False, cache_inverse="auto", fp32_floor=0.0, prefetch=False,
                  sweep_mode="auto", collision="maxwellian", walls=None, sweep_front=True,
-                 hp_sweep="auto", refine=True):
+                 hp_sweep="auto", refine=True, stage_predictor=False):
         self.lib = load()
         self._xyz = np.ascontiguousarray(xyz, dtype=np.float64)
         self._cells = np.ascontiguousarray(cells, dtype=np.int32)
@@ -215,7 +215,7 @@ class Solver:
                     C.c_void_p(stream) if stream else None, int(bool(eager)),
                     {"auto": 0, "on": 1, "off": 2}[cache_inverse], float(fp32_floor), 1 if prefetch else 0,
                     SWEEP_MODES[sweep_mode], 0 if sweep_front else 2, HP_SWEEPS[hp_sweep],
-                    0 if refine else 1)
+                    0 if refine else 1, 1 if stage_predictor else 0)
         h = C.c_void_p()
         _ck(self.lib.bgk_create(C.byref(m), C.byref(vg), C.byref(ph), C.byref(cf), C.byref(h)), "bgk_create")
         self.h = h

@@ -2372,6 +2372,44 @@ __global__ void k_copy_moments(size_t n, const double* __restrict__ A0, const do
     B[i] = A[i];
 }
 
+// Stage predictor (bgk_config.stage_predictor).  dst <- the current moments U[it & 1].
+__global__ void k_save_moments(size_t n, const DevState* __restrict__ ds, const double* __restrict__ U0,
+                               const double* __restrict__ U1, double* __restrict__ dst) {
+  if (ds->status != BGK_OK) return;
+  const double* U = (ds->it & 1) == 0 ? U0 : U1;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = U[i];
+}
+// The moments a stage starts from: U[it & 1] <- wk Uk + w0 S0 + w1 S1 per node (Uk the
+// moments of f^k, S0 and S1 those the first two stages ended with; S1 unused when w1 = 0),
+// where the result is physical (n > 0, theta > 0, finite); elsewhere the current moments
+// (the previous stage's) stay.  The factors built from the old moments go stale.
+__global__ void k_predict_moments(int nnode, int dim, DevState* ds, double* U0, double* U1,
+                                  const double* __restrict__ Uk, const double* __restrict__ S0,
+                                  const double* __restrict__ S1, double wk, double w0, double w1) {
+  if (ds->status != BGK_OK) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) ds->cf_fresh = 0;
+  double* U = (ds->it & 1) == 0 ? U0 : U1;
+  const int nm = dim + 2;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nnode; i += gridDim.x * blockDim.x) {
+    double v[5];
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+      if (m >= nm) break;
+      const size_t o = (size_t)i * nm + m;
+      double x = wk * Uk[o] + w0 * S0[o];
+      if (w1 != 0.0) x += w1 * S1[o];
+      v[m] = x;
+    }
+    const double n = v[0];
+    double u2 = 0.0;
+    for (int a = 0; a < dim; ++a) u2 += (v[1 + a] / n) * (v[1 + a] / n);
+    const double th = (2.0 * v[nm - 1] / n - u2) / dim;
+    if (!(n > 0.0) || !(th > 0.0) || !isfinite(n) || !isfinite(th)) continue;
+    for (int m = 0; m < nm; ++m) U[(size_t)i * nm + m] = v[m];
+  }
+}
+
 // Record the FP32 phase's iteration count of stage st in the main state.
 __global__ void k_record_fp32(const DevState* __restrict__ sh, DevState* main, int st) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {

@@ -55,14 +55,18 @@ struct bgk_handle {
   void* Ainv = nullptr;      // cached local inverses (schedule order), valid for nus_cached
   bool ainv_pairs = false;   // the FP64 cache holds float pairs (float-pair sweeps, k_sweep_pair)
   bool front_pairs = false;  // the front (fslots) serves the float-pair sweep (k_sweep_front_pair)
-  // Picard refinement of the mixed precision (bgk_config.refine): factors of the previous
-  // iterate, the new factors and their change as floats, zero factors and boundary data
-  // for the correction sweeps
   // overlapped input (bgk_upload_f_async / bgk_set_f_uploaded)
   void* f_stage = nullptr;
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t ev_uploaded = nullptr, ev_stage_free = nullptr;
   bool upload_pending = false;
+  // stage predictor (bgk_config.stage_predictor): the moments of f^k and of the first two
+  // stages' results
+  double* Ukm = nullptr;
+  double* Ust[2] = {nullptr, nullptr};
+  // Picard refinement of the mixed precision (bgk_config.refine): factors of the previous
+  // iterate, the new factors and their change as floats, zero factors and boundary data
+  // for the correction sweeps
   bool refine = false;
   bool refine_delta = false;  // the corrections read the previous change (walls, lagged edges)
   void* f_save = nullptr;     // the FP64 state before the full sweep when the FP32 phase failed
@@ -684,6 +688,40 @@ int shadow_phase(bgk_handle* h, int st, const void* qsrc, double qscale, double 
   return cudaGetLastError() == cudaSuccess ? BGK_OK : BGK_E_CUDA;
 }
 
+// Stage predictor (bgk_config.stage_predictor).  The moments stage s (s >= 1) starts from,
+// as weights of [U_k, U_0, U_1] (U_k of f^k, U_r of stage r's result): with G_r = dt times
+// the moment rate stage r implies, U_r = U_k + sum_{p<=r} A_rp G_p, the prediction is
+// U_k + sum_{r<s} A_sr G_r + A_ss G_{s-1} (the stage's own rate taken as the previous
+// one's).  The collision term conserves the moments, so this extrapolates transport only.
+// false: no prediction (a stage of zero diagonal weight).
+bool predictor_weights(const double A[3][3], int s, double w[3]) {
+  double G[3][3] = {};
+  for (int r = 0; r < s; ++r) {
+    if (A[r][r] == 0.0) return false;
+    double g[3] = {-1.0, 0.0, 0.0};
+    g[1 + r] += 1.0;
+    for (int p = 0; p < r; ++p)
+      for (int q = 0; q < 3; ++q) g[q] -= A[r][p] * G[p][q];
+    for (int q = 0; q < 3; ++q) G[r][q] = g[q] / A[r][r];
+  }
+  w[0] = 1.0;
+  w[1] = w[2] = 0.0;
+  for (int r = 0; r < s; ++r)
+    for (int q = 0; q < 3; ++q) w[q] += A[s][r] * G[r][q];
+  for (int q = 0; q < 3; ++q) w[q] += A[s][s] * G[s - 1][q];
+  return true;
+}
+
+bool predictor_on(const bgk_handle* h, bool bdf) { return h->Ukm && !bdf && !h->guess; }
+
+int build_predictor(bgk_handle* h) {
+  if (h->cfg.stage_predictor != 1 || h->phys.integrator == BGK_BE || h->phys.integrator == BGK_BDF2) return BGK_OK;
+  const size_t n = (size_t)h->nnode * h->nm * sizeof(double);
+  if (dalloc(h->Ukm, n) != BGK_OK || dalloc(h->Ust[0], n) != BGK_OK || dalloc(h->Ust[1], n) != BGK_OK)
+    return BGK_E_OOM;
+  return BGK_OK;
+}
+
 // One time step: per stage a while-loop over (Maxwellian + source, sweep, moments,
 // convergence test).  With exec_out != nullptr the step is captured as a CUDA graph in
 // which each stage loop is a conditional while-node; with exec_out == nullptr the same
@@ -766,6 +804,16 @@ int enqueue_step(bgk_handle* h, int mode_bdf2, cudaGraphExec_t* exec_out) {
     if (h->guess) {
       int rg = guess_hook(h);
       if (rg != BGK_OK) return rg;
+    }
+    if (predictor_on(h, bdf)) {
+      const size_t nu_ = (size_t)h->nnode * h->nm;
+      double w[3];
+      if (st == 0) {
+        k_save_moments<<<148, 256, 0, s>>>(nu_, h->ds, h->U[0], h->U[1], h->Ukm);
+      } else if (predictor_weights(A, st, w)) {
+        k_predict_moments<<<(h->nnode + 255) / 256, 256, 0, s>>>(h->nnode, h->g.dim, h->ds, h->U[0], h->U[1], h->Ukm,
+                                                                 h->Ust[0], h->Ust[1], w[0], w[1], w[2]);
+      }
     }
     if (h->shadow) {
       int rs = shadow_phase(h, st, qsrc, qscale, nus, tol, capture, f_ready, q_ready, f_copy);
@@ -868,6 +916,8 @@ int enqueue_step(bgk_handle* h, int mode_bdf2, cudaGraphExec_t* exec_out) {
         if (!d.cont) break;
       }
     }
+    if (predictor_on(h, bdf) && st < S - 1 && st < 2)
+      k_save_moments<<<148, 256, 0, s>>>((size_t)h->nnode * h->nm, h->ds, h->U[0], h->U[1], h->Ust[st]);
     // stage derivative F_s = f^(s) / (dt A_ss) - q^(s)   (Eq. dirk-recursive-def)
     if (!bdf && (st < S - 1 || !sa)) {
       if (st == 0)
@@ -1093,6 +1143,7 @@ void release(bgk_handle* h) {
   if (h->exec_main) cudaGraphExecDestroy(h->exec_main);
   if (h->exec_start) cudaGraphExecDestroy(h->exec_start);
   void* ptrs[] = {h->gX, h->gY, h->Uhist, h->have_hist, h->geof, h->wall, h->cf_prev, h->c32, h->d32,
+                  h->Ukm, h->Ust[0], h->Ust[1],
                   h->cf_zero32, h->fbc_zero32, h->f_save,
                   h->geo, h->nbr, h->nbr_face, h->perm, h->bnode, h->glist, h->lvl, h->ngen, h->nproc, h->Ainv,
                   h->fslots, h->f, h->fk,
@@ -1346,6 +1397,7 @@ int bgk_create(const bgk_mesh* mesh, const bgk_vgrid* vg, const bgk_physics* phy
     if (h->cfg.fp32_floor > 0.0) h->fp32_floor = h->cfg.fp32_floor;
     if (rc == BGK_OK) rc = build_refine(h);
   }
+  if (rc == BGK_OK) rc = build_predictor(h);
   if (rc == BGK_OK && !h->cfg.eager) rc = enqueue_step(h, 0, &h->exec_main);
   if (rc == BGK_OK && !h->cfg.eager && phys->integrator == BGK_BDF2) {
     cudaGraphExec_t e0 = h->exec_main;
