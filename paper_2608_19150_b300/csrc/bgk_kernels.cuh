@@ -95,6 +95,12 @@ __device__ __forceinline__ void proj_factors_cells(const VGrid& g, R u, R theta,
   const R sig = sqrt(theta), isig = R(1) / sig;
   const GridVals<R> gv{g};
   const R hh = gv.hh();
+  // the point weights repeat from cell to cell (uniform grid, the same expression per
+  // cell): their reciprocals once per call instead of a division per point (FP64 division
+  // is a multi-instruction sequence on B300's narrow FP64 pipe); the same values
+  R iwk[NP];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) iwk[k] = gv.iw(k);
   R tprev = -(R)INFINITY, phiprev = 0, Eprev = 0;
   if (cl0 > 0) {
     tprev = (gv.bnd(cl0) - u) * isig;
@@ -161,7 +167,7 @@ __device__ __forceinline__ void proj_factors_cells(const VGrid& g, R u, R theta,
 #pragma unroll
       for (int p = 0; p < NP; ++p) sacc += gv.lag(k, p) * J[p];
       const int m = cl * NP + k;
-      out[(size_t)m * stride] = (TO)(scale * sacc * gv.iw(m));
+      out[(size_t)m * stride] = (TO)(scale * sacc * iwk[k]);
     }
     tprev = tb;
     phiprev = phib;
