@@ -672,16 +672,23 @@ int shadow_phase(bgk_handle* h, int st, const void* qsrc, double qscale, double 
     sh->stream = keep;
   }
   k_record_fp32<<<1, 1, 0, s>>>(sh->ds, h->ds, st);
-  // the FP32 result becomes the FP64 state and its FP64 moments are taken in one pass over
-  // the FP32 data (the moments of the exact doubles of the FP32 values); when the FP32
+  // the FP32 result becomes the FP64 state and its FP64 moments are those of the exact
+  // doubles of the FP32 values (taken in one pass over the FP32 data where that pass also
+  // writes the doubles, else copied from the FP32 phase's last moment pass); when the FP32
   // phase failed, the FP64 state keeps its values and its moments come from them.  The
   // FP64 phase always starts with a full sweep, which writes every value of f and reads
   // the old ones only through walls and lagged edges: without those the doubles are not
   // written here
   const bool f_read = h->has_walls || h->lagged != 0;
-  k_moments<float><<<sh->mom_blocks, 128, 0, s>>>(h->g, (const float*)sh->f, h->nnode, h->U[0], h->U[1], h->ds, 0,
-                                                  h->partial, nullptr, h->phys.nu, h->phys.collision,
-                                                  f_read ? h->f : nullptr, sh->ds, 1);
+  if (f_read) {
+    k_moments<float><<<sh->mom_blocks, 128, 0, s>>>(h->g, (const float*)sh->f, h->nnode, h->U[0], h->U[1], h->ds, 0,
+                                                    h->partial, nullptr, h->phys.nu, h->phys.collision, h->f, sh->ds,
+                                                    1);
+  } else {
+    // the FP32 phase's last moment pass took exactly these moments (the same compensated
+    // sums of the same FP32 values): copied, not recomputed
+    k_copy_moments<<<148, 256, 0, s>>>((size_t)h->nnode * h->nm, sh->U[0], sh->U[1], sh->ds, h->U[0], h->U[1], h->ds);
+  }
   k_moments<double><<<h->mom_blocks, 128, 0, s>>>(h->g, (const double*)h->f, h->nnode, h->U[0], h->U[1], h->ds, 0,
                                                   h->partial, nullptr, h->phys.nu, h->phys.collision, nullptr,
                                                   sh->ds, 2);
