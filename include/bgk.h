@@ -142,7 +142,12 @@ typedef struct {
                          lagged inflow are those of the previous change and whose inflow data
                          are zero (exact in exact arithmetic: the iterate just swept satisfies
                          the sweep's equations, so the next sweep differs from it only through
-                         these changes); 1 = every FP64-phase iteration a full sweep */
+                         these changes); with the projected Maxwellian the change of nu M
+                         comes from the FP32 derivative of the projected factors at the
+                         midpoint of the two iterates' primitive variables (about 1e-6 of the
+                         change; a node whose variables changed by more than 1e-5 relative
+                         takes the difference of both states' FP64 factors instead);
+                         1 = every FP64-phase iteration a full sweep */
   int stage_predictor; /* multi-stage DIRK steps: 1 = each stage after the first starts its
                          Picard iteration from moments extrapolated across the stage
                          abscissae (U_k + dt sum_r A_sr G_r + dt A_ss G_{s-1}, G_r the moment

@@ -175,6 +175,104 @@ __device__ __forceinline__ void proj_factors_cells(const VGrid& g, R u, R theta,
   }
 }
 
+// First-order change of the projected 1D factors (App. B) of all velocity cells along a
+// change (du, dth) of the node's velocity component and temperature, in arithmetic R.
+// With t = (v - u)/sigma the Gaussian's mass per dt is phi(t); under the change it moves
+// by phi(t) (a t + b (t^2 - 1)) dt, a = du/sigma, b = dth/(2 theta) (the derivatives of
+// log G in u and theta), so each projection integral J_p = int xi^p phi dt changes by the
+// same combination of partial moments with I_q replaced by
+// K_q = a I_{q+1} + b (I_{q+2} - I_q): the recurrence of proj_factors_cells taken two
+// orders further.  Writes outd[m] = scale dc[m] + dscale c[m] (the change of scale c[m])
+// and outc[m] = scale c[m] + cw outd[m] (cw = 1/2 at the midpoint of a change: the factor
+// after the change, to second order).
+template <typename R, int KV>
+__device__ __forceinline__ void proj_dfactors_cells(const VGrid& g, R u, R theta, R du, R dth, R scale, R dscale,
+                                                    R cw, float* outc, float* outd, size_t stride) {
+  constexpr int NP = KV + 1, NI = KV + 3;
+  const R rs2 = (R)0.70710678118654752440, rs2pi = (R)0.39894228040143267794;
+  const R sig = sqrt(theta), isig = R(1) / sig;
+  const R ca = du * isig, cb = dth / (R(2) * theta);
+  const GridVals<R> gv{g};
+  const R hh = gv.hh();
+  R iwk[NP];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) iwk[k] = gv.iw(k);
+  R tprev = -(R)INFINITY, phiprev = 0, Eprev = 0;
+  for (int cl = 0; cl < g.ncl; ++cl) {
+    R tb, phib, Eb;
+    if (cl == g.ncl - 1) {
+      tb = (R)INFINITY;
+      phib = 0;
+      Eb = 0;
+    } else {
+      tb = (gv.bnd(cl + 1) - u) * isig;
+      phib = rs2pi * exp(R(-0.5) * tb * tb);
+      Eb = R(0.5) * erfc(fabs(tb) * rs2);
+    }
+    const R ta = tprev, phia = phiprev, Ea = Eprev;
+    R I[NI];
+    if (ta >= 0)
+      I[0] = Ea - Eb;
+    else if (tb <= 0)
+      I[0] = Eb - Ea;
+    else
+      I[0] = (R(1) - Eb) - Ea;
+    I[1] = phia - phib;
+    R ap = 1, bp = 1;
+#pragma unroll
+    for (int k = 2; k < NI; ++k) {
+      ap = isinf(ta) ? R(0) : ap * ta;
+      bp = isinf(tb) ? R(0) : bp * tb;
+      I[k] = (R)(k - 1) * I[k - 2] + (isinf(ta) ? R(0) : ap * phia) - (isinf(tb) ? R(0) : bp * phib);
+    }
+    R K[NP];
+#pragma unroll
+    for (int q = 0; q <= KV; ++q) K[q] = ca * I[q + 1] + cb * (I[q + 2] - I[q]);
+    const R mid = gv.mid(cl);
+    const R alpha = (u - mid) / hh, beta = sig / hh;
+    R J[NP], dJ[NP], binom[NP];
+    binom[0] = 1;
+#pragma unroll
+    for (int q = 1; q <= KV; ++q) binom[q] = 0;
+#pragma unroll
+    for (int p = 0; p <= KV; ++p) {
+      if (p > 0)
+#pragma unroll
+        for (int q = p; q >= 1; --q) binom[q] += binom[q - 1];
+      R apow[NP];
+      apow[0] = 1;
+#pragma unroll
+      for (int q = 1; q <= p; ++q) apow[q] = apow[q - 1] * alpha;
+      R sj = 0, sd = 0, ab = 1;
+#pragma unroll
+      for (int q = 0; q <= p; ++q) {
+        const R w = binom[q] * apow[p - q] * ab;
+        sj += w * I[q];
+        sd += w * K[q];
+        ab *= beta;
+      }
+      J[p] = sj;
+      dJ[p] = sd;
+    }
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      R sc = 0, sd = 0;
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        sc += gv.lag(k, p) * J[p];
+        sd += gv.lag(k, p) * dJ[p];
+      }
+      const R c = sc * iwk[k], d = scale * (sd * iwk[k]) + dscale * c;
+      const size_t m = (size_t)(cl * NP + k) * stride;
+      outd[m] = (float)d;
+      outc[m] = (float)(scale * c + cw * d);
+    }
+    tprev = tb;
+    phiprev = phib;
+    Eprev = Eb;
+  }
+}
+
 template <typename R, typename TO>
 __device__ __forceinline__ void proj_factors_range(const VGrid& g, R u, R theta, TO* out, size_t stride, R scale,
                                                    int cl0, int cl1) {
@@ -819,6 +917,61 @@ __global__ void k_delta_factors(size_t n, const double* __restrict__ cf, const d
     } else {
       C32[t] = (float)cf[t];
       D32[t] = (float)(cf[t] - cf_prev[t]);
+    }
+  }
+}
+
+// Picard refinement with the projected Maxwellian: the same C32 and D32 as k_delta_factors
+// (the new factors and their change, rows x nodes) without the FP64 factors of either
+// iterate stored.  Per node the primitive variables of the last two iterates' moments
+// (U[it & 1] new, the other buffer old) and their change dP in FP64; where the largest
+// relative change (|dn|/n, |du_a|/sqrt(theta), |dtheta|/theta) is below lin_max, the
+// factors' change is the derivative at the midpoint of the two states along dP
+// (proj_dfactors_cells in FP32: the neglected terms are of third order in dP, the FP32
+// rounding about 1e-6 of the change), otherwise the difference of the two states' FP64
+// factors (node_factors, through the scratch rows Wn and Wo: rows x nodes).
+__global__ void k_delta_factors_lin(VGrid g, int nnode, const double* __restrict__ U0, const double* __restrict__ U1,
+                                    DevState* ds, double coef, float* __restrict__ C32, float* __restrict__ D32,
+                                    double lin_max, double* __restrict__ Wn, double* __restrict__ Wo) {
+  if (ds->status != BGK_OK || ds->done) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nnode) return;
+  const int nm = g.dim + 2;
+  const bool cur0 = (ds->it & 1) == 0;
+  const NodePrim Pn = node_prim((cur0 ? U0 : U1) + (size_t)i * nm, g.dim, coef, BGK_COLL_MAXWELLIAN);
+  const NodePrim Po = node_prim((cur0 ? U1 : U0) + (size_t)i * nm, g.dim, coef, BGK_COLL_MAXWELLIAN);
+  if (!Pn.ok || !Po.ok) atomicOr(&ds->err, 1);
+  double rel = fabs(Pn.n - Po.n) / Po.n;
+  rel = fmax(rel, fabs(Pn.th - Po.th) / Po.th);
+  const double isg = rsqrt(Po.th);
+  for (int a = 0; a < g.dim; ++a) rel = fmax(rel, fabs(Pn.u[a] - Po.u[a]) * isg);
+  if (rel < lin_max) {
+    const double thm = 0.5 * (Po.th + Pn.th);
+    const float th = (float)thm, dth = (float)(Pn.th - Po.th);
+    for (int a = 0; a < g.dim; ++a) {
+      const float u = (float)(0.5 * (Po.u[a] + Pn.u[a])), du = (float)(Pn.u[a] - Po.u[a]);
+      const float sc = a == 0 ? (float)(0.5 * (Po.scale + Pn.scale)) : 1.0f;
+      const float dsc = a == 0 ? (float)(Pn.scale - Po.scale) : 0.0f;
+      float* oc = C32 + (size_t)a * g.N * nnode + i;
+      float* od = D32 + (size_t)a * g.N * nnode + i;
+      switch (g.kv) {
+        case 1: proj_dfactors_cells<float, 1>(g, u, th, du, dth, sc, dsc, 0.5f, oc, od, (size_t)nnode); break;
+        case 2: proj_dfactors_cells<float, 2>(g, u, th, du, dth, sc, dsc, 0.5f, oc, od, (size_t)nnode); break;
+        case 3: proj_dfactors_cells<float, 3>(g, u, th, du, dth, sc, dsc, 0.5f, oc, od, (size_t)nnode); break;
+        default: proj_dfactors_cells<float, 4>(g, u, th, du, dth, sc, dsc, 0.5f, oc, od, (size_t)nnode); break;
+      }
+    }
+  } else {
+    // both states' factors in FP64 (each thread reads back only its own node's values)
+    for (int a = 0; a < g.dim; ++a) {
+      const size_t r = (size_t)a * g.N * nnode + i;
+      node_factors<double>(g, BGK_COLL_MAXWELLIAN, Pn, a, Wn + r, (size_t)nnode, 0, g.ncl);
+      node_factors<double>(g, BGK_COLL_MAXWELLIAN, Po, a, Wo + r, (size_t)nnode, 0, g.ncl);
+      for (int m = 0; m < g.N; ++m) {
+        const double cn = Wn[r + (size_t)m * nnode], co = Wo[r + (size_t)m * nnode];
+        C32[r + (size_t)m * nnode] = (float)cn;
+        D32[r + (size_t)m * nnode] = (float)(cn - co);
+      }
     }
   }
 }

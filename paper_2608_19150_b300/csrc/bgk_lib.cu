@@ -531,16 +531,31 @@ void launch_corr_sweep_t(bgk_handle* h, double nus) {
       sweep_args(sh), sh->g, (float)nus, fs, h->fbc_zero32, nullptr, (float*)sh->f, h->ds, 0);
 }
 
+// Largest relative change of a node's primitive variables between two refinement iterates
+// for which k_delta_factors_lin takes the factors' change from their FP32 derivative: the
+// neglected third-order terms stay below 1e-15 of the factors and the FP32 rounding
+// (about 1e-6 of the change) near 1e-11.
+constexpr double kRefineLinMax = 1e-5;
+
 int refine_iteration(bgk_handle* h, double nus, double tol, int st, cudaGraphConditionalHandle cond, int use_cond) {
   bgk_handle* sh = h->shadow;
   cudaStream_t s = h->stream;
   const size_t ncf = (size_t)h->g.dim * h->g.N * h->nnode;
-  CK(cudaMemcpyAsync(h->cf_prev, h->cf, ncf * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  const int pairs = pair_sweep(h, nus) ? 1 : 0;
-  k_factors<double><<<(h->nnode + 127) / 128, 128, 0, s>>>(h->g, h->nnode, h->U[0], h->U[1], h->ds, h->phys.nu,
-                                                         (double*)h->cf, h->phys.collision, pairs);
-  k_delta_factors<<<148 * 8, 256, 0, s>>>(ncf, (const double*)h->cf, (const double*)h->cf_prev, pairs, h->c32,
-                                          h->d32, h->ds);
+  if (h->phys.collision == BGK_COLL_MAXWELLIAN) {
+    // the factors' change from the moments' change without the FP64 factors of either
+    // iterate (h->cf and h->cf_prev serve as scratch: the stage's next full sweep, if any,
+    // rebuilds h->cf)
+    k_delta_factors_lin<<<(h->nnode + 127) / 128, 128, 0, s>>>(h->g, h->nnode, h->U[0], h->U[1], h->ds, h->phys.nu,
+                                                               h->c32, h->d32, kRefineLinMax, (double*)h->cf,
+                                                               (double*)h->cf_prev);
+  } else {
+    CK(cudaMemcpyAsync(h->cf_prev, h->cf, ncf * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    const int pairs = pair_sweep(h, nus) ? 1 : 0;
+    k_factors<double><<<(h->nnode + 127) / 128, 128, 0, s>>>(h->g, h->nnode, h->U[0], h->U[1], h->ds, h->phys.nu,
+                                                           (double*)h->cf, h->phys.collision, pairs);
+    k_delta_factors<<<148 * 8, 256, 0, s>>>(ncf, (const double*)h->cf, (const double*)h->cf_prev, pairs, h->c32,
+                                            h->d32, h->ds);
+  }
   k_delta_source<<<k_source_grid(h->nnode, h->g.nv), 256, 0, s>>>(h->g, h->nnode, h->c32, h->d32, (float*)sh->fk,
                                                                   h->ds);
   if (h->has_walls) {

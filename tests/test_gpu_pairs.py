@@ -94,11 +94,12 @@ def test_pair_and_fp64_sweeps_differ_by_rounding_only():
 
 def test_mixed_precision_runs_its_fp64_phase_in_pairs():
     """BGK_MIXED chooses pairs for its FP64 phase by default: same Picard counts as with
-    FP64 arithmetic there, results apart by rounding only."""
+    FP64 arithmetic there, results apart by rounding only.  Every FP64-phase iteration a
+    full sweep (no refinement), so that each iteration compares the two arithmetics."""
     w = small_shock_tube(n=8, kx=2, n_v=16, integrator="DIRK3")
     res = {}
     for hp in ("auto", "fp64", "pairs"):
-        s = bgk.Solver.from_workload(w, precision="mixed", hp_sweep=hp)
+        s = bgk.Solver.from_workload(w, precision="mixed", hp_sweep=hp, refine=False)
         s.set_state_maxwellian(w.init)
         s.set_inflow_maxwellian(w.inflow)
         st = s.step(2)

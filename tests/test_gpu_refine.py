@@ -5,14 +5,17 @@ correction also takes the wall data and the lagged inflow from the previous chan
 
 In exact arithmetic the refined iterate equals the full sweep's (the sweep is linear in its
 source and the iterate just swept satisfies its equations), so the two runs take the same
-Picard iterations; the correction's FP32 rounding is relative to the small change d.  Bar,
-one step from the same state: the same iteration counts and f within 1e-10 relative (max
-norm) of the full-sweep run, against differences of order tau = 1e-8 between iterates.
-Over several steps the FP32 phase turns such differences into FP32-rounding-sized ones and
-both runs stop within the tolerance of the fixed point, so there both are compared with an
-FP64 run converged to 1e-13: within 1e-6, as the mixed precision is (and within 1.5x of
-each other's error).  Results differ from the full-sweep run
-(the switch takes effect)."""
+Picard iterations; the correction's FP32 rounding is relative to the small change d, and so
+is that of the change of the projected Maxwellian, taken from its FP32 derivative at the
+midpoint of two iterates (about 1e-6 of the change).  Bar, one single-stage step (BE, the
+first BDF2 step) from the same state: the same iteration counts and f within 1e-10
+relative (max norm) of the full-sweep run, against differences of order tau = 1e-8 between
+iterates.  A later stage or step starts its FP32 phase from the previous result rounded to
+floats: differences of 1e-12 then change some FP32 roundings, the two runs follow
+different FP32 iterates and both stop within the Picard tolerance of the fixed point, so
+multi-stage and multi-step runs are compared with an FP64 run converged to 1e-13: within
+1e-6, as the mixed precision is, and within 1.5x of the full-sweep run's error.  Results
+differ from the full-sweep run (the switch takes effect)."""
 import numpy as np
 import pytest
 
@@ -34,7 +37,7 @@ def _run(w, refine, steps=2, **kw):
     return s.get_f(), its
 
 
-@pytest.mark.parametrize("integ", ["BE", "DIRK3", "BDF2"])
+@pytest.mark.parametrize("integ", ["BE", "BDF2"])
 def test_refinement_reaches_the_full_sweep_iterate(integ):
     w = small_shock_tube(n=12, kx=2, n_v=16, integrator=integ)
     f0, it0 = _run(w, False, steps=1)
@@ -71,7 +74,7 @@ def test_refined_steps_stay_at_the_fp64_fixed_point(integ):
 @pytest.mark.parametrize("case", ["walls", "tets_with_cycles"])
 def test_refinement_with_walls_and_lagged_edges(case):
     if case == "walls":
-        w = small_shock_tube(n=10, kx=2, n_v=16, integrator="DIRK3")
+        w = small_shock_tube(n=10, kx=2, n_v=16, integrator="BE")
         kw = dict(walls={"y-": "reflect", "y+": "reflect"})
     else:
         w = twisted_workload(3, 8)
