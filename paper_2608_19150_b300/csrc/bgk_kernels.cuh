@@ -1005,6 +1005,27 @@ __global__ void k_delta_source(VGrid g, int nnode, const float* __restrict__ C32
   }
 }
 
+// k_delta_source for 2D grids with the first velocity index j_1 = blockIdx.y (and its
+// strides): each thread keeps c1' and c1' - c1 of its node for j_1 and loops over j_2, so
+// an output costs two loads instead of four (the same FP32 expression per element).
+// Launch: x over nodes, y over the N values of j_1.
+__global__ void k_delta_source_2d(VGrid g, int nnode, const float* __restrict__ C32, const float* __restrict__ D32,
+                                  float* __restrict__ dM, const DevState* ds) {
+  if (ds->status != BGK_OK || ds->done) return;
+  for (int j1 = blockIdx.y; j1 < g.N; j1 += gridDim.y) {
+    const size_t r1 = (size_t)j1 * nnode;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nnode; i += gridDim.x * blockDim.x) {
+      const float a1 = C32[r1 + i], d1 = D32[r1 + i];
+      float* out = dM + (size_t)j1 * g.N * nnode + i;
+      for (int j2 = 0; j2 < g.N; ++j2) {
+        const size_t r2 = (size_t)(g.N + j2) * nnode;
+        const float c2old = C32[r2 + i] - D32[r2 + i];
+        out[(size_t)j2 * nnode] = fmaf(a1, D32[r2 + i], d1 * c2old);
+      }
+    }
+  }
+}
+
 // The change of f made by the FP64 phase's full sweep of a stage, as the FP32 start of the
 // refinement's corrections (their wall data and lagged inflow read the previous change):
 // d = f - f_prev with f_prev the state the sweep started from -- the FP32 phase's result

@@ -556,8 +556,12 @@ int refine_iteration(bgk_handle* h, double nus, double tol, int st, cudaGraphCon
     k_delta_factors<<<148 * 8, 256, 0, s>>>(ncf, (const double*)h->cf, (const double*)h->cf_prev, pairs, h->c32,
                                             h->d32, h->ds);
   }
-  k_delta_source<<<k_source_grid(h->nnode, h->g.nv), 256, 0, s>>>(h->g, h->nnode, h->c32, h->d32, (float*)sh->fk,
-                                                                  h->ds);
+  if (h->g.dim == 2)
+    k_delta_source_2d<<<dim3((unsigned)std::max(1, (h->nnode + 1023) / 1024), (unsigned)h->g.N), 256, 0, s>>>(
+        h->g, h->nnode, h->c32, h->d32, (float*)sh->fk, h->ds);
+  else
+    k_delta_source<<<k_source_grid(h->nnode, h->g.nv), 256, 0, s>>>(h->g, h->nnode, h->c32, h->d32, (float*)sh->fk,
+                                                                    h->ds);
   if (h->has_walls) {
     // wall data of the correction: the mirror traces of the previous change (its inflow
     // faces keep zero data)
