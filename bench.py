@@ -405,7 +405,8 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def launches_per_step(st, guess=False, main_fp32=False, walls=False, refine=False, bdf2=False, mixed=False):
+def launches_per_step(st, guess=False, main_fp32=False, walls=False, refine=False, bdf2=False, mixed=False,
+                      projected=True):
     """Kernels one step launches (graph nodes of kernel type), from its statistics.  FP32
     sweeps form their source themselves (factors, sweep, moments, test per iteration);
     FP64 iterations add the source pass; walls add their refresh to every iteration.  The
@@ -413,9 +414,11 @@ def launches_per_step(st, guess=False, main_fp32=False, walls=False, refine=Fals
     hand-over moment pass and its fallback, plus the conversions of f and q that the
     stage-start moment pass and the stage combine do not already write (with a guess
     changing f first).  refine: the FP64 iterations after the first of a stage are
-    corrections (factors, factor change, source change, FP32 sweep, update with moments,
-    test).  A stage after the first reuses the moments the previous one left (no moment
-    pass; the mixed precision converts f for its FP32 phase only when walls read it)."""
+    corrections (the factors' change -- one kernel for the projected Maxwellian, a factor
+    pass and a difference otherwise --, the source change, the wall refresh, FP32 sweep,
+    update with moments, test).  A stage after the first reuses the moments the previous
+    one left (no moment pass; the mixed precision converts f for its FP32 phase only when
+    walls read it)."""
     n = 1
     per_main = (4 if main_fp32 else 5) + bool(walls)
     for k in range(st.n_stages):
@@ -429,12 +432,13 @@ def launches_per_step(st, guess=False, main_fp32=False, walls=False, refine=Fals
             conv = (1 + (0 if (bdf2 or k > 0) else 1)) if guess else 0
             n += 6 + conv + (4 + bool(walls)) * st.iterations_fp32[k]   # FP32 phase
         its = st.iterations[k]
-        n += (per_main + 6 * (its - 1)) if (refine and its > 0) else per_main * its
+        per_corr = (5 if projected else 6) + bool(walls)
+        n += (per_main + per_corr * (its - 1)) if (refine and its > 0) else per_main * its
     return n
 
 
 def timed_steps(s, steps, world, local, tstream, guess=False, main_fp32=False, walls=False, restore=None,
-                refine=False, mixed=False):
+                refine=False, mixed=False, projected=True):
     """Run `steps` steps of solver s (already warmed up; created on torch stream tstream),
     each bracketed by CUDA events on that stream; the time is the sum of the steps'
     device times (the statistics read between steps is not inside any bracket).
@@ -461,7 +465,7 @@ def timed_steps(s, steps, world, local, tstream, guess=False, main_fp32=False, w
         e1.synchronize()
         el += e0.elapsed_time(e1) * 1e-3
         iters.append({"fp64": list(st.iterations)[:st.n_stages], "fp32": list(st.iterations_fp32)[:st.n_stages]})
-        launches += launches_per_step(st, guess, main_fp32, walls, refine, mixed=mixed)
+        launches += launches_per_step(st, guess, main_fp32, walls, refine, mixed=mixed, projected=projected)
     s.synchronize()
     torch.cuda.synchronize()
     barrier(world)
@@ -617,7 +621,8 @@ def run_ours(args):
     el_max, sweeps, iters, launches, clk = timed_steps(s, args.steps, world, local, tstream,
                                                        main_fp32=args.precision == "fp32", walls=bool(walls),
                                                        restore=restore_main, refine=refine,
-                                                       mixed=args.precision == "mixed")
+                                                       mixed=args.precision == "mixed",
+                                                       projected=args.collision == "maxwellian")
     value = job_throughput(dof * sweeps, el_max, world)
     f_end, U_end = s.get_f(np.float64), s.get_moments()
     # end to end through the C ABI with host buffers: every step's f^k comes in from pinned

@@ -50,5 +50,10 @@ def test_launch_tally_counts_the_refinement_iterations():
     st = SimpleNamespace(n_stages=1, iterations=[3, 0, 0], iterations_fp32=[5, 0, 0])
     full = bench.launches_per_step(st)
     refined = bench.launches_per_step(st, refine=True)
-    # the first FP64 iteration as before (5), each later one 6 kernels instead of 5
-    assert refined - full == 2 * (6 - 5)
+    # the first FP64 iteration as before (5); each later one 5 kernels with the projected
+    # Maxwellian (factor change, source change, sweep, update with moments, test), 6 with
+    # the other collision models (factor pass and difference)
+    assert refined - full == 0
+    assert bench.launches_per_step(st, refine=True, projected=False) - full == 2 * (6 - 5)
+    # walls: the refresh in every iteration, corrections included
+    assert bench.launches_per_step(st, refine=True, walls=True) - refined == 3 + 5
