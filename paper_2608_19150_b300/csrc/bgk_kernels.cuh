@@ -929,11 +929,16 @@ __global__ void k_delta_factors(size_t n, const double* __restrict__ cf, const d
 // factors' change is the derivative at the midpoint of the two states along dP
 // (proj_dfactors_cells in FP32: the neglected terms are of third order in dP, the FP32
 // rounding about 1e-6 of the change), otherwise the difference of the two states' FP64
-// factors (node_factors, through the scratch rows Wn and Wo: rows x nodes).
+// factors (node_factors, through the scratch rows Wn and Wo: rows x nodes).  The rounding
+// of the derivatives adds up over the stage's corrections, so they serve only when the
+// stage's FP32 phase (state gate, stage st) ended normally within phase_max (its last
+// measure): the FP64 phase then moves the moments by about that much in all.
 __global__ void k_delta_factors_lin(VGrid g, int nnode, const double* __restrict__ U0, const double* __restrict__ U1,
                                     DevState* ds, double coef, float* __restrict__ C32, float* __restrict__ D32,
-                                    double lin_max, double* __restrict__ Wn, double* __restrict__ Wo) {
+                                    double lin_max, double* __restrict__ Wn, double* __restrict__ Wo,
+                                    const DevState* __restrict__ gate, int st, double phase_max) {
   if (ds->status != BGK_OK || ds->done) return;
+  const bool phase_ok = !gate->err && gate->status == BGK_OK && gate->meas[st] <= phase_max;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nnode) return;
   const int nm = g.dim + 2;
@@ -945,7 +950,7 @@ __global__ void k_delta_factors_lin(VGrid g, int nnode, const double* __restrict
   rel = fmax(rel, fabs(Pn.th - Po.th) / Po.th);
   const double isg = rsqrt(Po.th);
   for (int a = 0; a < g.dim; ++a) rel = fmax(rel, fabs(Pn.u[a] - Po.u[a]) * isg);
-  if (rel < lin_max) {
+  if (phase_ok && rel < lin_max) {
     const double thm = 0.5 * (Po.th + Pn.th);
     const float th = (float)thm, dth = (float)(Pn.th - Po.th);
     for (int a = 0; a < g.dim; ++a) {
@@ -1005,23 +1010,35 @@ __global__ void k_delta_source(VGrid g, int nnode, const float* __restrict__ C32
   }
 }
 
-// k_delta_source for 2D grids with the first velocity index j_1 = blockIdx.y (and its
-// strides): each thread keeps c1' and c1' - c1 of its node for j_1 and loops over j_2, so
-// an output costs two loads instead of four (the same FP32 expression per element).
-// Launch: x over nodes, y over the N values of j_1.
+// k_delta_source for 2D grids: a block of blockDim.x nodes first stages the second
+// velocity dimension's rows for its nodes in shared memory (c2 = c2' - (c2' - c2) and
+// c2' - c2: 2 N blockDim.x floats), then each thread loops over j_1 (c1' and c1' - c1 of
+// its node in registers) and j_2, so the loads are a small fraction of the stores (the
+// same FP32 expression per element).  Launch: x over node blocks, dynamic shared memory
+// 8 N blockDim.x bytes.
 __global__ void k_delta_source_2d(VGrid g, int nnode, const float* __restrict__ C32, const float* __restrict__ D32,
                                   float* __restrict__ dM, const DevState* ds) {
+  extern __shared__ float rows2[];  // [2][N][blockDim.x]: c2, then c2' - c2
   if (ds->status != BGK_OK || ds->done) return;
-  for (int j1 = blockIdx.y; j1 < g.N; j1 += gridDim.y) {
-    const size_t r1 = (size_t)j1 * nnode;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nnode; i += gridDim.x * blockDim.x) {
-      const float a1 = C32[r1 + i], d1 = D32[r1 + i];
-      float* out = dM + (size_t)j1 * g.N * nnode + i;
-      for (int j2 = 0; j2 < g.N; ++j2) {
-        const size_t r2 = (size_t)(g.N + j2) * nnode;
-        const float c2old = C32[r2 + i] - D32[r2 + i];
-        out[(size_t)j2 * nnode] = fmaf(a1, D32[r2 + i], d1 * c2old);
+  const int nb = (int)blockDim.x, t = (int)threadIdx.x, N = g.N;
+  for (int i0 = blockIdx.x * nb; i0 < nnode; i0 += gridDim.x * nb) {
+    const int i = i0 + t;
+    __syncthreads();
+    if (i < nnode)
+      for (int j2 = 0; j2 < N; ++j2) {
+        const size_t r2 = (size_t)(N + j2) * nnode + i;
+        const float d2 = D32[r2];
+        rows2[j2 * nb + t] = C32[r2] - d2;
+        rows2[(N + j2) * nb + t] = d2;
       }
+    __syncthreads();
+    if (i >= nnode) continue;
+    for (int j1 = 0; j1 < N; ++j1) {
+      const size_t r1 = (size_t)j1 * nnode + i;
+      const float a1 = C32[r1], d1 = D32[r1];
+      float* out = dM + (size_t)j1 * N * nnode + i;
+      for (int j2 = 0; j2 < N; ++j2)
+        out[(size_t)j2 * nnode] = fmaf(a1, rows2[(N + j2) * nb + t], d1 * rows2[j2 * nb + t]);
     }
   }
 }

@@ -536,6 +536,10 @@ void launch_corr_sweep_t(bgk_handle* h, double nus) {
 // neglected third-order terms stay below 1e-15 of the factors and the FP32 rounding
 // (about 1e-6 of the change) near 1e-11.
 constexpr double kRefineLinMax = 1e-5;
+// Largest final measure of a stage's FP32 phase (Eq. convergence-criteria) with which its
+// refinement uses those derivatives: the FP64 phase then moves the moments by about 1e-5 in
+// all, and the derivatives' rounding (about 1e-6 of each change) adds up to about 1e-11.
+constexpr double kRefineLinPhase = 1e-6;
 
 int refine_iteration(bgk_handle* h, double nus, double tol, int st, cudaGraphConditionalHandle cond, int use_cond) {
   bgk_handle* sh = h->shadow;
@@ -547,7 +551,7 @@ int refine_iteration(bgk_handle* h, double nus, double tol, int st, cudaGraphCon
     // rebuilds h->cf)
     k_delta_factors_lin<<<(h->nnode + 127) / 128, 128, 0, s>>>(h->g, h->nnode, h->U[0], h->U[1], h->ds, h->phys.nu,
                                                                h->c32, h->d32, kRefineLinMax, (double*)h->cf,
-                                                               (double*)h->cf_prev);
+                                                               (double*)h->cf_prev, sh->ds, st, kRefineLinPhase);
   } else {
     CK(cudaMemcpyAsync(h->cf_prev, h->cf, ncf * sizeof(double), cudaMemcpyDeviceToDevice, s));
     const int pairs = pair_sweep(h, nus) ? 1 : 0;
@@ -556,10 +560,11 @@ int refine_iteration(bgk_handle* h, double nus, double tol, int st, cudaGraphCon
     k_delta_factors<<<148 * 8, 256, 0, s>>>(ncf, (const double*)h->cf, (const double*)h->cf_prev, pairs, h->c32,
                                             h->d32, h->ds);
   }
-  if (h->g.dim == 2)
-    k_delta_source_2d<<<dim3((unsigned)std::max(1, (h->nnode + 1023) / 1024), (unsigned)h->g.N), 256, 0, s>>>(
-        h->g, h->nnode, h->c32, h->d32, (float*)sh->fk, h->ds);
-  else
+  if (h->g.dim == 2) {
+    const int nt = h->g.N <= 96 ? 64 : 32;
+    k_delta_source_2d<<<std::max(1, (h->nnode + nt - 1) / nt), nt, 8 * h->g.N * nt, s>>>(h->g, h->nnode, h->c32, h->d32,
+                                                                                       (float*)sh->fk, h->ds);
+  } else
     k_delta_source<<<k_source_grid(h->nnode, h->g.nv), 256, 0, s>>>(h->g, h->nnode, h->c32, h->d32, (float*)sh->fk,
                                                                     h->ds);
   if (h->has_walls) {

@@ -48,6 +48,29 @@ def test_refinement_reaches_the_full_sweep_iterate(integ):
     assert 0.0 < d < 1e-10, d
 
 
+def test_refinement_with_large_first_changes():
+    """The FP32 phase stopped early (floor 1e-3): the refinement then moves the moments by
+    about 1e-2, so its factor changes come from both states' FP64 factors (the FP32
+    derivatives serve only after an FP32 phase that ended within 1e-6), and it takes ~48
+    corrections, whose FP32 sweeps' rounding adds up to ~2e-9 against the full-sweep run
+    (the same with FP64 factor differences in every correction).  Bar: equal iteration
+    counts, and the step as close to an FP64 step converged to 1e-13 as the full-sweep
+    run is (within 1.5x plus 1e-9)."""
+    w = small_shock_tube(n=12, kx=2, n_v=16, integrator="BE")
+    f0, it0 = _run(w, False, steps=1, fp32_floor=1e-3)
+    f1, it1 = _run(w, True, steps=1, fp32_floor=1e-3)
+    p = bgk.Solver.from_workload(w, precision="fp64", tau=1e-13)
+    p.set_state_maxwellian(w.init)
+    p.set_inflow_maxwellian(w.inflow)
+    p.step(1)
+    tight = p.get_f()
+    assert it0 == it1
+    assert max(it1[0][1]) >= 3
+    e_full, e_ref = rel_err(f0, tight), rel_err(f1, tight)
+    assert e_ref < 1.5 * e_full + 1e-9, (e_ref, e_full)
+    assert 0.0 < rel_err(f1, f0) < 1e-8
+
+
 def test_refinement_on_the_p1_square():
     w = synth.workload_p1_square(n_side=16, seed=0, n_v=16, k_v=3, L=6.0, knudsen=1e-2)
     f0, it0 = _run(w, False, steps=1)
